@@ -1,0 +1,124 @@
+"""Seeded synthetic inputs shared by the CUDA path and the CPU oracle.
+
+This module holds none of the method's arithmetic: it only draws random numbers
+and evaluates closed-form forcing / advection fields at given points.  Both the
+library's tests and the oracle's tests take their inputs from here, so the two
+sides see bit-identical right-hand sides.
+
+Point layout used everywhere: each of the n elements per direction carries
+G = p + 2 Gauss-Legendre points; a field sampled "at the quadrature points" is an
+array (2, n*G, n*G) indexed [component, y point, x point], points element-major.
+"""
+import numpy as np
+
+_MASK = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+class SplitMix64:
+    """splitmix64 (Steele, Lea, Flood 2014), counter-based, on numpy uint64."""
+
+    def __init__(self, seed):
+        self.state = np.uint64(seed) & _MASK
+
+    def next_u64(self, count):
+        with np.errstate(over="ignore"):
+            k = np.arange(1, count + 1, dtype=np.uint64)
+            z = self.state + k * np.uint64(0x9E3779B97F4A7C15)
+            self.state = self.state + np.uint64(count) * np.uint64(0x9E3779B97F4A7C15)
+            z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+            z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+            z = z ^ (z >> np.uint64(31))
+        return z
+
+    def uniform(self, count):
+        """Uniform doubles in [0,1) from the top 53 bits."""
+        return (self.next_u64(count) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+    def normal(self, count):
+        """Standard normals by Box-Muller."""
+        m = (count + 1) // 2
+        u1 = 1.0 - self.uniform(m)          # (0,1]
+        u2 = self.uniform(m)
+        r = np.sqrt(-2.0 * np.log(u1))
+        z = np.concatenate([r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)])
+        return z[:count]
+
+
+def quad_points_1d(p, n):
+    """Abscissae of the (p+2)-point Gauss-Legendre rule in each of n uniform elements."""
+    g, _ = np.polynomial.legendre.leggauss(p + 2)
+    g = (g + 1.0) / 2.0
+    return np.concatenate([(e + g) / n for e in range(n)])
+
+
+def manufactured_forcing(p, n, sigma, nu):
+    """f = sigma u - nu Lap u + grad p for psi = sin^2(pi x) sin^2(pi y),
+    u = (d psi/dy, -d psi/dx), p = sin(pi x) sin(pi y) - 4/pi^2 (closed form)."""
+    x = quad_points_1d(p, n)
+    X, Y = np.meshgrid(x, x)
+    pi = np.pi
+    ux = pi * np.sin(pi * X) ** 2 * np.sin(2 * pi * Y)
+    uy = -pi * np.sin(2 * pi * X) * np.sin(pi * Y) ** 2
+    lap_ux = 2 * pi ** 3 * np.sin(2 * pi * Y) * (2 * np.cos(2 * pi * X) - 1)
+    lap_uy = -2 * pi ** 3 * np.sin(2 * pi * X) * (2 * np.cos(2 * pi * Y) - 1)
+    fx = sigma * ux - nu * lap_ux + pi * np.cos(pi * X) * np.sin(pi * Y)
+    fy = sigma * uy - nu * lap_uy + pi * np.sin(pi * X) * np.cos(pi * Y)
+    return np.ascontiguousarray(np.stack([fx, fy]))
+
+
+def manufactured_solution(p, n):
+    """(u_x, u_y, p) of the manufactured solution at the quadrature points."""
+    x = quad_points_1d(p, n)
+    X, Y = np.meshgrid(x, x)
+    pi = np.pi
+    ux = pi * np.sin(pi * X) ** 2 * np.sin(2 * pi * Y)
+    uy = -pi * np.sin(2 * pi * X) * np.sin(pi * Y) ** 2
+    pr = np.sin(pi * X) * np.sin(pi * Y) - 4.0 / pi ** 2
+    return ux, uy, pr
+
+
+def grf_forcing(p, n, seed, length=0.1, n_features=512):
+    """Two independent unit-variance Gaussian random fields with squared-exponential
+    covariance exp(-r^2 / (2 length^2)), by random Fourier features."""
+    x = quad_points_1d(p, n)
+    X, Y = np.meshgrid(x, x)
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(2):
+        w = rng.normal(2 * n_features).reshape(n_features, 2) / length
+        b = 2 * np.pi * rng.uniform(n_features)
+        f = np.zeros_like(X)
+        for k in range(n_features):
+            f += np.cos(w[k, 0] * X + w[k, 1] * Y + b[k])
+        out.append(f * np.sqrt(2.0 / n_features))
+    return np.ascontiguousarray(np.stack(out))
+
+
+def oseen_advection(p, n, max_speed=1.0):
+    """beta = curl of sin^2(pi x) sin^2(pi y), scaled so that max |beta| = max_speed
+    (divergence-free, zero on the boundary)."""
+    x = quad_points_1d(p, n)
+    X, Y = np.meshgrid(x, x)
+    pi = np.pi
+    bx = pi * np.sin(pi * X) ** 2 * np.sin(2 * pi * Y)
+    by = -pi * np.sin(2 * pi * X) * np.sin(pi * Y) ** 2
+    # max of |curl psi| over the square, from a fine sampling of the closed form
+    s = np.linspace(0, 1, 2001)
+    S, T = np.meshgrid(s, s)
+    vmax = np.sqrt((pi * np.sin(pi * S) ** 2 * np.sin(2 * pi * T)) ** 2
+                   + (pi * np.sin(2 * pi * S) * np.sin(pi * T) ** 2) ** 2).max()
+    return np.ascontiguousarray(np.stack([bx, by]) * (max_speed / vmax))
+
+
+def random_divfree_guess(p, n, seed):
+    """Random streamfunction coefficients on the (n+p-2)^2 interior, U(-1,1), and random
+    pressure coefficients on the (n+p-1)^2 pressure space, U(-1,1)."""
+    rng = SplitMix64(seed)
+    psi = 2.0 * rng.uniform((n + p - 2) ** 2) - 1.0
+    pr = 2.0 * rng.uniform((n + p - 1) ** 2) - 1.0
+    return psi, pr
+
+
+def random_vector(count, seed):
+    """Standard normal vector (for parity tests of single operators)."""
+    return SplitMix64(seed).normal(count)

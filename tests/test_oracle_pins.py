@@ -1,0 +1,359 @@
+"""Pins for the CPU oracle: each test checks it against something other than itself
+(closed forms, textbook identities, exactness of the discrete complex, brute-force
+direct solves, the paper's printed DOF counts and cycle counts)."""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import bspline as bs
+from oracle import stokes2d as o2
+from paper_1705_09282_gb300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.txt")
+
+
+def _table(name):
+    rows, cur = {}, None
+    for line in open(GOLD):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.isalpha() or line.startswith("table"):
+            cur = line
+            rows[cur] = []
+            continue
+        rows[cur].append([int(v) for v in line.split()])
+    return rows[name]
+
+
+# ---------------------------------------------------------------- B-splines --
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3, 4])
+def test_partition_of_unity_and_derivative(deg):
+    t = bs.uniform_open_knots(deg, 7)
+    x = np.linspace(0.0, 1.0, 301)
+    N = bs.basis_values(t, deg, x)
+    assert np.allclose(N.sum(axis=1), 1.0, atol=1e-14)
+    assert N.min() >= -1e-15
+    if deg >= 1:
+        h = 1e-6
+        xi = np.linspace(0.013, 0.987, 97)
+        fd = (bs.basis_values(t, deg, xi + h) - bs.basis_values(t, deg, xi - h)) / (2 * h)
+        assert np.allclose(bs.basis_derivs(t, deg, xi), fd, atol=1e-6 * 7 ** 2)
+
+
+@pytest.mark.parametrize("deg", [1, 2, 3])
+def test_marsden_linear_reproduction(deg):
+    # sum_i (Greville abscissa)_i N_i(x) = x  (textbook identity)
+    t = bs.uniform_open_knots(deg, 6)
+    n = bs.n_basis(t, deg)
+    grev = np.array([t[i + 1: i + deg + 1].mean() for i in range(n)])
+    x = np.linspace(0, 1, 101)
+    assert np.allclose(bs.basis_values(t, deg, x) @ grev, x, atol=1e-14)
+
+
+def test_cardinal_quadratic_mass_and_stiffness_rows():
+    # interior row of the quadratic B-spline mass matrix = h * [1, 26, 66, 26, 1] / 120
+    # and stiffness = (1/h) * [-1/6, -1/3, 1, -1/3, -1/6]  (cardinal B-spline closed forms)
+    n = 10
+    t = bs.uniform_open_knots(2, n)
+    x, w = o2.quad_points_1d(2, n)
+    V = bs.basis_values(t, 2, x)
+    D = bs.basis_derivs(t, 2, x)
+    M = V.T @ (w[:, None] * V)
+    S = D.T @ (w[:, None] * D)
+    i = 5
+    assert np.allclose(M[i, i - 2: i + 3], np.array([1, 26, 66, 26, 1]) / 120 / n, atol=1e-15)
+    assert np.allclose(S[i, i - 2: i + 3], np.array([-1 / 6, -1 / 3, 1, -1 / 3, -1 / 6]) * n, atol=1e-12)
+
+
+def test_knot_insertion_figure_example():
+    # Sec. 4.5 figure: Xi = (0,0,0,.2,.4,.6,.8,1,1,1) refined at the midpoints gives
+    # (0,0,0,.1,...,.9,1,1,1); the function is the same before and after.
+    t = np.array([0, 0, 0, .2, .4, .6, .8, 1, 1, 1.0])
+    tf, P = bs.refinement_matrix(t, 2, [.1, .3, .5, .7, .9])
+    assert np.allclose(tf, [0, 0, 0, .1, .2, .3, .4, .5, .6, .7, .8, .9, 1, 1, 1])
+    c = np.random.default_rng(1).standard_normal(7)
+    x = np.random.default_rng(2).uniform(0, 1, 200)
+    assert np.allclose(bs.basis_values(t, 2, x) @ c, bs.basis_values(tf, 2, x) @ (P @ c), atol=1e-14)
+
+
+@pytest.mark.parametrize("deg", [1, 2, 3])
+def test_dyadic_prolongation_interior_is_binomial(deg):
+    # uniform midpoint refinement: interior columns are 2^-deg * C(deg+1, k)  (Lane-Riesenfeld)
+    from math import comb
+    P = bs.dyadic_prolongation(deg, 8)
+    col = P[:, 4]
+    nz = col[np.abs(col) > 0]
+    assert np.allclose(nz, [comb(deg + 1, k) / 2 ** deg for k in range(deg + 2)])
+
+
+# ------------------------------------------------------- discretization --
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_paper_dof_column(p):
+    # Table 1 "DOFs" = (2^n_l + p)^2 = the unconstrained streamfunction space dimension
+    tab = _table("table1")
+    for row in tab:
+        nl = row[0]
+        dofs = row[1] if p == 2 else row[4]
+        assert (2 ** nl + p) ** 2 == dofs
+
+
+@pytest.mark.parametrize("p,n", [(2, 4), (2, 7), (3, 5)])
+def test_discrete_complex_exact(p, n):
+    S = o2.Stokes2D(p, n, 1.0, 1.0)
+    # dim V - dim Psi = dim Q - 1 (exactness of Psi -> V -> Q with the mean constraint)
+    assert S.n_u - S.n_psi_interior() == S.n_p - 1
+    psi = np.random.default_rng(0).uniform(-1, 1, S.n_psi_interior())
+    U = S.curl(psi)
+    assert S.div_inf(U) <= 1e-12 * n
+    # the curl really is d psi/dy, -d psi/dx: evaluate both at random points
+    xs = np.random.default_rng(3).uniform(0, 1, 40)
+    ys = np.random.default_rng(4).uniform(0, 1, 40)
+    Pf = np.zeros((n + p, n + p))
+    Pf[1:-1, 1:-1] = psi.reshape(n + p - 2, n + p - 2)
+    Vx, Dx = bs.basis_values(S.tp, p, xs), bs.basis_derivs(S.tp, p, xs)
+    Vy, Dy = bs.basis_values(S.tp, p, ys), bs.basis_derivs(S.tp, p, ys)
+    dpsi_dy = np.einsum('ki,kj,ji->k', Vx, Dy, Pf)
+    cx = np.zeros((n + p - 1, n + p))
+    cx[:, 1:-1] = U[: S.n_ux].reshape(n + p - 1, n + p - 2)
+    Wy = bs.basis_values(S.tq, p - 1, ys)
+    ux = np.einsum('ki,kj,ji->k', Vx, Wy, cx)
+    assert np.allclose(ux, dpsi_dy, atol=1e-11)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_divergence_pairing_is_b(p):
+    # q^T (B^T u) = int (div u_h) q_h, with the integral done by a 2x finer, higher
+    # order quadrature on function values (independent of the assembly tables)
+    n = 5
+    S = o2.Stokes2D(p, n, 1.0, 1.0)
+    rng = np.random.default_rng(7)
+    U = np.zeros(S.ndof)
+    U[: S.n_u] = rng.standard_normal(S.n_u)
+    qv = rng.standard_normal(S.n_p)
+    lhs = qv @ (S.K[S.n_u: S.n_u + S.n_p, : S.n_u] @ U[: S.n_u])
+    g, w = bs.gauss_legendre(p + 4)
+    m = 2 * n
+    x = np.concatenate([(e + g) / m for e in range(m)])
+    wx = np.concatenate([w / m for _ in range(m)])
+    Dv = bs.basis_values(S.tq, p - 1, x)
+    divc = S.div_coeffs(U)                                   # (iy, ix)
+    divh = Dv @ divc @ Dv.T
+    qh = Dv @ qv.reshape(n + p - 1, n + p - 1) @ Dv.T
+    rhs = np.sum(np.outer(wx, wx) * divh * qh)
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(rhs))
+
+
+@pytest.mark.parametrize("p,sigma,nu", [(2, 1.0, 1.0), (3, 1.0, 1.0), (2, 1000.0, 1.0), (2, 1.0, 0.01)])
+def test_manufactured_convergence_rate(p, sigma, nu):
+    # velocity L2 error ~ h^p for the divergence-conforming pair; pressure has zero mean
+    errs = []
+    for n in (8, 16):
+        S = o2.Stokes2D(p, n, sigma, nu)
+        F = S.load_vector(inputs.manufactured_forcing(p, n, sigma, nu))
+        U = spla.spsolve(S.K.tocsc(), F)
+        ux_e, uy_e, p_e = inputs.manufactured_solution(p, n)
+        x, w = o2.quad_points_1d(p, n)
+        Vp, Vq = bs.basis_values(S.tp, p, x), bs.basis_values(S.tq, p - 1, x)
+        cx = np.zeros((n + p - 1, n + p)); cx[:, 1:-1] = U[: S.n_ux].reshape(n + p - 1, n + p - 2)
+        cy = np.zeros((n + p, n + p - 1)); cy[1:-1, :] = U[S.n_ux: S.n_u].reshape(n + p - 2, n + p - 1)
+        uxh, uyh = Vq @ cx @ Vp.T, Vp @ cy @ Vq.T
+        ph = Vq @ U[S.n_u: S.n_u + S.n_p].reshape(n + p - 1, n + p - 1) @ Vq.T
+        W = np.outer(w, w)
+        errs.append((np.sqrt(np.sum(W * ((uxh - ux_e) ** 2 + (uyh - uy_e) ** 2))),
+                     np.sqrt(np.sum(W * (ph - p_e) ** 2)), abs(np.sum(W * ph)), S.div_inf(U)))
+    rate = np.log2(errs[0][0] / errs[1][0])
+    assert p - 0.35 <= rate <= p + 0.6, (rate, errs)
+    assert errs[1][1] < 0.05                      # pressure converges to the exact one
+    assert errs[1][2] < 1e-12                     # zero-mean pressure (Lagrange multiplier)
+    assert errs[1][3] < 1e-10                     # pointwise divergence-free (Lemma, Sec. 4.1)
+
+
+def test_oseen_manufactured_convergence():
+    # generalized Oseen with beta = manufactured-type divergence-free field
+    p, sigma, nu = 2, 1.0, 0.1
+    errs = []
+    for n in (8, 16):
+        beta = inputs.oseen_advection(p, n, 1.0)
+        S = o2.Stokes2D(p, n, sigma, nu, beta=beta)
+        ux_e, uy_e, _ = inputs.manufactured_solution(p, n)
+        x = inputs.quad_points_1d(p, n)
+        X, Y = np.meshgrid(x, x)
+        pi = np.pi
+        # beta . grad u for the manufactured u (closed form derivatives)
+        dux_dx = pi * 2 * pi * np.sin(pi * X) * np.cos(pi * X) * np.sin(2 * pi * Y)
+        dux_dy = pi * np.sin(pi * X) ** 2 * 2 * pi * np.cos(2 * pi * Y)
+        duy_dx = -pi * 2 * pi * np.cos(2 * pi * X) * np.sin(pi * Y) ** 2
+        duy_dy = -pi * np.sin(2 * pi * X) * 2 * pi * np.sin(pi * Y) * np.cos(pi * Y)
+        f = inputs.manufactured_forcing(p, n, sigma, nu)
+        f[0] += beta[0] * dux_dx + beta[1] * dux_dy
+        f[1] += beta[0] * duy_dx + beta[1] * duy_dy
+        U = spla.spsolve(S.K.tocsc(), S.load_vector(f))
+        _, w = o2.quad_points_1d(p, n)
+        Vp, Vq = bs.basis_values(S.tp, p, x), bs.basis_values(S.tq, p - 1, x)
+        cx = np.zeros((n + p - 1, n + p)); cx[:, 1:-1] = U[: S.n_ux].reshape(n + p - 1, n + p - 2)
+        cy = np.zeros((n + p, n + p - 1)); cy[1:-1, :] = U[S.n_ux: S.n_u].reshape(n + p - 2, n + p - 1)
+        W = np.outer(w, w)
+        errs.append(np.sqrt(np.sum(W * ((Vq @ cx @ Vp.T - ux_e) ** 2 + (Vp @ cy @ Vq.T - uy_e) ** 2))))
+    rate = np.log2(errs[0] / errs[1])
+    assert 1.65 <= rate <= 2.6, (rate, errs)
+
+
+# ---------------------------------------------------------------- multigrid --
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_prolongation_preserves_functions(p):
+    nc = 3
+    P = o2.prolongation(p, nc)
+    Sc, Sf = o2.Stokes2D(p, nc, 1, 1), o2.Stokes2D(p, 2 * nc, 1, 1)
+    rng = np.random.default_rng(5)
+    Uc = rng.standard_normal(Sc.ndof)
+    Uf = P @ Uc
+    x = rng.uniform(0, 1, 30)
+    y = rng.uniform(0, 1, 30)
+
+    def fields(S, U):
+        n = S.n
+        Vpx, Vqx = bs.basis_values(S.tp, p, x), bs.basis_values(S.tq, p - 1, x)
+        Vpy, Vqy = bs.basis_values(S.tp, p, y), bs.basis_values(S.tq, p - 1, y)
+        cx = np.zeros((n + p - 1, n + p)); cx[:, 1:-1] = U[: S.n_ux].reshape(n + p - 1, n + p - 2)
+        cy = np.zeros((n + p, n + p - 1)); cy[1:-1, :] = U[S.n_ux: S.n_u].reshape(n + p - 2, n + p - 1)
+        pp = U[S.n_u: S.n_u + S.n_p].reshape(n + p - 1, n + p - 1)
+        return (np.einsum('ki,kj,ji->k', Vpx, Vqy, cx), np.einsum('ki,kj,ji->k', Vqx, Vpy, cy),
+                np.einsum('ki,kj,ji->k', Vqx, Vqy, pp))
+
+    for a, b in zip(fields(Sc, Uc), fields(Sf, Uf)):
+        assert np.allclose(a, b, atol=1e-13)
+    assert Uf[-1] == Uc[-1]
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_galerkin_equals_reassembly_with_fine_penalty(p):
+    # for constant-coefficient Stokes on the identity map, R K P is the same bilinear
+    # form on the coarse space, i.e. re-assembly with the fine-mesh Nitsche penalty
+    nf = 8
+    Sf = o2.Stokes2D(p, nf, 3.0, 0.7)
+    P = o2.prolongation(p, nf // 2)
+    Kc = (P.T @ Sf.K @ P).toarray()
+    Sc = o2.Stokes2D(p, nf // 2, 3.0, 0.7, h_pen=1.0 / nf)
+    assert np.allclose(Kc, Sc.K.toarray(), atol=1e-11 * np.abs(Kc).max())
+
+
+@pytest.mark.parametrize("p,n", [(2, 8), (3, 8)])
+def test_patch_histograms_and_interior_dims(p, n):
+    from collections import Counter
+    S = o2.Stokes2D(p, n, 1, 1)
+    L = o2.Level(p, n, S.K, S.m, S)
+    L.build_patches()
+    h = Counter((P.n_v, P.n_q) for P in L.patches)
+    assert len(L.patches) == (n + p - 2) ** 2
+    # interior subdomain: dim V_i = 4, dim Q_i = 4 - 1 (zero mean), dim Psi_i = 1 (Sec. 5.2)
+    if p == 2:
+        assert h == Counter({(4, 4): (n - 2) ** 2, (7, 6): 4 * (n - 2), (12, 9): 4})
+    else:
+        assert h == Counter({(4, 4): (n - 3) ** 2, (7, 6): 4 * (n - 3), (10, 8): 4 * (n - 3),
+                             (12, 9): 4, (17, 12): 8, (24, 16): 4})
+
+
+def test_same_colour_patches_do_not_couple():
+    p, n = 2, 9
+    S = o2.Stokes2D(p, n, 1, 1)
+    L = o2.Level(p, n, S.K, S.m, S)
+    L.build_patches()
+    K = S.K.tocsr()
+    by_c = {}
+    for P in L.patches:
+        by_c.setdefault(P.colour, []).append(P)
+    assert len(by_c) == (p + 1) ** 2
+    for c, ps in by_c.items():
+        for i in range(len(ps)):
+            for j in range(i + 1, len(ps)):
+                assert not set(ps[i].dofs) & set(ps[j].dofs)
+                assert abs(K[ps[i].dofs][:, ps[j].dofs]).max() == 0.0
+
+
+def test_one_patch_sweep_is_exact_solve():
+    # p=2 on one element: the single interior streamfunction support is the whole domain
+    S = o2.Stokes2D(2, 1, 1.0, 1.0)
+    L = o2.Level(2, 1, S.K, S.m, S)
+    L.build_patches()
+    assert len(L.patches) == 1
+    F = S.load_vector(inputs.grf_forcing(2, 1, seed=3))
+    U = np.zeros(S.ndof)
+    L.sweep_multiplicative(U, F)
+    Ux = spla.spsolve(S.K.tocsc(), F)
+    assert np.allclose(U, Ux, atol=1e-13)
+
+
+@pytest.mark.parametrize("p,sm,eta", [(2, "mult", 0.5), (3, "mult", 0.5), (2, "add", 0.3)])
+def test_vcycles_converge_to_direct_solve(p, sm, eta):
+    n = 8
+    H = o2.Hierarchy(p, n, 3, 1.0, 1.0, smoother=sm, eta=eta, nu1=2, nu2=2)
+    F = H.fine.load_vector(inputs.grf_forcing(p, n, seed=11))
+    Ux = spla.spsolve(H.levels[-1].K.tocsc(), F)
+    U = np.zeros_like(F)
+    k, hist = H.solve(U, F, 1e-14, 80)
+    assert np.abs(U - Ux).max() <= 1e-12 * np.abs(Ux).max()
+
+
+def test_single_grid_vcycle_is_direct_solve():
+    H = o2.Hierarchy(2, 4, 1, 1.0, 1.0)
+    F = H.fine.load_vector(inputs.grf_forcing(2, 4, seed=5))
+    U = np.ones_like(F)
+    H.vcycle(U, F)
+    assert np.allclose(U, spla.spsolve(H.fine.K.tocsc(), F), atol=1e-13)
+
+
+@pytest.mark.parametrize("sm,eta", [("mult", 0.5), ("add", 0.5), ("add", 0.3)])
+def test_divergence_free_invariant(sm, eta):
+    # Sec. 5.3: from a divergence-free guess every iterate is pointwise divergence-free,
+    # for any number of sweeps, levels and cycles (also while additive diverges in p)
+    p, n = 2, 16
+    H = o2.Hierarchy(p, n, 4, 1.0, 1.0, smoother=sm, eta=eta, nu1=1, nu2=2)
+    S = H.fine
+    psi, pr = inputs.random_divfree_guess(p, n, seed=9)
+    U = S.curl(psi)
+    U[S.n_u: S.n_u + S.n_p] = pr
+    F = S.load_vector(inputs.grf_forcing(p, n, seed=10))
+    for _ in range(3):
+        H.vcycle(U, F)
+        assert S.div_inf(U) <= 1e-12 * max(1.0, np.abs(U[: S.n_u]).max())
+        H.smooth(n_l := H.n_levels - 1, U, F)
+        assert S.div_inf(U) <= 1e-12 * max(1.0, np.abs(U[: S.n_u]).max())
+
+
+def test_paper_table1_cycle_counts_loosely():
+    # protocol of Sec. 6: V(1,2), multiplicative, random divergence-free guess, 1e6 reduction,
+    # coarsest mesh one element.  The paper leaves ordering, guess and norm open, so only
+    # +-2 cycles are asked (p = 2).
+    tab = _table("table1")
+    for row in tab[1:4]:
+        nl, da1, da1000 = row[0], row[2], row[3]
+        n = 2 ** nl
+        for sigma, want in ((1.0, da1), (1000.0, da1000)):
+            H = o2.Hierarchy(2, n, nl + 1, sigma, 1.0, smoother="mult", nu1=1, nu2=2)
+            S = H.fine
+            psi, pr = inputs.random_divfree_guess(2, n, seed=nl)
+            U = S.curl(psi)
+            U[S.n_u: S.n_u + S.n_p] = pr
+            F = S.load_vector(inputs.manufactured_forcing(2, n, sigma, 1.0))
+            k, _ = H.solve(U, F, 1e-6, 40)
+            assert abs(k - want) <= 2, (nl, sigma, k, want)
+
+
+def test_mesh_independent_contraction():
+    rates = []
+    for n, L in ((16, 3), (32, 4)):
+        H = o2.Hierarchy(2, n, L, 1.0, 1.0, nu1=2, nu2=2)
+        F = H.fine.load_vector(inputs.grf_forcing(2, n, seed=21))
+        U = np.zeros_like(F)
+        k, hist = H.solve(U, F, 1e-8, 40)
+        rates.append((hist[-1] / hist[0]) ** (1.0 / k))
+    # V(2,2) contraction stays well below one and grows only slowly with the mesh
+    # (the paper's Tables 1-7 report mesh-independent cycle counts)
+    assert max(rates) < 0.35
+    assert abs(rates[0] - rates[1]) < 0.1
