@@ -1,0 +1,170 @@
+/*
+ * igamg.h -- C ABI of the GB300 library for the structure-preserving geometric
+ * multigrid V-cycle of Coley, Benzaken & Evans, "A geometric multigrid method for
+ * isogeometric compatible discretizations of the generalized Stokes and Oseen
+ * problems" (arXiv 1705.09282).
+ *
+ * Problem (Sec. 2, eqs. for the generalized Stokes / Oseen systems; weak form Sec. 3.1,
+ * Nitsche no-slip Sec. 3.3):
+ *     sigma u + beta.grad u - nu Lap u + grad p = f,  div u = 0  on (0,1)^2,
+ *     u.n = 0 strongly, u x n = 0 weakly with penalty C_I nu / h, C_I = 4(p-1) (Sec. 6).
+ * Discretization: 2D compatible B-splines (Sec. 4.3) -- streamfunction degree p,
+ * velocity S^{p,p-1} x S^{p-1,p}, pressure S^{p-1,p-1}, maximal smoothness, uniform
+ * knots, n_fine elements per direction; mean(p) = 0 by a Lagrange multiplier.
+ *
+ * Vector layout (U, F, R; device or host as stated, double, contiguous), on a level
+ * with n elements per direction, q = p-1:
+ *     [ u_x : (n+q) rows (y) x (n+p-2) columns (x, interior indices 1..n+p-2), x fastest
+ *       u_y : (n+p-2) rows (y, interior 1..n+p-2) x (n+q) columns (x), x fastest
+ *       p   : (n+q) x (n+q), x fastest
+ *       lambda (the multiplier) ]
+ * Levels are numbered 0 (coarsest, n_fine >> (n_levels-1) elements) .. n_levels-1 (finest).
+ *
+ * Conventions: every call enqueues its GPU work on the stream given to igamg_create
+ * (a cudaStream_t passed as void*) and returns without synchronising, unless it says
+ * otherwise.  The caller owns U, F, R (device memory, e.g. from PyTorch); the library
+ * owns the hierarchy and every workspace, allocated in igamg_create and freed in
+ * igamg_destroy; no other call allocates device memory.  A handle is not thread-safe.
+ * Return value: 0 on success, a negative IGAMG_E* code on error (nothing is enqueued
+ * then), IGAMG_NOT_CONVERGED (> 0) from igamg_solve when max_cycles ran out.
+ */
+#ifndef IGAMG_H
+#define IGAMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  IGAMG_OK = 0,
+  IGAMG_NOT_CONVERGED = 1,
+  IGAMG_EINVAL = -1,       /* bad argument: null pointer, size, level, degree ... */
+  IGAMG_EUNSUPPORTED = -2, /* valid but not built (e.g. dim = 3, p > 3) */
+  IGAMG_ESINGULAR = -3,    /* a local patch or the coarsest matrix had a zero pivot */
+  IGAMG_ENONFINITE = -4,   /* NaN / Inf in a residual norm */
+  IGAMG_ECUDA = -5,        /* a CUDA runtime call failed */
+  IGAMG_ETIMEOUT = -6
+};
+
+enum { IGAMG_MULT = 0, IGAMG_ADD = 1 };          /* eq. MSM / eq. ASM of Sec. 5.2 */
+enum { IGAMG_FP64 = 0, IGAMG_FP32_IR = 1 };      /* precision of the V-cycle */
+
+typedef struct {
+  int dim;            /* 2 */
+  int p;              /* streamfunction degree (Sec. 6 convention), 2 or 3 */
+  int n_fine;         /* elements per direction on the finest grid */
+  int n_levels;       /* number of grids; n_fine must be divisible by 2^(n_levels-1) */
+  double sigma, nu;   /* reaction and viscosity, both > 0 */
+  double c_penalty;   /* Nitsche constant C_I; <= 0 selects 4(p-1) (Sec. 6) */
+  const double* beta_qp; /* host; advection at the quadrature points, (2, nG, nG) like f,
+                            or NULL for generalized Stokes */
+  int smoother;       /* IGAMG_MULT or IGAMG_ADD */
+  double eta;         /* additive scaling factor (Sec. 5.2, eq. ASM); <= 0 selects 0.5 */
+  int nu1, nu2;       /* pre- / post-smoothing sweeps (Algorithm 1) */
+  int precision;      /* IGAMG_FP64 or IGAMG_FP32_IR */
+} igamg_problem;
+
+typedef struct {
+  int n;              /* elements per direction on this level */
+  int nx_ux, ny_ux;   /* u_x block: columns (x) and rows (y) */
+  int nx_uy, ny_uy;
+  int n_pdir;         /* pressure coefficients per direction, n+p-1 */
+  long long n_ux, n_uy, n_p, n_total; /* n_total includes lambda */
+  int n_patches;      /* interior streamfunction supports = (n+p-2)^2 */
+  int n_colours;      /* (p+1)^2 */
+  int n_quad;         /* quadrature points per element per direction (p+2) */
+} igamg_sizes;
+
+typedef struct {
+  int cycles;            /* V-cycles done */
+  double res0;           /* ||F - K U_0||_2 */
+  double rel_residual;   /* ||F - K U||_2 / res0 at exit */
+  double div_inf;        /* max |coefficient of div u| at exit */
+  double* history;       /* optional caller buffer for relative residuals, or NULL */
+  int history_cap;       /* its capacity */
+} igamg_report;
+
+typedef struct igamg_handle igamg_handle;
+
+/* Builds the level hierarchy (Sec. 5.1): 1D factors of every level's operator, the
+ * knot-insertion transfers, the patch subdomains with their bordered local inverses
+ * (Sec. 5.2), the colouring and the inverse of the coarsest matrix, and uploads them.
+ * Synchronous.  *out receives a new handle (free with igamg_destroy). */
+int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** out);
+void igamg_destroy(igamg_handle* h);
+const char* igamg_strerror(int code);
+
+/* Sizes of one level (0 = coarsest). */
+int igamg_get_sizes(const igamg_handle* h, int level, igamg_sizes* out);
+
+/* Writes the n*G 1D quadrature abscissae of the finest level into x (host, capacity cap);
+ * f and beta are sampled at their tensor products, layout (2, n*G, n*G) [comp][y][x]. */
+int igamg_quad_points(const igamg_handle* h, double* x, size_t cap, size_t* n_out);
+
+/* F = (l(v), 0, 0), l(v) = int v.f (Sec. 3.1), f at the quadrature points (device). */
+int igamg_load_vector(igamg_handle* h, const double* f_qp, double* F);
+
+/* R = F - K_l U on level l (Sec. 3.4; coarse K_l = R K P, Sec. 5.1).  If norm_out is
+ * not NULL the call synchronises and writes ||R||_2 there (host). */
+int igamg_residual(igamg_handle* h, int level, const double* U, const double* F,
+                   double* R, double* norm_out);
+
+/* `sweeps` applications of the level's Schwarz smoother to U in place (Sec. 5.2). */
+int igamg_smooth(igamg_handle* h, int level, double* U, const double* F, int sweeps);
+
+/* G = R_l r = P_{l-1}^T r: restriction from level l to level l-1 (Sec. 5.1). */
+int igamg_restrict(igamg_handle* h, int level, const double* r_fine, double* g_coarse);
+
+/* u_fine += P_{l-1} u_coarse: prolongation from level l-1 to level l (Sec. 5.1). */
+int igamg_prolong_add(igamg_handle* h, int level, const double* u_coarse, double* u_fine);
+
+/* U = K_0^{-1} G on the coarsest level (Algorithm 1, exact solve). */
+int igamg_coarse_solve(igamg_handle* h, const double* G, double* U);
+
+/* One V-cycle MGV(n_levels-1, U, F) of Algorithm 1, in place on U (device). */
+int igamg_vcycle(igamg_handle* h, double* U, const double* F);
+
+/* V-cycles until ||F - K U||_2 <= rtol ||F - K U_0||_2 or max_cycles (Sec. 6 protocol with
+ * the tolerance as a parameter).  Synchronises once per cycle to read the norm.
+ * rep may be NULL.  Returns IGAMG_NOT_CONVERGED (U holds the last iterate) if the
+ * tolerance was not met, IGAMG_ENONFINITE if a norm was NaN/Inf. */
+int igamg_solve(igamg_handle* h, double* U, const double* F, double rtol, int max_cycles,
+                igamg_report* rep);
+
+/* End-to-end form of igamg_solve with HOST buffers: copies f (host, quadrature points)
+ * and the initial U (host) to the device, builds F, solves, copies U back.  Synchronous. */
+int igamg_solve_host(igamg_handle* h, const double* f_qp_host, double* U_host, double rtol,
+                     int max_cycles, igamg_report* rep);
+
+/* max over pressure-space coefficients of |div u_h| (Lemma, Sec. 4.1: zero up to
+ * round-off for the iterates of Sec. 5.3).  Synchronises; result on the host. */
+int igamg_div_inf(igamg_handle* h, const double* U, double* out);
+
+/* Velocity blocks of U = curl psi = (d psi/dy, -d psi/dx) for psi given on the
+ * (n+p-2)^2 interior streamfunction coefficients (Sec. 4.3 complex); the pressure and
+ * lambda entries of U are not touched. */
+int igamg_curl(igamg_handle* h, const double* psi, double* U);
+
+/* ---- host-only inspection of the set-up (no GPU needed; for tests) -------------------
+ * Each call builds the hierarchy on the host and copies one piece out, dense, row-major.
+ * They exist so that the host set-up can be checked against an independent assembly
+ * without a GPU.  cap is the capacity of the output in doubles; *n_out gets the number
+ * of rows (the matrix is n_out x n_out or n_out x *n_cols). */
+
+/* K_l as the library applies it (Sec. 3.4; coarse levels = R K P of Sec. 5.1). */
+int igamg_host_level_matrix(const igamg_problem* prob, int level, double* K, size_t cap,
+                            long long* n_out);
+/* P_{l-1} (rows: level l, columns: level l-1), block diag(P^v, P^q, 1) of Sec. 5.1. */
+int igamg_host_prolongation(const igamg_problem* prob, int level, double* P, size_t cap,
+                            long long* n_rows, long long* n_cols);
+/* Patch tables of level l (Sec. 5.2): for patch k in colour-major order, colour[k] and
+ * its DOF list dofs[k*maxl .. k*maxl+maxl) (-1 padded).  Capacities in entries. */
+int igamg_host_patches(const igamg_problem* prob, int level, int* colour, int* dofs,
+                       size_t cap_patches, size_t cap_dofs, int* n_patches, int* maxl);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,88 @@
+// Internal declarations shared by the host set-up (setup.cpp) and the CUDA side (igamg.cu).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "igamg.h"
+
+namespace igamg {
+
+// A 1D banded matrix with half-width hw: entry (i, j) lives at v[i*(2hw+1) + (j-i+hw)].
+struct Band {
+  int rows = 0, cols = 0, hw = 0;
+  std::vector<double> v;
+  void init(int r, int c, int h) {
+    rows = r; cols = c; hw = h;
+    v.assign((size_t)r * (2 * h + 1), 0.0);
+  }
+  double get(int i, int j) const {
+    if (i < 0 || i >= rows || j < 0 || j >= cols) return 0.0;
+    int d = j - i + hw;
+    if (d < 0 || d > 2 * hw) return 0.0;
+    return v[(size_t)i * (2 * hw + 1) + d];
+  }
+  void add(int i, int j, double x);
+};
+
+// Per-level 1D factors of the Kronecker form of K_l (2D, identity map, constant sigma, nu):
+//   A_xx = X1 (x) Mq + X2 (x) Y2   [x-factor (x) y-factor],  A_yy = Mq (x) X1 + Y2 (x) X2,
+//   B_x  = D (x) Mq,  B_y = Mq (x) D,  m = mq (x) mq.
+// X1 = sigma M_p + nu S_p, X2 = nu M_p (degree p); Mq = M_{p-1}, Y2 = S_{p-1} + W_{p-1} with
+// W the Nitsche wall terms of Sec. 3.3 (penalty C_I / h_fine on every level).
+struct Level1D {
+  int n = 0, p = 0, q = 0;
+  Band X1, X2, Mq, Y2, D;     // all stored with half-width p
+  std::vector<double> mq;     // int N^q_k, k = 0..n+q-1
+  std::vector<double> dcoef;  // d/dx of degree-p splines: p/(t_{k+p}-t_k), k = 1..n+p-1 -> [k-1]
+};
+
+// 1D prolongation (fine x coarse) in two banded views.
+struct Transfer1D {
+  int nf = 0, nc = 0;          // rows (fine) and columns (coarse) of this view
+  static constexpr int WP = 3; // max nonzeros per fine row
+  static constexpr int WR = 5; // max nonzeros per coarse column
+  std::vector<int> c0;         // per fine row: first coarse column
+  std::vector<double> pv;      // nf * WP
+  std::vector<int> f0;         // per coarse column: first fine row
+  std::vector<double> rv;      // nc * WR
+};
+
+struct PatchTables {
+  int n_patches = 0, maxl = 0, n_cls = 0, n_colours = 0;
+  std::vector<int> dofs;       // n_patches * maxl (global dof ids, -1 padded), colour-major
+  std::vector<int> cls;        // n_patches
+  std::vector<int> nloc;       // per class: n_v + n_q
+  std::vector<double> cinv;    // n_cls * maxl * maxl: leading block of the bordered inverse
+  std::vector<int> colour_off; // n_colours + 1
+  std::vector<int> d2p_off;    // dof -> list of (patch * maxl + local row), CSR over dofs
+  std::vector<int> d2p_idx;
+};
+
+struct LevelHost {
+  Level1D f;
+  igamg_sizes sz{};
+  PatchTables pt;
+};
+
+struct HierarchyHost {
+  int p = 0, L = 0, n_fine = 0;
+  double sigma = 0, nu = 0, cpen = 0;
+  std::vector<LevelHost> lev;          // 0 = coarsest
+  std::vector<Transfer1D> tp_free;     // [l] : level l-1 -> l, degree p, interior indices
+  std::vector<Transfer1D> tq;          // [l] : degree p-1, all indices
+  std::vector<double> coarse_inv;      // ndof0 x ndof0
+  int ndof0 = 0;
+  // load vector tables on the finest level: per 1D basis i and local element k (0..d),
+  // values times quadrature weight at the G points; G = p+2
+  int G = 0;
+  std::vector<double> lv_p, lv_q;      // (n+p)*(p+1)*G and (n+q)*(q+1)*G
+  std::vector<double> quad_x;          // n*G abscissae (finest level)
+};
+
+// Builds everything; returns IGAMG_OK or an error code with a message in err.
+int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err);
+igamg_sizes level_sizes(int p, int n);
+double k_entry(const Level1D& L, const igamg_sizes& s, long long g1, long long g2);
+
+}  // namespace igamg

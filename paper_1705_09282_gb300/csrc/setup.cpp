@@ -1,0 +1,551 @@
+// Host-side set-up of the multigrid hierarchy (Sec. 4-5 of arXiv 1705.09282), in FP64.
+//
+// Route taken here (different from a plain 2D assembly on purpose): on the unit square
+// with constant sigma, nu every block of K is a sum of Kronecker products of 1D banded
+// matrices, so each level keeps only its 1D factors.  Coarse operators are the Galerkin
+// products R K P of Sec. 5.1; for this bilinear form they equal the same form on the
+// coarse spline space with the Nitsche penalty of the finest mesh (the coarse space is a
+// subspace of the fine one and every integral is exact), which is how they are built.
+// Knot-insertion prolongations (Sec. 4.5) are obtained by collocation at the fine
+// Greville abscissae (Schoenberg-Whitney), not by inserting knots one at a time.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <utility>
+
+#include "igamg_internal.h"
+
+namespace igamg {
+
+void Band::add(int i, int j, double x) {
+  int d = j - i + hw;
+  if (i < 0 || i >= rows || j < 0 || j >= cols || d < 0 || d > 2 * hw) {
+    if (x != 0.0) std::fprintf(stderr, "igamg: band overflow (%d,%d)\n", i, j);
+    return;
+  }
+  v[(size_t)i * (2 * hw + 1) + d] += x;
+}
+
+namespace {
+
+std::vector<double> knots(int d, int n) {
+  std::vector<double> t(n + 2 * d + 1);
+  for (int k = 0; k < (int)t.size(); ++k) {
+    int m = k - d;
+    t[k] = m <= 0 ? 0.0 : (m >= n ? 1.0 : (double)m / n);
+  }
+  return t;
+}
+
+// Values of the d+1 B-splines that are nonzero on knot span s (t_s <= x <= t_{s+1}),
+// i.e. N_{s-d..s}(x), by the triangular form of the Cox-de Boor recursion (Sec. 4.2).
+void span_values(const std::vector<double>& t, int d, int s, double x, double* N) {
+  double left[8], right[8];
+  N[0] = 1.0;
+  for (int j = 1; j <= d; ++j) {
+    left[j] = x - t[s + 1 - j];
+    right[j] = t[s + j] - x;
+    double carry = 0.0;
+    for (int r = 0; r < j; ++r) {
+      double tmp = N[r] / (right[r + 1] + left[j - r]);
+      N[r] = carry + right[r + 1] * tmp;
+      carry = left[j - r] * tmp;
+    }
+    N[j] = carry;
+  }
+}
+
+// Derivatives of N_{s-d..s} on span s: N'_{i,d} = d/(t_{i+d}-t_i) N_{i,d-1} - d/(t_{i+d+1}-t_{i+1}) N_{i+1,d-1}.
+void span_derivs(const std::vector<double>& t, int d, int s, double x, double* dN) {
+  if (d == 0) { dN[0] = 0.0; return; }
+  double Nl[8];
+  span_values(t, d - 1, s, x, Nl);  // N_{s-d+1..s, d-1}
+  for (int k = 0; k <= d; ++k) {
+    int i = s - d + k;
+    double a = 0.0, b = 0.0;
+    if (k >= 1) { double h = t[i + d] - t[i]; if (h > 0) a = d / h * Nl[k - 1]; }
+    if (k <= d - 1) { double h = t[i + d + 1] - t[i + 1]; if (h > 0) b = d / h * Nl[k]; }
+    dN[k] = a - b;
+  }
+}
+
+// Gauss-Legendre rule with m points on [0,1] (Newton on the Legendre recurrence).
+void gauss01(int m, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(m); w.resize(m);
+  for (int i = 0; i < m; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (m + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= m; ++k) { double pk = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = pk; }
+      if (m == 1) { p1 = z; p0 = 1.0; }
+      dp = m * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= m; ++k) { double pk = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = pk; }
+    dp = m * (z * p1 - p0) / (z * z - 1.0);
+    x[m - 1 - i] = 0.5 * (z + 1.0);
+    w[m - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);  // (2/((1-z^2) P'^2)) / 2
+  }
+}
+
+// In-place LU with partial pivoting of a dense n x n row-major matrix; returns false on
+// a pivot below tol * max|entry|.
+bool lu_inplace(std::vector<double>& A, int n, std::vector<int>& piv) {
+  double amax = 0.0;
+  for (double v : A) amax = std::max(amax, std::fabs(v));
+  piv.resize(n);
+  for (int k = 0; k < n; ++k) {
+    int r = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[(size_t)i * n + k]) > std::fabs(A[(size_t)r * n + k])) r = i;
+    piv[k] = r;
+    if (!(std::fabs(A[(size_t)r * n + k]) > 1e-14 * amax)) return false;
+    if (r != k) for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)r * n + j]);
+    double inv = 1.0 / A[(size_t)k * n + k];
+    for (int i = k + 1; i < n; ++i) {
+      double l = A[(size_t)i * n + k] * inv;
+      A[(size_t)i * n + k] = l;
+      if (l != 0.0)
+        for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+    }
+  }
+  return true;
+}
+
+void lu_solve(const std::vector<double>& LU, const std::vector<int>& piv, int n, double* b) {
+  for (int k = 0; k < n; ++k) { std::swap(b[k], b[piv[k]]); }
+  for (int i = 1; i < n; ++i) { double s = b[i]; for (int j = 0; j < i; ++j) s -= LU[(size_t)i * n + j] * b[j]; b[i] = s; }
+  for (int i = n - 1; i >= 0; --i) { double s = b[i]; for (int j = i + 1; j < n; ++j) s -= LU[(size_t)i * n + j] * b[j]; b[i] = s / LU[(size_t)i * n + i]; }
+}
+
+// Explicit inverse via LU; false if singular.
+bool invert(std::vector<double> A, int n, std::vector<double>& Ainv) {
+  std::vector<int> piv;
+  if (!lu_inplace(A, n, piv)) return false;
+  Ainv.assign((size_t)n * n, 0.0);
+  std::vector<double> col(n);
+  for (int j = 0; j < n; ++j) {
+    std::fill(col.begin(), col.end(), 0.0);
+    col[j] = 1.0;
+    lu_solve(A, piv, n, col.data());
+    for (int i = 0; i < n; ++i) Ainv[(size_t)i * n + j] = col[i];
+  }
+  return true;
+}
+
+// 1D factors on n elements (all integrals by (p+2)-point Gauss, exact for these polynomials).
+void build_level1d(int p, int n, double sigma, double nu, double pen_over_nu, Level1D& L) {
+  const int q = p - 1;
+  L.n = n; L.p = p; L.q = q;
+  auto tp = knots(p, n), tq = knots(q, n);
+  std::vector<double> gx, gw;
+  gauss01(p + 2, gx, gw);
+  Band Mp, Sp, Sq, Wq;
+  Mp.init(n + p, n + p, p); Sp.init(n + p, n + p, p);
+  L.Mq.init(n + q, n + q, p); Sq.init(n + q, n + q, p); Wq.init(n + q, n + q, p);
+  L.D.init(n + p, n + q, p);
+  const double h = 1.0 / n;
+  for (int e = 0; e < n; ++e) {
+    for (int g = 0; g < (int)gx.size(); ++g) {
+      double x = (e + gx[g]) * h, w = gw[g] * h;
+      double Np[8], dNp[8], Nq[8], dNq[8];
+      span_values(tp, p, e + p, x, Np); span_derivs(tp, p, e + p, x, dNp);
+      span_values(tq, q, e + q, x, Nq); span_derivs(tq, q, e + q, x, dNq);
+      for (int a = 0; a <= p; ++a)
+        for (int b = 0; b <= p; ++b) {
+          Mp.add(e + a, e + b, w * Np[a] * Np[b]);
+          Sp.add(e + a, e + b, w * dNp[a] * dNp[b]);
+        }
+      for (int a = 0; a <= q; ++a)
+        for (int b = 0; b <= q; ++b) {
+          L.Mq.add(e + a, e + b, w * Nq[a] * Nq[b]);
+          Sq.add(e + a, e + b, w * dNq[a] * dNq[b]);
+        }
+      for (int a = 0; a <= p; ++a)
+        for (int b = 0; b <= q; ++b) L.D.add(e + a, e + b, w * dNp[a] * Nq[b]);
+    }
+  }
+  // Nitsche wall terms for the tangential component, Sec. 3.3, per unit nu:
+  //   sum over walls x0 in {0,1} with outward normal s = -1 / +1:
+  //   -s (N_i N_j' + N_i' N_j)(x0) + (C_I / h_fine) N_i(x0) N_j(x0)
+  for (int wall = 0; wall < 2; ++wall) {
+    double x0 = wall ? 1.0 : 0.0, s = wall ? 1.0 : -1.0;
+    int span = wall ? (n - 1 + q) : q;
+    double Nq[8], dNq[8];
+    span_values(tq, q, span, x0, Nq); span_derivs(tq, q, span, x0, dNq);
+    int base = span - q;
+    for (int a = 0; a <= q; ++a)
+      for (int b = 0; b <= q; ++b)
+        Wq.add(base + a, base + b, -s * (Nq[a] * dNq[b] + dNq[a] * Nq[b]) + pen_over_nu * Nq[a] * Nq[b]);
+  }
+  L.X1.init(n + p, n + p, p); L.X2.init(n + p, n + p, p); L.Y2.init(n + q, n + q, p);
+  for (size_t k = 0; k < Mp.v.size(); ++k) {
+    L.X1.v[k] = sigma * Mp.v[k] + nu * Sp.v[k];
+    L.X2.v[k] = nu * Mp.v[k];
+  }
+  for (size_t k = 0; k < Sq.v.size(); ++k) L.Y2.v[k] = Sq.v[k] + Wq.v[k];
+  L.mq.resize(n + q);
+  for (int k = 0; k < n + q; ++k) L.mq[k] = (tq[k + q + 1] - tq[k]) / (q + 1);
+  L.dcoef.resize(n + q);
+  for (int k = 1; k <= n + q; ++k) L.dcoef[k - 1] = p / (tp[k + p] - tp[k]);
+}
+
+// Dense 1D prolongation (fine x coarse) for midpoint refinement, by collocation.
+std::vector<double> prolong_dense(int d, int nc, int& nfb, int& ncb) {
+  int nf = 2 * nc;
+  nfb = nf + d; ncb = nc + d;
+  auto tf = knots(d, nf), tc = knots(d, nc);
+  std::vector<double> Bf((size_t)nfb * nfb, 0.0), Bc((size_t)nfb * ncb, 0.0);
+  for (int r = 0; r < nfb; ++r) {
+    double g = 0.0;
+    if (d == 0) g = (tf[r] + tf[r + 1]) / 2;
+    else { for (int k = 1; k <= d; ++k) g += tf[r + k]; g /= d; }
+    int sf = std::min(std::max((int)std::floor(g * nf), 0), nf - 1) + d;
+    int sc = std::min(std::max((int)std::floor(g * nc), 0), nc - 1) + d;
+    double N[8];
+    span_values(tf, d, sf, g, N);
+    for (int k = 0; k <= d; ++k) Bf[(size_t)r * nfb + sf - d + k] = N[k];
+    span_values(tc, d, sc, g, N);
+    for (int k = 0; k <= d; ++k) Bc[(size_t)r * ncb + sc - d + k] = N[k];
+  }
+  std::vector<int> piv;
+  if (!lu_inplace(Bf, nfb, piv)) return {};
+  std::vector<double> P((size_t)nfb * ncb), col(nfb);
+  for (int j = 0; j < ncb; ++j) {
+    for (int r = 0; r < nfb; ++r) col[r] = Bc[(size_t)r * ncb + j];
+    lu_solve(Bf, piv, nfb, col.data());
+    for (int r = 0; r < nfb; ++r) P[(size_t)r * ncb + j] = std::fabs(col[r]) < 1e-13 ? 0.0 : col[r];
+  }
+  return P;
+}
+
+bool make_transfer(const std::vector<double>& P, int nfb, int ncb, int off, Transfer1D& T) {
+  // view rows/cols [off, nfb-off) x [off, ncb-off)
+  T.nf = nfb - 2 * off; T.nc = ncb - 2 * off;
+  T.c0.assign(T.nf, 0); T.pv.assign((size_t)T.nf * Transfer1D::WP, 0.0);
+  T.f0.assign(T.nc, 0); T.rv.assign((size_t)T.nc * Transfer1D::WR, 0.0);
+  auto at = [&](int f, int c) { return P[(size_t)(f + off) * ncb + (c + off)]; };
+  // entries outside the view must vanish (interior coarse functions do not touch the
+  // fine boundary functions)
+  if (off) for (int c = 0; c < T.nc; ++c) { if (P[(size_t)0 * ncb + c + off] != 0.0 || P[(size_t)(nfb - 1) * ncb + c + off] != 0.0) return false; }
+  for (int f = 0; f < T.nf; ++f) {
+    int first = -1, last = -1;
+    for (int c = 0; c < T.nc; ++c) if (at(f, c) != 0.0) { if (first < 0) first = c; last = c; }
+    if (first < 0) first = last = 0;
+    if (last - first + 1 > Transfer1D::WP) return false;
+    first = std::min(first, std::max(0, T.nc - Transfer1D::WP));
+    T.c0[f] = first;
+    for (int k = 0; k < Transfer1D::WP; ++k) { int c = first + k; T.pv[(size_t)f * Transfer1D::WP + k] = (c < T.nc) ? at(f, c) : 0.0; }
+  }
+  for (int c = 0; c < T.nc; ++c) {
+    int first = -1, last = -1;
+    for (int f = 0; f < T.nf; ++f) if (at(f, c) != 0.0) { if (first < 0) first = f; last = f; }
+    if (first < 0) first = last = 0;
+    if (last - first + 1 > Transfer1D::WR) return false;
+    first = std::min(first, std::max(0, T.nf - Transfer1D::WR));
+    T.f0[c] = first;
+    for (int k = 0; k < Transfer1D::WR; ++k) { int f = first + k; T.rv[(size_t)c * Transfer1D::WR + k] = (f < T.nf) ? at(f, c) : 0.0; }
+  }
+  return true;
+}
+
+// ---- DOF numbering and single matrix entries of K_l from the 1D factors ---------------
+struct Dof { int blk; int x, y; };  // blk 0 u_x, 1 u_y, 2 p, 3 lambda; x,y = full 1D indices
+
+Dof decode(const igamg_sizes& s, long long g) {
+  Dof d{};
+  if (g < s.n_ux) { d.blk = 0; d.y = (int)(g / s.nx_ux); d.x = (int)(g % s.nx_ux) + 1; }
+  else if (g < s.n_ux + s.n_uy) { long long r = g - s.n_ux; d.blk = 1; d.y = (int)(r / s.nx_uy) + 1; d.x = (int)(r % s.nx_uy); }
+  else if (g < s.n_ux + s.n_uy + s.n_p) { long long r = g - s.n_ux - s.n_uy; d.blk = 2; d.y = (int)(r / s.n_pdir); d.x = (int)(r % s.n_pdir); }
+  else { d.blk = 3; d.x = d.y = 0; }
+  return d;
+}
+
+long long gid(const igamg_sizes& s, int blk, int x, int y) {
+  switch (blk) {
+    case 0: if (x < 1 || x > s.nx_ux) return -1; return (long long)y * s.nx_ux + (x - 1);
+    case 1: if (y < 1 || y > s.ny_uy) return -1; return s.n_ux + (long long)(y - 1) * s.nx_uy + x;
+    case 2: return s.n_ux + s.n_uy + (long long)y * s.n_pdir + x;
+    default: return s.n_total - 1;
+  }
+}
+
+}  // namespace
+
+double k_entry(const Level1D& L, const igamg_sizes& s, long long g1, long long g2) {
+  Dof a = decode(s, g1), b = decode(s, g2);
+  auto m = [&](const Dof& d) { return L.mq[d.x] * L.mq[d.y]; };
+  if (a.blk == 0 && b.blk == 0) return L.X1.get(a.x, b.x) * L.Mq.get(a.y, b.y) + L.X2.get(a.x, b.x) * L.Y2.get(a.y, b.y);
+  if (a.blk == 1 && b.blk == 1) return L.Mq.get(a.x, b.x) * L.X1.get(a.y, b.y) + L.Y2.get(a.x, b.x) * L.X2.get(a.y, b.y);
+  if (a.blk == 0 && b.blk == 2) return -L.D.get(a.x, b.x) * L.Mq.get(a.y, b.y);
+  if (a.blk == 1 && b.blk == 2) return -L.Mq.get(a.x, b.x) * L.D.get(a.y, b.y);
+  if (a.blk == 2 && b.blk == 0) return L.D.get(b.x, a.x) * L.Mq.get(b.y, a.y);
+  if (a.blk == 2 && b.blk == 1) return L.Mq.get(b.x, a.x) * L.D.get(b.y, a.y);
+  if (a.blk == 2 && b.blk == 3) return m(a);
+  if (a.blk == 3 && b.blk == 2) return m(b);
+  return 0.0;
+}
+
+namespace {
+
+// 1D position class of a patch index a on n+p-2 interior positions: the first and last
+// T positions are their own classes, the rest share the translation-invariant class.
+int pos_class(int a, int n, int p) {
+  const int T = 2 * p + 2;
+  int last = n + p - 2;
+  if (a < T) return a;
+  if (last - a < T) return T + (last - a);
+  return 2 * T;
+}
+
+int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt, std::string& err) {
+  const int n = L.n, q = p - 1;
+  auto sup = [&](int i, int d) { return std::make_pair(std::max(0, i - d), std::min(n - 1, i)); };
+  auto inside = [](std::pair<int, int> a, std::pair<int, int> box) { return box.first <= a.first && a.second <= box.second; };
+  struct P { int a, b, colour; std::vector<int> dofs; int nv, nq; };
+  std::vector<P> all;
+  int np1 = p + 1;
+  for (int b = 1; b <= n + p - 2; ++b)
+    for (int a = 1; a <= n + p - 2; ++a) {
+      P P_; P_.a = a; P_.b = b; P_.colour = (b % np1) * np1 + (a % np1);
+      auto bx = sup(a, p), by = sup(b, p);
+      for (int y = std::max(0, b - p - 1); y <= std::min(n + q - 1, b + p + 1); ++y)
+        for (int x = std::max(1, a - p - 1); x <= std::min(n + p - 2, a + p + 1); ++x)
+          if (inside(sup(x, p), bx) && inside(sup(y, q), by)) P_.dofs.push_back((int)gid(s, 0, x, y));
+      for (int y = std::max(1, b - p - 1); y <= std::min(n + p - 2, b + p + 1); ++y)
+        for (int x = std::max(0, a - p - 1); x <= std::min(n + q - 1, a + p + 1); ++x)
+          if (inside(sup(x, q), bx) && inside(sup(y, p), by)) P_.dofs.push_back((int)gid(s, 1, x, y));
+      P_.nv = (int)P_.dofs.size();
+      for (int y = std::max(0, b - p - 1); y <= std::min(n + q - 1, b + p + 1); ++y)
+        for (int x = std::max(0, a - p - 1); x <= std::min(n + q - 1, a + p + 1); ++x)
+          if (inside(sup(x, q), bx) && inside(sup(y, q), by)) P_.dofs.push_back((int)gid(s, 2, x, y));
+      P_.nq = (int)P_.dofs.size() - P_.nv;
+      all.push_back(std::move(P_));
+    }
+  // colour-major, lexicographic (b, a) inside a colour
+  std::stable_sort(all.begin(), all.end(), [](const P& x, const P& y) { return x.colour < y.colour; });
+  int maxl = 0;
+  for (auto& P_ : all) maxl = std::max(maxl, (int)P_.dofs.size());
+  pt.n_patches = (int)all.size(); pt.maxl = maxl; pt.n_colours = np1 * np1;
+  pt.dofs.assign((size_t)pt.n_patches * maxl, -1);
+  pt.cls.assign(pt.n_patches, 0);
+  pt.colour_off.assign(pt.n_colours + 1, 0);
+  std::map<std::pair<int, int>, int> cmap;
+  std::vector<int> rep;
+  for (int i = 0; i < pt.n_patches; ++i) {
+    auto& P_ = all[i];
+    for (size_t k = 0; k < P_.dofs.size(); ++k) pt.dofs[(size_t)i * maxl + k] = P_.dofs[k];
+    pt.colour_off[P_.colour + 1]++;
+    auto key = std::make_pair(pos_class(P_.a, n, p), pos_class(P_.b, n, p));
+    auto it = cmap.find(key);
+    if (it == cmap.end()) { int id = (int)rep.size(); cmap[key] = id; rep.push_back(i); pt.cls[i] = id; }
+    else pt.cls[i] = it->second;
+  }
+  for (int c = 0; c < pt.n_colours; ++c) pt.colour_off[c + 1] += pt.colour_off[c];
+  // bordered local inverses, one per class (Sec. 5.2 local problems; zero-mean local
+  // pressure through the border m_j = int N^q_j)
+  pt.n_cls = (int)rep.size();
+  pt.nloc.assign(pt.n_cls, 0);
+  pt.cinv.assign((size_t)pt.n_cls * maxl * maxl, 0.0);
+  for (int c = 0; c < pt.n_cls; ++c) {
+    auto& P_ = all[rep[c]];
+    int nl = (int)P_.dofs.size(), nb = nl + 1;
+    std::vector<double> Kb((size_t)nb * nb, 0.0), inv;
+    for (int r = 0; r < nl; ++r)
+      for (int t = 0; t < nl; ++t) Kb[(size_t)r * nb + t] = k_entry(L, s, P_.dofs[r], P_.dofs[t]);
+    for (int r = P_.nv; r < nl; ++r) {
+      Dof d = decode(s, P_.dofs[r]);
+      double m = L.mq[d.x] * L.mq[d.y];
+      Kb[(size_t)r * nb + nl] = m; Kb[(size_t)nl * nb + r] = m;
+    }
+    if (!invert(Kb, nb, inv)) { err = "singular local patch matrix"; return IGAMG_ESINGULAR; }
+    pt.nloc[c] = nl;
+    for (int r = 0; r < nl; ++r)
+      for (int t = 0; t < nl; ++t) pt.cinv[((size_t)c * maxl + r) * maxl + t] = inv[(size_t)r * nb + t];
+  }
+  // dof -> (patch, local row) lists for the additive smoother, patch order ascending
+  long long nd = s.n_total;
+  pt.d2p_off.assign(nd + 1, 0);
+  for (int i = 0; i < pt.n_patches; ++i)
+    for (int k = 0; k < maxl; ++k) { int g = pt.dofs[(size_t)i * maxl + k]; if (g >= 0) pt.d2p_off[g + 1]++; }
+  for (long long g = 0; g < nd; ++g) pt.d2p_off[g + 1] += pt.d2p_off[g];
+  pt.d2p_idx.assign(pt.d2p_off[nd], 0);
+  std::vector<int> fill(pt.d2p_off.begin(), pt.d2p_off.end() - 1);
+  // the additive update sums corrections in the lexicographic patch order (b, then a)
+  std::vector<int> lex(pt.n_patches);
+  for (int i = 0; i < pt.n_patches; ++i) lex[i] = i;
+  std::sort(lex.begin(), lex.end(), [&](int x, int y) {
+    return all[x].b != all[y].b ? all[x].b < all[y].b : all[x].a < all[y].a; });
+  for (int i : lex)
+    for (int k = 0; k < maxl; ++k) { int g = pt.dofs[(size_t)i * maxl + k]; if (g >= 0) pt.d2p_idx[fill[g]++] = i * maxl + k; }
+  return IGAMG_OK;
+}
+
+}  // namespace
+
+igamg_sizes level_sizes(int p, int n) {
+  igamg_sizes s{};
+  int q = p - 1;
+  s.n = n;
+  s.nx_ux = n + p - 2; s.ny_ux = n + q;
+  s.nx_uy = n + q; s.ny_uy = n + p - 2;
+  s.n_pdir = n + q;
+  s.n_ux = (long long)s.nx_ux * s.ny_ux;
+  s.n_uy = (long long)s.nx_uy * s.ny_uy;
+  s.n_p = (long long)s.n_pdir * s.n_pdir;
+  s.n_total = s.n_ux + s.n_uy + s.n_p + 1;
+  s.n_patches = (n + p - 2) * (n + p - 2);
+  s.n_colours = (p + 1) * (p + 1);
+  s.n_quad = p + 2;
+  return s;
+}
+
+int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err) {
+  const int p = pr.p, L = pr.n_levels, nf = pr.n_fine;
+  H.p = p; H.L = L; H.n_fine = nf; H.sigma = pr.sigma; H.nu = pr.nu;
+  H.cpen = pr.c_penalty > 0 ? pr.c_penalty : 4.0 * (p - 1);
+  const double pen_over_nu = H.cpen * nf;  // C_I / h_fine on every level
+  H.lev.resize(L);
+  for (int l = 0; l < L; ++l) {
+    int n = nf >> (L - 1 - l);
+    auto& lv = H.lev[l];
+    build_level1d(p, n, pr.sigma, pr.nu, pen_over_nu, lv.f);
+    lv.sz = level_sizes(p, n);
+    if (l >= 1) {
+      int rc = build_patches(p, lv.f, lv.sz, lv.pt, err);
+      if (rc) return rc;
+    }
+  }
+  H.tp_free.resize(L); H.tq.resize(L);
+  for (int l = 1; l < L; ++l) {
+    int nc = nf >> (L - l);
+    int a, b;
+    auto Pp = prolong_dense(p, nc, a, b);
+    if (Pp.empty() || !make_transfer(Pp, a, b, 1, H.tp_free[l])) { err = "degree-p prolongation"; return IGAMG_ESINGULAR; }
+    auto Pq = prolong_dense(p - 1, nc, a, b);
+    if (Pq.empty() || !make_transfer(Pq, a, b, 0, H.tq[l])) { err = "degree-(p-1) prolongation"; return IGAMG_ESINGULAR; }
+  }
+  // coarsest matrix, dense, and its inverse
+  {
+    auto& lv = H.lev[0];
+    int nd = (int)lv.sz.n_total;
+    std::vector<double> K((size_t)nd * nd);
+    for (int i = 0; i < nd; ++i)
+      for (int j = 0; j < nd; ++j) K[(size_t)i * nd + j] = k_entry(lv.f, lv.sz, i, j);
+    if (!invert(K, nd, H.coarse_inv)) { err = "singular coarsest matrix"; return IGAMG_ESINGULAR; }
+    H.ndof0 = nd;
+  }
+  // load-vector tables on the finest level
+  {
+    const int G = p + 2, q = p - 1;
+    H.G = G;
+    std::vector<double> gx, gw;
+    gauss01(G, gx, gw);
+    auto tp = knots(p, nf), tq = knots(q, nf);
+    H.lv_p.assign((size_t)(nf + p) * (p + 1) * G, 0.0);
+    H.lv_q.assign((size_t)(nf + q) * (q + 1) * G, 0.0);
+    H.quad_x.resize((size_t)nf * G);
+    for (int e = 0; e < nf; ++e)
+      for (int g = 0; g < G; ++g) {
+        double x = (e + gx[g]) / nf, w = gw[g] / nf;
+        H.quad_x[(size_t)e * G + g] = x;
+        double N[8];
+        span_values(tp, p, e + p, x, N);
+        for (int a = 0; a <= p; ++a) { int i = e + a; int k = e - (i - p); H.lv_p[((size_t)i * (p + 1) + k) * G + g] = w * N[a]; }
+        span_values(tq, q, e + q, x, N);
+        for (int a = 0; a <= q; ++a) { int i = e + a; int k = e - (i - q); H.lv_q[((size_t)i * (q + 1) + k) * G + g] = w * N[a]; }
+      }
+  }
+  return IGAMG_OK;
+}
+
+}  // namespace igamg
+
+// ---- host-only inspection entry points -----------------------------------------------
+namespace {
+int host_build(const igamg_problem* prob, int level, igamg::HierarchyHost& H) {
+  if (!prob || prob->dim != 2 || (prob->p != 2 && prob->p != 3)) return IGAMG_EUNSUPPORTED;
+  if (prob->n_levels < 1 || prob->n_fine < 1 || prob->n_fine % (1 << (prob->n_levels - 1))) return IGAMG_EINVAL;
+  if (level < 0 || level >= prob->n_levels) return IGAMG_EINVAL;
+  if (igamg::level_sizes(prob->p, prob->n_fine >> (prob->n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
+  std::string err;
+  return igamg::build_hierarchy(*prob, H, err);
+}
+}  // namespace
+
+extern "C" int igamg_host_level_matrix(const igamg_problem* prob, int level, double* K, size_t cap,
+                                       long long* n_out) {
+  igamg::HierarchyHost H;
+  int rc = host_build(prob, level, H);
+  if (rc) return rc;
+  const auto& lv = H.lev[level];
+  long long n = lv.sz.n_total;
+  if (n_out) *n_out = n;
+  if (!K) return IGAMG_OK;
+  if (cap < (size_t)(n * n)) return IGAMG_EINVAL;
+  for (long long i = 0; i < n; ++i)
+    for (long long j = 0; j < n; ++j) K[i * n + j] = igamg::k_entry(lv.f, lv.sz, i, j);
+  return IGAMG_OK;
+}
+
+extern "C" int igamg_host_prolongation(const igamg_problem* prob, int level, double* P, size_t cap,
+                                       long long* n_rows, long long* n_cols) {
+  if (level < 1) return IGAMG_EINVAL;
+  igamg::HierarchyHost H;
+  int rc = host_build(prob, level, H);
+  if (rc) return rc;
+  const auto& f = H.lev[level].sz;
+  const auto& c = H.lev[level - 1].sz;
+  long long nr = f.n_total, nc = c.n_total;
+  if (n_rows) *n_rows = nr;
+  if (n_cols) *n_cols = nc;
+  if (!P) return IGAMG_OK;
+  if (cap < (size_t)(nr * nc)) return IGAMG_EINVAL;
+  std::fill(P, P + nr * nc, 0.0);
+  const auto& tp = H.tp_free[level];
+  const auto& tq = H.tq[level];
+  auto put = [&](long long roff, long long coff, int fnx, int cnx, const igamg::Transfer1D& TX,
+                 const igamg::Transfer1D& TY) {
+    for (int fy = 0; fy < TY.nf; ++fy)
+      for (int fx = 0; fx < TX.nf; ++fx)
+        for (int ky = 0; ky < igamg::Transfer1D::WP; ++ky)
+          for (int kx = 0; kx < igamg::Transfer1D::WP; ++kx) {
+            int cy = TY.c0[fy] + ky, cx = TX.c0[fx] + kx;
+            if (cy >= TY.nc || cx >= TX.nc) continue;
+            double w = TY.pv[(size_t)fy * igamg::Transfer1D::WP + ky] * TX.pv[(size_t)fx * igamg::Transfer1D::WP + kx];
+            if (w != 0.0) P[(roff + (long long)fy * fnx + fx) * nc + coff + (long long)cy * cnx + cx] += w;
+          }
+  };
+  put(0, 0, f.nx_ux, c.nx_ux, tp, tq);
+  put(f.n_ux, c.n_ux, f.nx_uy, c.nx_uy, tq, tp);
+  put(f.n_ux + f.n_uy, c.n_ux + c.n_uy, f.n_pdir, c.n_pdir, tq, tq);
+  P[(nr - 1) * nc + nc - 1] = 1.0;
+  return IGAMG_OK;
+}
+
+extern "C" int igamg_host_patches(const igamg_problem* prob, int level, int* colour, int* dofs,
+                                  size_t cap_patches, size_t cap_dofs, int* n_patches, int* maxl) {
+  if (level < 1) return IGAMG_EINVAL;
+  igamg::HierarchyHost H;
+  int rc = host_build(prob, level, H);
+  if (rc) return rc;
+  const auto& pt = H.lev[level].pt;
+  if (n_patches) *n_patches = pt.n_patches;
+  if (maxl) *maxl = pt.maxl;
+  if (colour) {
+    if (cap_patches < (size_t)pt.n_patches) return IGAMG_EINVAL;
+    for (int c = 0; c < pt.n_colours; ++c)
+      for (int k = pt.colour_off[c]; k < pt.colour_off[c + 1]; ++k) colour[k] = c;
+  }
+  if (dofs) {
+    if (cap_dofs < pt.dofs.size()) return IGAMG_EINVAL;
+    std::copy(pt.dofs.begin(), pt.dofs.end(), dofs);
+  }
+  return IGAMG_OK;
+}
+

@@ -1,0 +1,89 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared symbol, and its
+host-side set-up (1D Kronecker factors, knot-insertion transfers, patch tables) agrees
+with the oracle's independent assembly.  No GPU is needed."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import stokes2d as o2
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    from paper_1705_09282_gb300 import _lib
+    return _lib
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"\b(igamg_\w+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib().lib()
+    names = _declared_symbols()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(_lib().SIGNATURES) >= names
+
+
+def test_strerror():
+    L = _lib().lib()
+    assert L.igamg_strerror(-1) == b"invalid argument"
+    assert L.igamg_strerror(1).startswith(b"not converged")
+
+
+def test_bad_arguments_rejected_on_host():
+    import ctypes
+    L = _lib().lib()
+    pr = _lib().make_problem(2, 6, 3, 1.0, 1.0)       # 6 not divisible by 4
+    h = ctypes.c_void_p()
+    assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -1
+    pr = _lib().make_problem(4, 8, 2, 1.0, 1.0)       # p = 4 not built
+    assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -2
+    pr = _lib().make_problem(2, 8, 2, -1.0, 1.0)      # sigma <= 0
+    assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -1
+
+
+@pytest.mark.parametrize("p,sigma,nu", [(2, 1.0, 1.0), (3, 100.0, 0.3), (2, 1e-4, 1.0)])
+def test_level_operators_match_oracle_galerkin(p, sigma, nu):
+    from paper_1705_09282_gb300.solver import host_level_matrix
+    n, L = 8, 3
+    H = o2.Hierarchy(p, n, L, sigma, nu)
+    for lev in range(L):
+        Kg = host_level_matrix(p, n, L, sigma, nu, lev)
+        Ko = H.levels[lev].K.toarray()
+        scale = np.abs(Ko).max()
+        assert Kg.shape == Ko.shape
+        assert np.abs(Kg - Ko).max() <= 1e-12 * scale, (lev, np.abs(Kg - Ko).max() / scale)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_prolongations_match_oracle(p):
+    from paper_1705_09282_gb300.solver import host_prolongation
+    n, L = 16, 4
+    for lev in range(1, L):
+        Pg = host_prolongation(p, n, L, lev)
+        Po = o2.prolongation(p, n >> (L - lev)).toarray()
+        assert Pg.shape == Po.shape
+        assert np.abs(Pg - Po).max() <= 1e-13
+
+
+@pytest.mark.parametrize("p,n", [(2, 8), (3, 8), (2, 4), (3, 4)])
+def test_patch_tables_match_oracle(p, n):
+    from paper_1705_09282_gb300.solver import host_patches
+    col, dofs = host_patches(p, n, 2, 1)
+    S = o2.Stokes2D(p, n, 1, 1)
+    lev = o2.Level(p, n, S.K, S.m, S)
+    lev.build_patches()
+    want = [(P.colour, tuple(P.dofs)) for P in (lev.patches[i] for i in lev.colour_order)]
+    got = [(int(c), tuple(int(g) for g in d if g >= 0)) for c, d in zip(col, dofs)]
+    assert got == want
