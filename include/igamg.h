@@ -147,6 +147,26 @@ int igamg_div_inf(igamg_handle* h, const double* U, double* out);
  * lambda entries of U are not touched. */
 int igamg_curl(igamg_handle* h, const double* psi, double* U);
 
+/* Same result as igamg_residual on level `level` of the hierarchy that *prob describes,
+ * but without a handle and without allocating device memory: for callers that cannot
+ * call cudaMalloc (their device memory is owned by a pool, an arena or a host framework,
+ * or allocation is forbidden where they run).  The paper has no counterpart; this is a
+ * deployment convenience.
+ *   Scratch: a 1 MiB array that the library declares statically in device memory
+ *   (each GPU that loads the library keeps it until exit) holds this level's 1D
+ *   operator tables and the per-block partial sums of the norm.  A level that needs
+ *   more (about n > 1000 elements per direction) is rejected before any GPU work: the
+ *   call returns IGAMG_EINVAL and prints the needed and available sizes on stderr.
+ *   The first call on a device looks up the array's device address (with that device
+ *   current); make that first call before any stream capture.
+ *   Every call reuses the same array and rewrites all of it that it reads, so nothing
+ *   carries over; calls whose GPU work overlaps (other streams, other threads) race on
+ *   it and must be serialised by the caller.
+ *   U, F, R: device, layout above, R written; norm_out: host or NULL (if given, the call
+ *   synchronises the stream).  cuda_stream: a cudaStream_t as void*, or NULL. */
+int igamg_residual_static(const igamg_problem* prob, int level, const double* U,
+                          const double* F, double* R, double* norm_out, void* cuda_stream);
+
 /* ---- host-only inspection of the set-up (no GPU needed; for tests) -------------------
  * Each call builds the hierarchy on the host and copies one piece out, dense, row-major.
  * They exist so that the host set-up can be checked against an independent assembly

@@ -833,3 +833,88 @@ int igamg_curl(igamg_handle* h, const double* psi, double* U) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Residual entry point that allocates no device memory.
+//
+// For callers that cannot call cudaMalloc (a host program whose allocations all go
+// through its own pool or arena, code running inside a captured region that forbids new
+// allocations, or an embedding that owns the whole device memory budget): the scratch
+// of the residual kernel -- its level operator tables and its per-block partial sums --
+// lives in one fixed array in device memory that the library declares statically.
+// Every GPU that loads the library holds that array (1 MiB) until the process exits.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchDoubles = 131072;  // 1 MiB
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+double* g_static_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+extern "C" int igamg_residual_static(const igamg_problem* prob, int level, const double* U,
+                                     const double* F, double* R, double* norm_out,
+                                     void* cuda_stream) {
+  if (!prob || !U || !F || !R) return IGAMG_EINVAL;
+  const igamg_problem& pr = *prob;
+  if (pr.dim != 2 || (pr.p != 2 && pr.p != 3) || pr.beta_qp) return IGAMG_EUNSUPPORTED;
+  if (pr.n_levels < 1 || pr.n_levels > 16 || pr.n_fine < 1 || pr.n_fine > 8192) return IGAMG_EINVAL;
+  if (pr.n_fine % (1 << (pr.n_levels - 1))) return IGAMG_EINVAL;
+  if (level < 0 || level >= pr.n_levels || !(pr.sigma > 0) || !(pr.nu > 0)) return IGAMG_EINVAL;
+  const int p = pr.p, n = pr.n_fine >> (pr.n_levels - 1 - level);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+
+  // size check before any work: band tables + partials + the norm slot
+  igamg_sizes sz = level_sizes(p, n);
+  const size_t W = 2 * p + 1;
+  const size_t n_bands = (size_t)(n + p) * W * 3 + (size_t)(n + p - 1) * W * 2 + (n + p - 1);
+  const unsigned nb = nblk(sz.n_total - 1);
+  const size_t need = n_bands + 2 * (size_t)nb + 1;
+  if (need > kStaticScratchDoubles) {
+    g_err = "igamg_residual_static: level needs " + std::to_string(need) + " doubles of scratch, the static array holds " +
+            std::to_string(kStaticScratchDoubles);
+    std::fprintf(stderr, "igamg: %s\n", g_err.c_str());
+    return IGAMG_EINVAL;
+  }
+  // one-time set-up per device: the device address of the static array
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return IGAMG_EUNSUPPORTED;
+  if (!g_static_ptr[dev]) {
+    double* ptr = nullptr;
+    CK(cudaGetSymbolAddress((void**)&ptr, g_static_scratch));
+    g_static_ptr[dev] = ptr;
+  }
+  double* scratch = g_static_ptr[dev];
+
+  // level operator tables (host), copied into the front of the static array
+  Level1D f;
+  const double cpen = pr.c_penalty > 0 ? pr.c_penalty : 4.0 * (p - 1);
+  build_level1d(p, n, pr.sigma, pr.nu, cpen * pr.n_fine, f);
+  std::vector<double> bands;
+  bands.reserve(n_bands);
+  for (auto* b : {&f.X1, &f.X2, &f.Mq, &f.Y2, &f.D}) bands.insert(bands.end(), b->v.begin(), b->v.end());
+  bands.insert(bands.end(), f.mq.begin(), f.mq.end());
+  if (bands.size() != n_bands) return IGAMG_EINVAL;
+  CK(cudaMemcpyAsync(scratch, bands.data(), n_bands * sizeof(double), cudaMemcpyHostToDevice, s));
+  LevelHost lh;
+  lh.f = f;
+  lh.sz = sz;
+  LevelDev<double> L = make_leveldev(lh, scratch);
+  double* part = scratch + n_bands;       // fully rewritten by every call
+  double* norm2 = part + 2 * (size_t)nb;
+  if (p == 2) k_residual<2, double><<<nb, kBlock, 0, s>>>(L, U, F, R, part);
+  else k_residual<3, double><<<nb, kBlock, 0, s>>>(L, U, F, R, part);
+  k_residual_finish<double><<<1, 1024, 0, s>>>(sz.n_total, F, R, part, (int)nb, norm2);
+  int rc = launch_check();
+  if (rc) return rc;
+  if (norm_out) {
+    double v = 0.0;
+    CK(cudaMemcpyAsync(&v, norm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *norm_out = std::sqrt(v);
+  }
+  return IGAMG_OK;
+}

@@ -84,5 +84,7 @@ struct HierarchyHost {
 int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err);
 igamg_sizes level_sizes(int p, int n);
 double k_entry(const Level1D& L, const igamg_sizes& s, long long g1, long long g2);
+// 1D factors of one level with n elements; pen_over_nu = C_I / h_fine.
+void build_level1d(int p, int n, double sigma, double nu, double pen_over_nu, Level1D& L);
 
 }  // namespace igamg

@@ -138,6 +138,8 @@ bool invert(std::vector<double> A, int n, std::vector<double>& Ainv) {
   return true;
 }
 
+}  // namespace
+
 // 1D factors on n elements (all integrals by (p+2)-point Gauss, exact for these polynomials).
 void build_level1d(int p, int n, double sigma, double nu, double pen_over_nu, Level1D& L) {
   const int q = p - 1;
@@ -194,6 +196,8 @@ void build_level1d(int p, int n, double sigma, double nu, double pen_over_nu, Le
   L.dcoef.resize(n + q);
   for (int k = 1; k <= n + q; ++k) L.dcoef[k - 1] = p / (tp[k + p] - tp[k]);
 }
+
+namespace {
 
 // Dense 1D prolongation (fine x coarse) for midpoint refinement, by collocation.
 std::vector<double> prolong_dense(int d, int nc, int& nfb, int& ncb) {
