@@ -176,6 +176,9 @@ int igamg_residual_static(const igamg_problem* prob, int level, const double* U,
 /* K_l as the library applies it (Sec. 3.4; coarse levels = R K P of Sec. 5.1). */
 int igamg_host_level_matrix(const igamg_problem* prob, int level, double* K, size_t cap,
                             long long* n_out);
+/* K_l rebuilt through the row evaluation that the GPU kernels run (class stencils). */
+int igamg_host_operator_rows(const igamg_problem* prob, int level, double* K, size_t cap,
+                             long long* n_out);
 /* P_{l-1} (rows: level l, columns: level l-1), block diag(P^v, P^q, 1) of Sec. 5.1. */
 int igamg_host_prolongation(const igamg_problem* prob, int level, double* P, size_t cap,
                             long long* n_rows, long long* n_cols);

@@ -59,6 +59,7 @@ SIGNATURES = {
     "igamg_curl": (_I, [_P, _P, _P]),
     "igamg_residual_static": (_I, [ctypes.POINTER(Problem), _I, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "igamg_host_level_matrix": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL)]),
+    "igamg_host_operator_rows": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL)]),
     "igamg_host_prolongation": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL),
                                      ctypes.POINTER(_LL)]),
     "igamg_host_patches": (_I, [ctypes.POINTER(Problem), _I, _P, _P, _SZ, _SZ, ctypes.POINTER(_I),

@@ -1,12 +1,15 @@
-// CUDA kernels and the C ABI of the geometric multigrid V-cycle (arXiv 1705.09282,
+// C ABI and launch orchestration of the geometric multigrid V-cycle (arXiv 1705.09282,
 // Algorithm 1 with the overlapping Schwarz smoothers of Sec. 5.2), for sm_103a.
 //
-// Every level's operator is applied matrix-free from its 1D banded factors (Kronecker
-// form, see setup.cpp).  The multiplicative smoother runs one launch per patch colour:
+// Every level's operator is applied matrix-free from class stencils built from its 1D
+// factors (setup.cpp).  The multiplicative smoother runs one launch per patch colour:
 // inside a colour the patches share no degree of freedom and are not coupled by K, so
 // solving them concurrently is the same as solving them one after another (eq. MSM).
+// A V-cycle (and, in the FP32 mode, one step of FP64 iterative refinement around an
+// FP32 V-cycle) is captured once into a CUDA graph and replayed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -14,331 +17,27 @@
 #include <vector>
 
 #include "igamg_internal.h"
+#include "kernels.cuh"
 
 using namespace igamg;
+using namespace igamg::dev;
 
 namespace {
 
 constexpr int kBlock = 256;
-
-template <typename T>
-struct LevelDev {
-  int n, nxu, nyu, npd, nint;   // nint = n+p-2 (interior degree-p count)
-  long long n_ux, n_uy, n_p, n_total;
-  const T *X1, *X2, *Mq, *Y2, *D, *mq;
-};
-
-struct XferDev {
-  int nf, nc;
-  const int *c0, *f0;
-  const double *pv, *rv;
-};
-
-// (K U)_g for one row g (not the lambda row), from the 1D bands; Sec. 3.4 block structure.
-template <int P, typename T>
-__device__ __forceinline__ T row_KU(const LevelDev<T>& L, const T* __restrict__ U, long long g) {
-  constexpr int Q = P - 1, W = 2 * P + 1;
-  const T* ux = U;
-  const T* uy = U + L.n_ux;
-  const T* pr = U + L.n_ux + L.n_uy;
-  T acc = 0;
-  if (g < L.n_ux) {
-    int iy = (int)(g / L.nxu), ix = (int)(g % L.nxu) + 1;
-    const T* x1 = L.X1 + (size_t)ix * W; const T* x2 = L.X2 + (size_t)ix * W;
-    const T* mq = L.Mq + (size_t)iy * W; const T* y2 = L.Y2 + (size_t)iy * W;
-#pragma unroll
-    for (int dx = -P; dx <= P; ++dx) {
-      int jx = ix + dx;
-      if (jx < 1 || jx > L.nint) continue;
-      T a1 = x1[dx + P], a2 = x2[dx + P];
-#pragma unroll
-      for (int dy = -Q; dy <= Q; ++dy) {
-        int jy = iy + dy;
-        if (jy < 0 || jy >= L.nyu) continue;
-        acc += (a1 * mq[dy + P] + a2 * y2[dy + P]) * ux[(size_t)jy * L.nxu + jx - 1];
-      }
-    }
-    const T* d = L.D + (size_t)ix * W;
-#pragma unroll
-    for (int dx = -P; dx <= P - 1; ++dx) {
-      int kx = ix + dx;
-      if (kx < 0 || kx >= L.npd) continue;
-      T dd = d[dx + P];
-#pragma unroll
-      for (int dy = -Q; dy <= Q; ++dy) {
-        int ky = iy + dy;
-        if (ky < 0 || ky >= L.npd) continue;
-        acc -= dd * mq[dy + P] * pr[(size_t)ky * L.npd + kx];
-      }
-    }
-  } else if (g < L.n_ux + L.n_uy) {
-    long long r = g - L.n_ux;
-    int iy = (int)(r / L.npd) + 1, ix = (int)(r % L.npd);
-    const T* mqx = L.Mq + (size_t)ix * W; const T* y2x = L.Y2 + (size_t)ix * W;
-    const T* x1 = L.X1 + (size_t)iy * W; const T* x2 = L.X2 + (size_t)iy * W;
-#pragma unroll
-    for (int dx = -Q; dx <= Q; ++dx) {
-      int jx = ix + dx;
-      if (jx < 0 || jx >= L.npd) continue;
-      T a1 = mqx[dx + P], a2 = y2x[dx + P];
-#pragma unroll
-      for (int dy = -P; dy <= P; ++dy) {
-        int jy = iy + dy;
-        if (jy < 1 || jy > L.nint) continue;
-        acc += (a1 * x1[dy + P] + a2 * x2[dy + P]) * uy[(size_t)(jy - 1) * L.npd + jx];
-      }
-    }
-    const T* d = L.D + (size_t)iy * W;
-#pragma unroll
-    for (int dx = -Q; dx <= Q; ++dx) {
-      int kx = ix + dx;
-      if (kx < 0 || kx >= L.npd) continue;
-      T m = mqx[dx + P];
-#pragma unroll
-      for (int dy = -P; dy <= P - 1; ++dy) {
-        int ky = iy + dy;
-        if (ky < 0 || ky >= L.npd) continue;
-        acc -= m * d[dy + P] * pr[(size_t)ky * L.npd + kx];
-      }
-    }
-  } else {
-    long long r = g - L.n_ux - L.n_uy;
-    int ky = (int)(r / L.npd), kx = (int)(r % L.npd);
-    const T* mqx = L.Mq + (size_t)kx * W; const T* mqy = L.Mq + (size_t)ky * W;
-    // B_x^T u_x : D(ix,kx) Mq(iy,ky), ix in [kx-Q, kx+P]
-#pragma unroll
-    for (int s = -Q; s <= P; ++s) {
-      int ix = kx + s;
-      if (ix < 1 || ix > L.nint) continue;
-      T dd = L.D[(size_t)ix * W + (kx - ix + P)];
-#pragma unroll
-      for (int dy = -Q; dy <= Q; ++dy) {
-        int iy = ky + dy;
-        if (iy < 0 || iy >= L.nyu) continue;
-        acc += dd * mqy[dy + P] * ux[(size_t)iy * L.nxu + ix - 1];
-      }
-    }
-    // B_y^T u_y : Mq(ix,kx) D(iy,ky), iy in [ky-Q, ky+P]
-#pragma unroll
-    for (int s = -Q; s <= P; ++s) {
-      int iy = ky + s;
-      if (iy < 1 || iy > L.nint) continue;
-      T dd = L.D[(size_t)iy * W + (ky - iy + P)];
-#pragma unroll
-      for (int dx = -Q; dx <= Q; ++dx) {
-        int ix = kx + dx;
-        if (ix < 0 || ix >= L.npd) continue;
-        acc += mqx[dx + P] * dd * uy[(size_t)(iy - 1) * L.npd + ix];
-      }
-    }
-    acc += L.mq[kx] * L.mq[ky] * U[L.n_total - 1];
-  }
-  return acc;
-}
-
-template <typename T>
-__device__ __forceinline__ T block_sum(T v, T* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  T s = 0;
-  if (w == 0) {
-    s = (l < (int)(blockDim.x >> 5)) ? sh[l] : T(0);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  }
-  return s;  // valid in thread 0
-}
-
-// R = F - K U for every row but lambda; per-block partial sums of R^2 and of m.p.
-template <int P, typename T>
-__global__ void k_residual(LevelDev<T> L, const T* __restrict__ U, const T* __restrict__ F,
-                           T* __restrict__ R, double* __restrict__ part) {
-  __shared__ double sh[32];
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double r2 = 0.0, mp = 0.0;
-  if (g < L.n_total - 1) {
-    T r = F[g] - row_KU<P>(L, U, g);
-    R[g] = r;
-    r2 = (double)r * (double)r;
-    long long off = g - L.n_ux - L.n_uy;
-    if (off >= 0) {
-      int ky = (int)(off / L.npd), kx = (int)(off % L.npd);
-      mp = (double)L.mq[kx] * (double)L.mq[ky] * (double)U[g];
-    }
-  }
-  double s1 = block_sum(r2, sh);
-  double s2 = block_sum(mp, sh);
-  if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1; part[2 * blockIdx.x + 1] = s2; }
-}
-
-// lambda row and ||R||^2 from the partials (one block, fixed order).
-template <typename T>
-__global__ void k_residual_finish(long long n_total, const T* __restrict__ F, T* __restrict__ R,
-                                  const double* __restrict__ part, int nparts, double* __restrict__ norm2) {
-  __shared__ double sh[32];
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) { a += part[2 * i]; b += part[2 * i + 1]; }
-  double s1 = block_sum(a, sh);
-  double s2 = block_sum(b, sh);
-  if (threadIdx.x == 0) {
-    T rl = F[n_total - 1] - (T)s2;
-    R[n_total - 1] = rl;
-    if (norm2) *norm2 = s1 + (double)rl * (double)rl;
-  }
-}
-
-// One colour of the multiplicative Schwarz sweep: one warp per patch.  Lanes gather the
-// local residual rows, then apply the bordered local inverse and update U in place.
-template <int P, typename T>
-__global__ void k_mult_colour(LevelDev<T> L, T* __restrict__ U, const T* __restrict__ F,
-                              const int* __restrict__ dofs, const int* __restrict__ cls,
-                              const T* __restrict__ cinv, const int* __restrict__ nloc,
-                              int maxl, int first, int count) {
-  extern __shared__ unsigned char smem_raw[];
-  T* sh = reinterpret_cast<T*>(smem_raw);
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (warp >= count) return;
-  int patch = first + warp;
-  int c = cls[patch], nl = nloc[c];
-  T* r = sh + (threadIdx.x >> 5) * maxl;
-  const int* pd = dofs + (size_t)patch * maxl;
-  for (int k = lane; k < nl; k += 32) { int g = pd[k]; r[k] = F[g] - row_KU<P>(L, U, g); }
-  __syncwarp();
-  const T* A = cinv + (size_t)c * maxl * maxl;
-  for (int k = lane; k < nl; k += 32) {
-    T acc = 0;
-    const T* a = A + (size_t)k * maxl;
-    for (int s = 0; s < nl; ++s) acc += a[s] * r[s];
-    U[pd[k]] += acc;
-  }
-}
-
-// Additive sweep, part 1: local corrections from a common residual, kept per patch.
-template <typename T>
-__global__ void k_add_local(const T* __restrict__ R, const int* __restrict__ dofs, const int* __restrict__ cls,
-                            const T* __restrict__ cinv, const int* __restrict__ nloc, int maxl,
-                            int count, T* __restrict__ delta) {
-  extern __shared__ unsigned char smem_raw[];
-  T* sh = reinterpret_cast<T*>(smem_raw);
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (warp >= count) return;
-  int c = cls[warp], nl = nloc[c];
-  T* r = sh + (threadIdx.x >> 5) * maxl;
-  const int* pd = dofs + (size_t)warp * maxl;
-  for (int k = lane; k < nl; k += 32) r[k] = R[pd[k]];
-  __syncwarp();
-  const T* A = cinv + (size_t)c * maxl * maxl;
-  for (int k = lane; k < nl; k += 32) {
-    T acc = 0;
-    for (int s = 0; s < nl; ++s) acc += A[(size_t)k * maxl + s] * r[s];
-    delta[(size_t)warp * maxl + k] = acc;
-  }
-}
-
-// Additive sweep, part 2: U_g += eta * sum of the corrections of the patches holding g.
-template <typename T>
-__global__ void k_add_gather(long long n, T* __restrict__ U, const T* __restrict__ delta,
-                             const int* __restrict__ off, const int* __restrict__ idx, T eta) {
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  T s = 0;
-  for (int j = off[g]; j < off[g + 1]; ++j) s += delta[idx[j]];
-  if (off[g + 1] > off[g]) U[g] += eta * s;
-}
-
-// g_c = P^T r_f on all blocks (lambda copied).  fine/coarse layouts from the LevelDevs.
-template <typename T>
-__global__ void k_restrict(LevelDev<T> Lf, LevelDev<T> Lc, XferDev tp, XferDev tq,
-                           const T* __restrict__ rf, T* __restrict__ gc) {
-  constexpr int WR = Transfer1D::WR;
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= Lc.n_total) return;
-  if (g == Lc.n_total - 1) { gc[g] = rf[Lf.n_total - 1]; return; }
-  const XferDev *TX, *TY;
-  int cx, cy, fnx;
-  const T* src;
-  if (g < Lc.n_ux) { cy = (int)(g / Lc.nxu); cx = (int)(g % Lc.nxu); TX = &tp; TY = &tq; src = rf; fnx = Lf.nxu; }
-  else if (g < Lc.n_ux + Lc.n_uy) { long long r = g - Lc.n_ux; cy = (int)(r / Lc.npd); cx = (int)(r % Lc.npd); TX = &tq; TY = &tp; src = rf + Lf.n_ux; fnx = Lf.npd; }
-  else { long long r = g - Lc.n_ux - Lc.n_uy; cy = (int)(r / Lc.npd); cx = (int)(r % Lc.npd); TX = &tq; TY = &tq; src = rf + Lf.n_ux + Lf.n_uy; fnx = Lf.npd; }
-  int fx0 = TX->f0[cx], fy0 = TY->f0[cy];
-  T acc = 0;
-#pragma unroll
-  for (int ky = 0; ky < WR; ++ky) {
-    int fy = fy0 + ky;
-    T wy = (T)TY->rv[(size_t)cy * WR + ky];
-    if (fy >= TY->nf || wy == T(0)) continue;
-#pragma unroll
-    for (int kx = 0; kx < WR; ++kx) {
-      int fx = fx0 + kx;
-      T wx = (T)TX->rv[(size_t)cx * WR + kx];
-      if (fx >= TX->nf || wx == T(0)) continue;
-      acc += wy * wx * src[(size_t)fy * fnx + fx];
-    }
-  }
-  gc[g] = acc;
-}
-
-// u_f += P u_c (lambda added).
-template <typename T>
-__global__ void k_prolong_add(LevelDev<T> Lf, LevelDev<T> Lc, XferDev tp, XferDev tq,
-                              const T* __restrict__ uc, T* __restrict__ uf) {
-  constexpr int WP = Transfer1D::WP;
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= Lf.n_total) return;
-  if (g == Lf.n_total - 1) { uf[g] += uc[Lc.n_total - 1]; return; }
-  const XferDev *TX, *TY;
-  int fx, fy, cnx;
-  const T* src;
-  if (g < Lf.n_ux) { fy = (int)(g / Lf.nxu); fx = (int)(g % Lf.nxu); TX = &tp; TY = &tq; src = uc; cnx = Lc.nxu; }
-  else if (g < Lf.n_ux + Lf.n_uy) { long long r = g - Lf.n_ux; fy = (int)(r / Lf.npd); fx = (int)(r % Lf.npd); TX = &tq; TY = &tp; src = uc + Lc.n_ux; cnx = Lc.npd; }
-  else { long long r = g - Lf.n_ux - Lf.n_uy; fy = (int)(r / Lf.npd); fx = (int)(r % Lf.npd); TX = &tq; TY = &tq; src = uc + Lc.n_ux + Lc.n_uy; cnx = Lc.npd; }
-  int cx0 = TX->c0[fx], cy0 = TY->c0[fy];
-  T acc = 0;
-#pragma unroll
-  for (int ky = 0; ky < WP; ++ky) {
-    int cy = cy0 + ky;
-    T wy = (T)TY->pv[(size_t)fy * WP + ky];
-    if (cy >= TY->nc || wy == T(0)) continue;
-#pragma unroll
-    for (int kx = 0; kx < WP; ++kx) {
-      int cx = cx0 + kx;
-      T wx = (T)TX->pv[(size_t)fx * WP + kx];
-      if (cx >= TX->nc || wx == T(0)) continue;
-      acc += wy * wx * src[(size_t)cy * cnx + cx];
-    }
-  }
-  uf[g] += acc;
-}
-
-// U = K_0^{-1} G (dense inverse, one block).
-template <typename T>
-__global__ void k_coarse(int n, const T* __restrict__ Kinv, const T* __restrict__ G, T* __restrict__ U) {
-  extern __shared__ unsigned char smem_raw[];
-  T* g = reinterpret_cast<T*>(smem_raw);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) g[i] = G[i];
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    T acc = 0;
-    for (int j = 0; j < n; ++j) acc += Kinv[(size_t)i * n + j] * g[j];
-    U[i] = acc;
-  }
-}
+inline unsigned nblk(long long n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
 
 // max |div u| over the (n+q)^2 pressure-space coefficients (order-free max via bits).
-__global__ void k_div_inf(LevelDev<double> L, const double* __restrict__ dcoef, const double* __restrict__ U,
+__global__ void k_div_inf(LevelTab<double> L, const double* __restrict__ dcoef, const double* __restrict__ U,
                           unsigned long long* __restrict__ out) {
-  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
   double v = 0.0;
   if (k < L.n_p) {
-    int ky = (int)(k / L.npd), kx = (int)(k % L.npd);
+    int ky = k / L.npd, kx = k - ky * L.npd;
     const double* ux = U;
     const double* uy = U + L.n_ux;
-    auto UX = [&](int ix, int iy) { return (ix < 1 || ix > L.nint) ? 0.0 : ux[(size_t)iy * L.nxu + ix - 1]; };
-    auto UY = [&](int ix, int iy) { return (iy < 1 || iy > L.nint) ? 0.0 : uy[(size_t)(iy - 1) * L.npd + ix]; };
+    auto UX = [&](int ix, int iy) { return (ix < 1 || ix > L.nint) ? 0.0 : ux[iy * L.nxu + ix - 1]; };
+    auto UY = [&](int ix, int iy) { return (iy < 1 || iy > L.nint) ? 0.0 : uy[(iy - 1) * L.npd + ix]; };
     double c = dcoef[kx] * (UX(kx + 1, ky) - UX(kx, ky)) + dcoef[ky] * (UY(kx, ky + 1) - UY(kx, ky));
     v = fabs(c);
   }
@@ -347,35 +46,35 @@ __global__ void k_div_inf(LevelDev<double> L, const double* __restrict__ dcoef, 
 }
 
 // velocity = curl psi, psi on the (n+p-2)^2 interior streamfunction coefficients.
-__global__ void k_curl(LevelDev<double> L, const double* __restrict__ dcoef, const double* __restrict__ psi,
+__global__ void k_curl(LevelTab<double> L, const double* __restrict__ dcoef, const double* __restrict__ psi,
                        double* __restrict__ U) {
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= L.n_ux + L.n_uy) return;
   int ni = L.nint;
-  auto PS = [&](int ix, int iy) { return (ix < 1 || ix > ni || iy < 1 || iy > ni) ? 0.0 : psi[(size_t)(iy - 1) * ni + ix - 1]; };
+  auto PS = [&](int ix, int iy) { return (ix < 1 || ix > ni || iy < 1 || iy > ni) ? 0.0 : psi[(iy - 1) * ni + ix - 1]; };
   if (g < L.n_ux) {
-    int ky = (int)(g / L.nxu), ix = (int)(g % L.nxu) + 1;
+    int ky = g / L.nxu, ix = g - ky * L.nxu + 1;
     U[g] = dcoef[ky] * (PS(ix, ky + 1) - PS(ix, ky));
   } else {
-    long long r = g - L.n_ux;
-    int iy = (int)(r / L.npd) + 1, kx = (int)(r % L.npd);
+    int r = g - L.n_ux;
+    int iy = r / L.npd + 1, kx = r - (iy - 1) * L.npd;
     U[g] = -dcoef[kx] * (PS(kx + 1, iy) - PS(kx, iy));
   }
 }
 
 // F = (int v.f, 0, 0) on the finest level; tables hold weight * basis value per local element.
 template <int P>
-__global__ void k_load(LevelDev<double> L, const double* __restrict__ lvp, const double* __restrict__ lvq,
+__global__ void k_load(LevelTab<double> L, const double* __restrict__ lvp, const double* __restrict__ lvq,
                        const double* __restrict__ f, double* __restrict__ F) {
   constexpr int Q = P - 1, G = P + 2;
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= L.n_total) return;
   if (g >= L.n_ux + L.n_uy) { F[g] = 0.0; return; }
   int n = L.n, nG = n * G;
   int ix, iy, dxg, dyg;
   const double *tx, *ty, *fc;
-  if (g < L.n_ux) { iy = (int)(g / L.nxu); ix = (int)(g % L.nxu) + 1; dxg = P; dyg = Q; tx = lvp; ty = lvq; fc = f; }
-  else { long long r = g - L.n_ux; iy = (int)(r / L.npd) + 1; ix = (int)(r % L.npd); dxg = Q; dyg = P; tx = lvq; ty = lvp; fc = f + (size_t)nG * nG; }
+  if (g < L.n_ux) { iy = g / L.nxu; ix = g - iy * L.nxu + 1; dxg = P; dyg = Q; tx = lvp; ty = lvq; fc = f; }
+  else { int r = g - L.n_ux; iy = r / L.npd + 1; ix = r - (iy - 1) * L.npd; dxg = Q; dyg = P; tx = lvq; ty = lvp; fc = f + (size_t)nG * nG; }
   double acc = 0.0;
   for (int ky = 0; ky <= dyg; ++ky) {
     int ey = iy - dyg + ky;
@@ -396,49 +95,51 @@ __global__ void k_load(LevelDev<double> L, const double* __restrict__ lvp, const
   F[g] = acc;
 }
 
-inline unsigned nblk(long long n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
+template <typename T>
+struct TypedLevel {
+  LevelTab<T> L{};
+  T* cinv = nullptr;
+  Xfer<T> tp{}, tq{};            // transfer from level l-1 into level l (l >= 1)
+  T *U = nullptr, *F = nullptr, *R = nullptr;
+};
+
+template <typename T>
+struct Typed {
+  std::vector<TypedLevel<T>> lev;
+  T* coarse_inv = nullptr;
+  T* delta = nullptr;
+};
+
+struct LevelCommon {
+  igamg_sizes sz{};
+  int n_patches = 0, maxl = 0, n_colours = 0;
+  std::vector<int> colour_off, n8;
+  int *dofs = nullptr, *cls = nullptr, *nloc = nullptr, *d2p_off = nullptr, *d2p_idx = nullptr;
+  double* dcoef = nullptr;      // derivative coefficients (n+p-1), device
+  double* inv_dcoef = nullptr;  // their reciprocals
+};
 
 }  // namespace
-
-// ---------------------------------------------------------------------------------------
-// Handle
-// ---------------------------------------------------------------------------------------
-struct DevLevel {
-  igamg_sizes sz{};
-  LevelDev<double> L{};
-  double* bands = nullptr;      // X1 X2 Mq Y2 D mq dcoef
-  const double* dcoef = nullptr;
-  // patches
-  int n_patches = 0, maxl = 0, n_colours = 0;
-  std::vector<int> colour_off;
-  int *dofs = nullptr, *cls = nullptr, *nloc = nullptr, *d2p_off = nullptr, *d2p_idx = nullptr;
-  double* cinv = nullptr;
-  // transfer from level-1 (valid for level >= 1)
-  XferDev tp{}, tq{};
-  void* xfer_mem = nullptr;
-  // workspaces
-  double *U = nullptr, *F = nullptr, *R = nullptr;
-};
 
 struct igamg_handle {
   igamg_problem prob{};
   HierarchyHost host;
-  cudaStream_t stream = nullptr;
-  std::vector<DevLevel> lev;
-  double* coarse_inv = nullptr;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  std::vector<LevelCommon> lc;
+  Typed<double> d;
+  Typed<float> f;
   int ndof0 = 0;
   double* part = nullptr;      // residual partials (2 per block of the finest level)
   double* norm2 = nullptr;     // device scalar
   unsigned long long* divmax = nullptr;
-  double* delta = nullptr;     // additive corrections, n_patches * maxl (max over levels)
-  double* lv_p = nullptr; double* lv_q = nullptr;
+  double *lv_p = nullptr, *lv_q = nullptr;
   double* h_pinned = nullptr;  // 2 doubles
-  // host-buffer solve workspaces
-  double *f_dev = nullptr, *Fh = nullptr, *Uh = nullptr;
-  // captured V-cycle (+ residual norm) graph, keyed by the fine U/F pointers
-  cudaGraphExec_t graph = nullptr;
-  const void* gU = nullptr; const void* gF = nullptr;
-  cudaStream_t cap_stream = nullptr;
+  double *f_dev = nullptr, *Fh = nullptr, *Uh = nullptr;   // host-buffer solve workspaces
+  double* psi = nullptr;       // FP32 mode: streamfunction of the correction (fine interior)
+  // captured graphs: [0] solve step, [1] public V-cycle (starts with the residual in FP32 mode)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  const void* gU[2] = {nullptr, nullptr};
+  const void* gF[2] = {nullptr, nullptr};
   std::vector<void*> allocs;
 };
 
@@ -455,11 +156,12 @@ int dmalloc(igamg_handle* h, void** p, size_t bytes) {
   return IGAMG_OK;
 }
 
-template <typename V>
-int upload(igamg_handle* h, V** dst, const std::vector<V>& src) {
-  int rc = dmalloc(h, (void**)dst, src.size() * sizeof(V));
+template <typename V, typename S>
+int upload_as(igamg_handle* h, V** dst, const std::vector<S>& src) {
+  std::vector<V> tmp(src.begin(), src.end());
+  int rc = dmalloc(h, (void**)dst, tmp.size() * sizeof(V));
   if (rc) return rc;
-  CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(V), cudaMemcpyHostToDevice));
   return IGAMG_OK;
 }
 
@@ -469,98 +171,143 @@ int launch_check() {
   return IGAMG_OK;
 }
 
+template <typename T> Typed<T>& typed(igamg_handle* h);
+template <> Typed<double>& typed<double>(igamg_handle* h) { return h->d; }
+template <> Typed<float>& typed<float>(igamg_handle* h) { return h->f; }
+
 // ---- per-step launchers (enqueue on stream s) ------------------------------------------
-int do_residual(igamg_handle* h, int l, const double* U, const double* F, double* R, double* norm2, cudaStream_t s) {
-  auto& lv = h->lev[l];
-  long long n = lv.sz.n_total - 1;
-  unsigned nb = nblk(n);
-  if (h->prob.p == 2) k_residual<2, double><<<nb, kBlock, 0, s>>>(lv.L, U, F, R, h->part);
-  else k_residual<3, double><<<nb, kBlock, 0, s>>>(lv.L, U, F, R, h->part);
-  k_residual_finish<double><<<1, 1024, 0, s>>>(lv.sz.n_total, F, R, h->part, (int)nb, norm2);
+template <typename T>
+int do_residual(igamg_handle* h, int l, const T* U, const T* F, T* R, double* norm2, cudaStream_t s) {
+  auto& L = typed<T>(h).lev[l].L;
+  unsigned nb = nblk(L.n_total - 1);
+  if (h->prob.p == 2) k_residual<2, T><<<nb, kBlock, 0, s>>>(L, U, F, R, h->part);
+  else k_residual<3, T><<<nb, kBlock, 0, s>>>(L, U, F, R, h->part);
+  k_residual_finish<T><<<1, 1024, 0, s>>>(L.n_total, F, R, h->part, (int)nb, norm2);
   return launch_check();
 }
 
-int do_smooth(igamg_handle* h, int l, double* U, const double* F, cudaStream_t s) {
-  auto& lv = h->lev[l];
-  const int warps_per_block = kBlock / 32;
-  size_t shm = (size_t)warps_per_block * lv.maxl * sizeof(double);
+template <typename T>
+int do_smooth(igamg_handle* h, int l, T* U, const T* F, cudaStream_t s) {
+  auto& lc = h->lc[l];
+  auto& tl = typed<T>(h).lev[l];
+  size_t shm = (size_t)(kBlock / 32) * lc.maxl * sizeof(T);
   if (h->prob.smoother == IGAMG_MULT) {
-    for (int c = 0; c < lv.n_colours; ++c) {
-      int first = lv.colour_off[c], count = lv.colour_off[c + 1] - first;
+    for (int c = 0; c < lc.n_colours; ++c) {
+      int first = lc.colour_off[c], count = lc.colour_off[c + 1] - first;
       if (count == 0) continue;
-      unsigned nb = (unsigned)((count + warps_per_block - 1) / warps_per_block);
+      int n8 = lc.n8[c], ngen = count - n8;
+      int nb8 = (n8 + 31) / 32, nbg = (ngen + 7) / 8;
+      unsigned nb = (unsigned)(nb8 + nbg);
       if (h->prob.p == 2)
-        k_mult_colour<2, double><<<nb, kBlock, shm, s>>>(lv.L, U, F, lv.dofs, lv.cls, lv.cinv, lv.nloc, lv.maxl, first, count);
+        k_mult_colour<2, T><<<nb, kBlock, shm, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, lc.nloc, lc.maxl, first, n8, ngen, nb8);
       else
-        k_mult_colour<3, double><<<nb, kBlock, shm, s>>>(lv.L, U, F, lv.dofs, lv.cls, lv.cinv, lv.nloc, lv.maxl, first, count);
+        k_mult_colour<3, T><<<nb, kBlock, shm, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, lc.nloc, lc.maxl, first, n8, ngen, nb8);
     }
   } else {
-    int rc = do_residual(h, l, U, F, lv.R, nullptr, s);
+    int rc = do_residual<T>(h, l, U, F, tl.R, nullptr, s);
     if (rc) return rc;
-    unsigned nb = (unsigned)((lv.n_patches + warps_per_block - 1) / warps_per_block);
-    k_add_local<double><<<nb, kBlock, shm, s>>>(lv.R, lv.dofs, lv.cls, lv.cinv, lv.nloc, lv.maxl, lv.n_patches, h->delta);
-    double eta = h->prob.eta > 0 ? h->prob.eta : 0.5;
-    k_add_gather<double><<<nblk(lv.sz.n_total), kBlock, 0, s>>>(lv.sz.n_total, U, h->delta, lv.d2p_off, lv.d2p_idx, eta);
+    unsigned nb = (unsigned)((lc.n_patches + kBlock / 32 - 1) / (kBlock / 32));
+    if (h->prob.p == 2)
+      k_add_local<2, T><<<nb, kBlock, shm, s>>>(tl.R, lc.dofs, lc.cls, tl.cinv, lc.nloc, lc.maxl, lc.n_patches, typed<T>(h).delta);
+    else
+      k_add_local<3, T><<<nb, kBlock, shm, s>>>(tl.R, lc.dofs, lc.cls, tl.cinv, lc.nloc, lc.maxl, lc.n_patches, typed<T>(h).delta);
+    T eta = (T)(h->prob.eta > 0 ? h->prob.eta : 0.5);
+    k_add_gather<T><<<nblk(lc.sz.n_total), kBlock, 0, s>>>((int)lc.sz.n_total, U, typed<T>(h).delta, lc.d2p_off, lc.d2p_idx, eta);
   }
   return launch_check();
 }
 
-int do_restrict(igamg_handle* h, int l, const double* rf, double* gc, cudaStream_t s) {
-  auto& f = h->lev[l]; auto& c = h->lev[l - 1];
-  k_restrict<double><<<nblk(c.sz.n_total), kBlock, 0, s>>>(f.L, c.L, f.tp, f.tq, rf, gc);
+template <typename T>
+int do_restrict(igamg_handle* h, int l, const T* rf, T* gc, cudaStream_t s) {
+  auto& f = typed<T>(h).lev[l];
+  auto& c = typed<T>(h).lev[l - 1];
+  k_restrict<T><<<nblk(c.L.n_total), kBlock, 0, s>>>(f.L, c.L, f.tp, f.tq, rf, gc);
   return launch_check();
 }
 
-int do_prolong(igamg_handle* h, int l, const double* uc, double* uf, cudaStream_t s) {
-  auto& f = h->lev[l]; auto& c = h->lev[l - 1];
-  k_prolong_add<double><<<nblk(f.sz.n_total), kBlock, 0, s>>>(f.L, c.L, f.tp, f.tq, uc, uf);
+template <typename T>
+int do_prolong(igamg_handle* h, int l, const T* uc, T* uf, cudaStream_t s) {
+  auto& f = typed<T>(h).lev[l];
+  auto& c = typed<T>(h).lev[l - 1];
+  k_prolong_add<T><<<nblk(f.L.n_total), kBlock, 0, s>>>(f.L, c.L, f.tp, f.tq, uc, uf);
   return launch_check();
 }
 
-int do_coarse(igamg_handle* h, const double* G, double* U, cudaStream_t s) {
-  k_coarse<double><<<1, 1024, h->ndof0 * sizeof(double), s>>>(h->ndof0, h->coarse_inv, G, U);
+template <typename T>
+int do_coarse(igamg_handle* h, const T* G, T* U, cudaStream_t s) {
+  k_coarse<T><<<1, 1024, h->ndof0 * sizeof(T), s>>>(h->ndof0, typed<T>(h).coarse_inv, G, U);
   return launch_check();
 }
 
 // Algorithm 1 (MGV) from the finest level, unrolled into launches.
-int do_vcycle(igamg_handle* h, double* U, const double* F, cudaStream_t s) {
-  const int L = (int)h->lev.size();
-  if (L == 1) return do_coarse(h, F, U, s);
+template <typename T>
+int do_vcycle(igamg_handle* h, T* U, const T* F, cudaStream_t s) {
+  auto& ty = typed<T>(h);
+  const int L = (int)ty.lev.size();
+  if (L == 1) return do_coarse<T>(h, F, U, s);
   int rc;
   for (int l = L - 1; l >= 1; --l) {
-    double* Ul = (l == L - 1) ? U : h->lev[l].U;
-    const double* Fl = (l == L - 1) ? F : h->lev[l].F;
-    if (l < L - 1) CK(cudaMemsetAsync(Ul, 0, h->lev[l].sz.n_total * sizeof(double), s));
-    for (int k = 0; k < h->prob.nu1; ++k) if ((rc = do_smooth(h, l, Ul, Fl, s))) return rc;
-    if ((rc = do_residual(h, l, Ul, Fl, h->lev[l].R, nullptr, s))) return rc;
-    if ((rc = do_restrict(h, l, h->lev[l].R, h->lev[l - 1].F, s))) return rc;
+    T* Ul = (l == L - 1) ? U : ty.lev[l].U;
+    const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
+    if (l < L - 1) CK(cudaMemsetAsync(Ul, 0, ty.lev[l].L.n_total * sizeof(T), s));
+    for (int k = 0; k < h->prob.nu1; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+    if ((rc = do_residual<T>(h, l, Ul, Fl, ty.lev[l].R, nullptr, s))) return rc;
+    if ((rc = do_restrict<T>(h, l, ty.lev[l].R, ty.lev[l - 1].F, s))) return rc;
   }
-  if ((rc = do_coarse(h, h->lev[0].F, h->lev[0].U, s))) return rc;
+  if ((rc = do_coarse<T>(h, ty.lev[0].F, ty.lev[0].U, s))) return rc;
   for (int l = 1; l <= L - 1; ++l) {
-    double* Ul = (l == L - 1) ? U : h->lev[l].U;
-    const double* Fl = (l == L - 1) ? F : h->lev[l].F;
-    if ((rc = do_prolong(h, l, h->lev[l - 1].U, Ul, s))) return rc;
-    for (int k = 0; k < h->prob.nu2; ++k) if ((rc = do_smooth(h, l, Ul, Fl, s))) return rc;
+    T* Ul = (l == L - 1) ? U : ty.lev[l].U;
+    const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
+    if ((rc = do_prolong<T>(h, l, ty.lev[l - 1].U, Ul, s))) return rc;
+    for (int k = 0; k < h->prob.nu2; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
   }
   return IGAMG_OK;
 }
 
-// Graph = one V-cycle followed by the fine residual norm into h->norm2.
-int ensure_graph(igamg_handle* h, double* U, const double* F) {
-  if (h->graph && h->gU == U && h->gF == F) return IGAMG_OK;
-  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+// FP32 mode, one refinement step: given R64 = F - K U (FP64), an FP32 V-cycle on K e = R64,
+// then U += (curl psi(e), e_p, e_lambda) in FP64 and R64 = F - K U with its norm.
+int do_ir_step(igamg_handle* h, double* U, const double* F, cudaStream_t s) {
+  const int L = (int)h->d.lev.size();
+  auto& top32 = h->f.lev[L - 1];
+  double* R64 = h->d.lev[L - 1].R;
+  const auto& Ld = h->d.lev[L - 1].L;
+  k_to_float<<<nblk(Ld.n_total), kBlock, 0, s>>>(Ld.n_total, R64, top32.F);
+  CK(cudaMemsetAsync(top32.U, 0, Ld.n_total * sizeof(float), s));
+  int rc = do_vcycle<float>(h, top32.U, top32.F, s);
+  if (rc) return rc;
+  k_integrate_psi<<<nblk(Ld.nint, 128), 128, 0, s>>>(Ld.nint, Ld.nxu, h->lc[L - 1].inv_dcoef, top32.U, h->psi);
+  k_curl_update<<<nblk(Ld.n_total), kBlock, 0, s>>>(Ld, h->lc[L - 1].dcoef, h->psi, top32.U, U);
+  if ((rc = launch_check())) return rc;
+  return do_residual<double>(h, L - 1, U, F, R64, h->norm2, s);
+}
+
+// one solve step: FP64 mode -> V-cycle + residual norm; FP32 mode -> refinement step.
+int do_step(igamg_handle* h, double* U, const double* F, cudaStream_t s) {
+  const int L = (int)h->d.lev.size();
+  if (h->prob.precision == IGAMG_FP32_IR) return do_ir_step(h, U, F, s);
+  int rc = do_vcycle<double>(h, U, F, s);
+  if (rc) return rc;
+  return do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, h->norm2, s);
+}
+
+// kind 0: solve step; kind 1: public V-cycle (FP32 mode starts by forming R64)
+int ensure_graph(igamg_handle* h, int kind, double* U, const double* F) {
+  if (h->graph[kind] && h->gU[kind] == U && h->gF[kind] == F) return IGAMG_OK;
+  if (h->graph[kind]) { cudaGraphExecDestroy(h->graph[kind]); h->graph[kind] = nullptr; }
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int L = (int)h->lev.size();
-  int rc = do_vcycle(h, U, F, h->cap_stream);
-  if (!rc) rc = do_residual(h, L - 1, U, F, h->lev[L - 1].R, h->norm2, h->cap_stream);
+  int L = (int)h->d.lev.size();
+  int rc = IGAMG_OK;
+  if (kind == 1 && h->prob.precision == IGAMG_FP32_IR)
+    rc = do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, nullptr, h->cap_stream);
+  if (!rc) rc = do_step(h, U, F, h->cap_stream);
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
   if (rc) { if (e == cudaSuccess) cudaGraphDestroy(g); return rc; }
   CK(e);
-  cudaError_t ei = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaError_t ei = cudaGraphInstantiate(&h->graph[kind], g, 0);
   cudaGraphDestroy(g);
   CK(ei);
-  h->gU = U; h->gF = F;
+  h->gU[kind] = U; h->gF[kind] = F;
   return IGAMG_OK;
 }
 
@@ -571,20 +318,33 @@ int read_norm(igamg_handle* h, double* out) {
   return IGAMG_OK;
 }
 
+int div_inf_impl(igamg_handle* h, const double* U, double* out) {
+  const int L = (int)h->d.lev.size();
+  auto& Lt = h->d.lev[L - 1].L;
+  CK(cudaMemsetAsync(h->divmax, 0, sizeof(unsigned long long), h->stream));
+  k_div_inf<<<nblk(Lt.n_p), kBlock, 0, h->stream>>>(Lt, h->lc[L - 1].dcoef, U, h->divmax);
+  int rc = launch_check();
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h->h_pinned, h->divmax, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *out = h->h_pinned[0];
+  return IGAMG_OK;
+}
+
 int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max_cycles, igamg_report* rep) {
-  int L = (int)h->lev.size();
-  int rc = do_residual(h, L - 1, U, F, h->lev[L - 1].R, h->norm2, h->stream);
+  int L = (int)h->d.lev.size();
+  int rc = do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, h->norm2, h->stream);
   if (rc) return rc;
   double r0;
   if ((rc = read_norm(h, &r0))) return rc;
   if (!std::isfinite(r0)) return IGAMG_ENONFINITE;
-  if ((rc = ensure_graph(h, U, F))) return rc;
+  if ((rc = ensure_graph(h, 0, U, F))) return rc;
   int k = 0;
   double rk = r0;
   int status = IGAMG_NOT_CONVERGED;
   if (r0 == 0.0) status = IGAMG_OK;
   while (status == IGAMG_NOT_CONVERGED && k < max_cycles) {
-    CK(cudaGraphLaunch(h->graph, h->stream));
+    CK(cudaGraphLaunch(h->graph[0], h->stream));
     ++k;
     if ((rc = read_norm(h, &rk))) return rc;
     if (!std::isfinite(rk)) { status = IGAMG_ENONFINITE; break; }
@@ -594,28 +354,68 @@ int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max
   if (rep) {
     rep->cycles = k; rep->res0 = r0; rep->rel_residual = r0 > 0 ? rk / r0 : 0.0;
     double dv = 0.0;
-    int rc2 = igamg_div_inf(h, U, &dv);
-    if (rc2) return rc2;
+    if ((rc = div_inf_impl(h, U, &dv))) return rc;
     rep->div_inf = dv;
   }
   return status;
 }
 
-LevelDev<double> make_leveldev(const LevelHost& lh, double* bands) {
-  const auto& f = lh.f;
-  int n = f.n, p = f.p, q = f.q;
-  size_t W = 2 * p + 1;
-  LevelDev<double> L{};
-  L.n = n; L.nxu = n + p - 2; L.nyu = n + q; L.npd = n + q; L.nint = n + p - 2;
-  L.n_ux = lh.sz.n_ux; L.n_uy = lh.sz.n_uy; L.n_p = lh.sz.n_p; L.n_total = lh.sz.n_total;
-  double* c = bands;
-  L.X1 = c; c += (n + p) * W;
-  L.X2 = c; c += (n + p) * W;
-  L.Mq = c; c += (n + q) * W;
-  L.Y2 = c; c += (n + q) * W;
-  L.D = c; c += (n + p) * W;
-  L.mq = c; c += (n + q);
+template <typename T>
+LevelTab<T> make_tab(const igamg_sizes& sz, int p, const T* sx, const T* sy, const T* sp) {
+  LevelTab<T> L{};
+  int n = sz.n;
+  L.n = n; L.nxu = n + p - 2; L.npd = n + p - 1; L.nint = n + p - 2; L.lastp = n + p - 1; L.lastq = n + p - 2;
+  L.n_ux = (int)sz.n_ux; L.n_uy = (int)sz.n_uy; L.n_p = (int)sz.n_p; L.n_total = (int)sz.n_total;
+  L.sx = sx; L.sy = sy; L.sp = sp;
   return L;
+}
+
+// Upload the typed (double or float) copy of every level's tables and workspaces.
+template <typename T>
+int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
+  const int L = h->prob.n_levels, p = h->prob.p;
+  ty.lev.resize(L);
+  int rc;
+  for (int l = 0; l < L; ++l) {
+    auto& lh = h->host.lev[l];
+    auto& tl = ty.lev[l];
+    T *sx, *sy, *sp;
+    if ((rc = upload_as(h, &sx, lh.st.sx)) || (rc = upload_as(h, &sy, lh.st.sy)) || (rc = upload_as(h, &sp, lh.st.sp))) return rc;
+    tl.L = make_tab<T>(lh.sz, p, sx, sy, sp);
+    if (l >= 1) {
+      if ((rc = upload_as(h, &tl.cinv, lh.pt.cinv))) return rc;
+      for (int which = 0; which < 2; ++which) {
+        const Transfer1D& Tr = which ? h->host.tq[l] : h->host.tp_free[l];
+        Xfer<T>& X = which ? tl.tq : tl.tp;
+        int *c0, *f0; T *pv, *rv;
+        if ((rc = upload_as(h, &c0, Tr.c0)) || (rc = upload_as(h, &f0, Tr.f0)) || (rc = upload_as(h, &pv, Tr.pv)) ||
+            (rc = upload_as(h, &rv, Tr.rv))) return rc;
+        X.nf = Tr.nf; X.nc = Tr.nc; X.c0 = c0; X.f0 = f0; X.pv = pv; X.rv = rv;
+      }
+    }
+    size_t nb = (size_t)lh.sz.n_total * sizeof(T);
+    if ((rc = dmalloc(h, (void**)&tl.R, nb))) return rc;
+    if ((rc = dmalloc(h, (void**)&tl.U, nb))) return rc;
+    if ((rc = dmalloc(h, (void**)&tl.F, nb))) return rc;
+  }
+  if ((rc = upload_as(h, &ty.coarse_inv, h->host.coarse_inv))) return rc;
+  if ((rc = dmalloc(h, (void**)&ty.delta, std::max<size_t>(max_delta, 1) * sizeof(T)))) return rc;
+  return IGAMG_OK;
+}
+
+int validate(const igamg_problem& pr) {
+  if (pr.dim != 2) return IGAMG_EUNSUPPORTED;
+  if (pr.p != 2 && pr.p != 3) return IGAMG_EUNSUPPORTED;
+  if (pr.beta_qp) return IGAMG_EUNSUPPORTED;
+  if (pr.n_levels < 1 || pr.n_levels > 16 || pr.n_fine < 1) return IGAMG_EINVAL;
+  if (pr.n_fine % (1 << (pr.n_levels - 1))) return IGAMG_EINVAL;
+  if (!(pr.sigma > 0) || !(pr.nu > 0) || pr.nu1 < 0 || pr.nu2 < 0) return IGAMG_EINVAL;
+  if (pr.smoother != IGAMG_MULT && pr.smoother != IGAMG_ADD) return IGAMG_EINVAL;
+  if (pr.precision != IGAMG_FP64 && pr.precision != IGAMG_FP32_IR) return IGAMG_EUNSUPPORTED;
+  if (pr.n_fine > 8192) return IGAMG_EINVAL;
+  // the coarsest grid is solved with a dense inverse held in shared memory by one block
+  if (level_sizes(pr.p, pr.n_fine >> (pr.n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
+  return IGAMG_OK;
 }
 
 }  // namespace
@@ -643,79 +443,52 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
   if (!prob || !out) return IGAMG_EINVAL;
   *out = nullptr;
   const igamg_problem& pr = *prob;
-  if (pr.dim != 2) return IGAMG_EUNSUPPORTED;
-  if (pr.p != 2 && pr.p != 3) return IGAMG_EUNSUPPORTED;
-  if (pr.beta_qp) return IGAMG_EUNSUPPORTED;
-  if (pr.n_levels < 1 || pr.n_levels > 16 || pr.n_fine < 1) return IGAMG_EINVAL;
-  if (pr.n_fine % (1 << (pr.n_levels - 1))) return IGAMG_EINVAL;
-  if (!(pr.sigma > 0) || !(pr.nu > 0) || pr.nu1 < 0 || pr.nu2 < 0) return IGAMG_EINVAL;
-  if (pr.smoother != IGAMG_MULT && pr.smoother != IGAMG_ADD) return IGAMG_EINVAL;
-  if (pr.precision != IGAMG_FP64) return IGAMG_EUNSUPPORTED;
-  if (pr.n_fine > 8192) return IGAMG_EINVAL;
-  // the coarsest grid is solved with a dense inverse held in shared memory by one block
-  if (level_sizes(pr.p, pr.n_fine >> (pr.n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
+  int rc = validate(pr);
+  if (rc) return rc;
   auto* h = new igamg_handle();
   h->prob = pr;
   h->stream = (cudaStream_t)cuda_stream;
-  int rc = build_hierarchy(pr, h->host, g_err);
+  rc = build_hierarchy(pr, h->host, g_err);
   if (rc) { delete h; return rc; }
   auto fail = [&](int code) { igamg_destroy(h); return code; };
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(IGAMG_ECUDA);
   const int L = pr.n_levels, p = pr.p;
-  h->lev.resize(L);
+  h->lc.resize(L);
   size_t max_delta = 0;
   for (int l = 0; l < L; ++l) {
     auto& lh = h->host.lev[l];
-    auto& dl = h->lev[l];
-    dl.sz = lh.sz;
-    const auto& f = lh.f;
-    std::vector<double> bands;
-    for (auto* b : {&f.X1, &f.X2, &f.Mq, &f.Y2, &f.D}) bands.insert(bands.end(), b->v.begin(), b->v.end());
-    bands.insert(bands.end(), f.mq.begin(), f.mq.end());
-    size_t dc_off = bands.size();
-    bands.insert(bands.end(), f.dcoef.begin(), f.dcoef.end());
-    if ((rc = upload(h, &dl.bands, bands))) return fail(rc);
-    dl.L = make_leveldev(lh, dl.bands);
-    dl.dcoef = dl.bands + dc_off;
+    auto& lc = h->lc[l];
+    lc.sz = lh.sz;
+    if ((rc = upload_as(h, &lc.dcoef, lh.f.dcoef))) return fail(rc);
+    std::vector<double> inv(lh.f.dcoef.size());
+    for (size_t k = 0; k < inv.size(); ++k) inv[k] = 1.0 / lh.f.dcoef[k];
+    if ((rc = upload_as(h, &lc.inv_dcoef, inv))) return fail(rc);
     if (l >= 1) {
       const auto& pt = lh.pt;
-      dl.n_patches = pt.n_patches; dl.maxl = pt.maxl; dl.n_colours = pt.n_colours;
-      dl.colour_off = pt.colour_off;
-      if ((rc = upload(h, &dl.dofs, pt.dofs))) return fail(rc);
-      if ((rc = upload(h, &dl.cls, pt.cls))) return fail(rc);
-      if ((rc = upload(h, &dl.nloc, pt.nloc))) return fail(rc);
-      if ((rc = upload(h, &dl.cinv, pt.cinv))) return fail(rc);
-      if ((rc = upload(h, &dl.d2p_off, pt.d2p_off))) return fail(rc);
-      if ((rc = upload(h, &dl.d2p_idx, pt.d2p_idx))) return fail(rc);
+      lc.n_patches = pt.n_patches; lc.maxl = pt.maxl; lc.n_colours = pt.n_colours;
+      lc.colour_off = pt.colour_off; lc.n8 = pt.n8;
+      if ((rc = upload_as(h, &lc.dofs, pt.dofs)) || (rc = upload_as(h, &lc.cls, pt.cls)) ||
+          (rc = upload_as(h, &lc.nloc, pt.nloc)) || (rc = upload_as(h, &lc.d2p_off, pt.d2p_off)) ||
+          (rc = upload_as(h, &lc.d2p_idx, pt.d2p_idx)))
+        return fail(rc);
       max_delta = std::max(max_delta, (size_t)pt.n_patches * pt.maxl);
-      for (int which = 0; which < 2; ++which) {
-        const Transfer1D& T = which ? h->host.tq[l] : h->host.tp_free[l];
-        XferDev& X = which ? dl.tq : dl.tp;
-        int *c0, *f0; double *pv, *rv;
-        if ((rc = upload(h, &c0, T.c0)) || (rc = upload(h, &f0, T.f0)) || (rc = upload(h, &pv, T.pv)) || (rc = upload(h, &rv, T.rv))) return fail(rc);
-        X.nf = T.nf; X.nc = T.nc; X.c0 = c0; X.f0 = f0; X.pv = pv; X.rv = rv;
-      }
-    }
-    size_t nb = (size_t)dl.sz.n_total * sizeof(double);
-    if ((rc = dmalloc(h, (void**)&dl.R, nb))) return fail(rc);
-    if (l < L - 1) {
-      if ((rc = dmalloc(h, (void**)&dl.U, nb))) return fail(rc);
-      if ((rc = dmalloc(h, (void**)&dl.F, nb))) return fail(rc);
+      if (pt.maxl > (p == 2 ? MaxLocal<2>::value : MaxLocal<3>::value)) return fail(IGAMG_EUNSUPPORTED);
     }
   }
+  if ((rc = upload_typed<double>(h, h->d, max_delta))) return fail(rc);
+  if (pr.precision == IGAMG_FP32_IR && (rc = upload_typed<float>(h, h->f, max_delta))) return fail(rc);
   h->ndof0 = h->host.ndof0;
-  if ((rc = upload(h, &h->coarse_inv, h->host.coarse_inv))) return fail(rc);
-  long long nfine = h->lev[L - 1].sz.n_total;
+  long long nfine = h->lc[L - 1].sz.n_total;
   if ((rc = dmalloc(h, (void**)&h->part, 2 * sizeof(double) * (nblk(nfine) + 1)))) return fail(rc);
   if ((rc = dmalloc(h, (void**)&h->norm2, sizeof(double)))) return fail(rc);
   if ((rc = dmalloc(h, (void**)&h->divmax, sizeof(unsigned long long)))) return fail(rc);
-  if ((rc = dmalloc(h, (void**)&h->delta, std::max<size_t>(max_delta, 1) * sizeof(double)))) return fail(rc);
-  if ((rc = upload(h, &h->lv_p, h->host.lv_p))) return fail(rc);
-  if ((rc = upload(h, &h->lv_q, h->host.lv_q))) return fail(rc);
+  if ((rc = upload_as(h, &h->lv_p, h->host.lv_p)) || (rc = upload_as(h, &h->lv_q, h->host.lv_q))) return fail(rc);
   size_t nG = (size_t)pr.n_fine * (p + 2);
   if ((rc = dmalloc(h, (void**)&h->f_dev, 2 * nG * nG * sizeof(double)))) return fail(rc);
   if ((rc = dmalloc(h, (void**)&h->Fh, nfine * sizeof(double)))) return fail(rc);
   if ((rc = dmalloc(h, (void**)&h->Uh, nfine * sizeof(double)))) return fail(rc);
+  size_t nint = (size_t)(pr.n_fine + p - 2);
+  if ((rc = dmalloc(h, (void**)&h->psi, nint * nint * sizeof(double)))) return fail(rc);
   if (cudaMallocHost((void**)&h->h_pinned, 2 * sizeof(double)) != cudaSuccess) return fail(IGAMG_ECUDA);
   *out = h;
   return IGAMG_OK;
@@ -723,7 +496,7 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
 
 void igamg_destroy(igamg_handle* h) {
   if (!h) return;
-  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (auto& g : h->graph) if (g) cudaGraphExecDestroy(g);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -731,8 +504,8 @@ void igamg_destroy(igamg_handle* h) {
 }
 
 int igamg_get_sizes(const igamg_handle* h, int level, igamg_sizes* out) {
-  if (!h || !out || level < 0 || level >= (int)h->lev.size()) return IGAMG_EINVAL;
-  *out = h->lev[level].sz;
+  if (!h || !out || level < 0 || level >= (int)h->lc.size()) return IGAMG_EINVAL;
+  *out = h->lc[level].sz;
   return IGAMG_OK;
 }
 
@@ -748,46 +521,46 @@ int igamg_quad_points(const igamg_handle* h, double* x, size_t cap, size_t* n_ou
 
 int igamg_load_vector(igamg_handle* h, const double* f_qp, double* F) {
   if (!h || !f_qp || !F) return IGAMG_EINVAL;
-  auto& lv = h->lev.back();
-  if (h->prob.p == 2) k_load<2><<<nblk(lv.sz.n_total), kBlock, 0, h->stream>>>(lv.L, h->lv_p, h->lv_q, f_qp, F);
-  else k_load<3><<<nblk(lv.sz.n_total), kBlock, 0, h->stream>>>(lv.L, h->lv_p, h->lv_q, f_qp, F);
+  auto& Lt = h->d.lev.back().L;
+  if (h->prob.p == 2) k_load<2><<<nblk(Lt.n_total), kBlock, 0, h->stream>>>(Lt, h->lv_p, h->lv_q, f_qp, F);
+  else k_load<3><<<nblk(Lt.n_total), kBlock, 0, h->stream>>>(Lt, h->lv_p, h->lv_q, f_qp, F);
   return launch_check();
 }
 
 int igamg_residual(igamg_handle* h, int level, const double* U, const double* F, double* R, double* norm_out) {
-  if (!h || !U || !F || !R || level < 0 || level >= (int)h->lev.size()) return IGAMG_EINVAL;
-  int rc = do_residual(h, level, U, F, R, h->norm2, h->stream);
+  if (!h || !U || !F || !R || level < 0 || level >= (int)h->lc.size()) return IGAMG_EINVAL;
+  int rc = do_residual<double>(h, level, U, F, R, h->norm2, h->stream);
   if (rc) return rc;
   if (norm_out) return read_norm(h, norm_out);
   return IGAMG_OK;
 }
 
 int igamg_smooth(igamg_handle* h, int level, double* U, const double* F, int sweeps) {
-  if (!h || !U || !F || level < 1 || level >= (int)h->lev.size() || sweeps < 0) return IGAMG_EINVAL;
-  for (int k = 0; k < sweeps; ++k) { int rc = do_smooth(h, level, U, F, h->stream); if (rc) return rc; }
+  if (!h || !U || !F || level < 1 || level >= (int)h->lc.size() || sweeps < 0) return IGAMG_EINVAL;
+  for (int k = 0; k < sweeps; ++k) { int rc = do_smooth<double>(h, level, U, F, h->stream); if (rc) return rc; }
   return IGAMG_OK;
 }
 
 int igamg_restrict(igamg_handle* h, int level, const double* r_fine, double* g_coarse) {
-  if (!h || !r_fine || !g_coarse || level < 1 || level >= (int)h->lev.size()) return IGAMG_EINVAL;
-  return do_restrict(h, level, r_fine, g_coarse, h->stream);
+  if (!h || !r_fine || !g_coarse || level < 1 || level >= (int)h->lc.size()) return IGAMG_EINVAL;
+  return do_restrict<double>(h, level, r_fine, g_coarse, h->stream);
 }
 
 int igamg_prolong_add(igamg_handle* h, int level, const double* u_coarse, double* u_fine) {
-  if (!h || !u_coarse || !u_fine || level < 1 || level >= (int)h->lev.size()) return IGAMG_EINVAL;
-  return do_prolong(h, level, u_coarse, u_fine, h->stream);
+  if (!h || !u_coarse || !u_fine || level < 1 || level >= (int)h->lc.size()) return IGAMG_EINVAL;
+  return do_prolong<double>(h, level, u_coarse, u_fine, h->stream);
 }
 
 int igamg_coarse_solve(igamg_handle* h, const double* G, double* U) {
   if (!h || !G || !U) return IGAMG_EINVAL;
-  return do_coarse(h, G, U, h->stream);
+  return do_coarse<double>(h, G, U, h->stream);
 }
 
 int igamg_vcycle(igamg_handle* h, double* U, const double* F) {
   if (!h || !U || !F) return IGAMG_EINVAL;
-  int rc = ensure_graph(h, U, F);
+  int rc = ensure_graph(h, 1, U, F);
   if (rc) return rc;
-  CK(cudaGraphLaunch(h->graph, h->stream));
+  CK(cudaGraphLaunch(h->graph[1], h->stream));
   return IGAMG_OK;
 }
 
@@ -800,7 +573,7 @@ int igamg_solve_host(igamg_handle* h, const double* f_qp_host, double* U_host, d
                      igamg_report* rep) {
   if (!h || !f_qp_host || !U_host || !(rtol >= 0) || max_cycles < 0) return IGAMG_EINVAL;
   size_t nG = (size_t)h->prob.n_fine * (h->prob.p + 2);
-  size_t nt = (size_t)h->lev.back().sz.n_total;
+  size_t nt = (size_t)h->lc.back().sz.n_total;
   CK(cudaMemcpyAsync(h->f_dev, f_qp_host, 2 * nG * nG * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->Uh, U_host, nt * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   int rc = igamg_load_vector(h, h->f_dev, h->Fh);
@@ -814,21 +587,13 @@ int igamg_solve_host(igamg_handle* h, const double* f_qp_host, double* U_host, d
 
 int igamg_div_inf(igamg_handle* h, const double* U, double* out) {
   if (!h || !U || !out) return IGAMG_EINVAL;
-  auto& lv = h->lev.back();
-  CK(cudaMemsetAsync(h->divmax, 0, sizeof(unsigned long long), h->stream));
-  k_div_inf<<<nblk(lv.sz.n_p), kBlock, 0, h->stream>>>(lv.L, lv.dcoef, U, h->divmax);
-  int rc = launch_check();
-  if (rc) return rc;
-  CK(cudaMemcpyAsync(h->h_pinned, h->divmax, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  *out = h->h_pinned[0];
-  return IGAMG_OK;
+  return div_inf_impl(h, U, out);
 }
 
 int igamg_curl(igamg_handle* h, const double* psi, double* U) {
   if (!h || !psi || !U) return IGAMG_EINVAL;
-  auto& lv = h->lev.back();
-  k_curl<<<nblk(lv.sz.n_ux + lv.sz.n_uy), kBlock, 0, h->stream>>>(lv.L, lv.dcoef, psi, U);
+  auto& Lt = h->d.lev.back().L;
+  k_curl<<<nblk(Lt.n_ux + Lt.n_uy), kBlock, 0, h->stream>>>(Lt, h->lc.back().dcoef, psi, U);
   return launch_check();
 }
 
@@ -866,12 +631,13 @@ extern "C" int igamg_residual_static(const igamg_problem* prob, int level, const
   const int p = pr.p, n = pr.n_fine >> (pr.n_levels - 1 - level);
   cudaStream_t s = (cudaStream_t)cuda_stream;
 
-  // size check before any work: band tables + partials + the norm slot
+  // size check before any work: class stencil tables + partials + the norm slot
   igamg_sizes sz = level_sizes(p, n);
-  const size_t W = 2 * p + 1;
-  const size_t n_bands = (size_t)(n + p) * W * 3 + (size_t)(n + p - 1) * W * 2 + (n + p - 1);
+  const int TC = 2 * p + 1, NC = 2 * TC + 1;
+  const size_t RX = (size_t)(4 * p + 1) * (2 * p - 1), RP = (size_t)4 * p * (2 * p - 1) + 1;
+  const size_t n_tab = (size_t)NC * NC * (2 * RX + RP);
   const unsigned nb = nblk(sz.n_total - 1);
-  const size_t need = n_bands + 2 * (size_t)nb + 1;
+  const size_t need = n_tab + 2 * (size_t)nb + 1;
   if (need > kStaticScratchDoubles) {
     g_err = "igamg_residual_static: level needs " + std::to_string(need) + " doubles of scratch, the static array holds " +
             std::to_string(kStaticScratchDoubles);
@@ -889,21 +655,21 @@ extern "C" int igamg_residual_static(const igamg_problem* prob, int level, const
   }
   double* scratch = g_static_ptr[dev];
 
-  // level operator tables (host), copied into the front of the static array
+  // this level's class stencils (host), copied into the front of the static array
   Level1D f;
   const double cpen = pr.c_penalty > 0 ? pr.c_penalty : 4.0 * (p - 1);
   build_level1d(p, n, pr.sigma, pr.nu, cpen * pr.n_fine, f);
-  std::vector<double> bands;
-  bands.reserve(n_bands);
-  for (auto* b : {&f.X1, &f.X2, &f.Mq, &f.Y2, &f.D}) bands.insert(bands.end(), b->v.begin(), b->v.end());
-  bands.insert(bands.end(), f.mq.begin(), f.mq.end());
-  if (bands.size() != n_bands) return IGAMG_EINVAL;
-  CK(cudaMemcpyAsync(scratch, bands.data(), n_bands * sizeof(double), cudaMemcpyHostToDevice, s));
-  LevelHost lh;
-  lh.f = f;
-  lh.sz = sz;
-  LevelDev<double> L = make_leveldev(lh, scratch);
-  double* part = scratch + n_bands;       // fully rewritten by every call
+  Stencils st;
+  build_stencils(p, f, sz, st);
+  std::vector<double> tab;
+  tab.reserve(n_tab);
+  tab.insert(tab.end(), st.sx.begin(), st.sx.end());
+  tab.insert(tab.end(), st.sy.begin(), st.sy.end());
+  tab.insert(tab.end(), st.sp.begin(), st.sp.end());
+  if (tab.size() != n_tab) return IGAMG_EINVAL;
+  CK(cudaMemcpyAsync(scratch, tab.data(), n_tab * sizeof(double), cudaMemcpyHostToDevice, s));
+  LevelTab<double> L = make_tab<double>(sz, p, scratch, scratch + st.sx.size(), scratch + st.sx.size() + st.sy.size());
+  double* part = scratch + n_tab;         // fully rewritten by every call
   double* norm2 = part + 2 * (size_t)nb;
   if (p == 2) k_residual<2, double><<<nb, kBlock, 0, s>>>(L, U, F, R, part);
   else k_residual<3, double><<<nb, kBlock, 0, s>>>(L, U, F, R, part);
@@ -915,6 +681,40 @@ extern "C" int igamg_residual_static(const igamg_problem* prob, int level, const
     CK(cudaMemcpyAsync(&v, norm2, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     *norm_out = std::sqrt(v);
+  }
+  return IGAMG_OK;
+}
+
+// Host-only: K_l rebuilt column by column through the same row evaluation the kernels
+// use (class stencils, clamped neighbour indices), for checking the tables on a CPU.
+extern "C" int igamg_host_operator_rows(const igamg_problem* prob, int level, double* K, size_t cap,
+                                        long long* n_out) {
+  if (!prob) return IGAMG_EINVAL;
+  int rc = validate(*prob);
+  if (rc) return rc;
+  if (level < 0 || level >= prob->n_levels) return IGAMG_EINVAL;
+  HierarchyHost H;
+  std::string err;
+  if ((rc = build_hierarchy(*prob, H, err))) return rc;
+  const auto& lh = H.lev[level];
+  LevelTab<double> L = make_tab<double>(lh.sz, prob->p, lh.st.sx.data(), lh.st.sy.data(), lh.st.sp.data());
+  long long n = lh.sz.n_total;
+  if (n_out) *n_out = n;
+  if (!K) return IGAMG_OK;
+  if (cap < (size_t)(n * n)) return IGAMG_EINVAL;
+  std::vector<double> e(n, 0.0);
+  for (long long j = 0; j < n; ++j) {
+    e[j] = 1.0;
+    for (long long i = 0; i + 1 < n; ++i)
+      K[i * n + j] = prob->p == 2 ? row_KU<2, double>(L, e.data(), (int)i) : row_KU<3, double>(L, e.data(), (int)i);
+    double lam = 0.0;  // lambda row: m . p
+    for (long long i = lh.sz.n_ux + lh.sz.n_uy; i + 1 < n; ++i) {
+      int r = (int)(i - lh.sz.n_ux - lh.sz.n_uy);
+      int ky = r / L.npd, kx = r - ky * L.npd;
+      lam += lh.f.mq[kx] * lh.f.mq[ky] * e[i];
+    }
+    K[(n - 1) * n + j] = lam;
+    e[j] = 0.0;
   }
   return IGAMG_OK;
 }

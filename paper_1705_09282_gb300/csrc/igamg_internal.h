@@ -55,14 +55,30 @@ struct PatchTables {
   std::vector<int> nloc;       // per class: n_v + n_q
   std::vector<double> cinv;    // n_cls * maxl * maxl: leading block of the bordered inverse
   std::vector<int> colour_off; // n_colours + 1
+  std::vector<int> n8;         // per colour: patches with 4+4 DOFs, stored first in the colour
   std::vector<int> d2p_off;    // dof -> list of (patch * maxl + local row), CSR over dofs
   std::vector<int> d2p_idx;
 };
+
+// Row stencils of K_l by row class.  A row's class is the pair of 1D position classes
+// of its two indices (cls1 below): positions within T of either end are their own class,
+// all others share the translation-invariant interior class.  Coefficients of neighbours
+// outside the index range are stored as zero.
+//   u_x rows: A[dx][dy] (dx in -p..p, dy in -q..q) then B[kx][dy] (kx in -p..p-1)   RX values
+//   u_y rows: A[dx][dy] (dx in -q..q, dy in -p..p) then B[dx][ky] (ky in -p..p-1)   RX values
+//   p rows:   Bx[s][dy] (s in -q..p, dy in -q..q), By[dx][s], then m                  RP values
+struct Stencils {
+  int T = 0, NC = 0, RX = 0, RP = 0;
+  std::vector<double> sx, sy, sp;
+};
+
+inline int cls1(int i, int last, int T) { return i < T ? i : (last - i < T ? 2 * T - (last - i) : T); }
 
 struct LevelHost {
   Level1D f;
   igamg_sizes sz{};
   PatchTables pt;
+  Stencils st;
 };
 
 struct HierarchyHost {
@@ -86,5 +102,6 @@ igamg_sizes level_sizes(int p, int n);
 double k_entry(const Level1D& L, const igamg_sizes& s, long long g1, long long g2);
 // 1D factors of one level with n elements; pen_over_nu = C_I / h_fine.
 void build_level1d(int p, int n, double sigma, double nu, double pen_over_nu, Level1D& L);
+void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st);
 
 }  // namespace igamg

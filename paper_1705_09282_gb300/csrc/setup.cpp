@@ -331,8 +331,12 @@ int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt
       P_.nq = (int)P_.dofs.size() - P_.nv;
       all.push_back(std::move(P_));
     }
-  // colour-major, lexicographic (b, a) inside a colour
-  std::stable_sort(all.begin(), all.end(), [](const P& x, const P& y) { return x.colour < y.colour; });
+  // colour-major; inside a colour the 4+4-DOF patches first, then the larger wall
+  // patches, each group lexicographic in (b, a).  The order inside a colour does not
+  // change the result: same-colour patches share no DOF and are not coupled by K.
+  std::stable_sort(all.begin(), all.end(), [](const P& x, const P& y) {
+    if (x.colour != y.colour) return x.colour < y.colour;
+    return (x.dofs.size() != 8) < (y.dofs.size() != 8); });
   int maxl = 0;
   for (auto& P_ : all) maxl = std::max(maxl, (int)P_.dofs.size());
   pt.n_patches = (int)all.size(); pt.maxl = maxl; pt.n_colours = np1 * np1;
@@ -351,6 +355,9 @@ int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt
     else pt.cls[i] = it->second;
   }
   for (int c = 0; c < pt.n_colours; ++c) pt.colour_off[c + 1] += pt.colour_off[c];
+  pt.n8.assign(pt.n_colours, 0);
+  for (int c = 0; c < pt.n_colours; ++c)
+    for (int k = pt.colour_off[c]; k < pt.colour_off[c + 1] && all[k].dofs.size() == 8; ++k) pt.n8[c]++;
   // bordered local inverses, one per class (Sec. 5.2 local problems; zero-mean local
   // pressure through the border m_j = int N^q_j)
   pt.n_cls = (int)rep.size();
@@ -409,6 +416,83 @@ igamg_sizes level_sizes(int p, int n) {
   return s;
 }
 
+void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st) {
+  const int q = p - 1, n = L.n;
+  st.T = 2 * p + 1;
+  st.NC = 2 * st.T + 1;
+  st.RX = (4 * p + 1) * (2 * q + 1);
+  st.RP = 4 * p * (2 * q + 1) + 1;
+  const int T = st.T, NC = st.NC, RX = st.RX, RP = st.RP;
+  const int lastp = n + p - 1, lastq = n + q - 1, nint = n + p - 2;
+  st.sx.assign((size_t)NC * NC * RX, 0.0);
+  st.sy.assign((size_t)NC * NC * RX, 0.0);
+  st.sp.assign((size_t)NC * NC * RP, 0.0);
+  std::vector<char> done(NC * NC);
+  auto inq = [&](int k) { return k >= 0 && k <= lastq; };
+  auto inp_free = [&](int k) { return k >= 1 && k <= nint; };
+  std::fill(done.begin(), done.end(), 0);
+  for (int iy = 0; iy <= lastq; ++iy)
+    for (int ix = 1; ix <= nint; ++ix) {
+      int c = cls1(ix, lastp, T) * NC + cls1(iy, lastq, T);
+      if (done[c]) continue;
+      done[c] = 1;
+      double* r = &st.sx[(size_t)c * RX];
+      for (int dx = -p; dx <= p; ++dx)
+        for (int dy = -q; dy <= q; ++dy) {
+          int jx = ix + dx, jy = iy + dy;
+          if (inp_free(jx) && inq(jy))
+            r[(dx + p) * (2 * q + 1) + dy + q] = L.X1.get(ix, jx) * L.Mq.get(iy, jy) + L.X2.get(ix, jx) * L.Y2.get(iy, jy);
+        }
+      for (int kx = -p; kx <= p - 1; ++kx)
+        for (int dy = -q; dy <= q; ++dy) {
+          int jx = ix + kx, jy = iy + dy;
+          if (inq(jx) && inq(jy))
+            r[(2 * p + 1) * (2 * q + 1) + (kx + p) * (2 * q + 1) + dy + q] = -L.D.get(ix, jx) * L.Mq.get(iy, jy);
+        }
+    }
+  std::fill(done.begin(), done.end(), 0);
+  for (int iy = 1; iy <= nint; ++iy)
+    for (int ix = 0; ix <= lastq; ++ix) {
+      int c = cls1(ix, lastq, T) * NC + cls1(iy, lastp, T);
+      if (done[c]) continue;
+      done[c] = 1;
+      double* r = &st.sy[(size_t)c * RX];
+      for (int dx = -q; dx <= q; ++dx)
+        for (int dy = -p; dy <= p; ++dy) {
+          int jx = ix + dx, jy = iy + dy;
+          if (inq(jx) && inp_free(jy))
+            r[(dx + q) * (2 * p + 1) + dy + p] = L.Mq.get(ix, jx) * L.X1.get(iy, jy) + L.Y2.get(ix, jx) * L.X2.get(iy, jy);
+        }
+      for (int dx = -q; dx <= q; ++dx)
+        for (int ky = -p; ky <= p - 1; ++ky) {
+          int jx = ix + dx, jy = iy + ky;
+          if (inq(jx) && inq(jy))
+            r[(2 * q + 1) * (2 * p + 1) + (dx + q) * (2 * p) + ky + p] = -L.Mq.get(ix, jx) * L.D.get(iy, jy);
+        }
+    }
+  std::fill(done.begin(), done.end(), 0);
+  for (int ky = 0; ky <= lastq; ++ky)
+    for (int kx = 0; kx <= lastq; ++kx) {
+      int c = cls1(kx, lastq, T) * NC + cls1(ky, lastq, T);
+      if (done[c]) continue;
+      done[c] = 1;
+      double* r = &st.sp[(size_t)c * RP];
+      for (int sI = -q; sI <= p; ++sI)
+        for (int dy = -q; dy <= q; ++dy) {
+          int ix = kx + sI, iy = ky + dy;
+          if (inp_free(ix) && inq(iy)) r[(sI + q) * (2 * q + 1) + dy + q] = L.D.get(ix, kx) * L.Mq.get(iy, ky);
+        }
+      for (int dx = -q; dx <= q; ++dx)
+        for (int sI = -q; sI <= p; ++sI) {
+          int ix = kx + dx, iy = ky + sI;
+          if (inq(ix) && inp_free(iy)) r[2 * p * (2 * q + 1) + (dx + q) * (2 * p) + sI + q] = L.Mq.get(ix, kx) * L.D.get(iy, ky);
+        }
+      r[RP - 1] = L.mq[kx] * L.mq[ky];
+    }
+  (void)s;
+}
+
+
 int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err) {
   const int p = pr.p, L = pr.n_levels, nf = pr.n_fine;
   H.p = p; H.L = L; H.n_fine = nf; H.sigma = pr.sigma; H.nu = pr.nu;
@@ -420,6 +504,7 @@ int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err)
     auto& lv = H.lev[l];
     build_level1d(p, n, pr.sigma, pr.nu, pen_over_nu, lv.f);
     lv.sz = level_sizes(p, n);
+    build_stencils(p, lv.f, lv.sz, lv.st);
     if (l >= 1) {
       int rc = build_patches(p, lv.f, lv.sz, lv.pt, err);
       if (rc) return rc;

@@ -161,6 +161,16 @@ def host_level_matrix(p, n_fine, n_levels, sigma, nu, level, c_penalty=0.0):
     return K
 
 
+def host_operator_rows(p, n_fine, n_levels, sigma, nu, level):
+    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu)
+    n = ctypes.c_longlong()
+    check(lib().igamg_host_operator_rows(ctypes.byref(pr), level, None, 0, ctypes.byref(n)), "host_operator_rows")
+    K = np.zeros((n.value, n.value))
+    check(lib().igamg_host_operator_rows(ctypes.byref(pr), level, K.ctypes.data_as(ctypes.c_void_p), K.size,
+                                         ctypes.byref(n)), "host_operator_rows")
+    return K
+
+
 def host_prolongation(p, n_fine, n_levels, level):
     pr = _lib.make_problem(p, n_fine, n_levels, 1.0, 1.0)
     r, c = ctypes.c_longlong(), ctypes.c_longlong()
