@@ -6,8 +6,10 @@ Workload (one "step"): the sigma/nu sweep {1e-4, 1e-2, 1, 1e2, 1e4} (nu = 1) of 
 forcing from a seeded Gaussian random field (squared-exponential kernel, length 0.1),
 zero initial guess, solved to a 1e-8 relative residual: 10 solves per step.
 
-Metric: MDOF/s per V-cycle = sum over solves of (DOFs x V-cycles) / time / 1e6, with the
-solve time to 1e-8 also reported.  Inputs are resident in HBM when the timed region
+Metric: MDOF/s per V-cycle = sum over solves of (DOFs x V-cycles) / time / 1e6, for the
+plain FP64 GPU multigrid (the line's value), with the solve time to 1e-8 also reported; the
+same sweep solved by FP32 V-cycles inside FP64 iterative refinement is reported beside it
+(same tolerance, its own time and speed-up over FP64).  Inputs are resident in HBM when the timed region
 starts; L2 is flushed (a 512 MB write) before every timed step, outside its events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -107,12 +109,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def launches_per_solve(p, cycles):
+def launches_per_solve(p, cycles, mixed=False):
     """Kernels of ours in one igamg_solve: per V-cycle, per smoothed level (nu1+nu2)
     colour launches + residual (2) + restriction + prolongation; coarse solve; the
-    fine residual norm (2).  Plus the initial residual (2) and the final div check."""
+    fine residual norm (2).  The FP32 mode adds the down-cast, the streamfunction
+    integration and the curl update per cycle.  Plus the initial residual (2) and the
+    final divergence check."""
     colours = (p + 1) ** 2
-    per_cycle = (N_LEVELS - 1) * (4 * colours + 2 + 1 + 1) + 1 + 2
+    per_cycle = (N_LEVELS - 1) * (4 * colours + 2 + 1 + 1) + 1 + 2 + (3 if mixed else 0)
     return 2 + cycles * per_cycle + 1
 
 
@@ -120,7 +124,8 @@ def run_ours(args):
     import torch
 
     from paper_1705_09282_gb300 import inputs
-    from paper_1705_09282_gb300.solver import Solver
+    from paper_1705_09282_gb300._lib import IGAMG_FP32_IR
+    from paper_1705_09282_gb300.solver import Solver, solve_batch
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -141,39 +146,64 @@ def run_ours(args):
         f_dev = torch.tensor(f_host, device=dev)
         for s in SIGMAS:
             S = Solver(p, N_FINE, N_LEVELS, s, 1.0, nu1=2, nu2=2, device=dev, stream=stream)
+            S32 = Solver(p, N_FINE, N_LEVELS, s, 1.0, nu1=2, nu2=2, device=dev, stream=stream,
+                         precision=IGAMG_FP32_IR)
             F = S.load_vector(f_dev)
-            problems.append({"p": p, "sigma": s, "S": S, "F": F, "U": S.empty(), "f_host": f_host,
-                             "ndof": S.ndof()})
+            problems.append({"p": p, "sigma": s, "S": S, "S32": S32, "F": F, "U": S.empty(),
+                             "f_host": f_host, "ndof": S.ndof()})
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step():
-        tot_dof_cycles, cycles = 0, []
+    def step(key="S"):
+        """The whole sweep: all solves side by side through igamg_solve_batch."""
         for pr in problems:
             pr["U"].zero_()
-            rep = pr["S"].solve(pr["U"], pr["F"], rtol=RTOL, max_cycles=MAXC, history=False)
-            assert rep["converged"], (pr["p"], pr["sigma"], rep)
+        reps = solve_batch([pr[key] for pr in problems], [pr["U"] for pr in problems],
+                           [pr["F"] for pr in problems], rtol=RTOL, max_cycles=MAXC)
+        tot_dof_cycles, cycles, worst = 0, [], 0.0
+        for pr, rep in zip(problems, reps):
+            assert rep["converged"], (pr["p"], pr["sigma"], key, rep)
             tot_dof_cycles += pr["ndof"] * rep["cycles"]
             cycles.append(rep["cycles"])
-        return tot_dof_cycles, cycles
+            worst = max(worst, rep["div_inf"])
+        return tot_dof_cycles, cycles, worst
+
+    def single_solve_ms(key):
+        """Latency of one solve alone (the first problem), for context."""
+        pr = problems[0]
+        pr["U"].zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = pr[key].solve(pr["U"], pr["F"], rtol=RTOL, max_cycles=MAXC, history=False)
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t0), rep["cycles"]
+
+    def timed(key, steps):
+        ms, dofcyc, cyc, worst = [], 0, None, 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            dc, cyc, w = step(key)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            dofcyc += dc
+            worst = max(worst, w)
+        return ms, dofcyc, cyc, worst
 
     for _ in range(args.warmup):
-        step()
+        step("S")
+        step("S32")
     torch.cuda.synchronize()
     barrier()
     clk = ClockSampler(local)
     clk.start()
-    ms_steps, dofcyc, cyc_list = [], 0, None
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        dc, cyc_list = step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_steps.append(e0.elapsed_time(e1))
-        dofcyc += dc
+    ms_steps, dofcyc, cyc_list, div64 = timed("S", args.steps)
+    ms32, dofcyc32, cyc32, div32 = timed("S32", args.steps)
     clocks = clk.stop()
+    lat64, lat64_cyc = single_solve_ms("S")
+    lat32, lat32_cyc = single_solve_ms("S32")
     t_total = sum(ms_steps) / 1e3
     if world > 1:
         import torch.distributed as dist
@@ -183,6 +213,15 @@ def run_ours(args):
     value = world * dofcyc / t_total / 1e6
     solves = len(problems)
     solve_ms = 1e3 * t_total / (args.steps * solves)
+    t32 = sum(ms32) / 1e3
+    mixed = {"precision": "FP32 V-cycles (FP32 smoother, operator, transfers, coarse solve) inside FP64 "
+                          "iterative refinement; FP64 outer residual; velocity update = FP64 curl of a streamfunction",
+             "value": world * dofcyc32 / t32 / 1e6, "unit": "MDOF/s per V-cycle",
+             "solve_ms_to_1e-8": 1e3 * t32 / (args.steps * solves),
+             "speedup_vs_fp64_solve_time": t_total / t32,
+             "single_solve_ms": lat32, "single_solve_case": f"p=2, sigma=1e-4, {lat32_cyc} cycles",
+             "cycles": {f"p{pr['p']}_sigma{pr['sigma']:g}": c for pr, c in zip(problems, cyc32)},
+             "max_div_inf": div32}
 
     # ---- dominant kernel: one multiplicative colour sweep on the finest level ---------
     pk, pk_src = peaks()
@@ -199,17 +238,22 @@ def run_ours(args):
     torch.cuda.synchronize()
     colours = sz.n_colours
     launch_s = e0.elapsed_time(e1) / 1e3 / (sweeps * colours)
-    # algorithmic bytes of one colour launch (per-unit figures in the design notes):
-    # U read once (8 B / DOF) + per patch: F and U of its DOFs read, U written (24 B / DOF),
-    # its DOF index list (4 B / DOF) and class id (4 B).
+    # algorithmic FP64 flops of one colour launch (per-unit figures in the design notes):
+    # per patch, its 8 residual rows (2 flops per stencil coefficient: u_x, u_y rows
+    # (4p+1)(2p-1), p rows 4p(2p-1)+1), the 8x8 local inverse (2 x 64) and 16 adds.
+    p0 = problems[0]["p"]
+    rx, rp = (4 * p0 + 1) * (2 * p0 - 1), 4 * p0 * (2 * p0 - 1) + 1
+    flops_patch = 2 * (4 * rx + 4 * rp) + 2 * 64 + 16
     n_patch_colour = sz.n_patches / colours
-    dofs_per_patch = 8.0
-    alg_bytes = 8.0 * sz.n_total + n_patch_colour * (dofs_per_patch * 28.0 + 4.0)
-    achieved = alg_bytes / launch_s / 1e9
-    roofline = {"kernel": "k_mult_colour (finest level, p=2)", "bound": "hbm", "achieved": achieved,
-                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                "traffic": None, "peak_source": pk_src, "avg_launch_us": launch_s * 1e6,
-                "working_set_note": "the finest-level vectors (1.6 MB) are L2-resident across colours"}
+    achieved = n_patch_colour * flops_patch / launch_s / 1e12
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12    # 152 SMs x 2 DFMA/clk x 2 flops
+    roofline = {"kernel": "k_mult_colour<2,double> (one colour, finest level, p=2)", "bound": "alu",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s (FP64)", "frac": achieved / fp64_peak,
+                "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x median SM clock",
+                "avg_launch_us": launch_s * 1e6, "flops_per_launch": n_patch_colour * flops_patch,
+                "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_source": pk_src,
+                "working_set_note": "finest-level vectors (1.6 MB) stay in L2; the kernel is FP64-issue bound"}
 
     # ---- end to end through the host-buffer C-ABI call --------------------------------
     pin = {}
@@ -240,15 +284,20 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Gaussian random field forcing)", "config": workload_config(),
             "solve_ms_to_1e-8": solve_ms,
+            "solve_ms_note": "sweep time / solves, the 10 solves running side by side (igamg_solve_batch)",
+            "single_solve_ms": lat64, "single_solve_case": f"p=2, sigma=1e-4, {lat64_cyc} cycles, alone",
             "cycles": {f"p{pr['p']}_sigma{pr['sigma']:g}": c for pr, c in zip(problems, cyc_list)},
-            "roofline": roofline, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": sum(launches_per_solve(pr["p"], c) for pr, c in zip(problems, cyc_list)) * args.steps}
+            "roofline": roofline, "e2e": e2e, "clocks": clocks, "mixed_fp32_ir": mixed,
+            "max_div_inf": div64,
+            "gpu_launches": (sum(launches_per_solve(pr["p"], c) for pr, c in zip(problems, cyc_list))
+                             + sum(launches_per_solve(pr["p"], c, mixed=True) for pr, c in zip(problems, cyc32))) * args.steps}
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(line), flush=True)
     for pr in problems:
         pr["S"].close()
+        pr["S32"].close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -138,6 +138,16 @@ int igamg_solve(igamg_handle* h, double* U, const double* F, double rtol, int ma
 int igamg_solve_host(igamg_handle* h, const double* f_qp_host, double* U_host, double rtol,
                      int max_cycles, igamg_report* rep);
 
+/* n independent solves at once (same contract as igamg_solve for each), e.g. a sweep of
+ * sigma/nu values or of right-hand sides: each handle's work runs on its own internal
+ * stream (ordered after, and joined back into, the stream given to its igamg_create), so
+ * latency-bound small solves overlap on the GPU.  U[i], F[i]: device vectors of
+ * handles[i]; reports, status: NULL or arrays of n (status[i] = igamg_solve's return
+ * value for solve i).  Handles must be distinct.  Returns the first negative status, else
+ * IGAMG_NOT_CONVERGED if any solve ran out of cycles, else 0.  Synchronous. */
+int igamg_solve_batch(int n, igamg_handle** handles, double** U, const double** F, double rtol,
+                      int max_cycles, igamg_report* reports, int* status);
+
 /* max over pressure-space coefficients of |div u_h| (Lemma, Sec. 4.1: zero up to
  * round-off for the iterates of Sec. 5.3).  Synchronises; result on the host. */
 int igamg_div_inf(igamg_handle* h, const double* U, double* out);

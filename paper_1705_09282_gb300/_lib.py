@@ -55,6 +55,8 @@ SIGNATURES = {
     "igamg_vcycle": (_I, [_P, _P, _P]),
     "igamg_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Report)]),
     "igamg_solve_host": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Report)]),
+    "igamg_solve_batch": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I,
+                               ctypes.POINTER(Report), ctypes.POINTER(_I)]),
     "igamg_div_inf": (_I, [_P, _P, ctypes.POINTER(_D)]),
     "igamg_curl": (_I, [_P, _P, _P]),
     "igamg_residual_static": (_I, [ctypes.POINTER(Problem), _I, _P, _P, _P, ctypes.POINTER(_D), _P]),

@@ -11,6 +11,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -108,6 +112,10 @@ struct Typed {
   std::vector<TypedLevel<T>> lev;
   T* coarse_inv = nullptr;
   T* delta = nullptr;
+  int fused_lc = -1;            // levels 0..fused_lc run in one block (k_fused_coarse), or -1
+  int fused_max = -1;           // deepest feasible choice (descriptor is built for it)
+  size_t fused_smem = 0;
+  FusedDesc<T> fused{};
 };
 
 struct LevelCommon {
@@ -141,6 +149,8 @@ struct igamg_handle {
   const void* gU[2] = {nullptr, nullptr};
   const void* gF[2] = {nullptr, nullptr};
   std::vector<void*> allocs;
+  cudaStream_t exec_stream = nullptr;  // used by igamg_solve_batch
+  cudaEvent_t ev = nullptr;
 };
 
 namespace {
@@ -239,13 +249,43 @@ int do_coarse(igamg_handle* h, const T* G, T* U, cudaStream_t s) {
   return launch_check();
 }
 
-// Algorithm 1 (MGV) from the finest level, unrolled into launches.
+template <typename T>
+int do_fused(igamg_handle* h, const T* Fin, T* Uio, int load_u, cudaStream_t s) {
+  auto& ty = typed<T>(h);
+  ty.fused.nlev = ty.fused_lc + 1;
+  if (h->prob.p == 2) k_fused_coarse<2, T><<<1, 1024, ty.fused_smem, s>>>(ty.fused, Fin, Uio, load_u);
+  else k_fused_coarse<3, T><<<1, 1024, ty.fused_smem, s>>>(ty.fused, Fin, Uio, load_u);
+  return launch_check();
+}
+
+// Algorithm 1 (MGV) from the finest level, unrolled into launches; the coarsest levels
+// (0 .. fused_lc) run inside one block when they fit in its shared memory.
 template <typename T>
 int do_vcycle(igamg_handle* h, T* U, const T* F, cudaStream_t s) {
   auto& ty = typed<T>(h);
   const int L = (int)ty.lev.size();
   if (L == 1) return do_coarse<T>(h, F, U, s);
   int rc;
+  const int lc = ty.fused_lc;
+  if (lc == L - 1) return do_fused<T>(h, F, U, 1, s);
+  if (lc >= 1) {
+    for (int l = L - 1; l > lc; --l) {
+      T* Ul = (l == L - 1) ? U : ty.lev[l].U;
+      const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
+      if (l < L - 1) CK(cudaMemsetAsync(Ul, 0, ty.lev[l].L.n_total * sizeof(T), s));
+      for (int k = 0; k < h->prob.nu1; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+      if ((rc = do_residual<T>(h, l, Ul, Fl, ty.lev[l].R, nullptr, s))) return rc;
+      if ((rc = do_restrict<T>(h, l, ty.lev[l].R, ty.lev[l - 1].F, s))) return rc;
+    }
+    if ((rc = do_fused<T>(h, ty.lev[lc].F, ty.lev[lc].U, 0, s))) return rc;
+    for (int l = lc + 1; l <= L - 1; ++l) {
+      T* Ul = (l == L - 1) ? U : ty.lev[l].U;
+      const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
+      if ((rc = do_prolong<T>(h, l, ty.lev[l - 1].U, Ul, s))) return rc;
+      for (int k = 0; k < h->prob.nu2; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+    }
+    return IGAMG_OK;
+  }
   for (int l = L - 1; l >= 1; --l) {
     T* Ul = (l == L - 1) ? U : ty.lev[l].U;
     const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
@@ -275,7 +315,7 @@ int do_ir_step(igamg_handle* h, double* U, const double* F, cudaStream_t s) {
   CK(cudaMemsetAsync(top32.U, 0, Ld.n_total * sizeof(float), s));
   int rc = do_vcycle<float>(h, top32.U, top32.F, s);
   if (rc) return rc;
-  k_integrate_psi<<<nblk(Ld.nint, 128), 128, 0, s>>>(Ld.nint, Ld.nxu, h->lc[L - 1].inv_dcoef, top32.U, h->psi);
+  k_integrate_psi<<<nblk((long long)Ld.nint * 32, 128), 128, 0, s>>>(Ld.nint, Ld.nxu, h->lc[L - 1].inv_dcoef, top32.U, h->psi);
   k_curl_update<<<nblk(Ld.n_total), kBlock, 0, s>>>(Ld, h->lc[L - 1].dcoef, h->psi, top32.U, U);
   if ((rc = launch_check())) return rc;
   return do_residual<double>(h, L - 1, U, F, R64, h->norm2, s);
@@ -311,24 +351,91 @@ int ensure_graph(igamg_handle* h, int kind, double* U, const double* F) {
   return IGAMG_OK;
 }
 
-int read_norm(igamg_handle* h, double* out) {
-  CK(cudaMemcpyAsync(h->h_pinned, h->norm2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+int read_norm(igamg_handle* h, double* out, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h->h_pinned, h->norm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   *out = std::sqrt(h->h_pinned[0]);
   return IGAMG_OK;
 }
+int read_norm(igamg_handle* h, double* out) { return read_norm(h, out, h->stream); }
 
-int div_inf_impl(igamg_handle* h, const double* U, double* out) {
+int div_inf_impl(igamg_handle* h, const double* U, double* out, cudaStream_t s) {
   const int L = (int)h->d.lev.size();
   auto& Lt = h->d.lev[L - 1].L;
-  CK(cudaMemsetAsync(h->divmax, 0, sizeof(unsigned long long), h->stream));
-  k_div_inf<<<nblk(Lt.n_p), kBlock, 0, h->stream>>>(Lt, h->lc[L - 1].dcoef, U, h->divmax);
+  CK(cudaMemsetAsync(h->divmax, 0, sizeof(unsigned long long), s));
+  k_div_inf<<<nblk(Lt.n_p), kBlock, 0, s>>>(Lt, h->lc[L - 1].dcoef, U, h->divmax);
   int rc = launch_check();
   if (rc) return rc;
-  CK(cudaMemcpyAsync(h->h_pinned, h->divmax, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpyAsync(h->h_pinned, h->divmax, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   *out = h->h_pinned[0];
   return IGAMG_OK;
+}
+int div_inf_impl(igamg_handle* h, const double* U, double* out) { return div_inf_impl(h, U, out, h->stream); }
+
+// Several independent solves at once, each on its handle's own execution stream: one
+// round launches one captured step per unfinished solve, then reads all their norms.
+// Small solves are latency bound, so running them side by side fills the GPU.
+int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, double rtol, int max_cycles,
+                     igamg_report* reps, int* status) {
+  std::vector<double> r0(n, 0.0), rk(n, 0.0);
+  std::vector<int> k(n, 0), st(n, IGAMG_NOT_CONVERGED);
+  int rc;
+  for (int i = 0; i < n; ++i) {
+    igamg_handle* h = hs[i];
+    CK(cudaEventRecord(h->ev, h->stream));
+    CK(cudaStreamWaitEvent(h->exec_stream, h->ev, 0));
+    int L = (int)h->d.lev.size();
+    if ((rc = do_residual<double>(h, L - 1, Us[i], Fs[i], h->d.lev[L - 1].R, h->norm2, h->exec_stream))) return rc;
+    CK(cudaMemcpyAsync(h->h_pinned, h->norm2, sizeof(double), cudaMemcpyDeviceToHost, h->exec_stream));
+  }
+  for (int i = 0; i < n; ++i) {
+    CK(cudaStreamSynchronize(hs[i]->exec_stream));
+    r0[i] = rk[i] = std::sqrt(hs[i]->h_pinned[0]);
+    if (!std::isfinite(r0[i])) st[i] = IGAMG_ENONFINITE;
+    else if (r0[i] == 0.0) st[i] = IGAMG_OK;
+    if ((rc = ensure_graph(hs[i], 0, Us[i], Fs[i]))) return rc;
+  }
+  for (;;) {
+    int active = 0;
+    for (int i = 0; i < n; ++i) {
+      if (st[i] != IGAMG_NOT_CONVERGED || k[i] >= max_cycles) continue;
+      igamg_handle* h = hs[i];
+      CK(cudaGraphLaunch(h->graph[0], h->exec_stream));
+      CK(cudaMemcpyAsync(h->h_pinned, h->norm2, sizeof(double), cudaMemcpyDeviceToHost, h->exec_stream));
+      ++k[i];
+      ++active;
+    }
+    if (!active) break;
+    for (int i = 0; i < n; ++i) {
+      if (st[i] != IGAMG_NOT_CONVERGED || k[i] == 0) continue;
+      igamg_handle* h = hs[i];
+      CK(cudaStreamSynchronize(h->exec_stream));
+      rk[i] = std::sqrt(h->h_pinned[0]);
+      igamg_report* rep = reps ? &reps[i] : nullptr;
+      if (rep && rep->history && k[i] - 1 < rep->history_cap) rep->history[k[i] - 1] = rk[i] / r0[i];
+      if (!std::isfinite(rk[i])) st[i] = IGAMG_ENONFINITE;
+      else if (rk[i] <= rtol * r0[i]) st[i] = IGAMG_OK;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    igamg_handle* h = hs[i];
+    if (reps) {
+      reps[i].cycles = k[i]; reps[i].res0 = r0[i]; reps[i].rel_residual = r0[i] > 0 ? rk[i] / r0[i] : 0.0;
+      double dv = 0.0;
+      if ((rc = div_inf_impl(h, Us[i], &dv, h->exec_stream))) return rc;
+      reps[i].div_inf = dv;
+    }
+    CK(cudaEventRecord(h->ev, h->exec_stream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev, 0));
+    if (status) status[i] = st[i];
+  }
+  int worst = IGAMG_OK;
+  for (int i = 0; i < n; ++i) {
+    if (st[i] < 0) return st[i];
+    if (st[i] == IGAMG_NOT_CONVERGED) worst = IGAMG_NOT_CONVERGED;
+  }
+  return worst;
 }
 
 int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max_cycles, igamg_report* rep) {
@@ -370,6 +477,118 @@ LevelTab<T> make_tab(const igamg_sizes& sz, int p, const T* sx, const T* sy, con
   return L;
 }
 
+// Choose the coarse levels that run in one block (multiplicative smoother only): all
+// levels with at most 32 (FP64) / 64 (FP32) elements per direction whose vectors fit in
+// shared memory, and fill the kernel's level descriptors.
+template <typename T>
+int setup_fused(igamg_handle* h, Typed<T>& ty) {
+  ty.fused_lc = -1;
+  const int L = h->prob.n_levels;
+  if (h->prob.smoother != IGAMG_MULT || L < 2) return IGAMG_OK;
+  const int nmax = sizeof(T) == 8 ? 32 : 64;
+  const size_t limit = 200 * 1024;
+  int best = -1;
+  size_t best_bytes = 0;
+  for (int lc = 1; lc < L && lc < kMaxFused; ++lc) {
+    if (h->lc[lc].sz.n > nmax) break;
+    size_t words = 0;
+    int maxl = 0;
+    for (int l = 0; l <= lc; ++l) {
+      words += 3 * (size_t)((h->lc[l].sz.n_total + 3) / 4 * 4);
+      maxl = std::max(maxl, h->lc[l].maxl);
+    }
+    words += 32 * (size_t)maxl;
+    size_t bytes = words * sizeof(T);
+    if (bytes > limit) break;
+    if (h->lc[lc].n_colours > kMaxColours) break;
+    best = lc; best_bytes = bytes;
+  }
+  ty.fused_max = best;
+  if (best < 1) return IGAMG_OK;
+  FusedDesc<T>& D = ty.fused;
+  D = FusedDesc<T>{};
+  D.nlev = best + 1; D.nu1 = h->prob.nu1; D.nu2 = h->prob.nu2; D.ndof0 = h->ndof0 ? h->ndof0 : h->host.ndof0;
+  D.coarse_inv = ty.coarse_inv;
+  int off = 0;
+  int maxl = 0;
+  for (int l = 0; l <= best; ++l) {
+    FusedLevel<T>& V = D.lev[l];
+    const auto& lc = h->lc[l];
+    V.L = ty.lev[l].L; V.tp = ty.lev[l].tp; V.tq = ty.lev[l].tq; V.cinv = ty.lev[l].cinv;
+    V.dofs = lc.dofs; V.cls = lc.cls; V.nloc = lc.nloc; V.maxl = lc.maxl; V.n_colours = lc.n_colours;
+    for (int k = 0; k <= lc.n_colours && l >= 1; ++k) V.colour_off[k] = lc.colour_off[k];
+    for (int k = 0; k < lc.n_colours && l >= 1; ++k) V.n8[k] = lc.n8[k];
+    int nt = (int)((lc.sz.n_total + 3) / 4 * 4);
+    V.offU = off; off += nt;
+    V.offF = off; off += nt;
+    V.offR = off; off += nt;
+    maxl = std::max(maxl, lc.maxl);
+  }
+  D.scratch_off = off;
+  ty.fused_smem = best_bytes;
+  ty.fused_lc = best;           // refined by autotune_fused
+  cudaError_t e = h->prob.p == 2
+      ? cudaFuncSetAttribute(k_fused_coarse<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best_bytes)
+      : cudaFuncSetAttribute(k_fused_coarse<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best_bytes);
+  if (e != cudaSuccess) { g_err = cudaGetErrorString(e); return IGAMG_ECUDA; }
+  return IGAMG_OK;
+}
+
+// Autotuner: time a few V-cycles with each feasible depth of the one-block coarse part
+// (none, levels 0..1, 0..2, ...) and keep the fastest.  The choice depends only on the
+// shape (p, n_fine, levels, value type, smoother) and is cached per process.
+struct TuneKey {
+  int p, n, L, bytes, sm, nu1, nu2;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(p, n, L, bytes, sm, nu1, nu2) < std::tie(o.p, o.n, o.L, o.bytes, o.sm, o.nu1, o.nu2);
+  }
+};
+std::map<TuneKey, int>& tune_cache() { static std::map<TuneKey, int> m; return m; }
+std::mutex& tune_mutex() { static std::mutex m; return m; }
+
+template <typename T>
+int autotune_fused(igamg_handle* h, Typed<T>& ty) {
+  if (ty.fused_max < 1) { ty.fused_lc = -1; return IGAMG_OK; }
+  const int L = h->prob.n_levels;
+  TuneKey key{h->prob.p, h->prob.n_fine, L, (int)sizeof(T), h->prob.smoother, h->prob.nu1, h->prob.nu2};
+  const char* env = std::getenv("IGAMG_FUSED_LEVELS");   // fixed choice (tests, experiments)
+  if (env) { ty.fused_lc = std::min(std::atoi(env), ty.fused_max); if (ty.fused_lc < 1) ty.fused_lc = -1; return IGAMG_OK; }
+  {
+    std::lock_guard<std::mutex> lk(tune_mutex());
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end()) { ty.fused_lc = it->second; return IGAMG_OK; }
+  }
+  T* U = ty.lev[L - 1].U;
+  T* F = ty.lev[L - 1].F;
+  size_t nb = (size_t)ty.lev[L - 1].L.n_total * sizeof(T);
+  CK(cudaMemsetAsync(U, 0, nb, h->stream));
+  CK(cudaMemsetAsync(F, 0, nb, h->stream));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  int best = -1;
+  for (int cand = -1; cand <= ty.fused_max; ++cand) {
+    if (cand == 0) continue;
+    ty.fused_lc = cand;
+    int rc = do_vcycle<T>(h, U, F, h->stream);
+    if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+    CK(cudaEventRecord(e0, h->stream));
+    for (int r = 0; r < 3; ++r) if ((rc = do_vcycle<T>(h, U, F, h->stream))) return rc;
+    CK(cudaEventRecord(e1, h->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) { best_ms = ms; best = cand; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ty.fused_lc = best;
+  std::lock_guard<std::mutex> lk(tune_mutex());
+  tune_cache()[key] = best;
+  return IGAMG_OK;
+}
+
 // Upload the typed (double or float) copy of every level's tables and workspaces.
 template <typename T>
 int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
@@ -400,7 +619,7 @@ int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
   }
   if ((rc = upload_as(h, &ty.coarse_inv, h->host.coarse_inv))) return rc;
   if ((rc = dmalloc(h, (void**)&ty.delta, std::max<size_t>(max_delta, 1) * sizeof(T)))) return rc;
-  return IGAMG_OK;
+  return setup_fused<T>(h, ty);
 }
 
 int validate(const igamg_problem& pr) {
@@ -472,9 +691,9 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
           (rc = upload_as(h, &lc.d2p_idx, pt.d2p_idx)))
         return fail(rc);
       max_delta = std::max(max_delta, (size_t)pt.n_patches * pt.maxl);
-      if (pt.maxl > (p == 2 ? MaxLocal<2>::value : MaxLocal<3>::value)) return fail(IGAMG_EUNSUPPORTED);
     }
   }
+  h->ndof0 = h->host.ndof0;
   if ((rc = upload_typed<double>(h, h->d, max_delta))) return fail(rc);
   if (pr.precision == IGAMG_FP32_IR && (rc = upload_typed<float>(h, h->f, max_delta))) return fail(rc);
   h->ndof0 = h->host.ndof0;
@@ -490,6 +709,10 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
   size_t nint = (size_t)(pr.n_fine + p - 2);
   if ((rc = dmalloc(h, (void**)&h->psi, nint * nint * sizeof(double)))) return fail(rc);
   if (cudaMallocHost((void**)&h->h_pinned, 2 * sizeof(double)) != cudaSuccess) return fail(IGAMG_ECUDA);
+  if ((rc = autotune_fused<double>(h, h->d))) return fail(rc);
+  if (pr.precision == IGAMG_FP32_IR && (rc = autotune_fused<float>(h, h->f))) return fail(rc);
+  if (cudaStreamCreateWithFlags(&h->exec_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(IGAMG_ECUDA);
+  if (cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess) return fail(IGAMG_ECUDA);
   *out = h;
   return IGAMG_OK;
 }
@@ -500,6 +723,8 @@ void igamg_destroy(igamg_handle* h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->exec_stream) cudaStreamDestroy(h->exec_stream);
+  if (h->ev) cudaEventDestroy(h->ev);
   delete h;
 }
 
@@ -585,6 +810,16 @@ int igamg_solve_host(igamg_handle* h, const double* f_qp_host, double* U_host, d
   return st;
 }
 
+int igamg_solve_batch(int n, igamg_handle** handles, double** U, const double** F, double rtol, int max_cycles,
+                      igamg_report* reports, int* status) {
+  if (n < 0 || (n > 0 && (!handles || !U || !F)) || !(rtol >= 0) || max_cycles < 0) return IGAMG_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!handles[i] || !U[i] || !F[i]) return IGAMG_EINVAL;
+    for (int j = 0; j < i; ++j) if (handles[j] == handles[i]) return IGAMG_EINVAL;
+  }
+  return solve_batch_impl(n, handles, U, F, rtol, max_cycles, reports, status);
+}
+
 int igamg_div_inf(igamg_handle* h, const double* U, double* out) {
   if (!h || !U || !out) return IGAMG_EINVAL;
   return div_inf_impl(h, U, out);
@@ -634,8 +869,8 @@ extern "C" int igamg_residual_static(const igamg_problem* prob, int level, const
   // size check before any work: class stencil tables + partials + the norm slot
   igamg_sizes sz = level_sizes(p, n);
   const int TC = 2 * p + 1, NC = 2 * TC + 1;
-  const size_t RX = (size_t)(4 * p + 1) * (2 * p - 1), RP = (size_t)4 * p * (2 * p - 1) + 1;
-  const size_t n_tab = (size_t)NC * NC * (2 * RX + RP);
+  const size_t RU = (size_t)(2 * p + 1) * (2 * p - 1) + (size_t)2 * p * (2 * p - 1) + 1;
+  const size_t n_tab = (size_t)NC * NC * 3 * RU;
   const unsigned nb = nblk(sz.n_total - 1);
   const size_t need = n_tab + 2 * (size_t)nb + 1;
   if (need > kStaticScratchDoubles) {

@@ -64,11 +64,17 @@ struct PatchTables {
 // of its two indices (cls1 below): positions within T of either end are their own class,
 // all others share the translation-invariant interior class.  Coefficients of neighbours
 // outside the index range are stored as zero.
-//   u_x rows: A[dx][dy] (dx in -p..p, dy in -q..q) then B[kx][dy] (kx in -p..p-1)   RX values
-//   u_y rows: A[dx][dy] (dx in -q..q, dy in -p..p) then B[dx][ky] (ky in -p..p-1)   RX values
-//   p rows:   Bx[s][dy] (s in -q..p, dy in -q..q), By[dx][s], then m                  RP values
+// Every record has the same length RU = B0 + B1 + 1 so that all row kinds run the same
+// unconditional loops: box 0 (B0 = (2p+1)(2p-1) entries), box 1 (B1 = 2p(2p-1)), then the
+// lambda coefficient; boxes are stored x-major (y fastest), shorter boxes zero-padded.
+//   u_x rows: box 0 = A_xx over u_x (dx in -p..p, dy in -q..q), box 1 = -B_x over p
+//             (kx in -p..p-1, dy in -q..q), last 0
+//   u_y rows: box 0 = A_yy over u_y (dx in -q..q, dy in -p..p), box 1 = -B_y over p
+//             (dx in -q..q, ky in -p..p-1), last 0
+//   p rows:   box 0 = B_x^T over u_x (s in -q..p, dy in -q..q), box 1 = B_y^T over u_y
+//             (dx in -q..q, s in -q..p), last m_k
 struct Stencils {
-  int T = 0, NC = 0, RX = 0, RP = 0;
+  int T = 0, NC = 0, B0 = 0, B1 = 0, RU = 0;
   std::vector<double> sx, sy, sp;
 };
 

@@ -29,21 +29,19 @@ struct Xfer {                            // 1D prolongation, two banded views
 
 constexpr int kWP = 3, kWR = 5;          // Transfer1D::WP / WR
 
-// largest local system of a patch for even n >= 2 (the corner / whole-domain patches):
-// 12 + 9 DOFs for P = 2, 24 + 16 for P = 3
-template <int P>
-struct MaxLocal { static constexpr int value = P == 2 ? 21 : 40; };
-
-// acc = sum_s a[s] r[s] for s < nl <= ML, unrolled so that all loads issue together.
-template <int ML, typename T>
-__device__ __forceinline__ T dot_bounded(const T* __restrict__ a, const T* r, int nl) {
-  T s0 = T(0), s1 = T(0);
-#pragma unroll
-  for (int s = 0; s < ML; s += 2) {
-    if (s < nl) s0 = fma(a[s], r[s], s0);
-    if (s + 1 < ML && s + 1 < nl) s1 = fma(a[s + 1], r[s + 1], s1);
+// acc = sum_{s < nl} a[s] r[s] with four independent chains (loads issue together).
+template <typename T>
+__device__ __forceinline__ T dot_n(const T* __restrict__ a, const T* r, int nl) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int s = 0;
+  for (; s + 4 <= nl; s += 4) {
+    s0 = fma(a[s], r[s], s0);
+    s1 = fma(a[s + 1], r[s + 1], s1);
+    s2 = fma(a[s + 2], r[s + 2], s2);
+    s3 = fma(a[s + 3], r[s + 3], s3);
   }
-  return s0 + s1;
+  for (; s < nl; ++s) s0 = fma(a[s], r[s], s0);
+  return (s0 + s1) + (s2 + s3);
 }
 
 template <int P>
@@ -55,90 +53,64 @@ __host__ __device__ __forceinline__ int cls1d(int i, int last) {
 __host__ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // (K U)_g for one row g (not the lambda row): Sec. 3.4 blocks [A -B; B^T 0] plus m lambda.
+//
+// Every row is two boxes of neighbours (velocity part, then pressure or second velocity
+// part) plus the m lambda term.  All three row kinds run the same unconditional loops
+// over fixed-size, zero-padded stencil records with clamped (always valid) neighbour
+// indices: no lane diverges on the row kind (each FP64 instruction already costs 64 issue
+// cycles per warp on GB300) and every load can be issued ahead of the FMAs.
 template <int P, typename T>
 __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __restrict__ U, int g) {
   constexpr int Q = P - 1, TC = 2 * P + 1, NC = 2 * TC + 1;
-  constexpr int WQ = 2 * Q + 1, WPP = 2 * P + 1, RX = (4 * P + 1) * WQ, RP = 4 * P * WQ + 1;
-  const T* ux = U;
-  const T* uy = U + L.n_ux;
-  const T* pr = U + L.n_ux + L.n_uy;
-  T acc = T(0), acc2 = T(0);   // two chains: shorter FP64 dependency
-  if (g < L.n_ux) {
-    int iy = g / L.nxu, ix = g - iy * L.nxu + 1;
-    const T* st = L.sx + (cls1d<P>(ix, L.lastp) * NC + cls1d<P>(iy, L.lastq)) * RX;
+  constexpr int WQ = 2 * Q + 1, WPP = 2 * P + 1;
+  constexpr int B0 = WPP * WQ, B1 = 2 * P * WQ, RU = B0 + B1 + 1;
+  const int nu = L.n_ux + L.n_uy;
+  const bool is_x = g < L.n_ux, is_p = g >= nu, is_y = !is_x && !is_p;
+  const int off = is_x ? 0 : (is_p ? nu : L.n_ux);
+  const int rs = is_x ? L.nxu : L.npd;
+  const int r = g - off;
+  const int q_ = r / rs;
+  const int iy = q_ + (is_y ? 1 : 0);
+  const int ix = r - q_ * rs + (is_x ? 1 : 0);
+  const int cx = cls1d<P>(ix, is_x ? L.lastp : L.lastq);
+  const int cy = cls1d<P>(iy, is_y ? L.lastp : L.lastq);
+  const T* st = (is_x ? L.sx : (is_p ? L.sp : L.sy)) + (cx * NC + cy) * RU;
+  // box 0: own velocity block (u rows) or u_x (p rows)
+  const int b0_base = is_y ? L.n_ux : 0;
+  const int b0_stride = is_y ? L.npd : L.nxu;
+  const int b0_x0 = is_x ? -P : -Q, b0_y0 = is_y ? -P : -Q, b0_wy = is_y ? WPP : WQ;
+  const int b0_xlo = is_y ? 0 : 1, b0_xhi = is_y ? L.lastq : L.nint, b0_xsh = is_y ? 0 : 1;
+  const int b0_ylo = is_y ? 1 : 0, b0_yhi = is_y ? L.nint : L.lastq, b0_ysh = is_y ? 1 : 0;
+  // box 1: pressure (u rows) or u_y (p rows)
+  const int b1_base = is_p ? L.n_ux : nu;
+  const int b1_x0 = is_x ? -P : -Q, b1_y0 = is_x ? -Q : (is_p ? -Q : -P), b1_wy = is_x ? WQ : 2 * P;
+  const int b1_ylo = is_p ? 1 : 0, b1_yhi = is_p ? L.nint : L.lastq, b1_ysh = is_p ? 1 : 0;
+  T acc = T(0), acc2 = T(0);
 #pragma unroll
-    for (int dx = -P; dx <= P; ++dx) {
-      int jx = clampi(ix + dx, 1, L.nint) - 1;
-#pragma unroll
-      for (int dy = -Q; dy <= Q; ++dy) {
-        int jy = clampi(iy + dy, 0, L.lastq);
-        acc = fma(st[(dx + P) * WQ + dy + Q], ux[jy * L.nxu + jx], acc);
-      }
-    }
-#pragma unroll
-    for (int kx = -P; kx <= P - 1; ++kx) {
-      int jx = clampi(ix + kx, 0, L.lastq);
-#pragma unroll
-      for (int dy = -Q; dy <= Q; ++dy) {
-        int jy = clampi(iy + dy, 0, L.lastq);
-        acc2 = fma(st[WPP * WQ + (kx + P) * WQ + dy + Q], pr[jy * L.npd + jx], acc2);
-      }
-    }
-  } else if (g < L.n_ux + L.n_uy) {
-    int r = g - L.n_ux;
-    int iy = r / L.npd + 1, ix = r - (iy - 1) * L.npd;
-    const T* st = L.sy + (cls1d<P>(ix, L.lastq) * NC + cls1d<P>(iy, L.lastp)) * RX;
-#pragma unroll
-    for (int dx = -Q; dx <= Q; ++dx) {
-      int jx = clampi(ix + dx, 0, L.lastq);
-#pragma unroll
-      for (int dy = -P; dy <= P; ++dy) {
-        int jy = clampi(iy + dy, 1, L.nint) - 1;
-        acc = fma(st[(dx + Q) * WPP + dy + P], uy[jy * L.npd + jx], acc);
-      }
-    }
-#pragma unroll
-    for (int dx = -Q; dx <= Q; ++dx) {
-      int jx = clampi(ix + dx, 0, L.lastq);
-#pragma unroll
-      for (int ky = -P; ky <= P - 1; ++ky) {
-        int jy = clampi(iy + ky, 0, L.lastq);
-        acc2 = fma(st[WQ * WPP + (dx + Q) * (2 * P) + ky + P], pr[jy * L.npd + jx], acc2);
-      }
-    }
-  } else {
-    int r = g - L.n_ux - L.n_uy;
-    int ky = r / L.npd, kx = r - ky * L.npd;
-    const T* st = L.sp + (cls1d<P>(kx, L.lastq) * NC + cls1d<P>(ky, L.lastq)) * RP;
-#pragma unroll
-    for (int s = -Q; s <= P; ++s) {
-      int ix = clampi(kx + s, 1, L.nint) - 1;
-#pragma unroll
-      for (int dy = -Q; dy <= Q; ++dy) {
-        int iy = clampi(ky + dy, 0, L.lastq);
-        acc = fma(st[(s + Q) * WQ + dy + Q], ux[iy * L.nxu + ix], acc);
-      }
-    }
-#pragma unroll
-    for (int dx = -Q; dx <= Q; ++dx) {
-      int ix = clampi(kx + dx, 0, L.lastq);
-#pragma unroll
-      for (int s = -Q; s <= P; ++s) {
-        int iy = clampi(ky + s, 1, L.nint) - 1;
-        acc2 = fma(st[2 * P * WQ + (dx + Q) * (2 * P) + s + Q], uy[iy * L.npd + ix], acc2);
-      }
-    }
-    acc = fma(st[RP - 1], U[L.n_total - 1], acc);
+  for (int j = 0; j < B0; ++j) {
+    int dx = j / b0_wy, dy = j - dx * b0_wy;
+    int x = clampi(ix + b0_x0 + dx, b0_xlo, b0_xhi) - b0_xsh;
+    int y = clampi(iy + b0_y0 + dy, b0_ylo, b0_yhi) - b0_ysh;
+    acc = fma(st[j], U[b0_base + y * b0_stride + x], acc);
   }
+#pragma unroll
+  for (int j = 0; j < B1; ++j) {
+    int dx = j / b1_wy, dy = j - dx * b1_wy;
+    int x = clampi(ix + b1_x0 + dx, 0, L.lastq);
+    int y = clampi(iy + b1_y0 + dy, b1_ylo, b1_yhi) - b1_ysh;
+    acc2 = fma(st[B0 + j], U[b1_base + y * L.npd + x], acc2);
+  }
+  acc = fma(st[RU - 1], U[L.n_total - 1], acc);
   return acc + acc2;
 }
 
 // m_k for a pressure row (the last stencil entry).
 template <int P, typename T>
 __device__ __forceinline__ T mean_coef(const LevelTab<T>& L, int r) {
-  constexpr int Q = P - 1, TC = 2 * P + 1, NC = 2 * TC + 1, RP = 4 * P * (2 * Q + 1) + 1;
+  constexpr int Q = P - 1, TC = 2 * P + 1, NC = 2 * TC + 1;
+  constexpr int RU = (2 * P + 1) * (2 * Q + 1) + 2 * P * (2 * Q + 1) + 1;
   int ky = r / L.npd, kx = r - ky * L.npd;
-  return L.sp[(cls1d<P>(kx, L.lastq) * NC + cls1d<P>(ky, L.lastq)) * RP + RP - 1];
+  return L.sp[(cls1d<P>(kx, L.lastq) * NC + cls1d<P>(ky, L.lastq)) * RU + RU - 1];
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -190,10 +162,104 @@ __global__ void k_residual_finish(int n_total, const T* __restrict__ F, T* __res
   }
 }
 
-// One colour of the multiplicative Schwarz sweep (eq. MSM).  Blocks [0, nb8): four
-// 8-DOF patches per warp, lane = (patch, local row); the local residual row, then the
-// bordered local inverse applied through shuffles.  Blocks [nb8, ...): one warp per
-// larger (wall) patch.  Same-colour patches share no DOF and are not coupled by K.
+// ---- building blocks shared by the per-level kernels and the fused coarse-level kernel --
+
+// One lane of an 8-DOF patch (four patches per warp, lane = (patch, local row)): the local
+// residual row, then the bordered local inverse through shuffles, then the update.  All
+// 32 lanes of the warp must call it together (the shuffles span the warp).
+template <int P, typename T>
+__device__ __forceinline__ void fast_patch_lane(const LevelTab<T>& L, T* U, const T* F, const int* __restrict__ dofs,
+                                                const int* __restrict__ cls, const T* __restrict__ cinv, int maxl,
+                                                int first, int n8, int grp, int lane) {
+  int row = lane & 7;
+  bool active = grp < n8;
+  int patch = first + (active ? grp : 0);
+  int g = dofs[patch * maxl + row];
+  T r = F[g] - row_KU<P>(L, U, g);
+  const T* A = cinv + ((size_t)cls[patch] * maxl + row) * maxl;
+  T d0 = T(0), d1 = T(0);
+#pragma unroll
+  for (int s = 0; s < 8; s += 2) {
+    d0 = fma(A[s], __shfl_sync(0xffffffffu, r, (lane & ~7) + s), d0);
+    d1 = fma(A[s + 1], __shfl_sync(0xffffffffu, r, (lane & ~7) + s + 1), d1);
+  }
+  if (active) U[g] += d0 + d1;
+}
+
+// A larger (wall) patch solved by one warp; r is warp-private scratch of maxl entries.
+template <int P, typename T>
+__device__ __forceinline__ void general_patch_warp(const LevelTab<T>& L, T* U, const T* F, const int* __restrict__ dofs,
+                                                   const int* __restrict__ cls, const T* __restrict__ cinv,
+                                                   const int* __restrict__ nloc, int maxl, int patch, int lane, T* r) {
+  int c = cls[patch], nl = nloc[c];
+  const int* pd = dofs + (size_t)patch * maxl;
+  for (int k = lane; k < nl; k += 32) { int g = pd[k]; r[k] = F[g] - row_KU<P>(L, U, g); }
+  __syncwarp();
+  const T* A = cinv + (size_t)c * maxl * maxl;
+  for (int k = lane; k < nl; k += 32) U[pd[k]] += dot_n(A + (size_t)k * maxl, r, nl);
+  __syncwarp();
+}
+
+// g_c = P^T r_f at coarse entry g (not lambda).
+template <typename T>
+__device__ __forceinline__ T restrict_elem(const LevelTab<T>& Lf, const LevelTab<T>& Lc, const Xfer<T>& tp,
+                                           const Xfer<T>& tq, const T* rf, int g) {
+  int cx, cy, fnx;
+  const T* src;
+  bool bx_p, by_p;
+  if (g < Lc.n_ux) { cy = g / Lc.nxu; cx = g - cy * Lc.nxu; bx_p = true; by_p = false; src = rf; fnx = Lf.nxu; }
+  else if (g < Lc.n_ux + Lc.n_uy) { int r = g - Lc.n_ux; cy = r / Lc.npd; cx = r - cy * Lc.npd; bx_p = false; by_p = true; src = rf + Lf.n_ux; fnx = Lf.npd; }
+  else { int r = g - Lc.n_ux - Lc.n_uy; cy = r / Lc.npd; cx = r - cy * Lc.npd; bx_p = false; by_p = false; src = rf + Lf.n_ux + Lf.n_uy; fnx = Lf.npd; }
+  const int* fx0p = bx_p ? tp.f0 : tq.f0; const T* rx = bx_p ? tp.rv : tq.rv; int nfx = bx_p ? tp.nf : tq.nf;
+  const int* fy0p = by_p ? tp.f0 : tq.f0; const T* ry = by_p ? tp.rv : tq.rv; int nfy = by_p ? tp.nf : tq.nf;
+  int fx0 = fx0p[cx], fy0 = fy0p[cy];
+  T acc = T(0);
+#pragma unroll
+  for (int ky = 0; ky < kWR; ++ky) {
+    int fy = min(fy0 + ky, nfy - 1);            // weights past the end are zero
+    T wy = ry[cy * kWR + ky];
+    T s = T(0);
+#pragma unroll
+    for (int kx = 0; kx < kWR; ++kx) {
+      int fx = min(fx0 + kx, nfx - 1);
+      s = fma(rx[cx * kWR + kx], src[fy * fnx + fx], s);
+    }
+    acc = fma(wy, s, acc);
+  }
+  return acc;
+}
+
+// (P u_c) at fine entry g (not lambda).
+template <typename T>
+__device__ __forceinline__ T prolong_elem(const LevelTab<T>& Lf, const LevelTab<T>& Lc, const Xfer<T>& tp,
+                                          const Xfer<T>& tq, const T* uc, int g) {
+  int fx, fy, cnx;
+  const T* src;
+  bool bx_p, by_p;
+  if (g < Lf.n_ux) { fy = g / Lf.nxu; fx = g - fy * Lf.nxu; bx_p = true; by_p = false; src = uc; cnx = Lc.nxu; }
+  else if (g < Lf.n_ux + Lf.n_uy) { int r = g - Lf.n_ux; fy = r / Lf.npd; fx = r - fy * Lf.npd; bx_p = false; by_p = true; src = uc + Lc.n_ux; cnx = Lc.npd; }
+  else { int r = g - Lf.n_ux - Lf.n_uy; fy = r / Lf.npd; fx = r - fy * Lf.npd; bx_p = false; by_p = false; src = uc + Lc.n_ux + Lc.n_uy; cnx = Lc.npd; }
+  const int* cx0p = bx_p ? tp.c0 : tq.c0; const T* px = bx_p ? tp.pv : tq.pv; int ncx = bx_p ? tp.nc : tq.nc;
+  const int* cy0p = by_p ? tp.c0 : tq.c0; const T* py = by_p ? tp.pv : tq.pv; int ncy = by_p ? tp.nc : tq.nc;
+  int cx0 = cx0p[fx], cy0 = cy0p[fy];
+  T acc = T(0);
+#pragma unroll
+  for (int ky = 0; ky < kWP; ++ky) {
+    int cy = min(cy0 + ky, ncy - 1);            // weights past the end are zero
+    T s = T(0);
+#pragma unroll
+    for (int kx = 0; kx < kWP; ++kx) {
+      int cx = min(cx0 + kx, ncx - 1);
+      s = fma(px[fx * kWP + kx], src[cy * cnx + cx], s);
+    }
+    acc = fma(py[fy * kWP + ky], s, acc);
+  }
+  return acc;
+}
+
+// One colour of the multiplicative Schwarz sweep (eq. MSM).  Blocks [0, nb8): four 8-DOF
+// patches per warp.  Blocks [nb8, ...): one warp per larger (wall) patch.  Same-colour
+// patches share no DOF and are not coupled by K, so they may be solved in any order.
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_mult_colour(LevelTab<T> L, T* __restrict__ U, const T* __restrict__ F,
                                                      const int* __restrict__ dofs, const int* __restrict__ cls,
@@ -201,31 +267,14 @@ __global__ void __launch_bounds__(256) k_mult_colour(LevelTab<T> L, T* __restric
                                                      int maxl, int first, int n8, int ngen, int nb8) {
   int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if ((int)blockIdx.x < nb8) {
-    int grp = (blockIdx.x * 8 + wib) * 4 + (lane >> 3);
-    int row = lane & 7;
-    bool active = grp < n8;
-    int patch = first + (active ? grp : 0);
-    int g = dofs[patch * maxl + row];
-    T r = active ? F[g] - row_KU<P>(L, U, g) : T(0);
-    const T* A = cinv + ((size_t)cls[patch] * maxl + row) * maxl;
-    T d = T(0);
-#pragma unroll
-    for (int s = 0; s < 8; ++s) d = fma(A[s], __shfl_sync(0xffffffffu, r, (lane & ~7) + s), d);
-    if (active) U[g] += d;
+    fast_patch_lane<P>(L, U, F, dofs, cls, cinv, maxl, first, n8, (blockIdx.x * 8 + wib) * 4 + (lane >> 3), lane);
     return;
   }
   extern __shared__ unsigned char smem_raw[];
   T* sh = reinterpret_cast<T*>(smem_raw);
   int w = ((int)blockIdx.x - nb8) * 8 + wib;
   if (w >= ngen) return;
-  int patch = first + n8 + w;
-  int c = cls[patch], nl = nloc[c];
-  T* r = sh + wib * maxl;
-  const int* pd = dofs + (size_t)patch * maxl;
-  for (int k = lane; k < nl; k += 32) { int g = pd[k]; r[k] = F[g] - row_KU<P>(L, U, g); }
-  __syncwarp();
-  const T* A = cinv + (size_t)c * maxl * maxl;
-  for (int k = lane; k < nl; k += 32) U[pd[k]] += dot_bounded<MaxLocal<P>::value>(A + (size_t)k * maxl, r, nl);
+  general_patch_warp<P>(L, U, F, dofs, cls, cinv, nloc, maxl, first + n8 + w, lane, sh + wib * maxl);
 }
 
 // Additive sweep (eq. ASM), part 1: local corrections from one common residual, kept per patch.
@@ -246,7 +295,7 @@ __global__ void __launch_bounds__(256) k_add_local(const T* __restrict__ R, cons
   __syncwarp();
   const T* A = cinv + (size_t)c * maxl * maxl;
   for (int k = lane; k < nl; k += 32)
-    delta[(size_t)warp * maxl + k] = dot_bounded<MaxLocal<P>::value>(A + (size_t)k * maxl, r, nl);
+    delta[(size_t)warp * maxl + k] = dot_n(A + (size_t)k * maxl, r, nl);
 }
 
 // Additive sweep, part 2: U_g += eta * (sum of the corrections of the patches holding g).
@@ -260,42 +309,13 @@ __global__ void k_add_gather(int n, T* __restrict__ U, const T* __restrict__ del
   if (off[g + 1] > off[g]) U[g] += eta * s;
 }
 
-// block of a coarse/fine vector: (x count, first entry, which 1D views in x and y)
-template <typename T>
-struct BlockView { int x, y, nx; const T* base; };
-
 // g_c = P^T r_f (lambda copied); one thread per coarse entry.
 template <typename T>
 __global__ void k_restrict(LevelTab<T> Lf, LevelTab<T> Lc, Xfer<T> tp, Xfer<T> tq, const T* __restrict__ rf,
                            T* __restrict__ gc) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= Lc.n_total) return;
-  if (g == Lc.n_total - 1) { gc[g] = rf[Lf.n_total - 1]; return; }
-  int cx, cy, fnx;
-  const T* src;
-  bool bx_p, by_p;
-  if (g < Lc.n_ux) { cy = g / Lc.nxu; cx = g - cy * Lc.nxu; bx_p = true; by_p = false; src = rf; fnx = Lf.nxu; }
-  else if (g < Lc.n_ux + Lc.n_uy) { int r = g - Lc.n_ux; cy = r / Lc.npd; cx = r - cy * Lc.npd; bx_p = false; by_p = true; src = rf + Lf.n_ux; fnx = Lf.npd; }
-  else { int r = g - Lc.n_ux - Lc.n_uy; cy = r / Lc.npd; cx = r - cy * Lc.npd; bx_p = false; by_p = false; src = rf + Lf.n_ux + Lf.n_uy; fnx = Lf.npd; }
-  const int* fx0p = bx_p ? tp.f0 : tq.f0; const T* rx = bx_p ? tp.rv : tq.rv; int nfx = bx_p ? tp.nf : tq.nf;
-  const int* fy0p = by_p ? tp.f0 : tq.f0; const T* ry = by_p ? tp.rv : tq.rv; int nfy = by_p ? tp.nf : tq.nf;
-  int fx0 = fx0p[cx], fy0 = fy0p[cy];
-  T acc = T(0);
-#pragma unroll
-  for (int ky = 0; ky < kWR; ++ky) {
-    int fy = fy0 + ky;
-    T wy = ry[cy * kWR + ky];
-    if (fy >= nfy) continue;
-    T s = T(0);
-#pragma unroll
-    for (int kx = 0; kx < kWR; ++kx) {
-      int fx = fx0 + kx;
-      if (fx >= nfx) continue;
-      s = fma(rx[cx * kWR + kx], src[fy * fnx + fx], s);
-    }
-    acc = fma(wy, s, acc);
-  }
-  gc[g] = acc;
+  gc[g] = (g == Lc.n_total - 1) ? rf[Lf.n_total - 1] : restrict_elem(Lf, Lc, tp, tq, rf, g);
 }
 
 // u_f += P u_c (lambda added); one thread per fine entry.
@@ -304,31 +324,7 @@ __global__ void k_prolong_add(LevelTab<T> Lf, LevelTab<T> Lc, Xfer<T> tp, Xfer<T
                               T* __restrict__ uf) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= Lf.n_total) return;
-  if (g == Lf.n_total - 1) { uf[g] += uc[Lc.n_total - 1]; return; }
-  int fx, fy, cnx;
-  const T* src;
-  bool bx_p, by_p;
-  if (g < Lf.n_ux) { fy = g / Lf.nxu; fx = g - fy * Lf.nxu; bx_p = true; by_p = false; src = uc; cnx = Lc.nxu; }
-  else if (g < Lf.n_ux + Lf.n_uy) { int r = g - Lf.n_ux; fy = r / Lf.npd; fx = r - fy * Lf.npd; bx_p = false; by_p = true; src = uc + Lc.n_ux; cnx = Lc.npd; }
-  else { int r = g - Lf.n_ux - Lf.n_uy; fy = r / Lf.npd; fx = r - fy * Lf.npd; bx_p = false; by_p = false; src = uc + Lc.n_ux + Lc.n_uy; cnx = Lc.npd; }
-  const int* cx0p = bx_p ? tp.c0 : tq.c0; const T* px = bx_p ? tp.pv : tq.pv; int ncx = bx_p ? tp.nc : tq.nc;
-  const int* cy0p = by_p ? tp.c0 : tq.c0; const T* py = by_p ? tp.pv : tq.pv; int ncy = by_p ? tp.nc : tq.nc;
-  int cx0 = cx0p[fx], cy0 = cy0p[fy];
-  T acc = T(0);
-#pragma unroll
-  for (int ky = 0; ky < kWP; ++ky) {
-    int cy = cy0 + ky;
-    if (cy >= ncy) continue;
-    T s = T(0);
-#pragma unroll
-    for (int kx = 0; kx < kWP; ++kx) {
-      int cx = cx0 + kx;
-      if (cx >= ncx) continue;
-      s = fma(px[fx * kWP + kx], src[cy * cnx + cx], s);
-    }
-    acc = fma(py[fy * kWP + ky], s, acc);
-  }
-  uf[g] += acc;
+  uf[g] += (g == Lf.n_total - 1) ? uc[Lc.n_total - 1] : prolong_elem(Lf, Lc, tp, tq, uc, g);
 }
 
 // U = K_0^{-1} G (dense inverse, one block).
@@ -342,9 +338,119 @@ __global__ void k_coarse(int n, const T* __restrict__ Kinv, const T* __restrict_
   for (int i = threadIdx.x >> 5; i < n; i += nw) {
     const T* row = Kinv + (size_t)i * n;
     T acc = T(0);
+#pragma unroll 4
     for (int j = lane; j < n; j += 32) acc = fma(row[j], g[j], acc);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) U[i] = acc;
+  }
+}
+
+// ---- the coarse end of the V-cycle in one thread block ------------------------------------
+constexpr int kMaxFused = 8;        // levels handled by one fused launch
+constexpr int kMaxColours = 16;     // (p+1)^2 for p <= 3
+
+template <typename T>
+struct FusedLevel {
+  LevelTab<T> L;
+  Xfer<T> tp, tq;                   // transfer from the level below into this one (l >= 1)
+  const T* cinv;
+  const int *dofs, *cls, *nloc;
+  int maxl, n_colours;
+  int colour_off[kMaxColours + 1], n8[kMaxColours];
+  int offU, offF, offR;             // offsets of this level's vectors in shared memory
+};
+
+template <typename T>
+struct FusedDesc {
+  int nlev;                         // levels 0 .. nlev-1 of the hierarchy
+  int nu1, nu2, ndof0, scratch_off; // scratch: one maxl-vector per warp for wall patches
+  const T* coarse_inv;
+  FusedLevel<T> lev[kMaxFused];
+};
+
+// MGV(l_c, U, F) of Algorithm 1 for the coarsest levels 0 .. l_c = nlev-1, entirely inside
+// one block: every level vector lives in shared memory and the phases (colours, residual,
+// transfers, coarse solve) are separated by __syncthreads instead of kernel launches.
+// F_{l_c} is read from Fin; U_{l_c} starts from Uio (load_u) or zero and is written back.
+template <int P, typename T>
+__global__ void __launch_bounds__(1024) k_fused_coarse(FusedDesc<T> D, const T* __restrict__ Fin, T* __restrict__ Uio,
+                                                       int load_u) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+  const int lc = D.nlev - 1;
+  {
+    const FusedLevel<T>& V = D.lev[lc];
+    T* U = sm + V.offU; T* F = sm + V.offF;
+    for (int i = tid; i < V.L.n_total; i += nt) { F[i] = Fin[i]; U[i] = load_u ? Uio[i] : T(0); }
+  }
+  __syncthreads();
+  auto smooth = [&](int l) {
+    const FusedLevel<T>& V = D.lev[l];
+    T* U = sm + V.offU; const T* F = sm + V.offF;
+    T* scratch = sm + D.scratch_off + warp * V.maxl;
+    for (int c = 0; c < V.n_colours; ++c) {
+      int first = V.colour_off[c], n8 = V.n8[c], ngen = V.colour_off[c + 1] - first - n8;
+      int lanes = ((n8 * 8 + 31) / 32) * 32;
+      for (int t = tid; t < lanes; t += nt) fast_patch_lane<P>(V.L, U, F, V.dofs, V.cls, V.cinv, V.maxl, first, n8, t >> 3, lane);
+      for (int w = warp; w < ngen; w += nwarp)
+        general_patch_warp<P>(V.L, U, F, V.dofs, V.cls, V.cinv, V.nloc, V.maxl, first + n8 + w, lane, scratch);
+      __syncthreads();
+    }
+  };
+  auto residual = [&](int l) {
+    const FusedLevel<T>& V = D.lev[l];
+    const T* U = sm + V.offU; const T* F = sm + V.offF; T* R = sm + V.offR;
+    const int nu = V.L.n_ux + V.L.n_uy;
+    double mp = 0.0;
+    for (int g = tid; g < V.L.n_total - 1; g += nt) {
+      R[g] = F[g] - row_KU<P>(V.L, U, g);
+      if (g >= nu) mp += (double)mean_coef<P>(V.L, g - nu) * (double)U[g];
+    }
+    double s = block_sum(mp, red);
+    if (tid == 0) R[V.L.n_total - 1] = (T)((double)F[V.L.n_total - 1] - s);
+    __syncthreads();
+  };
+  for (int l = lc; l >= 1; --l) {
+    for (int k = 0; k < D.nu1; ++k) smooth(l);
+    residual(l);
+    const FusedLevel<T>& V = D.lev[l];
+    const FusedLevel<T>& C = D.lev[l - 1];
+    const T* R = sm + V.offR;
+    T* Fc = sm + C.offF; T* Uc = sm + C.offU;
+    for (int g = tid; g < C.L.n_total; g += nt) {
+      Fc[g] = (g == C.L.n_total - 1) ? R[V.L.n_total - 1] : restrict_elem(V.L, C.L, V.tp, V.tq, R, g);
+      Uc[g] = T(0);
+    }
+    __syncthreads();
+  }
+  {  // exact coarsest solve, one warp per row of K_0^{-1}
+    const FusedLevel<T>& C = D.lev[0];
+    const T* G = sm + C.offF; T* U0 = sm + C.offU;
+    for (int i = warp; i < D.ndof0; i += nwarp) {
+      const T* row = D.coarse_inv + (size_t)i * D.ndof0;
+      T acc = T(0);
+#pragma unroll 4
+      for (int j = lane; j < D.ndof0; j += 32) acc = fma(row[j], G[j], acc);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) U0[i] = acc;
+    }
+    __syncthreads();
+  }
+  for (int l = 1; l <= lc; ++l) {
+    const FusedLevel<T>& V = D.lev[l];
+    const FusedLevel<T>& C = D.lev[l - 1];
+    T* U = sm + V.offU; const T* Uc = sm + C.offU;
+    for (int g = tid; g < V.L.n_total; g += nt)
+      U[g] += (g == V.L.n_total - 1) ? Uc[C.L.n_total - 1] : prolong_elem(V.L, C.L, V.tp, V.tq, Uc, g);
+    __syncthreads();
+    for (int k = 0; k < D.nu2; ++k) smooth(l);
+  }
+  {
+    const FusedLevel<T>& V = D.lev[lc];
+    const T* U = sm + V.offU;
+    for (int i = tid; i < V.L.n_total; i += nt) Uio[i] = U[i];
   }
 }
 
@@ -356,13 +462,24 @@ __global__ void k_to_float(int n, const double* __restrict__ a, float* __restric
 
 // Discrete streamfunction of a velocity correction by integration along y of its u_x
 // block: psi(ix, k+1) = psi(ix, k) + e_x(ix, k) / dcoef_k, psi = 0 on the bottom wall.
-// One thread per interior column; psi stored on the (n+p-2)^2 interior, FP64.
+// One warp per interior column: each lane sums a contiguous run, then a warp scan.
+// psi is stored on the (n+p-2)^2 interior, FP64.
 __global__ void k_integrate_psi(int nint, int nxu, const double* __restrict__ inv_dcoef,
                                 const float* __restrict__ e, double* __restrict__ psi) {
-  int ix = blockIdx.x * blockDim.x + threadIdx.x;  // interior column 0..nint-1
+  int ix = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // interior column
+  int lane = threadIdx.x & 31;
   if (ix >= nint) return;
-  double acc = 0.0;
-  for (int k = 0; k < nint; ++k) {
+  int per = (nint + 31) / 32;
+  int k0 = lane * per, k1 = min(k0 + per, nint);
+  double run = 0.0;
+  for (int k = k0; k < k1; ++k) run = fma((double)e[k * nxu + ix], inv_dcoef[k], run);
+  double incl = run;                      // inclusive scan of the lane totals
+  for (int o = 1; o < 32; o <<= 1) {
+    double v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  double acc = incl - run;                // exclusive prefix
+  for (int k = k0; k < k1; ++k) {
     acc = fma((double)e[k * nxu + ix], inv_dcoef[k], acc);
     psi[k * nint + ix] = acc;
   }

@@ -420,13 +420,14 @@ void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st)
   const int q = p - 1, n = L.n;
   st.T = 2 * p + 1;
   st.NC = 2 * st.T + 1;
-  st.RX = (4 * p + 1) * (2 * q + 1);
-  st.RP = 4 * p * (2 * q + 1) + 1;
-  const int T = st.T, NC = st.NC, RX = st.RX, RP = st.RP;
+  st.B0 = (2 * p + 1) * (2 * q + 1);
+  st.B1 = 2 * p * (2 * q + 1);
+  st.RU = st.B0 + st.B1 + 1;
+  const int T = st.T, NC = st.NC, B0 = st.B0, RU = st.RU;
   const int lastp = n + p - 1, lastq = n + q - 1, nint = n + p - 2;
-  st.sx.assign((size_t)NC * NC * RX, 0.0);
-  st.sy.assign((size_t)NC * NC * RX, 0.0);
-  st.sp.assign((size_t)NC * NC * RP, 0.0);
+  st.sx.assign((size_t)NC * NC * RU, 0.0);
+  st.sy.assign((size_t)NC * NC * RU, 0.0);
+  st.sp.assign((size_t)NC * NC * RU, 0.0);
   std::vector<char> done(NC * NC);
   auto inq = [&](int k) { return k >= 0 && k <= lastq; };
   auto inp_free = [&](int k) { return k >= 1 && k <= nint; };
@@ -436,7 +437,7 @@ void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st)
       int c = cls1(ix, lastp, T) * NC + cls1(iy, lastq, T);
       if (done[c]) continue;
       done[c] = 1;
-      double* r = &st.sx[(size_t)c * RX];
+      double* r = &st.sx[(size_t)c * RU];
       for (int dx = -p; dx <= p; ++dx)
         for (int dy = -q; dy <= q; ++dy) {
           int jx = ix + dx, jy = iy + dy;
@@ -446,8 +447,7 @@ void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st)
       for (int kx = -p; kx <= p - 1; ++kx)
         for (int dy = -q; dy <= q; ++dy) {
           int jx = ix + kx, jy = iy + dy;
-          if (inq(jx) && inq(jy))
-            r[(2 * p + 1) * (2 * q + 1) + (kx + p) * (2 * q + 1) + dy + q] = -L.D.get(ix, jx) * L.Mq.get(iy, jy);
+          if (inq(jx) && inq(jy)) r[B0 + (kx + p) * (2 * q + 1) + dy + q] = -L.D.get(ix, jx) * L.Mq.get(iy, jy);
         }
     }
   std::fill(done.begin(), done.end(), 0);
@@ -456,7 +456,7 @@ void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st)
       int c = cls1(ix, lastq, T) * NC + cls1(iy, lastp, T);
       if (done[c]) continue;
       done[c] = 1;
-      double* r = &st.sy[(size_t)c * RX];
+      double* r = &st.sy[(size_t)c * RU];
       for (int dx = -q; dx <= q; ++dx)
         for (int dy = -p; dy <= p; ++dy) {
           int jx = ix + dx, jy = iy + dy;
@@ -466,8 +466,7 @@ void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st)
       for (int dx = -q; dx <= q; ++dx)
         for (int ky = -p; ky <= p - 1; ++ky) {
           int jx = ix + dx, jy = iy + ky;
-          if (inq(jx) && inq(jy))
-            r[(2 * q + 1) * (2 * p + 1) + (dx + q) * (2 * p) + ky + p] = -L.Mq.get(ix, jx) * L.D.get(iy, jy);
+          if (inq(jx) && inq(jy)) r[B0 + (dx + q) * (2 * p) + ky + p] = -L.Mq.get(ix, jx) * L.D.get(iy, jy);
         }
     }
   std::fill(done.begin(), done.end(), 0);
@@ -476,7 +475,7 @@ void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st)
       int c = cls1(kx, lastq, T) * NC + cls1(ky, lastq, T);
       if (done[c]) continue;
       done[c] = 1;
-      double* r = &st.sp[(size_t)c * RP];
+      double* r = &st.sp[(size_t)c * RU];
       for (int sI = -q; sI <= p; ++sI)
         for (int dy = -q; dy <= q; ++dy) {
           int ix = kx + sI, iy = ky + dy;
@@ -485,13 +484,12 @@ void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st)
       for (int dx = -q; dx <= q; ++dx)
         for (int sI = -q; sI <= p; ++sI) {
           int ix = kx + dx, iy = ky + sI;
-          if (inq(ix) && inp_free(iy)) r[2 * p * (2 * q + 1) + (dx + q) * (2 * p) + sI + q] = L.Mq.get(ix, kx) * L.D.get(iy, ky);
+          if (inq(ix) && inp_free(iy)) r[B0 + (dx + q) * (2 * p) + sI + q] = L.Mq.get(ix, kx) * L.D.get(iy, ky);
         }
-      r[RP - 1] = L.mq[kx] * L.mq[ky];
+      r[RU - 1] = L.mq[kx] * L.mq[ky];
     }
   (void)s;
 }
-
 
 int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err) {
   const int p = pr.p, L = pr.n_levels, nf = pr.n_fine;

@@ -150,6 +150,26 @@ class Solver:
         return U
 
 
+def solve_batch(solvers, Us, Fs, rtol=1e-8, max_cycles=100, history=False):
+    """Independent solves side by side (igamg_solve_batch): one captured step per
+    unfinished solve per round, each on its handle's own stream."""
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s._h.value for s in solvers])
+    up = (ctypes.c_void_p * n)(*[_ptr(u).value for u in Us])
+    fp = (ctypes.c_void_p * n)(*[_ptr(f).value for f in Fs])
+    reps = (_lib.Report * n)()
+    hists = []
+    for i in range(n):
+        cap = max_cycles if history else 0
+        hist = (ctypes.c_double * max(cap, 1))()
+        reps[i].history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if cap else None
+        reps[i].history_cap = cap
+        hists.append(hist)
+    status = (ctypes.c_int * n)()
+    check(lib().igamg_solve_batch(n, hs, up, fp, float(rtol), int(max_cycles), reps, status), "igamg_solve_batch")
+    return [Solver._report_dict(reps[i], hists[i], status[i]) for i in range(n)]
+
+
 # ---- host-only inspection (no GPU) ----------------------------------------------------
 def host_level_matrix(p, n_fine, n_levels, sigma, nu, level, c_penalty=0.0):
     pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, c_penalty=c_penalty)

@@ -215,3 +215,53 @@ def test_zero_rhs_and_nonfinite():
         S.solve(U, F, rtol=1e-8, max_cycles=5)
     assert e.value.code == -4
     assert torch.isfinite(U).all()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_solve_matches_single_solves(precision):
+    torch = _torch()
+    from paper_1705_09282_gb300._lib import IGAMG_FP32_IR, IGAMG_FP64
+    from paper_1705_09282_gb300.solver import Solver, solve_batch
+    prec = IGAMG_FP32_IR if precision == "mixed" else IGAMG_FP64
+    cases = [(2, 1e-4), (2, 1.0), (3, 1e2), (2, 1e4)]
+    n, L = 32, 4
+    solvers, Fs, Us, singles = [], [], [], []
+    for p, sigma in cases:
+        S = Solver(p, n, L, sigma, 1.0, precision=prec)
+        F = S.load_vector(torch.tensor(inputs.grf_forcing(p, n, seed=int(sigma * 7) + p), device="cuda"))
+        U1 = S.empty()
+        singles.append((S.solve(U1, F, rtol=1e-8, max_cycles=60), U1.cpu().numpy()))
+        solvers.append(S); Fs.append(F); Us.append(S.empty())
+    reps = solve_batch(solvers, Us, Fs, rtol=1e-8, max_cycles=60, history=True)
+    for (rep1, U1), rep, U in zip(singles, reps, Us):
+        assert rep["converged"] and rep["cycles"] == rep1["cycles"]
+        assert np.array_equal(U.cpu().numpy(), U1)
+        assert rep["history"] == pytest.approx(rep1["history"], rel=0, abs=0)
+
+
+@pytest.mark.parametrize("depth", ["-1", "1", "2", "3"])
+@pytest.mark.parametrize("p", [2, 3])
+def test_one_block_coarse_levels_same_iterates(depth, p, monkeypatch):
+    # the coarsest levels run inside one thread block (fixed depth here instead of the
+    # autotuned one); iterates must not depend on that choice
+    monkeypatch.setenv("IGAMG_FUSED_LEVELS", depth)
+    n, L = 32, 4
+    S = _solver(p, n, L)
+    S32 = _solver(p, n, L, precision=1)
+    monkeypatch.delenv("IGAMG_FUSED_LEVELS")
+    H = o2.Hierarchy(p, n, L, 1.0, 1.0)
+    f = inputs.grf_forcing(p, n, seed=41)
+    F = H.fine.load_vector(f)
+    U = np.zeros_like(F)
+    Fg = S.load_vector(_t(f))
+    Ug = S.empty()
+    for _ in range(2):
+        H.vcycle(U, F)
+        S.vcycle(Ug, Fg)
+        assert _rel(_np(Ug), U) < RTOL_IT
+    U32 = S32.empty()
+    rep = S32.solve(U32, Fg, rtol=1e-9, max_cycles=60)
+    assert rep["converged"]
+    U = np.zeros_like(F)
+    H.solve(U, F, 1e-12, 80)
+    assert _rel(_np(U32), U) < 1e-7
