@@ -349,6 +349,28 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(spec):
+    """Untimed workload for profilers: two solves of one case of the sweep.
+    spec = "p<degree>-<fp64|mixed>[-sigma<value>]", e.g. "p2-fp64"."""
+    import torch
+
+    from paper_1705_09282_gb300 import inputs
+    from paper_1705_09282_gb300._lib import IGAMG_FP32_IR, IGAMG_FP64
+    from paper_1705_09282_gb300.solver import Solver
+    parts = spec.split("-")
+    p = int(parts[0][1:])
+    prec = IGAMG_FP32_IR if parts[1] == "mixed" else IGAMG_FP64
+    sigma = float(parts[2][5:]) if len(parts) > 2 else 1.0
+    S = Solver(p, N_FINE, N_LEVELS, sigma, 1.0, nu1=2, nu2=2, precision=prec)
+    F = S.load_vector(torch.tensor(inputs.grf_forcing(p, N_FINE, seed=SEED), device="cuda"))
+    U = S.empty()
+    for _ in range(2):
+        U.zero_()
+        rep = S.solve(U, F, rtol=RTOL, max_cycles=MAXC, history=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": spec, "cycles": rep["cycles"], "rel_residual": rep["rel_residual"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -356,7 +378,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", default=None,
+                    help="run two untimed solves of one case (for ncu), e.g. p2-fp64 or p2-mixed")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -148,6 +148,52 @@ int igamg_solve_host(igamg_handle* h, const double* f_qp_host, double* U_host, d
 int igamg_solve_batch(int n, igamg_handle** handles, double** U, const double** F, double rtol,
                       int max_cycles, igamg_report* reports, int* status);
 
+/* As igamg_solve / igamg_solve_batch, but stopping at an absolute residual norm
+ * ||F - K U||_2 <= atol (per solve), e.g. atol = 1e-8 ||F||_2 to compare initial guesses
+ * fairly (a better guess must not be asked for a smaller residual). */
+int igamg_solve_abs(igamg_handle* h, double* U, const double* F, double atol, int max_cycles,
+                    igamg_report* rep);
+int igamg_solve_batch_abs(int n, igamg_handle** handles, double** U, const double** F,
+                          const double* atol, int max_cycles, igamg_report* reports, int* status);
+
+/* Discrete streamfunction psi (FP64, (n+p-2)^2 interior coefficients) of a divergence-free
+ * velocity in U, by integrating u_x = d psi/dy along y from the bottom wall (Sec. 4.3
+ * complex: curl is onto the divergence-free velocities).  Target data for the warm start. */
+int igamg_streamfunction(igamg_handle* h, const double* U, double* psi);
+
+/* Learned warm start from a two-channel network output grid (float, (2, n+p, n+p), device):
+ * U = (curl psi, p, 0) with psi = psi_scale * channel 0 on the interior (boundary ring
+ * ignored) and the pressure coefficients = p_scale * channel 1 on its leading
+ * (n+p-1) x (n+p-1) points.  The velocity is exactly divergence-free (north star (4)). */
+int igamg_warm_start(igamg_handle* h, const float* grid, double psi_scale, double p_scale, double* U);
+
+/* ---- the warm-start network ------------------------------------------------------------
+ * 3x3 convolutions in_channels -> width -> width -> width -> 2, GELU after the first three
+ * (only in_channels = 3, width = 32 are built); layer l spreads its taps by dilations[l]
+ * in {1, 2, 4, 8} (NULL: all 1), which widens the receptive field without more layers.
+ * Inputs x: (B, 3, H, W) float, device; outputs / targets: (B, 2, H, W) float, device
+ * (channel 0: scaled streamfunction, channel 1: scaled pressure).  The loss is the sum of
+ * the channels' mean squared errors, channel 0 over the interior points (the boundary
+ * ring, where psi = 0, is excluded), channel 1 over the leading (H-1) x (W-1) points.
+ * Weights are used in BF16 with FP32 accumulation; the optimizer (Adam) keeps an FP32
+ * master copy.  Work goes on the given stream; workspaces grow on first use of a larger
+ * B*H*W. */
+typedef struct igamg_nn igamg_nn;
+int igamg_nn_create(int in_channels, int width, const int* dilations, unsigned long long seed,
+                    void* cuda_stream, igamg_nn** out);
+void igamg_nn_destroy(igamg_nn* nn);
+int igamg_nn_num_params(const igamg_nn* nn);
+/* parameters in the order w1 (32,3,3,3), b1, w2 (32,32,3,3), b2, w3, b3, w4 (2,32,3,3), b4 */
+int igamg_nn_get_params(igamg_nn* nn, float* host, size_t cap);
+int igamg_nn_set_params(igamg_nn* nn, const float* host, size_t n);
+int igamg_nn_forward(igamg_nn* nn, int B, int H, int W, const float* x, float* out);
+/* loss (host) and, if grad_host != NULL, the gradient (host, parameter order); no update */
+int igamg_nn_loss_grad(igamg_nn* nn, int B, int H, int W, const float* x, const float* target,
+                       double* loss, float* grad_host);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on one minibatch; loss (host) optional */
+int igamg_nn_train_step(igamg_nn* nn, int B, int H, int W, const float* x, const float* target,
+                        float lr, double* loss);
+
 /* max over pressure-space coefficients of |div u_h| (Lemma, Sec. 4.1: zero up to
  * round-off for the iterates of Sec. 5.3).  Synchronises; result on the host. */
 int igamg_div_inf(igamg_handle* h, const double* U, double* out);

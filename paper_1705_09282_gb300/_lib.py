@@ -57,6 +57,19 @@ SIGNATURES = {
     "igamg_solve_host": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Report)]),
     "igamg_solve_batch": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I,
                                ctypes.POINTER(Report), ctypes.POINTER(_I)]),
+    "igamg_solve_abs": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Report)]),
+    "igamg_solve_batch_abs": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                   ctypes.POINTER(_D), _I, ctypes.POINTER(Report), ctypes.POINTER(_I)]),
+    "igamg_streamfunction": (_I, [_P, _P, _P]),
+    "igamg_warm_start": (_I, [_P, _P, _D, _D, _P]),
+    "igamg_nn_create": (_I, [_I, _I, ctypes.POINTER(_I), ctypes.c_ulonglong, _P, ctypes.POINTER(_P)]),
+    "igamg_nn_destroy": (None, [_P]),
+    "igamg_nn_num_params": (_I, [_P]),
+    "igamg_nn_get_params": (_I, [_P, _P, _SZ]),
+    "igamg_nn_set_params": (_I, [_P, _P, _SZ]),
+    "igamg_nn_forward": (_I, [_P, _I, _I, _I, _P, _P]),
+    "igamg_nn_loss_grad": (_I, [_P, _I, _I, _I, _P, _P, ctypes.POINTER(_D), _P]),
+    "igamg_nn_train_step": (_I, [_P, _I, _I, _I, _P, _P, ctypes.c_float, ctypes.POINTER(_D)]),
     "igamg_div_inf": (_I, [_P, _P, ctypes.POINTER(_D)]),
     "igamg_curl": (_I, [_P, _P, _P]),
     "igamg_residual_static": (_I, [ctypes.POINTER(Problem), _I, _P, _P, _P, ctypes.POINTER(_D), _P]),

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC] + ARCH
-CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", CSRC]
 
 
 def _nvcc():
@@ -61,7 +61,7 @@ def build(verbose=False, extra_nvcc=()):
             if o.strip():
                 print(o)
     tmp = LIB + ".tmp"
-    _run([nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart_static"])
+    _run([nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart_static", "-Xcompiler", "-pthread"])
     os.replace(tmp, LIB)
     return LIB
 

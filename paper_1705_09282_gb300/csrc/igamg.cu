@@ -49,6 +49,47 @@ __global__ void k_div_inf(LevelTab<double> L, const double* __restrict__ dcoef, 
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
 }
 
+// Streamfunction of a (divergence-free) velocity by integration of its u_x block along y:
+// psi(ix, k+1) = psi(ix, k) + u_x(ix, k) / dcoef_k, psi = 0 on the bottom wall; one warp
+// per interior column (lane runs, then a warp scan), FP64.
+__global__ void k_streamfunction(int nint, int nxu, const double* __restrict__ inv_dcoef, const double* __restrict__ U,
+                                 double* __restrict__ psi) {
+  int ix = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (ix >= nint) return;
+  int per = (nint + 31) / 32;
+  int k0 = lane * per, k1 = min(k0 + per, nint);
+  double run = 0.0;
+  for (int k = k0; k < k1; ++k) run = fma(U[k * nxu + ix], inv_dcoef[k], run);
+  double incl = run;
+  for (int o = 1; o < 32; o <<= 1) {
+    double v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  double acc = incl - run;
+  for (int k = k0; k < k1; ++k) {
+    acc = fma(U[k * nxu + ix], inv_dcoef[k], acc);
+    psi[k * nint + ix] = acc;
+  }
+}
+
+// psi (interior, FP64) = scale * grid[1..H-2, 1..W-2] of a network output grid (H = W = n+p).
+__global__ void k_grid_to_psi(int nint, const float* __restrict__ grid, double scale, double* __restrict__ psi) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nint * nint) return;
+  int y = i / nint, x = i - y * nint;
+  psi[i] = scale * (double)grid[(y + 1) * (nint + 2) + x + 1];
+}
+
+// pressure coefficients (npd x npd) = scale * grid[0..npd-1, 0..npd-1] of an H x H grid.
+__global__ void k_grid_to_pressure(int npd, const float* __restrict__ grid, int H, double scale,
+                                   double* __restrict__ pr) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npd * npd) return;
+  int y = i / npd, x = i - y * npd;
+  pr[i] = scale * (double)grid[y * H + x];
+}
+
 // velocity = curl psi, psi on the (n+p-2)^2 interior streamfunction coefficients.
 __global__ void k_curl(LevelTab<double> L, const double* __restrict__ dcoef, const double* __restrict__ psi,
                        double* __restrict__ U) {
@@ -103,6 +144,7 @@ template <typename T>
 struct TypedLevel {
   LevelTab<T> L{};
   T* cinv = nullptr;
+  T* cinv8 = nullptr;
   Xfer<T> tp{}, tq{};            // transfer from level l-1 into level l (l >= 1)
   T *U = nullptr, *F = nullptr, *R = nullptr;
 };
@@ -209,18 +251,18 @@ int do_smooth(igamg_handle* h, int l, T* U, const T* F, cudaStream_t s) {
       int nb8 = (n8 + 31) / 32, nbg = (ngen + 7) / 8;
       unsigned nb = (unsigned)(nb8 + nbg);
       if (h->prob.p == 2)
-        k_mult_colour<2, T><<<nb, kBlock, shm, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+        k_mult_colour<2, T><<<nb, kBlock, shm, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
       else
-        k_mult_colour<3, T><<<nb, kBlock, shm, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+        k_mult_colour<3, T><<<nb, kBlock, shm, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
     }
   } else {
     int rc = do_residual<T>(h, l, U, F, tl.R, nullptr, s);
     if (rc) return rc;
     unsigned nb = (unsigned)((lc.n_patches + kBlock / 32 - 1) / (kBlock / 32));
     if (h->prob.p == 2)
-      k_add_local<2, T><<<nb, kBlock, shm, s>>>(tl.R, lc.dofs, lc.cls, tl.cinv, lc.nloc, lc.maxl, lc.n_patches, typed<T>(h).delta);
+      k_add_local<2, T><<<nb, kBlock, shm, s>>>(tl.R, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, lc.n_patches, typed<T>(h).delta);
     else
-      k_add_local<3, T><<<nb, kBlock, shm, s>>>(tl.R, lc.dofs, lc.cls, tl.cinv, lc.nloc, lc.maxl, lc.n_patches, typed<T>(h).delta);
+      k_add_local<3, T><<<nb, kBlock, shm, s>>>(tl.R, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, lc.n_patches, typed<T>(h).delta);
     T eta = (T)(h->prob.eta > 0 ? h->prob.eta : 0.5);
     k_add_gather<T><<<nblk(lc.sz.n_total), kBlock, 0, s>>>((int)lc.sz.n_total, U, typed<T>(h).delta, lc.d2p_off, lc.d2p_idx, eta);
   }
@@ -377,7 +419,7 @@ int div_inf_impl(igamg_handle* h, const double* U, double* out) { return div_inf
 // round launches one captured step per unfinished solve, then reads all their norms.
 // Small solves are latency bound, so running them side by side fills the GPU.
 int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, double rtol, int max_cycles,
-                     igamg_report* reps, int* status) {
+                     igamg_report* reps, int* status, const double* atol = nullptr) {
   std::vector<double> r0(n, 0.0), rk(n, 0.0);
   std::vector<int> k(n, 0), st(n, IGAMG_NOT_CONVERGED);
   int rc;
@@ -393,7 +435,7 @@ int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, d
     CK(cudaStreamSynchronize(hs[i]->exec_stream));
     r0[i] = rk[i] = std::sqrt(hs[i]->h_pinned[0]);
     if (!std::isfinite(r0[i])) st[i] = IGAMG_ENONFINITE;
-    else if (r0[i] == 0.0) st[i] = IGAMG_OK;
+    else if (r0[i] == 0.0 || (atol && r0[i] <= atol[i])) st[i] = IGAMG_OK;
     if ((rc = ensure_graph(hs[i], 0, Us[i], Fs[i]))) return rc;
   }
   for (;;) {
@@ -415,7 +457,7 @@ int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, d
       igamg_report* rep = reps ? &reps[i] : nullptr;
       if (rep && rep->history && k[i] - 1 < rep->history_cap) rep->history[k[i] - 1] = rk[i] / r0[i];
       if (!std::isfinite(rk[i])) st[i] = IGAMG_ENONFINITE;
-      else if (rk[i] <= rtol * r0[i]) st[i] = IGAMG_OK;
+      else if (rk[i] <= (atol ? atol[i] : rtol * r0[i])) st[i] = IGAMG_OK;
     }
   }
   for (int i = 0; i < n; ++i) {
@@ -438,7 +480,8 @@ int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, d
   return worst;
 }
 
-int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max_cycles, igamg_report* rep) {
+int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max_cycles, igamg_report* rep,
+               double atol = -1.0) {
   int L = (int)h->d.lev.size();
   int rc = do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, h->norm2, h->stream);
   if (rc) return rc;
@@ -449,14 +492,14 @@ int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max
   int k = 0;
   double rk = r0;
   int status = IGAMG_NOT_CONVERGED;
-  if (r0 == 0.0) status = IGAMG_OK;
+  if (r0 == 0.0 || (atol >= 0 && r0 <= atol)) status = IGAMG_OK;
   while (status == IGAMG_NOT_CONVERGED && k < max_cycles) {
     CK(cudaGraphLaunch(h->graph[0], h->stream));
     ++k;
     if ((rc = read_norm(h, &rk))) return rc;
     if (!std::isfinite(rk)) { status = IGAMG_ENONFINITE; break; }
     if (rep && rep->history && k - 1 < rep->history_cap) rep->history[k - 1] = rk / r0;
-    if (rk <= rtol * r0) status = IGAMG_OK;
+    if (rk <= (atol >= 0 ? atol : rtol * r0)) status = IGAMG_OK;
   }
   if (rep) {
     rep->cycles = k; rep->res0 = r0; rep->rel_residual = r0 > 0 ? rk / r0 : 0.0;
@@ -468,8 +511,9 @@ int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max
 }
 
 template <typename T>
-LevelTab<T> make_tab(const igamg_sizes& sz, int p, const T* sx, const T* sy, const T* sp) {
+LevelTab<T> make_tab(const igamg_sizes& sz, int p, const T* sx, const T* sy, const T* sp, const T* srow = nullptr) {
   LevelTab<T> L{};
+  L.srow = srow;
   int n = sz.n;
   L.n = n; L.nxu = n + p - 2; L.npd = n + p - 1; L.nint = n + p - 2; L.lastp = n + p - 1; L.lastq = n + p - 2;
   L.n_ux = (int)sz.n_ux; L.n_uy = (int)sz.n_uy; L.n_p = (int)sz.n_p; L.n_total = (int)sz.n_total;
@@ -514,7 +558,7 @@ int setup_fused(igamg_handle* h, Typed<T>& ty) {
   for (int l = 0; l <= best; ++l) {
     FusedLevel<T>& V = D.lev[l];
     const auto& lc = h->lc[l];
-    V.L = ty.lev[l].L; V.tp = ty.lev[l].tp; V.tq = ty.lev[l].tq; V.cinv = ty.lev[l].cinv;
+    V.L = ty.lev[l].L; V.tp = ty.lev[l].tp; V.tq = ty.lev[l].tq; V.cinv = ty.lev[l].cinv; V.cinv8 = ty.lev[l].cinv8;
     V.dofs = lc.dofs; V.cls = lc.cls; V.nloc = lc.nloc; V.maxl = lc.maxl; V.n_colours = lc.n_colours;
     for (int k = 0; k <= lc.n_colours && l >= 1; ++k) V.colour_off[k] = lc.colour_off[k];
     for (int k = 0; k < lc.n_colours && l >= 1; ++k) V.n8[k] = lc.n8[k];
@@ -598,11 +642,13 @@ int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
   for (int l = 0; l < L; ++l) {
     auto& lh = h->host.lev[l];
     auto& tl = ty.lev[l];
-    T *sx, *sy, *sp;
+    T *sx, *sy, *sp, *srow = nullptr;
     if ((rc = upload_as(h, &sx, lh.st.sx)) || (rc = upload_as(h, &sy, lh.st.sy)) || (rc = upload_as(h, &sp, lh.st.sp))) return rc;
-    tl.L = make_tab<T>(lh.sz, p, sx, sy, sp);
+    if (!lh.rows.empty() && (rc = upload_as(h, &srow, lh.rows))) return rc;
+    tl.L = make_tab<T>(lh.sz, p, sx, sy, sp, srow);
     if (l >= 1) {
       if ((rc = upload_as(h, &tl.cinv, lh.pt.cinv))) return rc;
+      if ((rc = upload_as(h, &tl.cinv8, lh.pt.cinv8))) return rc;
       for (int which = 0; which < 2; ++which) {
         const Transfer1D& Tr = which ? h->host.tq[l] : h->host.tp_free[l];
         Xfer<T>& X = which ? tl.tq : tl.tp;
@@ -625,7 +671,6 @@ int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
 int validate(const igamg_problem& pr) {
   if (pr.dim != 2) return IGAMG_EUNSUPPORTED;
   if (pr.p != 2 && pr.p != 3) return IGAMG_EUNSUPPORTED;
-  if (pr.beta_qp) return IGAMG_EUNSUPPORTED;
   if (pr.n_levels < 1 || pr.n_levels > 16 || pr.n_fine < 1) return IGAMG_EINVAL;
   if (pr.n_fine % (1 << (pr.n_levels - 1))) return IGAMG_EINVAL;
   if (!(pr.sigma > 0) || !(pr.nu > 0) || pr.nu1 < 0 || pr.nu2 < 0) return IGAMG_EINVAL;
@@ -820,9 +865,43 @@ int igamg_solve_batch(int n, igamg_handle** handles, double** U, const double** 
   return solve_batch_impl(n, handles, U, F, rtol, max_cycles, reports, status);
 }
 
+int igamg_solve_abs(igamg_handle* h, double* U, const double* F, double atol, int max_cycles, igamg_report* rep) {
+  if (!h || !U || !F || !(atol >= 0) || max_cycles < 0) return IGAMG_EINVAL;
+  return solve_impl(h, U, F, 0.0, max_cycles, rep, atol);
+}
+
+int igamg_solve_batch_abs(int n, igamg_handle** handles, double** U, const double** F, const double* atol,
+                          int max_cycles, igamg_report* reports, int* status) {
+  if (n < 0 || (n > 0 && (!handles || !U || !F || !atol)) || max_cycles < 0) return IGAMG_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!handles[i] || !U[i] || !F[i] || !(atol[i] >= 0)) return IGAMG_EINVAL;
+    for (int j = 0; j < i; ++j) if (handles[j] == handles[i]) return IGAMG_EINVAL;
+  }
+  return solve_batch_impl(n, handles, U, F, 0.0, max_cycles, reports, status, atol);
+}
+
 int igamg_div_inf(igamg_handle* h, const double* U, double* out) {
   if (!h || !U || !out) return IGAMG_EINVAL;
   return div_inf_impl(h, U, out);
+}
+
+int igamg_streamfunction(igamg_handle* h, const double* U, double* psi) {
+  if (!h || !U || !psi) return IGAMG_EINVAL;
+  auto& Lt = h->d.lev.back().L;
+  k_streamfunction<<<nblk((long long)Lt.nint * 32, 128), 128, 0, h->stream>>>(Lt.nint, Lt.nxu, h->lc.back().inv_dcoef, U, psi);
+  return launch_check();
+}
+
+int igamg_warm_start(igamg_handle* h, const float* grid, double psi_scale, double p_scale, double* U) {
+  if (!h || !grid || !U) return IGAMG_EINVAL;
+  auto& Lt = h->d.lev.back().L;
+  k_grid_to_psi<<<nblk((long long)Lt.nint * Lt.nint), kBlock, 0, h->stream>>>(Lt.nint, grid, psi_scale, h->psi);
+  CK(cudaMemsetAsync(U, 0, Lt.n_total * sizeof(double), h->stream));
+  k_curl<<<nblk(Lt.n_ux + Lt.n_uy), kBlock, 0, h->stream>>>(Lt, h->lc.back().dcoef, h->psi, U);
+  const int H = Lt.nint + 2;
+  k_grid_to_pressure<<<nblk(Lt.n_p), kBlock, 0, h->stream>>>(Lt.npd, grid + (size_t)H * H, H, p_scale,
+                                                              U + Lt.n_ux + Lt.n_uy);
+  return launch_check();
 }
 
 int igamg_curl(igamg_handle* h, const double* psi, double* U) {
@@ -859,7 +938,7 @@ extern "C" int igamg_residual_static(const igamg_problem* prob, int level, const
                                      void* cuda_stream) {
   if (!prob || !U || !F || !R) return IGAMG_EINVAL;
   const igamg_problem& pr = *prob;
-  if (pr.dim != 2 || (pr.p != 2 && pr.p != 3) || pr.beta_qp) return IGAMG_EUNSUPPORTED;
+  if (pr.dim != 2 || (pr.p != 2 && pr.p != 3) || pr.beta_qp) return IGAMG_EUNSUPPORTED;  // Stokes only
   if (pr.n_levels < 1 || pr.n_levels > 16 || pr.n_fine < 1 || pr.n_fine > 8192) return IGAMG_EINVAL;
   if (pr.n_fine % (1 << (pr.n_levels - 1))) return IGAMG_EINVAL;
   if (level < 0 || level >= pr.n_levels || !(pr.sigma > 0) || !(pr.nu > 0)) return IGAMG_EINVAL;
@@ -932,7 +1011,8 @@ extern "C" int igamg_host_operator_rows(const igamg_problem* prob, int level, do
   std::string err;
   if ((rc = build_hierarchy(*prob, H, err))) return rc;
   const auto& lh = H.lev[level];
-  LevelTab<double> L = make_tab<double>(lh.sz, prob->p, lh.st.sx.data(), lh.st.sy.data(), lh.st.sp.data());
+  LevelTab<double> L = make_tab<double>(lh.sz, prob->p, lh.st.sx.data(), lh.st.sy.data(), lh.st.sp.data(),
+                                        lh.rows.empty() ? nullptr : lh.rows.data());
   long long n = lh.sz.n_total;
   if (n_out) *n_out = n;
   if (!K) return IGAMG_OK;

@@ -49,11 +49,12 @@ struct Transfer1D {
 };
 
 struct PatchTables {
-  int n_patches = 0, maxl = 0, n_cls = 0, n_colours = 0;
+  int n_patches = 0, maxl = 0, n_cls = 0, n_colours = 0, n_cls8 = 0;
   std::vector<int> dofs;       // n_patches * maxl (global dof ids, -1 padded), colour-major
-  std::vector<int> cls;        // n_patches
-  std::vector<int> nloc;       // per class: n_v + n_q
+  std::vector<int> cls;        // n_patches: index into cinv8 (8-DOF patches) or cinv (others)
+  std::vector<int> nloc;       // per class of cinv: n_v + n_q
   std::vector<double> cinv;    // n_cls * maxl * maxl: leading block of the bordered inverse
+  std::vector<double> cinv8;   // n_cls8 * 64: the same for 8-DOF patches, packed 8 x 8
   std::vector<int> colour_off; // n_colours + 1
   std::vector<int> n8;         // per colour: patches with 4+4 DOFs, stored first in the colour
   std::vector<int> d2p_off;    // dof -> list of (patch * maxl + local row), CSR over dofs
@@ -85,6 +86,10 @@ struct LevelHost {
   igamg_sizes sz{};
   PatchTables pt;
   Stencils st;
+  // General (non-Kronecker) operators, e.g. generalized Oseen: one stencil record of RU
+  // coefficients per row (rows 0 .. n_total-2, same layout as the class records); empty
+  // when the class stencils describe the level.
+  std::vector<double> rows;
 };
 
 struct HierarchyHost {
@@ -106,6 +111,8 @@ struct HierarchyHost {
 int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err);
 igamg_sizes level_sizes(int p, int n);
 double k_entry(const Level1D& L, const igamg_sizes& s, long long g1, long long g2);
+// entry (g1, g2) of a level given by per-row stencil records
+double k_entry_rows(const LevelHost& lv, int p, long long g1, long long g2);
 // 1D factors of one level with n elements; pen_over_nu = C_I / h_fine.
 void build_level1d(int p, int n, double sigma, double nu, double pen_over_nu, Level1D& L);
 void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st);

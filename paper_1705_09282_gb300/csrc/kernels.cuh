@@ -18,6 +18,7 @@ struct LevelTab {
   int n, nxu, npd, nint, lastp, lastq;   // nxu = n+p-2 = nint, npd = n+p-1, lastp = n+p-1, lastq = n+p-2
   int n_ux, n_uy, n_p, n_total;
   const T *sx, *sy, *sp;                 // class stencils (see Stencils in igamg_internal.h)
+  const T* srow;                         // per-row records (general operators), or null
 };
 
 template <typename T>
@@ -74,7 +75,7 @@ __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __re
   const int ix = r - q_ * rs + (is_x ? 1 : 0);
   const int cx = cls1d<P>(ix, is_x ? L.lastp : L.lastq);
   const int cy = cls1d<P>(iy, is_y ? L.lastp : L.lastq);
-  const T* st = (is_x ? L.sx : (is_p ? L.sp : L.sy)) + (cx * NC + cy) * RU;
+  const T* st = L.srow ? L.srow + (size_t)g * RU : (is_x ? L.sx : (is_p ? L.sp : L.sy)) + (cx * NC + cy) * RU;
   // box 0: own velocity block (u rows) or u_x (p rows)
   const int b0_base = is_y ? L.n_ux : 0;
   const int b0_stride = is_y ? L.npd : L.nxu;
@@ -109,6 +110,7 @@ template <int P, typename T>
 __device__ __forceinline__ T mean_coef(const LevelTab<T>& L, int r) {
   constexpr int Q = P - 1, TC = 2 * P + 1, NC = 2 * TC + 1;
   constexpr int RU = (2 * P + 1) * (2 * Q + 1) + 2 * P * (2 * Q + 1) + 1;
+  if (L.srow) return L.srow[(size_t)(L.n_ux + L.n_uy + r) * RU + RU - 1];
   int ky = r / L.npd, kx = r - ky * L.npd;
   return L.sp[(cls1d<P>(kx, L.lastq) * NC + cls1d<P>(ky, L.lastq)) * RU + RU - 1];
 }
@@ -169,14 +171,14 @@ __global__ void k_residual_finish(int n_total, const T* __restrict__ F, T* __res
 // 32 lanes of the warp must call it together (the shuffles span the warp).
 template <int P, typename T>
 __device__ __forceinline__ void fast_patch_lane(const LevelTab<T>& L, T* U, const T* F, const int* __restrict__ dofs,
-                                                const int* __restrict__ cls, const T* __restrict__ cinv, int maxl,
+                                                const int* __restrict__ cls, const T* __restrict__ cinv8, int maxl,
                                                 int first, int n8, int grp, int lane) {
   int row = lane & 7;
   bool active = grp < n8;
   int patch = first + (active ? grp : 0);
   int g = dofs[patch * maxl + row];
   T r = F[g] - row_KU<P>(L, U, g);
-  const T* A = cinv + ((size_t)cls[patch] * maxl + row) * maxl;
+  const T* A = cinv8 + (size_t)cls[patch] * 64 + row * 8;
   T d0 = T(0), d1 = T(0);
 #pragma unroll
   for (int s = 0; s < 8; s += 2) {
@@ -263,11 +265,12 @@ __device__ __forceinline__ T prolong_elem(const LevelTab<T>& Lf, const LevelTab<
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_mult_colour(LevelTab<T> L, T* __restrict__ U, const T* __restrict__ F,
                                                      const int* __restrict__ dofs, const int* __restrict__ cls,
-                                                     const T* __restrict__ cinv, const int* __restrict__ nloc,
+                                                     const T* __restrict__ cinv, const T* __restrict__ cinv8,
+                                                     const int* __restrict__ nloc,
                                                      int maxl, int first, int n8, int ngen, int nb8) {
   int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if ((int)blockIdx.x < nb8) {
-    fast_patch_lane<P>(L, U, F, dofs, cls, cinv, maxl, first, n8, (blockIdx.x * 8 + wib) * 4 + (lane >> 3), lane);
+    fast_patch_lane<P>(L, U, F, dofs, cls, cinv8, maxl, first, n8, (blockIdx.x * 8 + wib) * 4 + (lane >> 3), lane);
     return;
   }
   extern __shared__ unsigned char smem_raw[];
@@ -281,21 +284,24 @@ __global__ void __launch_bounds__(256) k_mult_colour(LevelTab<T> L, T* __restric
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_add_local(const T* __restrict__ R, const int* __restrict__ dofs,
                                                    const int* __restrict__ cls, const T* __restrict__ cinv,
-                                                   const int* __restrict__ nloc, int maxl, int count,
-                                                   T* __restrict__ delta) {
+                                                   const T* __restrict__ cinv8, const int* __restrict__ nloc,
+                                                   int maxl, int count, T* __restrict__ delta) {
   extern __shared__ unsigned char smem_raw[];
   T* sh = reinterpret_cast<T*>(smem_raw);
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= count) return;
-  int c = cls[warp], nl = nloc[c];
-  T* r = sh + (threadIdx.x >> 5) * maxl;
   const int* pd = dofs + (size_t)warp * maxl;
+  // 8-DOF patches use the packed 8 x 8 table (their ninth DOF slot is padding)
+  bool is8 = maxl == 8 || pd[8] < 0;
+  int c = cls[warp], nl = is8 ? 8 : nloc[c];
+  const T* A = is8 ? cinv8 + (size_t)c * 64 : cinv + (size_t)c * maxl * maxl;
+  int ld = is8 ? 8 : maxl;
+  T* r = sh + (threadIdx.x >> 5) * maxl;
   for (int k = lane; k < nl; k += 32) r[k] = R[pd[k]];
   __syncwarp();
-  const T* A = cinv + (size_t)c * maxl * maxl;
   for (int k = lane; k < nl; k += 32)
-    delta[(size_t)warp * maxl + k] = dot_n(A + (size_t)k * maxl, r, nl);
+    delta[(size_t)warp * maxl + k] = dot_n(A + (size_t)k * ld, r, nl);
 }
 
 // Additive sweep, part 2: U_g += eta * (sum of the corrections of the patches holding g).
@@ -353,7 +359,7 @@ template <typename T>
 struct FusedLevel {
   LevelTab<T> L;
   Xfer<T> tp, tq;                   // transfer from the level below into this one (l >= 1)
-  const T* cinv;
+  const T *cinv, *cinv8;
   const int *dofs, *cls, *nloc;
   int maxl, n_colours;
   int colour_off[kMaxColours + 1], n8[kMaxColours];
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(1024) k_fused_coarse(FusedDesc<T> D, const T* 
     for (int c = 0; c < V.n_colours; ++c) {
       int first = V.colour_off[c], n8 = V.n8[c], ngen = V.colour_off[c + 1] - first - n8;
       int lanes = ((n8 * 8 + 31) / 32) * 32;
-      for (int t = tid; t < lanes; t += nt) fast_patch_lane<P>(V.L, U, F, V.dofs, V.cls, V.cinv, V.maxl, first, n8, t >> 3, lane);
+      for (int t = tid; t < lanes; t += nt) fast_patch_lane<P>(V.L, U, F, V.dofs, V.cls, V.cinv8, V.maxl, first, n8, t >> 3, lane);
       for (int w = warp; w < ngen; w += nwarp)
         general_patch_warp<P>(V.L, U, F, V.dofs, V.cls, V.cinv, V.nloc, V.maxl, first + n8 + w, lane, scratch);
       __syncthreads();

@@ -11,7 +11,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <atomic>
 #include <map>
+#include <thread>
 #include <utility>
 
 #include "igamg_internal.h"
@@ -297,6 +299,184 @@ double k_entry(const Level1D& L, const igamg_sizes& s, long long g1, long long g
 
 namespace {
 
+
+// ---- general per-row operators (generalized Oseen) ----------------------------------------
+// Record index of column c in the stencil record of row r (layout of Stencils), or -1.
+int box_index(int p, const Dof& r, const Dof& c) {
+  const int q = p - 1, WQ = 2 * q + 1, WPP = 2 * p + 1, B0 = WPP * WQ, RU = B0 + 2 * p * WQ + 1;
+  int dx = c.x - r.x, dy = c.y - r.y;
+  if (r.blk == 0) {
+    if (c.blk == 0 && dx >= -p && dx <= p && dy >= -q && dy <= q) return (dx + p) * WQ + dy + q;
+    if (c.blk == 2 && dx >= -p && dx <= p - 1 && dy >= -q && dy <= q) return B0 + (dx + p) * WQ + dy + q;
+  } else if (r.blk == 1) {
+    if (c.blk == 1 && dx >= -q && dx <= q && dy >= -p && dy <= p) return (dx + q) * WPP + dy + p;
+    if (c.blk == 2 && dx >= -q && dx <= q && dy >= -p && dy <= p - 1) return B0 + (dx + q) * (2 * p) + dy + p;
+  } else if (r.blk == 2) {
+    if (c.blk == 0 && dx >= -q && dx <= p && dy >= -q && dy <= q) return (dx + q) * WQ + dy + q;
+    if (c.blk == 1 && dx >= -q && dx <= q && dy >= -q && dy <= p) return B0 + (dx + q) * (2 * p) + dy + q;
+    if (c.blk == 3) return RU - 1;
+  }
+  return -1;
+}
+
+// Inverse of box_index: the column of record entry e of row r (blk = -1 if none / outside).
+Dof box_col(const igamg_sizes& s, int p, const Dof& r, int e) {
+  const int q = p - 1, WQ = 2 * q + 1, WPP = 2 * p + 1, B0 = WPP * WQ, RU = B0 + 2 * p * WQ + 1;
+  const int nint = s.n + p - 2, lastq = s.n + q - 1;
+  Dof c{-1, 0, 0};
+  auto ok_free = [&](int v) { return v >= 1 && v <= nint; };
+  auto ok_q = [&](int v) { return v >= 0 && v <= lastq; };
+  if (e == RU - 1) { if (r.blk == 2) c.blk = 3; return c; }
+  if (r.blk == 0) {
+    if (e < B0) { c = {0, r.x + e / WQ - p, r.y + e % WQ - q}; if (!ok_free(c.x) || !ok_q(c.y)) c.blk = -1; }
+    else { int f = e - B0; c = {2, r.x + f / WQ - p, r.y + f % WQ - q}; if (!ok_q(c.x) || !ok_q(c.y)) c.blk = -1; }
+  } else if (r.blk == 1) {
+    if (e < B0) { c = {1, r.x + e / WPP - q, r.y + e % WPP - p}; if (!ok_q(c.x) || !ok_free(c.y)) c.blk = -1; }
+    else { int f = e - B0; c = {2, r.x + f / (2 * p) - q, r.y + f % (2 * p) - p}; if (!ok_q(c.x) || !ok_q(c.y)) c.blk = -1; }
+  } else if (r.blk == 2) {
+    if (e < B0) {
+      if (e >= 2 * p * WQ) return c;
+      c = {0, r.x + e / WQ - q, r.y + e % WQ - q}; if (!ok_free(c.x) || !ok_q(c.y)) c.blk = -1;
+    } else { int f = e - B0; c = {1, r.x + f / (2 * p) - q, r.y + f % (2 * p) - q}; if (!ok_q(c.x) || !ok_free(c.y)) c.blk = -1; }
+  }
+  return c;
+}
+
+// Per-row records of a level given by its class stencils (the Stokes part).
+void rows_from_classes(int p, const LevelHost& lv, std::vector<double>& rows) {
+  const Stencils& st = lv.st;
+  const int n = lv.sz.n, RU = st.RU, NC = st.NC, T = st.T;
+  const int lastp = n + p - 1, lastq = n + p - 2;
+  long long nr = lv.sz.n_total - 1;
+  rows.assign((size_t)nr * RU, 0.0);
+  for (long long g = 0; g < nr; ++g) {
+    Dof d = decode(lv.sz, g);
+    const double* src;
+    if (d.blk == 0) src = &st.sx[(size_t)(cls1(d.x, lastp, T) * NC + cls1(d.y, lastq, T)) * RU];
+    else if (d.blk == 1) src = &st.sy[(size_t)(cls1(d.x, lastq, T) * NC + cls1(d.y, lastp, T)) * RU];
+    else src = &st.sp[(size_t)(cls1(d.x, lastq, T) * NC + cls1(d.y, lastq, T)) * RU];
+    std::copy(src, src + RU, &rows[(size_t)g * RU]);
+  }
+}
+
+// + int v . (beta . grad u) for both velocity blocks (Sec. 3.1, generalized Oseen), beta at
+// the (p+2)-point Gauss points, layout (2, n*G, n*G) [component][y point][x point].
+void add_advection(int p, const LevelHost& lv, const double* beta, std::vector<double>& rows) {
+  const int q = p - 1, n = lv.sz.n, G = p + 2, nG = n * G;
+  const int WQ = 2 * q + 1, WPP = 2 * p + 1, RU = WPP * WQ + 2 * p * WQ + 1;
+  std::vector<double> gx, gw;
+  gauss01(G, gx, gw);
+  auto tp = knots(p, n), tq = knots(q, n);
+  const double* bxs = beta;
+  const double* bys = beta + (size_t)nG * nG;
+  for (int ey = 0; ey < n; ++ey)
+    for (int ex = 0; ex < n; ++ex)
+      for (int gyi = 0; gyi < G; ++gyi)
+        for (int gxi = 0; gxi < G; ++gxi) {
+          double x = (ex + gx[gxi]) / n, y = (ey + gx[gyi]) / n, w = gw[gxi] * gw[gyi] / ((double)n * n);
+          double bx = bxs[(size_t)(ey * G + gyi) * nG + ex * G + gxi], by = bys[(size_t)(ey * G + gyi) * nG + ex * G + gxi];
+          double Npx[8], dNpx[8], Nqx[8], dNqx[8], Npy[8], dNpy[8], Nqy[8], dNqy[8];
+          span_values(tp, p, ex + p, x, Npx); span_derivs(tp, p, ex + p, x, dNpx);
+          span_values(tq, q, ex + q, x, Nqx); span_derivs(tq, q, ex + q, x, dNqx);
+          span_values(tp, p, ey + p, y, Npy); span_derivs(tp, p, ey + p, y, dNpy);
+          span_values(tq, q, ey + q, y, Nqy); span_derivs(tq, q, ey + q, y, dNqy);
+          for (int a = 0; a <= p; ++a)          // u_x: degree p in x, q in y
+            for (int b = 0; b <= q; ++b) {
+              long long g = gid(lv.sz, 0, ex + a, ey + b);
+              if (g < 0) continue;
+              double phi = w * Npx[a] * Nqy[b];
+              for (int a2 = 0; a2 <= p; ++a2)
+                for (int b2 = 0; b2 <= q; ++b2) {
+                  if (gid(lv.sz, 0, ex + a2, ey + b2) < 0) continue;
+                  double adv = bx * dNpx[a2] * Nqy[b2] + by * Npx[a2] * dNqy[b2];
+                  rows[(size_t)g * RU + (a2 - a + p) * WQ + (b2 - b + q)] += phi * adv;
+                }
+            }
+          for (int a = 0; a <= q; ++a)          // u_y: degree q in x, p in y
+            for (int b = 0; b <= p; ++b) {
+              long long g = gid(lv.sz, 1, ex + a, ey + b);
+              if (g < 0) continue;
+              double phi = w * Nqx[a] * Npy[b];
+              for (int a2 = 0; a2 <= q; ++a2)
+                for (int b2 = 0; b2 <= p; ++b2) {
+                  if (gid(lv.sz, 1, ex + a2, ey + b2) < 0) continue;
+                  double adv = bx * dNqx[a2] * Npy[b2] + by * Nqx[a2] * dNpy[b2];
+                  rows[(size_t)g * RU + (a2 - a + q) * WPP + (b2 - b + p)] += phi * adv;
+                }
+            }
+        }
+}
+
+// K_c = P^T K_f P (Sec. 5.1) in per-row stencil form.  P is block diagonal with tensor
+// products of the 1D knot-insertion views tp (degree p, interior indices) and tq.
+int galerkin_rows(int p, const LevelHost& F, const LevelHost& C, const Transfer1D& tp, const Transfer1D& tq,
+                  std::vector<double>& out, std::string& err) {
+  const int q = p - 1, RU = (2 * p + 1) * (2 * q + 1) + 2 * p * (2 * q + 1) + 1;
+  const int WR = Transfer1D::WR, WP = Transfer1D::WP;
+  long long nC = C.sz.n_total - 1;
+  out.assign((size_t)nC * RU, 0.0);
+  std::atomic<int> bad{0};
+  auto work = [&](long long i0, long long i1) {
+    for (long long i = i0; i < i1; ++i) {
+      Dof ri = decode(C.sz, i);
+      const Transfer1D& TX = ri.blk == 0 ? tp : tq;
+      const Transfer1D& TY = ri.blk == 1 ? tp : tq;
+      int sx = ri.blk == 0 ? 1 : 0, sy = ri.blk == 1 ? 1 : 0;   // view index = full - shift
+      int cxv = ri.x - sx, cyv = ri.y - sy;
+      double* orow = &out[(size_t)i * RU];
+      for (int kx = 0; kx < WR; ++kx) {
+        int fxv = TX.f0[cxv] + kx;
+        double wx = TX.rv[(size_t)cxv * WR + kx];
+        if (wx == 0.0 || fxv >= TX.nf) continue;
+        for (int ky = 0; ky < WR; ++ky) {
+          int fyv = TY.f0[cyv] + ky;
+          double wy = TY.rv[(size_t)cyv * WR + ky];
+          if (wy == 0.0 || fyv >= TY.nf) continue;
+          long long a = gid(F.sz, ri.blk, fxv + sx, fyv + sy);
+          Dof ra = decode(F.sz, a);
+          const double* frow = &F.rows[(size_t)a * RU];
+          double wa = wx * wy;
+          for (int e = 0; e < RU; ++e) {
+            double val = frow[e];
+            if (val == 0.0) continue;
+            Dof cb = box_col(F.sz, p, ra, e);
+            if (cb.blk < 0) continue;
+            if (cb.blk == 3) { orow[RU - 1] += wa * val; continue; }
+            const Transfer1D& JX = cb.blk == 0 ? tp : tq;
+            const Transfer1D& JY = cb.blk == 1 ? tp : tq;
+            int jsx = cb.blk == 0 ? 1 : 0, jsy = cb.blk == 1 ? 1 : 0;
+            int bxv = cb.x - jsx, byv = cb.y - jsy;
+            for (int jx = 0; jx < WP; ++jx) {
+              int cjx = JX.c0[bxv] + jx;
+              double wjx = JX.pv[(size_t)bxv * WP + jx];
+              if (wjx == 0.0 || cjx >= JX.nc) continue;
+              for (int jy = 0; jy < WP; ++jy) {
+                int cjy = JY.c0[byv] + jy;
+                double wjy = JY.pv[(size_t)byv * WP + jy];
+                if (wjy == 0.0 || cjy >= JY.nc) continue;
+                Dof cj{cb.blk, cjx + jsx, cjy + jsy};
+                int idx = box_index(p, ri, cj);
+                if (idx < 0) { bad = 1; continue; }
+                orow[idx] += wa * val * wjx * wjy;
+              }
+            }
+          }
+        }
+      }
+    }
+  };
+  unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  long long chunk = (nC + nth - 1) / nth;
+  for (unsigned t = 0; t < nth; ++t) {
+    long long i0 = t * chunk, i1 = std::min(nC, i0 + chunk);
+    if (i0 < i1) th.emplace_back(work, i0, i1);
+  }
+  for (auto& t : th) t.join();
+  if (bad) { err = "Galerkin product left the coarse stencil pattern"; return IGAMG_EINVAL; }
+  return IGAMG_OK;
+}
+
 // 1D position class of a patch index a on n+p-2 interior positions: the first and last
 // T positions are their own classes, the rest share the translation-invariant class.
 int pos_class(int a, int n, int p) {
@@ -307,7 +487,9 @@ int pos_class(int a, int n, int p) {
   return 2 * T;
 }
 
-int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt, std::string& err) {
+template <typename Entry>
+int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt, std::string& err, Entry kent,
+                  bool per_patch) {
   const int n = L.n, q = p - 1;
   auto sup = [&](int i, int d) { return std::make_pair(std::max(0, i - d), std::min(n - 1, i)); };
   auto inside = [](std::pair<int, int> a, std::pair<int, int> box) { return box.first <= a.first && a.second <= box.second; };
@@ -343,13 +525,19 @@ int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt
   pt.dofs.assign((size_t)pt.n_patches * maxl, -1);
   pt.cls.assign(pt.n_patches, 0);
   pt.colour_off.assign(pt.n_colours + 1, 0);
-  std::map<std::pair<int, int>, int> cmap;
-  std::vector<int> rep;
+  // classes: patches whose local matrices are equal share one inverse (translation
+  // invariance of the constant-coefficient Stokes operator); with per_patch every patch
+  // has its own.  8-DOF patches index the packed 8 x 8 table, the others the maxl table.
+  std::map<std::pair<int, int>, int> cmap8, cmapg;
+  std::vector<int> rep8, repg;
   for (int i = 0; i < pt.n_patches; ++i) {
     auto& P_ = all[i];
     for (size_t k = 0; k < P_.dofs.size(); ++k) pt.dofs[(size_t)i * maxl + k] = P_.dofs[k];
     pt.colour_off[P_.colour + 1]++;
-    auto key = std::make_pair(pos_class(P_.a, n, p), pos_class(P_.b, n, p));
+    bool is8 = P_.dofs.size() == 8;
+    auto& cmap = is8 ? cmap8 : cmapg;
+    auto& rep = is8 ? rep8 : repg;
+    auto key = per_patch ? std::make_pair(P_.a, P_.b) : std::make_pair(pos_class(P_.a, n, p), pos_class(P_.b, n, p));
     auto it = cmap.find(key);
     if (it == cmap.end()) { int id = (int)rep.size(); cmap[key] = id; rep.push_back(i); pt.cls[i] = id; }
     else pt.cls[i] = it->second;
@@ -360,24 +548,37 @@ int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt
     for (int k = pt.colour_off[c]; k < pt.colour_off[c + 1] && all[k].dofs.size() == 8; ++k) pt.n8[c]++;
   // bordered local inverses, one per class (Sec. 5.2 local problems; zero-mean local
   // pressure through the border m_j = int N^q_j)
-  pt.n_cls = (int)rep.size();
-  pt.nloc.assign(pt.n_cls, 0);
-  pt.cinv.assign((size_t)pt.n_cls * maxl * maxl, 0.0);
-  for (int c = 0; c < pt.n_cls; ++c) {
-    auto& P_ = all[rep[c]];
+  auto local_inverse = [&](const P& P_, std::vector<double>& inv) -> bool {
     int nl = (int)P_.dofs.size(), nb = nl + 1;
-    std::vector<double> Kb((size_t)nb * nb, 0.0), inv;
+    std::vector<double> Kb((size_t)nb * nb, 0.0);
     for (int r = 0; r < nl; ++r)
-      for (int t = 0; t < nl; ++t) Kb[(size_t)r * nb + t] = k_entry(L, s, P_.dofs[r], P_.dofs[t]);
+      for (int t = 0; t < nl; ++t) Kb[(size_t)r * nb + t] = kent(P_.dofs[r], P_.dofs[t]);
     for (int r = P_.nv; r < nl; ++r) {
       Dof d = decode(s, P_.dofs[r]);
       double m = L.mq[d.x] * L.mq[d.y];
       Kb[(size_t)r * nb + nl] = m; Kb[(size_t)nl * nb + r] = m;
     }
-    if (!invert(Kb, nb, inv)) { err = "singular local patch matrix"; return IGAMG_ESINGULAR; }
+    return invert(Kb, nb, inv);
+  };
+  pt.n_cls = (int)repg.size();
+  pt.n_cls8 = (int)rep8.size();
+  pt.nloc.assign(std::max(pt.n_cls, 1), 0);
+  pt.cinv.assign((size_t)std::max(pt.n_cls, 1) * maxl * maxl, 0.0);
+  pt.cinv8.assign((size_t)std::max(pt.n_cls8, 1) * 64, 0.0);
+  for (int c = 0; c < pt.n_cls; ++c) {
+    auto& P_ = all[repg[c]];
+    int nl = (int)P_.dofs.size(), nb = nl + 1;
+    std::vector<double> inv;
+    if (!local_inverse(P_, inv)) { err = "singular local patch matrix"; return IGAMG_ESINGULAR; }
     pt.nloc[c] = nl;
     for (int r = 0; r < nl; ++r)
       for (int t = 0; t < nl; ++t) pt.cinv[((size_t)c * maxl + r) * maxl + t] = inv[(size_t)r * nb + t];
+  }
+  for (int c = 0; c < pt.n_cls8; ++c) {
+    std::vector<double> inv;
+    if (!local_inverse(all[rep8[c]], inv)) { err = "singular local patch matrix"; return IGAMG_ESINGULAR; }
+    for (int r = 0; r < 8; ++r)
+      for (int t = 0; t < 8; ++t) pt.cinv8[(size_t)c * 64 + r * 8 + t] = inv[(size_t)r * 9 + t];
   }
   // dof -> (patch, local row) lists for the additive smoother, patch order ascending
   long long nd = s.n_total;
@@ -398,6 +599,14 @@ int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt
 }
 
 }  // namespace
+
+double k_entry_rows(const LevelHost& lv, int p, long long g1, long long g2) {
+  const int q = p - 1, RU = (2 * p + 1) * (2 * q + 1) + 2 * p * (2 * q + 1) + 1;
+  Dof a = decode(lv.sz, g1), b = decode(lv.sz, g2);
+  if (a.blk == 3) return b.blk == 2 ? lv.rows[(size_t)g2 * RU + RU - 1] : 0.0;
+  int idx = box_index(p, a, b);
+  return idx < 0 ? 0.0 : lv.rows[(size_t)g1 * RU + idx];
+}
 
 igamg_sizes level_sizes(int p, int n) {
   igamg_sizes s{};
@@ -497,16 +706,13 @@ int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err)
   H.cpen = pr.c_penalty > 0 ? pr.c_penalty : 4.0 * (p - 1);
   const double pen_over_nu = H.cpen * nf;  // C_I / h_fine on every level
   H.lev.resize(L);
+  const bool general = pr.beta_qp != nullptr;     // generalized Oseen: per-row operators
   for (int l = 0; l < L; ++l) {
     int n = nf >> (L - 1 - l);
     auto& lv = H.lev[l];
     build_level1d(p, n, pr.sigma, pr.nu, pen_over_nu, lv.f);
     lv.sz = level_sizes(p, n);
     build_stencils(p, lv.f, lv.sz, lv.st);
-    if (l >= 1) {
-      int rc = build_patches(p, lv.f, lv.sz, lv.pt, err);
-      if (rc) return rc;
-    }
   }
   H.tp_free.resize(L); H.tq.resize(L);
   for (int l = 1; l < L; ++l) {
@@ -517,13 +723,32 @@ int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err)
     auto Pq = prolong_dense(p - 1, nc, a, b);
     if (Pq.empty() || !make_transfer(Pq, a, b, 0, H.tq[l])) { err = "degree-(p-1) prolongation"; return IGAMG_ESINGULAR; }
   }
+  if (general) {
+    // fine level: the Stokes part from the class stencils plus the advection term; coarse
+    // levels: Galerkin products (the advection field is not polynomial, so re-assembly
+    // would not equal R K P)
+    rows_from_classes(p, H.lev[L - 1], H.lev[L - 1].rows);
+    add_advection(p, H.lev[L - 1], pr.beta_qp, H.lev[L - 1].rows);
+    for (int l = L - 2; l >= 0; --l) {
+      int rc = galerkin_rows(p, H.lev[l + 1], H.lev[l], H.tp_free[l + 1], H.tq[l + 1], H.lev[l].rows, err);
+      if (rc) return rc;
+    }
+  }
+  for (int l = 1; l < L; ++l) {
+    auto& lv = H.lev[l];
+    int rc = general ? build_patches(p, lv.f, lv.sz, lv.pt, err,
+                                     [&](long long a, long long b) { return k_entry_rows(lv, p, a, b); }, true)
+                     : build_patches(p, lv.f, lv.sz, lv.pt, err,
+                                     [&](long long a, long long b) { return k_entry(lv.f, lv.sz, a, b); }, false);
+    if (rc) return rc;
+  }
   // coarsest matrix, dense, and its inverse
   {
     auto& lv = H.lev[0];
     int nd = (int)lv.sz.n_total;
     std::vector<double> K((size_t)nd * nd);
     for (int i = 0; i < nd; ++i)
-      for (int j = 0; j < nd; ++j) K[(size_t)i * nd + j] = k_entry(lv.f, lv.sz, i, j);
+      for (int j = 0; j < nd; ++j) K[(size_t)i * nd + j] = general ? k_entry_rows(lv, p, i, j) : k_entry(lv.f, lv.sz, i, j);
     if (!invert(K, nd, H.coarse_inv)) { err = "singular coarsest matrix"; return IGAMG_ESINGULAR; }
     H.ndof0 = nd;
   }
@@ -557,6 +782,7 @@ int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err)
 namespace {
 int host_build(const igamg_problem* prob, int level, igamg::HierarchyHost& H) {
   if (!prob || prob->dim != 2 || (prob->p != 2 && prob->p != 3)) return IGAMG_EUNSUPPORTED;
+  if (!(prob->sigma > 0) || !(prob->nu > 0)) return IGAMG_EINVAL;
   if (prob->n_levels < 1 || prob->n_fine < 1 || prob->n_fine % (1 << (prob->n_levels - 1))) return IGAMG_EINVAL;
   if (level < 0 || level >= prob->n_levels) return IGAMG_EINVAL;
   if (igamg::level_sizes(prob->p, prob->n_fine >> (prob->n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
@@ -576,7 +802,8 @@ extern "C" int igamg_host_level_matrix(const igamg_problem* prob, int level, dou
   if (!K) return IGAMG_OK;
   if (cap < (size_t)(n * n)) return IGAMG_EINVAL;
   for (long long i = 0; i < n; ++i)
-    for (long long j = 0; j < n; ++j) K[i * n + j] = igamg::k_entry(lv.f, lv.sz, i, j);
+    for (long long j = 0; j < n; ++j)
+      K[i * n + j] = lv.rows.empty() ? igamg::k_entry(lv.f, lv.sz, i, j) : igamg::k_entry_rows(lv, prob->p, i, j);
   return IGAMG_OK;
 }
 

@@ -77,21 +77,70 @@ def manufactured_solution(p, n):
     return ux, uy, pr
 
 
-def grf_forcing(p, n, seed, length=0.1, n_features=512):
+def grf_grid(xs, ys, seed, length=0.1, n_features=512):
     """Two independent unit-variance Gaussian random fields with squared-exponential
-    covariance exp(-r^2 / (2 length^2)), by random Fourier features."""
-    x = quad_points_1d(p, n)
-    X, Y = np.meshgrid(x, x)
+    covariance exp(-r^2 / (2 length^2)), by random Fourier features
+    f(x, y) = sqrt(2/M) sum_k cos(w_k . (x, y) + b_k), on the tensor grid ys x xs
+    (result (2, len(ys), len(xs))).  The sum is evaluated as Re(E_y^T diag(e^{i b}) E_x)
+    with E_x[k, j] = exp(i w_kx x_j); the same seed gives the same fields on any grid."""
     rng = SplitMix64(seed)
+    xs, ys = np.asarray(xs, dtype=np.float64), np.asarray(ys, dtype=np.float64)
     out = []
     for _ in range(2):
         w = rng.normal(2 * n_features).reshape(n_features, 2) / length
         b = 2 * np.pi * rng.uniform(n_features)
-        f = np.zeros_like(X)
-        for k in range(n_features):
-            f += np.cos(w[k, 0] * X + w[k, 1] * Y + b[k])
+        ex = np.exp(1j * np.outer(w[:, 0], xs))          # (M, nx)
+        ey = np.exp(1j * np.outer(w[:, 1], ys))          # (M, ny)
+        f = np.real((ey * np.exp(1j * b)[:, None]).T @ ex)
         out.append(f * np.sqrt(2.0 / n_features))
     return np.ascontiguousarray(np.stack(out))
+
+
+def grf_forcing(p, n, seed, length=0.1, n_features=512):
+    """The GRF forcing at the quadrature points, layout (2, n*G, n*G)."""
+    x = quad_points_1d(p, n)
+    return grf_grid(x, x, seed, length, n_features)
+
+
+def streamfunction_grid(p, n):
+    """Sample points of the warm-start network's input grid: the (n+p) Greville abscissae
+    (knot averages) of the degree-p open uniform knot vector on n elements, per direction."""
+    t = np.concatenate([np.zeros(p + 1), np.arange(1, n) / n, np.ones(p + 1)])
+    return np.array([t[i + 1: i + p + 1].mean() for i in range(n + p)])
+
+
+def warm_start_input(p, n, seed, sigma, nu):
+    """Network input (3, n+p, n+p) float32: the GRF forcing (same seed as grf_forcing) at the
+    streamfunction grid, and log10(sigma/nu) broadcast."""
+    g = streamfunction_grid(p, n)
+    f = grf_grid(g, g, seed)
+    lg = np.full((1, len(g), len(g)), np.log10(sigma / nu))
+    return np.ascontiguousarray(np.concatenate([f, lg]).astype(np.float32))
+
+
+def warm_start_scale(sigma, nu):
+    """Output scale of the warm-start network: the streamfunction of a unit forcing with
+    wavenumber ~10 (the GRF length 0.1) is about 1 / (k (sigma + nu k^2)); the network
+    predicts psi / scale."""
+    return 1.0 / (10.0 * (sigma + 100.0 * nu))
+
+
+def warm_start_pressure_scale():
+    """Output scale of the network's pressure channel: the pressure balances the gradient
+    part of a unit-variance forcing of length 0.1, so it is of size ~0.1 whatever sigma/nu."""
+    return 0.1
+
+
+def batch_problems(count, seed0, sizes=(64, 96, 128), log_ratio=(-2.0, 4.0)):
+    """(n, sigma, nu, seed) for `count` independent problems: sizes round-robin, nu = 1,
+    sigma/nu log-uniform in 10^log_ratio, forcing seeds seed0 + i."""
+    rng = SplitMix64(seed0)
+    u = rng.uniform(count)
+    out = []
+    for i in range(count):
+        ratio = 10.0 ** (log_ratio[0] + (log_ratio[1] - log_ratio[0]) * u[i])
+        out.append((sizes[i % len(sizes)], ratio, 1.0, seed0 + i))
+    return out
 
 
 def oseen_advection(p, n, max_speed=1.0):

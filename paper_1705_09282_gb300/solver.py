@@ -24,13 +24,16 @@ class Solver:
     """Owns one igamg_handle: the level hierarchy of Sec. 5.1 for a 2D problem."""
 
     def __init__(self, p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.5, nu1=2, nu2=2,
-                 c_penalty=0.0, precision=_lib.IGAMG_FP64, device="cuda", stream=None):
+                 c_penalty=0.0, precision=_lib.IGAMG_FP64, device="cuda", stream=None, beta=None):
+        """beta: advection at the quadrature points (host array (2, nG, nG)) for the
+        generalized Oseen problem, or None for generalized Stokes."""
         self.device = torch.device(device)
         if self.device.type != "cuda":
             raise RuntimeError("the igamg solver runs on a CUDA device only")
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
         self.problem = _lib.make_problem(p, n_fine, n_levels, sigma, nu, smoother, eta, nu1, nu2,
-                                         c_penalty, precision)
+                                         c_penalty, precision, beta=self._beta)
         self.p, self.n_fine, self.n_levels = p, n_fine, n_levels
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -171,8 +174,9 @@ def solve_batch(solvers, Us, Fs, rtol=1e-8, max_cycles=100, history=False):
 
 
 # ---- host-only inspection (no GPU) ----------------------------------------------------
-def host_level_matrix(p, n_fine, n_levels, sigma, nu, level, c_penalty=0.0):
-    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, c_penalty=c_penalty)
+def host_level_matrix(p, n_fine, n_levels, sigma, nu, level, c_penalty=0.0, beta=None):
+    beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
+    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, c_penalty=c_penalty, beta=beta)
     n = ctypes.c_longlong()
     check(lib().igamg_host_level_matrix(ctypes.byref(pr), level, None, 0, ctypes.byref(n)), "host_level_matrix")
     K = np.zeros((n.value, n.value))
@@ -181,8 +185,9 @@ def host_level_matrix(p, n_fine, n_levels, sigma, nu, level, c_penalty=0.0):
     return K
 
 
-def host_operator_rows(p, n_fine, n_levels, sigma, nu, level):
-    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu)
+def host_operator_rows(p, n_fine, n_levels, sigma, nu, level, beta=None):
+    beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
+    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, beta=beta)
     n = ctypes.c_longlong()
     check(lib().igamg_host_operator_rows(ctypes.byref(pr), level, None, 0, ctypes.byref(n)), "host_operator_rows")
     K = np.zeros((n.value, n.value))

@@ -102,3 +102,24 @@ def test_patch_tables_match_oracle(p, n):
     got = [(int(c), tuple(int(g) for g in d if g >= 0)) for c, d in zip(col, dofs)]
     assert [c for c, _ in got] == sorted(c for c, _ in got)
     assert sorted(got) == want
+
+
+@pytest.mark.parametrize("p,n,L", [(2, 8, 3), (3, 8, 3), (2, 16, 3)])
+def test_oseen_operators_match_oracle_galerkin(p, n, L):
+    # generalized Oseen: fine operator with the advection term, coarse operators = R K P
+    # (not re-assembly); the kernels' per-row records reproduce them on every level
+    from paper_1705_09282_gb300 import inputs
+    from paper_1705_09282_gb300.solver import host_level_matrix, host_operator_rows
+    beta = inputs.oseen_advection(p, n, 1.0)
+    sigma, nu = 1.0, 0.01
+    H = o2.Hierarchy(p, n, L, sigma, nu, beta=beta)
+    for lev in range(L):
+        Ko = H.levels[lev].K.toarray()
+        scale = np.abs(Ko).max()
+        Kg = host_level_matrix(p, n, L, sigma, nu, lev, beta=beta)
+        assert np.abs(Kg - Ko).max() <= 1e-12 * scale, (lev, np.abs(Kg - Ko).max() / scale)
+        Kr = host_operator_rows(p, n, L, sigma, nu, lev, beta=beta)
+        assert np.abs(Kr - Ko).max() <= 1e-12 * scale, lev
+    # and the operator is not symmetric (the advection term is present)
+    K = H.levels[-1].K.toarray()
+    assert np.abs(K - K.T).max() > 1e-6 * np.abs(K).max()
