@@ -171,3 +171,62 @@ def random_divfree_guess(p, n, seed):
 def random_vector(count, seed):
     """Standard normal vector (for parity tests of single operators)."""
     return SplitMix64(seed).normal(count)
+
+
+# ---- 3D (unit cube) ------------------------------------------------------------------
+
+def _poly_terms_3d():
+    """The cube's manufactured velocity u = curl psi for psi = (a(x) b(y) b(z), 0,
+    b(x) b(y) a(z)), a(t) = t(t-1), b(t) = t^2 (t-1)^2, as sums of separable products
+    c * fx(x) fy(y) fz(z) per component (numpy polynomials)."""
+    P = np.polynomial.Polynomial
+    a = P([0.0, -1.0, 1.0])
+    b = P([0.0, 0.0, 1.0, -2.0, 1.0])
+    db = b.deriv()
+    ux = [(1.0, b, db, a)]
+    uy = [(1.0, a, b, db), (-1.0, db, b, a)]
+    uz = [(-1.0, a, db, b)]
+    return [ux, uy, uz]
+
+
+def _eval_terms(terms, X, Y, Z, lap=False):
+    out = np.zeros_like(X)
+    for c, fx, fy, fz in terms:
+        if lap:
+            out += c * (fx.deriv(2)(X) * fy(Y) * fz(Z) + fx(X) * fy.deriv(2)(Y) * fz(Z)
+                        + fx(X) * fy(Y) * fz.deriv(2)(Z))
+        else:
+            out += c * fx(X) * fy(Y) * fz(Z)
+    return out
+
+
+def manufactured_solution_3d(p, n):
+    """(u_x, u_y, u_z, p) of the cube's manufactured solution at the quadrature points,
+    arrays [z, y, x]; p = sin(pi x) sin(pi y) - 4/pi^2 (zero mean)."""
+    x = quad_points_1d(p, n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    us = [_eval_terms(t, X, Y, Z) for t in _poly_terms_3d()]
+    pr = np.sin(np.pi * X) * np.sin(np.pi * Y) - 4.0 / np.pi ** 2
+    return us[0], us[1], us[2], pr
+
+
+def manufactured_forcing_3d(p, n, sigma, nu):
+    """f = sigma u - nu Lap u + grad p for the cube's manufactured solution, at the
+    quadrature points, layout (3, nG, nG, nG) [component, z, y, x]."""
+    x = quad_points_1d(p, n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    pi = np.pi
+    grad = [pi * np.cos(pi * X) * np.sin(pi * Y), pi * np.sin(pi * X) * np.cos(pi * Y), np.zeros_like(X)]
+    f = [sigma * _eval_terms(t, X, Y, Z) - nu * _eval_terms(t, X, Y, Z, lap=True) + g
+         for t, g in zip(_poly_terms_3d(), grad)]
+    return np.ascontiguousarray(np.stack(f))
+
+
+def random_divfree_guess_3d(p, n, seed):
+    """Random vector-potential coefficients, U(-1,1), on the constrained space
+    (three families of (n+p-1)(n+p-2)^2 each) and random pressure coefficients on the
+    (n+p-1)^3 pressure space, U(-1,1)."""
+    rng = SplitMix64(seed)
+    psi = 2.0 * rng.uniform(3 * (n + p - 1) * (n + p - 2) ** 2) - 1.0
+    pr = 2.0 * rng.uniform((n + p - 1) ** 3) - 1.0
+    return psi, pr
