@@ -351,13 +351,23 @@ def run_reference(args):
 
 def profile_case(spec):
     """Untimed workload for profilers: two solves of one case of the sweep.
-    spec = "p<degree>-<fp64|mixed>[-sigma<value>]", e.g. "p2-fp64"."""
+    spec = "p<degree>-<fp64|mixed>[-sigma<value>]", e.g. "p2-fp64", or "cube-p2-<fp64|mixed>"
+    (one solve of the 64^3 cube)."""
     import torch
 
     from paper_1705_09282_gb300 import inputs
     from paper_1705_09282_gb300._lib import IGAMG_FP32_IR, IGAMG_FP64
     from paper_1705_09282_gb300.solver import Solver
     parts = spec.split("-")
+    if parts[0] == "cube":
+        prec = IGAMG_FP32_IR if parts[2] == "mixed" else IGAMG_FP64
+        S = Solver(int(parts[1][1:]), 64, 5, 1.0, 1.0, nu1=2, nu2=2, precision=prec, dim=3)
+        F = S.load_vector(torch.tensor(inputs.manufactured_forcing_3d(S.p, 64, 1.0, 1.0), device="cuda"))
+        U = S.empty()
+        rep = S.solve(U, F, rtol=RTOL, max_cycles=MAXC, history=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": spec, "cycles": rep["cycles"], "rel_residual": rep["rel_residual"]}))
+        return
     p = int(parts[0][1:])
     prec = IGAMG_FP32_IR if parts[1] == "mixed" else IGAMG_FP64
     sigma = float(parts[2][5:]) if len(parts) > 2 else 1.0
@@ -371,6 +381,163 @@ def profile_case(spec):
     print(json.dumps({"profile_case": spec, "cycles": rep["cycles"], "rel_residual": rep["rel_residual"]}))
 
 
+def _timed(fn, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def run_oseen(args):
+    """Generalized Oseen, 512 x 512, 8 grids, p = 2, nu = 1e-2, sigma = 1, advection the curl
+    of sin^2(pi x) sin^2(pi y) scaled to max |beta| = 0.5 (Re = 50 < Da = 100), GRF forcing:
+    FP64 and FP32-in-FP64 solves to 1e-8; per-row operators (HBM-resident)."""
+    import torch
+
+    from paper_1705_09282_gb300 import inputs
+    from paper_1705_09282_gb300._lib import IGAMG_FP32_IR, IGAMG_FP64
+    from paper_1705_09282_gb300.solver import Solver
+    p, n, L, sigma, nu = 2, 512, 8, 1.0, 1e-2
+    beta = inputs.oseen_advection(p, n, 0.5)
+    f = torch.tensor(inputs.grf_forcing(p, n, seed=1707), device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, prec in (("fp64", IGAMG_FP64), ("mixed", IGAMG_FP32_IR)):
+        t0 = time.perf_counter()
+        S = Solver(p, n, L, sigma, nu, beta=beta, precision=prec)
+        setup = time.perf_counter() - t0
+        F = S.load_vector(f)
+        U = S.empty()
+        for _ in range(args.warmup):
+            U.zero_()
+            S.solve(U, F, rtol=RTOL, max_cycles=MAXC, history=False)
+        ts, cyc = [], None
+        for _ in range(args.steps):
+            U.zero_()
+            dt, rep = _timed(lambda: S.solve(U, F, rtol=RTOL, max_cycles=MAXC, history=False), stream)
+            assert rep["converged"], rep
+            ts.append(dt)
+            cyc, div = rep["cycles"], rep["div_inf"]
+        t = sum(ts) / len(ts)
+        # the FP32 or FP64 colour kernel on the finest level, timed alone
+        sz = S.sizes()
+        sweeps = 10
+        dt_sm, _ = _timed(lambda: S.smooth(U, F, sweeps=sweeps), stream)
+        out[name] = {"solve_ms": 1e3 * t, "cycles": cyc, "mdof_per_s_per_cycle": S.ndof() * cyc / t / 1e6,
+                     "div_inf": div, "setup_s": setup, "fp64_colour_launch_us": 1e6 * dt_sm / (sweeps * sz.n_colours)}
+        S.close()
+    pk, src = peaks()
+    line = {"metric": "Oseen solve time to 1e-8 rel. residual (config 3)", "workload": "oseen",
+            "config": {"workload": "2D generalized Oseen, unit square, p=2, 512x512, 8 levels, nu=1e-2, sigma=1, "
+                                   "max|beta|=0.5 (Re=50, Da=100), GRF forcing seed 1707, V(2,2) multiplicative",
+                       "ndof": None}, "results": out, "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_source": src}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """Config 5 style batch: independent 2D generalized Stokes solves of sizes 64/96/128
+    (round-robin), sigma/nu log-uniform in [1e-2, 1e4], GRF forcing, side by side; zero
+    initial guess versus the learned warm start (network trained on separate problems
+    solved by the same multigrid), both to the absolute residual 1e-8 ||F||."""
+    import numpy as np
+    import torch
+
+    from paper_1705_09282_gb300 import inputs
+    from paper_1705_09282_gb300 import warmstart as ws
+    p = 2
+    count = args.batch_count
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    probs = [ws.Problem(p, n, ws.levels_for(n), s, nu, seed) for (n, s, nu, seed) in inputs.batch_problems(count, 1709)]
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    train = [ws.Problem(p, n, ws.levels_for(n), s, nu, seed)
+             for (n, s, nu, seed) in inputs.batch_problems(args.train_count, 50000)]
+    grids = ws.targets(train)
+    net = ws.Network(seed=1)
+    losses = ws.train(net, train, grids, steps=args.train_steps, batch=16, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    atol = [1e-8 * float(torch.linalg.norm(pr.F)) for pr in probs]
+    ndof = np.array([pr.solver.ndof() for pr in probs])
+
+    def cold():
+        for pr in probs:
+            pr.U.zero_()
+        return ws.solve_batch_abs([pr.solver for pr in probs], [pr.U for pr in probs], [pr.F for pr in probs], atol, MAXC)
+
+    def warm():
+        ws.predict_guesses(net, probs)
+        return ws.solve_batch_abs([pr.solver for pr in probs], [pr.U for pr in probs], [pr.F for pr in probs], atol, MAXC)
+
+    cold()
+    warm()
+    tc, rc = _timed(cold, stream)
+    tw, rw = _timed(warm, stream)
+    cc = np.array([r["cycles"] for r in rc])
+    cw = np.array([r["cycles"] for r in rw])
+    line = {"metric": "batched solve time to 1e-8 ||F|| and MDOF/s per V-cycle (config 5)", "workload": "batch",
+            "config": {"solves": count, "sizes": [64, 96, 128], "p": p, "sigma_over_nu": "log-uniform [1e-2, 1e4]",
+                       "train_problems": args.train_count, "train_steps": args.train_steps},
+            "zero_guess": {"seconds": tc, "mean_cycles": float(cc.mean()), "mdof_per_s_per_cycle": float((ndof * cc).sum() / tc / 1e6)},
+            "warm_start": {"seconds": tw, "mean_cycles": float(cw.mean()), "mdof_per_s_per_cycle": float((ndof * cw).sum() / tw / 1e6),
+                           "includes": "network inference + curl for every solve"},
+            "cycles_saved_total": int(cc.sum() - cw.sum()), "worse_count": int((cw > cc).sum()),
+            "max_div_inf": max(r["div_inf"] for r in rw), "setup_s": t_setup, "train_s": t_train,
+            "train_loss_first_last": [float(np.mean(losses[:5])), float(np.mean(losses[-20:]))]}
+    print(json.dumps(line), flush=True)
+
+
+def run_cube(args):
+    """3D generalized Stokes on the unit cube: p = 2, 64^3 elements, 5 grids, sigma/nu in
+    {1, 1e3}, the cube's manufactured forcing (Sec. 6.3), V(2,2) multiplicative smoother over
+    the vector-potential supports; FP64 and FP32-in-FP64 solves from zero to 1e-8."""
+    import torch
+
+    from paper_1705_09282_gb300 import inputs
+    from paper_1705_09282_gb300._lib import IGAMG_FP32_IR, IGAMG_FP64
+    from paper_1705_09282_gb300.solver import Solver
+    p, n, L = 2, 64, 5
+    stream = torch.cuda.current_stream()
+    out = {}
+    for sigma in (1.0, 1e3):
+        f = torch.tensor(inputs.manufactured_forcing_3d(p, n, sigma, 1.0), device="cuda")
+        for name, prec in (("fp64", IGAMG_FP64), ("mixed", IGAMG_FP32_IR)):
+            t0 = time.perf_counter()
+            S = Solver(p, n, L, sigma, 1.0, precision=prec, dim=3)
+            setup = time.perf_counter() - t0
+            F = S.load_vector(f)
+            U = S.empty()
+            for _ in range(args.warmup):
+                U.zero_()
+                S.solve(U, F, rtol=RTOL, max_cycles=MAXC, history=False)
+            ts = []
+            for _ in range(args.steps):
+                U.zero_()
+                dt, rep = _timed(lambda: S.solve(U, F, rtol=RTOL, max_cycles=MAXC, history=False), stream)
+                assert rep["converged"], rep
+                ts.append(dt)
+            t = sum(ts) / len(ts)
+            sz = S.sizes()
+            sweeps = 4
+            dt_sm, _ = _timed(lambda: S.smooth(U, F, sweeps=sweeps), stream)
+            out["%s_sigma%g" % (name, sigma)] = {
+                "solve_ms": 1e3 * t, "cycles": rep["cycles"], "rel_residual": rep["rel_residual"],
+                "mdof_per_s_per_cycle": S.ndof() * rep["cycles"] / t / 1e6, "div_inf": rep["div_inf"],
+                "setup_s": setup, "fine_sweep_ms": 1e3 * dt_sm / sweeps, "colours": sz.n_colours}
+            S.close()
+    line = {"metric": "3D solve time to 1e-8 rel. residual & MDOF/s per V-cycle (config 4)", "workload": "cube",
+            "config": {"workload": "3D generalized Stokes, unit cube, p=2 (velocity S^{2,1,1} x S^{1,2,1} x S^{1,1,2}), "
+                                   "64^3 elements, 5 levels, sigma/nu in {1, 1e3}, manufactured forcing of Sec. 6.3, "
+                                   "V(2,2) multiplicative vector-potential Schwarz, zero initial guess, to 1e-8",
+                       "ndof": 3 * 64 * 65 * 65 + 65 ** 3 + 1}, "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -378,6 +545,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="stokes", choices=["stokes", "oseen", "batch", "cube"],
+                    help="stokes: the headline sweep (default); oseen / batch / cube: extra measurements")
+    ap.add_argument("--batch-count", type=int, default=1024)
+    ap.add_argument("--train-count", type=int, default=384)
+    ap.add_argument("--train-steps", type=int, default=6000)
     ap.add_argument("--profile-case", default=None,
                     help="run two untimed solves of one case (for ncu), e.g. p2-fp64 or p2-mixed")
     args = ap.parse_args()
@@ -386,6 +558,12 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "oseen":
+        run_oseen(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "cube":
+        run_cube(args)
     else:
         run_ours(args)
 

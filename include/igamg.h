@@ -20,6 +20,16 @@
  *       lambda (the multiplier) ]
  * Levels are numbered 0 (coarsest, n_fine >> (n_levels-1) elements) .. n_levels-1 (finest).
  *
+ * 3D (dim = 3, unit cube; Sec. 4.3 in three dimensions, Sec. 6.3): velocity
+ * S^{p,q,q} x S^{q,p,q} x S^{q,q,p}, pressure S^{q,q,q}; with ni = n+p-2, nq = n+q:
+ *     [ u_x : (z: nq) x (y: nq) x (x: ni, interior 1..ni), x fastest
+ *       u_y : nq x ni x nq     u_z : ni x nq x nq      p : nq x nq x nq      lambda ]
+ * f and beta are sampled at the quadrature points as (3, nG, nG, nG) [comp][z][y][x].
+ * Subdomains are the supports of the vector-potential basis functions (Sec. 5.2), in
+ * three families; the smoother is multiplicative (eq. MSM) only and beta must be NULL
+ * (other choices return IGAMG_EUNSUPPORTED), as are igamg_streamfunction,
+ * igamg_warm_start and igamg_residual_static.
+ *
  * Conventions: every call enqueues its GPU work on the stream given to igamg_create
  * (a cudaStream_t passed as void*) and returns without synchronising, unless it says
  * otherwise.  The caller owns U, F, R (device memory, e.g. from PyTorch); the library
@@ -52,7 +62,7 @@ enum { IGAMG_MULT = 0, IGAMG_ADD = 1 };          /* eq. MSM / eq. ASM of Sec. 5.
 enum { IGAMG_FP64 = 0, IGAMG_FP32_IR = 1 };      /* precision of the V-cycle */
 
 typedef struct {
-  int dim;            /* 2 */
+  int dim;            /* 2, or 3 (unit cube, see the 3D layout above) */
   int p;              /* streamfunction degree (Sec. 6 convention), 2 or 3 */
   int n_fine;         /* elements per direction on the finest grid */
   int n_levels;       /* number of grids; n_fine must be divisible by 2^(n_levels-1) */
@@ -72,9 +82,12 @@ typedef struct {
   int nx_uy, ny_uy;
   int n_pdir;         /* pressure coefficients per direction, n+p-1 */
   long long n_ux, n_uy, n_p, n_total; /* n_total includes lambda */
-  int n_patches;      /* interior streamfunction supports = (n+p-2)^2 */
-  int n_colours;      /* (p+1)^2 */
+  int n_patches;      /* interior streamfunction supports = (n+p-2)^2 (3D: vector-potential
+                         supports, 3 (n+p-1)(n+p-2)^2) */
+  int n_colours;      /* (p+1)^2 (3D: 3 p (p+1)^2) */
   int n_quad;         /* quadrature points per element per direction (p+2) */
+  int dim;            /* 2 or 3 */
+  long long n_uz;     /* 3D: size of the u_z block (0 in 2D) */
 } igamg_sizes;
 
 typedef struct {
@@ -200,7 +213,11 @@ int igamg_div_inf(igamg_handle* h, const double* U, double* out);
 
 /* Velocity blocks of U = curl psi = (d psi/dy, -d psi/dx) for psi given on the
  * (n+p-2)^2 interior streamfunction coefficients (Sec. 4.3 complex); the pressure and
- * lambda entries of U are not touched. */
+ * lambda entries of U are not touched.
+ * 3D: psi is a vector potential in S^{q,p,p} x S^{p,q,p} x S^{p,p,q} with psi x n = 0,
+ * given as three consecutive families of nq*ni*ni coefficients each, x fastest:
+ *   psi_x: (z: ni, interior) x (y: ni, interior) x (x: nq),
+ *   psi_y: (z: ni) x (y: nq) x (x: ni),   psi_z: (z: nq) x (y: ni) x (x: ni). */
 int igamg_curl(igamg_handle* h, const double* psi, double* U);
 
 /* Same result as igamg_residual on level `level` of the hierarchy that *prob describes,
@@ -235,6 +252,10 @@ int igamg_host_level_matrix(const igamg_problem* prob, int level, double* K, siz
 /* K_l rebuilt through the row evaluation that the GPU kernels run (class stencils). */
 int igamg_host_operator_rows(const igamg_problem* prob, int level, double* K, size_t cap,
                              long long* n_out);
+/* KV = K_l V (V, KV: host, n = level's n_total entries) through the same row evaluation
+ * the GPU kernels run: a cheap check of the row tables on large levels. */
+int igamg_host_operator_apply(const igamg_problem* prob, int level, const double* V, double* KV,
+                              size_t n);
 /* P_{l-1} (rows: level l, columns: level l-1), block diag(P^v, P^q, 1) of Sec. 5.1. */
 int igamg_host_prolongation(const igamg_problem* prob, int level, double* P, size_t cap,
                             long long* n_rows, long long* n_cols);

@@ -28,7 +28,7 @@ class Sizes(ctypes.Structure):
                 ("nx_uy", ctypes.c_int), ("ny_uy", ctypes.c_int), ("n_pdir", ctypes.c_int),
                 ("n_ux", ctypes.c_longlong), ("n_uy", ctypes.c_longlong), ("n_p", ctypes.c_longlong),
                 ("n_total", ctypes.c_longlong), ("n_patches", ctypes.c_int), ("n_colours", ctypes.c_int),
-                ("n_quad", ctypes.c_int)]
+                ("n_quad", ctypes.c_int), ("dim", ctypes.c_int), ("n_uz", ctypes.c_longlong)]
 
 
 class Report(ctypes.Structure):
@@ -75,6 +75,7 @@ SIGNATURES = {
     "igamg_residual_static": (_I, [ctypes.POINTER(Problem), _I, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "igamg_host_level_matrix": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL)]),
     "igamg_host_operator_rows": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL)]),
+    "igamg_host_operator_apply": (_I, [ctypes.POINTER(Problem), _I, _P, _P, _SZ]),
     "igamg_host_prolongation": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL),
                                      ctypes.POINTER(_LL)]),
     "igamg_host_patches": (_I, [ctypes.POINTER(Problem), _I, _P, _P, _SZ, _SZ, ctypes.POINTER(_I),
@@ -114,9 +115,9 @@ def check(code, where):
 
 
 def make_problem(p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.5, nu1=2, nu2=2,
-                 c_penalty=0.0, precision=IGAMG_FP64, beta=None):
+                 c_penalty=0.0, precision=IGAMG_FP64, beta=None, dim=2):
     pr = Problem()
-    pr.dim, pr.p, pr.n_fine, pr.n_levels = 2, p, n_fine, n_levels
+    pr.dim, pr.p, pr.n_fine, pr.n_levels = dim, p, n_fine, n_levels
     pr.sigma, pr.nu, pr.c_penalty = float(sigma), float(nu), float(c_penalty)
     pr.beta_qp = beta.ctypes.data if beta is not None else None
     pr.smoother = IGAMG_ADD if smoother == "add" else IGAMG_MULT

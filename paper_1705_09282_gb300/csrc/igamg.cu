@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "igamg3d.h"
 #include "igamg_internal.h"
 #include "kernels.cuh"
 
@@ -193,11 +194,18 @@ struct igamg_handle {
   std::vector<void*> allocs;
   cudaStream_t exec_stream = nullptr;  // used by igamg_solve_batch
   cudaEvent_t ev = nullptr;
+  igamg3d_handle* d3 = nullptr;        // dim = 3: everything lives in the 3D driver
 };
 
 namespace {
 
 thread_local std::string g_err;
+
+}  // namespace
+
+void igamg::set_error(const std::string& msg) { g_err = msg; }
+
+namespace {
 
 #define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { g_err = std::string(#x) + ": " + cudaGetErrorString(e_); return IGAMG_ECUDA; } } while (0)
 
@@ -610,24 +618,40 @@ int autotune_fused(igamg_handle* h, Typed<T>& ty) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  // each candidate is timed the way solves run it: one V-cycle captured into a graph,
+  // replayed (launch overheads of the per-level path are those of graph replay)
   float best_ms = 1e30f;
   int best = -1;
+  const bool verbose = std::getenv("IGAMG_VERBOSE") != nullptr;
   for (int cand = -1; cand <= ty.fused_max; ++cand) {
     if (cand == 0) continue;
     ty.fused_lc = cand;
-    int rc = do_vcycle<T>(h, U, F, h->stream);
-    if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
-    CK(cudaEventRecord(e0, h->stream));
-    for (int r = 0; r < 3; ++r) if ((rc = do_vcycle<T>(h, U, F, h->stream))) return rc;
-    CK(cudaEventRecord(e1, h->stream));
-    CK(cudaEventSynchronize(e1));
+    cudaGraph_t g;
+    cudaGraphExec_t ge = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = do_vcycle<T>(h, U, F, h->cap_stream);
+    cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc) { if (ec == cudaSuccess) cudaGraphDestroy(g); cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+    CK(ec);
+    cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CK(ei);
     float ms = 0;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaError_t e = cudaGraphLaunch(ge, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = cudaGraphLaunch(ge, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaGraphExecDestroy(ge);
+    CK(e);
+    if (verbose) std::fprintf(stderr, "igamg: fused coarse levels %d: %.1f us per V-cycle\n", cand, 1e3f * ms / 5);
     if (ms < best_ms) { best_ms = ms; best = cand; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ty.fused_lc = best;
+  if (verbose) std::fprintf(stderr, "igamg: chose fused coarse levels %d\n", best);
   std::lock_guard<std::mutex> lk(tune_mutex());
   tune_cache()[key] = best;
   return IGAMG_OK;
@@ -666,6 +690,26 @@ int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
   if ((rc = upload_as(h, &ty.coarse_inv, h->host.coarse_inv))) return rc;
   if ((rc = dmalloc(h, (void**)&ty.delta, std::max<size_t>(max_delta, 1) * sizeof(T)))) return rc;
   return setup_fused<T>(h, ty);
+}
+
+bool any_3d(int n, igamg_handle** hs) {
+  for (int i = 0; i < n; ++i) if (hs[i]->d3) return true;
+  return false;
+}
+
+// Batches holding 3D handles run their solves one after another (each 3D solve already
+// fills the GPU); the contract (statuses, reports, return value) is that of the 2D batch.
+int batch_3d(int n, igamg_handle** hs, double** Us, const double** Fs, double rtol, const double* atol,
+             int max_cycles, igamg_report* reps, int* status) {
+  int worst = IGAMG_OK;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]->d3) return IGAMG_EUNSUPPORTED;   // 2D and 3D handles are not mixed in one batch
+    int st = h3_solve(hs[i]->d3, Us[i], Fs[i], rtol, max_cycles, reps ? &reps[i] : nullptr, atol ? atol[i] : -1.0);
+    if (status) status[i] = st;
+    if (st < 0) return st;
+    if (st == IGAMG_NOT_CONVERGED) worst = IGAMG_NOT_CONVERGED;
+  }
+  return worst;
 }
 
 int validate(const igamg_problem& pr) {
@@ -707,6 +751,17 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
   if (!prob || !out) return IGAMG_EINVAL;
   *out = nullptr;
   const igamg_problem& pr = *prob;
+  if (pr.dim == 3) {
+    igamg3d_handle* h3 = nullptr;
+    int rc3 = h3_create(prob, cuda_stream, &h3);
+    if (rc3) return rc3;
+    auto* h = new igamg_handle();
+    h->prob = pr;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->d3 = h3;
+    *out = h;
+    return IGAMG_OK;
+  }
   int rc = validate(pr);
   if (rc) return rc;
   auto* h = new igamg_handle();
@@ -764,6 +819,7 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
 
 void igamg_destroy(igamg_handle* h) {
   if (!h) return;
+  if (h->d3) h3_destroy(h->d3);
   for (auto& g : h->graph) if (g) cudaGraphExecDestroy(g);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -774,6 +830,7 @@ void igamg_destroy(igamg_handle* h) {
 }
 
 int igamg_get_sizes(const igamg_handle* h, int level, igamg_sizes* out) {
+  if (h && out && h->d3) return h3_sizes(h->d3, level, out);
   if (!h || !out || level < 0 || level >= (int)h->lc.size()) return IGAMG_EINVAL;
   *out = h->lc[level].sz;
   return IGAMG_OK;
@@ -781,16 +838,18 @@ int igamg_get_sizes(const igamg_handle* h, int level, igamg_sizes* out) {
 
 int igamg_quad_points(const igamg_handle* h, double* x, size_t cap, size_t* n_out) {
   if (!h || !n_out) return IGAMG_EINVAL;
-  *n_out = h->host.quad_x.size();
+  const std::vector<double>& qx = h->d3 ? h3_quad_x(h->d3) : h->host.quad_x;
+  *n_out = qx.size();
   if (x) {
-    if (cap < h->host.quad_x.size()) return IGAMG_EINVAL;
-    std::memcpy(x, h->host.quad_x.data(), h->host.quad_x.size() * sizeof(double));
+    if (cap < qx.size()) return IGAMG_EINVAL;
+    std::memcpy(x, qx.data(), qx.size() * sizeof(double));
   }
   return IGAMG_OK;
 }
 
 int igamg_load_vector(igamg_handle* h, const double* f_qp, double* F) {
   if (!h || !f_qp || !F) return IGAMG_EINVAL;
+  if (h->d3) return h3_load_vector(h->d3, f_qp, F);
   auto& Lt = h->d.lev.back().L;
   if (h->prob.p == 2) k_load<2><<<nblk(Lt.n_total), kBlock, 0, h->stream>>>(Lt, h->lv_p, h->lv_q, f_qp, F);
   else k_load<3><<<nblk(Lt.n_total), kBlock, 0, h->stream>>>(Lt, h->lv_p, h->lv_q, f_qp, F);
@@ -798,6 +857,7 @@ int igamg_load_vector(igamg_handle* h, const double* f_qp, double* F) {
 }
 
 int igamg_residual(igamg_handle* h, int level, const double* U, const double* F, double* R, double* norm_out) {
+  if (h && U && F && R && h->d3) return h3_residual(h->d3, level, U, F, R, norm_out);
   if (!h || !U || !F || !R || level < 0 || level >= (int)h->lc.size()) return IGAMG_EINVAL;
   int rc = do_residual<double>(h, level, U, F, R, h->norm2, h->stream);
   if (rc) return rc;
@@ -806,28 +866,33 @@ int igamg_residual(igamg_handle* h, int level, const double* U, const double* F,
 }
 
 int igamg_smooth(igamg_handle* h, int level, double* U, const double* F, int sweeps) {
+  if (h && U && F && h->d3) return h3_smooth(h->d3, level, U, F, sweeps);
   if (!h || !U || !F || level < 1 || level >= (int)h->lc.size() || sweeps < 0) return IGAMG_EINVAL;
   for (int k = 0; k < sweeps; ++k) { int rc = do_smooth<double>(h, level, U, F, h->stream); if (rc) return rc; }
   return IGAMG_OK;
 }
 
 int igamg_restrict(igamg_handle* h, int level, const double* r_fine, double* g_coarse) {
+  if (h && r_fine && g_coarse && h->d3) return h3_restrict(h->d3, level, r_fine, g_coarse);
   if (!h || !r_fine || !g_coarse || level < 1 || level >= (int)h->lc.size()) return IGAMG_EINVAL;
   return do_restrict<double>(h, level, r_fine, g_coarse, h->stream);
 }
 
 int igamg_prolong_add(igamg_handle* h, int level, const double* u_coarse, double* u_fine) {
+  if (h && u_coarse && u_fine && h->d3) return h3_prolong_add(h->d3, level, u_coarse, u_fine);
   if (!h || !u_coarse || !u_fine || level < 1 || level >= (int)h->lc.size()) return IGAMG_EINVAL;
   return do_prolong<double>(h, level, u_coarse, u_fine, h->stream);
 }
 
 int igamg_coarse_solve(igamg_handle* h, const double* G, double* U) {
   if (!h || !G || !U) return IGAMG_EINVAL;
+  if (h->d3) return h3_coarse_solve(h->d3, G, U);
   return do_coarse<double>(h, G, U, h->stream);
 }
 
 int igamg_vcycle(igamg_handle* h, double* U, const double* F) {
   if (!h || !U || !F) return IGAMG_EINVAL;
+  if (h->d3) return h3_vcycle(h->d3, U, F);
   int rc = ensure_graph(h, 1, U, F);
   if (rc) return rc;
   CK(cudaGraphLaunch(h->graph[1], h->stream));
@@ -836,12 +901,14 @@ int igamg_vcycle(igamg_handle* h, double* U, const double* F) {
 
 int igamg_solve(igamg_handle* h, double* U, const double* F, double rtol, int max_cycles, igamg_report* rep) {
   if (!h || !U || !F || !(rtol >= 0) || max_cycles < 0) return IGAMG_EINVAL;
+  if (h->d3) return h3_solve(h->d3, U, F, rtol, max_cycles, rep, -1.0);
   return solve_impl(h, U, F, rtol, max_cycles, rep);
 }
 
 int igamg_solve_host(igamg_handle* h, const double* f_qp_host, double* U_host, double rtol, int max_cycles,
                      igamg_report* rep) {
   if (!h || !f_qp_host || !U_host || !(rtol >= 0) || max_cycles < 0) return IGAMG_EINVAL;
+  if (h->d3) return h3_solve_host(h->d3, f_qp_host, U_host, rtol, max_cycles, rep);
   size_t nG = (size_t)h->prob.n_fine * (h->prob.p + 2);
   size_t nt = (size_t)h->lc.back().sz.n_total;
   CK(cudaMemcpyAsync(h->f_dev, f_qp_host, 2 * nG * nG * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -862,11 +929,13 @@ int igamg_solve_batch(int n, igamg_handle** handles, double** U, const double** 
     if (!handles[i] || !U[i] || !F[i]) return IGAMG_EINVAL;
     for (int j = 0; j < i; ++j) if (handles[j] == handles[i]) return IGAMG_EINVAL;
   }
+  if (any_3d(n, handles)) return batch_3d(n, handles, U, F, rtol, nullptr, max_cycles, reports, status);
   return solve_batch_impl(n, handles, U, F, rtol, max_cycles, reports, status);
 }
 
 int igamg_solve_abs(igamg_handle* h, double* U, const double* F, double atol, int max_cycles, igamg_report* rep) {
   if (!h || !U || !F || !(atol >= 0) || max_cycles < 0) return IGAMG_EINVAL;
+  if (h->d3) return h3_solve(h->d3, U, F, 0.0, max_cycles, rep, atol);
   return solve_impl(h, U, F, 0.0, max_cycles, rep, atol);
 }
 
@@ -877,16 +946,19 @@ int igamg_solve_batch_abs(int n, igamg_handle** handles, double** U, const doubl
     if (!handles[i] || !U[i] || !F[i] || !(atol[i] >= 0)) return IGAMG_EINVAL;
     for (int j = 0; j < i; ++j) if (handles[j] == handles[i]) return IGAMG_EINVAL;
   }
+  if (any_3d(n, handles)) return batch_3d(n, handles, U, F, 0.0, atol, max_cycles, reports, status);
   return solve_batch_impl(n, handles, U, F, 0.0, max_cycles, reports, status, atol);
 }
 
 int igamg_div_inf(igamg_handle* h, const double* U, double* out) {
   if (!h || !U || !out) return IGAMG_EINVAL;
+  if (h->d3) return h3_div_inf(h->d3, U, out);
   return div_inf_impl(h, U, out);
 }
 
 int igamg_streamfunction(igamg_handle* h, const double* U, double* psi) {
   if (!h || !U || !psi) return IGAMG_EINVAL;
+  if (h->d3) return IGAMG_EUNSUPPORTED;
   auto& Lt = h->d.lev.back().L;
   k_streamfunction<<<nblk((long long)Lt.nint * 32, 128), 128, 0, h->stream>>>(Lt.nint, Lt.nxu, h->lc.back().inv_dcoef, U, psi);
   return launch_check();
@@ -894,6 +966,7 @@ int igamg_streamfunction(igamg_handle* h, const double* U, double* psi) {
 
 int igamg_warm_start(igamg_handle* h, const float* grid, double psi_scale, double p_scale, double* U) {
   if (!h || !grid || !U) return IGAMG_EINVAL;
+  if (h->d3) return IGAMG_EUNSUPPORTED;
   auto& Lt = h->d.lev.back().L;
   k_grid_to_psi<<<nblk((long long)Lt.nint * Lt.nint), kBlock, 0, h->stream>>>(Lt.nint, grid, psi_scale, h->psi);
   CK(cudaMemsetAsync(U, 0, Lt.n_total * sizeof(double), h->stream));
@@ -906,6 +979,7 @@ int igamg_warm_start(igamg_handle* h, const float* grid, double psi_scale, doubl
 
 int igamg_curl(igamg_handle* h, const double* psi, double* U) {
   if (!h || !psi || !U) return IGAMG_EINVAL;
+  if (h->d3) return h3_curl(h->d3, psi, U);
   auto& Lt = h->d.lev.back().L;
   k_curl<<<nblk(Lt.n_ux + Lt.n_uy), kBlock, 0, h->stream>>>(Lt, h->lc.back().dcoef, psi, U);
   return launch_check();
@@ -1004,6 +1078,7 @@ extern "C" int igamg_residual_static(const igamg_problem* prob, int level, const
 extern "C" int igamg_host_operator_rows(const igamg_problem* prob, int level, double* K, size_t cap,
                                         long long* n_out) {
   if (!prob) return IGAMG_EINVAL;
+  if (prob->dim == 3) return host_operator_rows3(prob, level, K, cap, n_out);
   int rc = validate(*prob);
   if (rc) return rc;
   if (level < 0 || level >= prob->n_levels) return IGAMG_EINVAL;
@@ -1031,5 +1106,33 @@ extern "C" int igamg_host_operator_rows(const igamg_problem* prob, int level, do
     K[(n - 1) * n + j] = lam;
     e[j] = 0.0;
   }
+  return IGAMG_OK;
+}
+
+// Host-only: KV = K_l V through the same row evaluation the kernels use.
+extern "C" int igamg_host_operator_apply(const igamg_problem* prob, int level, const double* V, double* KV,
+                                         size_t n) {
+  if (!prob || !V || !KV) return IGAMG_EINVAL;
+  if (prob->dim == 3) return host_operator_apply3(prob, level, V, KV, n);
+  int rc = validate(*prob);
+  if (rc) return rc;
+  if (level < 0 || level >= prob->n_levels) return IGAMG_EINVAL;
+  HierarchyHost H;
+  std::string err;
+  if ((rc = build_hierarchy(*prob, H, err))) return rc;
+  const auto& lh = H.lev[level];
+  if (n != (size_t)lh.sz.n_total) return IGAMG_EINVAL;
+  LevelTab<double> L = make_tab<double>(lh.sz, prob->p, lh.st.sx.data(), lh.st.sy.data(), lh.st.sp.data(),
+                                        lh.rows.empty() ? nullptr : lh.rows.data());
+  double lam = 0.0;
+  for (size_t i = 0; i + 1 < n; ++i) {
+    KV[i] = prob->p == 2 ? row_KU<2, double>(L, V, (int)i) : row_KU<3, double>(L, V, (int)i);
+    if ((long long)i >= lh.sz.n_ux + lh.sz.n_uy) {
+      int r = (int)(i - lh.sz.n_ux - lh.sz.n_uy);
+      int ky = r / L.npd, kx = r - ky * L.npd;
+      lam += lh.f.mq[kx] * lh.f.mq[ky] * V[i];
+    }
+  }
+  KV[n - 1] = lam;
   return IGAMG_OK;
 }

@@ -117,4 +117,65 @@ double k_entry_rows(const LevelHost& lv, int p, long long g1, long long g2);
 void build_level1d(int p, int n, double sigma, double nu, double pen_over_nu, Level1D& L);
 void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st);
 
+// helpers of setup.cpp shared with the 3D set-up
+std::vector<double> knots(int d, int n);
+void span_values(const std::vector<double>& t, int d, int s, double x, double* N);
+void gauss01(int m, std::vector<double>& x, std::vector<double>& w);
+bool invert(std::vector<double> A, int n, std::vector<double>& Ainv);
+std::vector<double> prolong_dense(int d, int nc, int& nfb, int& ncb);
+bool make_transfer(const std::vector<double>& P, int nfb, int ncb, int off, Transfer1D& T);
+
+// ---- 3D (unit cube) ----------------------------------------------------------------------
+// Layout of U on a level with n elements per direction, q = p-1, ni = n+p-2, nq = n+p-1:
+//   u_x: (z: nq) x (y: nq) x (x: ni, full indices 1..ni), x fastest; u_y: nq x ni x nq;
+//   u_z: ni x nq x nq; p: nq^3; lambda.  Component c is degree p along axis c.
+struct Sizes3 {
+  int n = 0, p = 0, ni = 0, nq = 0;
+  long long n_uc = 0, n_u = 0, n_p = 0, n_total = 0;
+};
+Sizes3 sizes3(int p, int n);
+
+// Row records of K_l by row class, one table per row kind (u_x, u_y, u_z, p rows); a
+// class is the triple of 1D position classes (cls1) of the row's indices.  Every record
+// has RU = B0 + 2 B1 + 1 entries: three boxes of neighbours, each "long" along one axis
+// (entries ordered long-axis slowest, then axis (c+1)%3, then (c+2)%3 fastest), then the
+// lambda coefficient.
+//   u_c rows: box 0 = A_cc over u_c (long axis c, offsets -p..p; -q..q across),
+//             box 1 = -B_c over p (long axis c, -p..p-1), box 2 = zeros (over p)
+//   p rows:   box k = B_k^T over u_k (long axis k, offsets -q..p; -q..q across; box 0
+//             holds 2p of its 2p+1 long positions), lambda coefficient m_k last
+// B0 = (2p+1)(2q+1)^2, B1 = 2p(2q+1)^2.  Neighbours outside the index range have zero
+// coefficients.  cmap[kind][class] -> record index (compact: only classes that occur).
+struct Stencils3 {
+  int T = 0, NC = 0, B0 = 0, B1 = 0, RU = 0;
+  std::vector<int> cmap[4];
+  std::vector<double> rec[4];
+};
+
+struct LevelHost3 {
+  Level1D f;
+  Sizes3 sz;
+  igamg_sizes pub{};
+  PatchTables pt;
+  Stencils3 st;
+};
+
+struct HierarchyHost3 {
+  int p = 0, L = 0, n_fine = 0;
+  double sigma = 0, nu = 0, cpen = 0;
+  std::vector<LevelHost3> lev;
+  std::vector<Transfer1D> tp_free, tq;
+  std::vector<double> coarse_inv;
+  int ndof0 = 0;
+  int G = 0;
+  std::vector<double> lv_p, lv_q, quad_x;
+};
+
+int build_hierarchy3(const igamg_problem& pr, HierarchyHost3& H, std::string& err);
+// the finest level's 1D factors and row records only (no patches, transfers, coarse inverse)
+int build_level_only3(const igamg_problem& pr, HierarchyHost3& H, std::string& err);
+double k_entry3(const Level1D& L, const Sizes3& s, long long g1, long long g2);
+// entry (g1, g2) evaluated from the row records, as the GPU kernels do
+double k_entry3_records(const LevelHost3& lv, int p, long long g1, long long g2);
+
 }  // namespace igamg

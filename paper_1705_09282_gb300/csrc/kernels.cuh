@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(1024) k_fused_coarse(FusedDesc<T> D, const T* 
 }
 
 // ---- mixed precision helpers ---------------------------------------------------------
-__global__ void k_to_float(int n, const double* __restrict__ a, float* __restrict__ b) {
+static __global__ void k_to_float(int n, const double* __restrict__ a, float* __restrict__ b) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
 }
@@ -470,7 +470,7 @@ __global__ void k_to_float(int n, const double* __restrict__ a, float* __restric
 // block: psi(ix, k+1) = psi(ix, k) + e_x(ix, k) / dcoef_k, psi = 0 on the bottom wall.
 // One warp per interior column: each lane sums a contiguous run, then a warp scan.
 // psi is stored on the (n+p-2)^2 interior, FP64.
-__global__ void k_integrate_psi(int nint, int nxu, const double* __restrict__ inv_dcoef,
+static __global__ void k_integrate_psi(int nint, int nxu, const double* __restrict__ inv_dcoef,
                                 const float* __restrict__ e, double* __restrict__ psi) {
   int ix = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // interior column
   int lane = threadIdx.x & 31;

@@ -1,0 +1,272 @@
+// Device kernels of the 3D (unit cube) V-cycle: Algorithm 1 with the multiplicative
+// Schwarz smoother over vector-potential supports (Sec. 5.2), the transfers of Sec. 5.1 per
+// tensor direction, templated on the degree P and on the value type T.
+//
+// Row evaluation: every row is three boxes of neighbours, each long along one axis
+// (2P+1 or 2P positions) and 2P-1 wide across, read with one fused multiply-add per
+// neighbour from the row's class record (records and layout: Stencils3 in
+// igamg_internal.h).  Neighbour indices are clamped into range (their coefficients are
+// zero), so no lane branches on where its row sits.
+#pragma once
+#include "kernels.cuh"
+
+namespace igamg {
+namespace dev {
+
+template <typename T>
+struct LevelTab3 {
+  int n, ni, nq;                         // ni = n+p-2 (free degree-p indices 1..ni), nq = n+p-1
+  int n_uc, n_u, n_p, n_total;
+  const int *cm0, *cm1, *cm2, *cm3;      // class -> record, per row kind
+  const T *rc0, *rc1, *rc2, *rc3;        // records, per row kind
+};
+
+template <int P>
+struct Rec3 {
+  static constexpr int Q = P - 1, W = 2 * Q + 1;
+  static constexpr int B0 = (2 * P + 1) * W * W, B1 = 2 * P * W * W, RU = B0 + 2 * B1 + 1;
+  static constexpr int TC = 2 * P + 1, NC = 2 * TC + 1;
+};
+
+__host__ __device__ __forceinline__ int sel3(int c, int a, int b, int d) { return c == 0 ? a : (c == 1 ? b : d); }
+
+// row g -> kind (0..2 velocity component, 3 pressure) and full indices (x, y, z)
+template <typename T>
+__host__ __device__ __forceinline__ void decode3(const LevelTab3<T>& L, int g, int& kind, int& x, int& y, int& z) {
+  kind = (g >= L.n_uc) + (g >= 2 * L.n_uc) + (g >= L.n_u);
+  int base = kind < 3 ? kind * L.n_uc : L.n_u;
+  int r = g - base;
+  int dx = kind == 0 ? L.ni : L.nq, dy = kind == 1 ? L.ni : L.nq;
+  int t = r / dx;
+  x = r - t * dx;
+  z = t / dy;
+  y = t - z * dy;
+  x += kind == 0; y += kind == 1; z += kind == 2;
+}
+
+// Per-axis data of block blk along axis a: valid full-index range [lo, hi] (local index =
+// full - lo) and stride.
+template <typename T>
+__host__ __device__ __forceinline__ void axis3(const LevelTab3<T>& L, int blk, int a, int& lo, int& hi, int& stride) {
+  bool own = blk < 3 && a == blk;
+  lo = own ? 1 : 0;
+  hi = own ? L.ni : L.nq - 1;
+  int dx = blk == 0 ? L.ni : L.nq, dy = blk == 1 ? L.ni : L.nq;
+  stride = a == 0 ? 1 : (a == 1 ? dx : dx * dy);
+}
+
+// sum over one box: LEN positions along axis c (from pos_c + org), 2Q+1 across on the two
+// other axes (from pos - Q), coefficients coef[(a W + e1) W + e2].
+template <int P, int LEN, typename T>
+__host__ __device__ __forceinline__ T box3(const LevelTab3<T>& L, const T* __restrict__ coef, const T* __restrict__ U,
+                                  int blk, int c, int org, int x, int y, int z) {
+  constexpr int Q = P - 1, W = 2 * Q + 1;
+  const int o1 = c == 2 ? 0 : c + 1, o2 = c == 0 ? 2 : c - 1;
+  const int pc = sel3(c, x, y, z), p1 = sel3(o1, x, y, z), p2 = sel3(o2, x, y, z);
+  int loc, hic, sc, lo1, hi1, s1, lo2, hi2, s2;
+  axis3(L, blk, c, loc, hic, sc);
+  axis3(L, blk, o1, lo1, hi1, s1);
+  axis3(L, blk, o2, lo2, hi2, s2);
+  const T* base = U + (blk < 3 ? blk * L.n_uc : L.n_u);
+  int A[LEN], B1[W], B2[W];
+#pragma unroll
+  for (int a = 0; a < LEN; ++a) A[a] = (clampi(pc + org + a, loc, hic) - loc) * sc;
+#pragma unroll
+  for (int e = 0; e < W; ++e) {
+    B1[e] = (clampi(p1 - Q + e, lo1, hi1) - lo1) * s1;
+    B2[e] = (clampi(p2 - Q + e, lo2, hi2) - lo2) * s2;
+  }
+  T s0 = T(0), sA = T(0), sB = T(0), sC = T(0);
+#pragma unroll
+  for (int a = 0; a < LEN; ++a)
+#pragma unroll
+    for (int e1 = 0; e1 < W; ++e1)
+#pragma unroll
+      for (int e2 = 0; e2 < W; ++e2) {
+        const int j = (a * W + e1) * W + e2;
+        T v = base[A[a] + B1[e1] + B2[e2]];
+        if ((j & 3) == 0) s0 = fma(coef[j], v, s0);
+        else if ((j & 3) == 1) sA = fma(coef[j], v, sA);
+        else if ((j & 3) == 2) sB = fma(coef[j], v, sB);
+        else sC = fma(coef[j], v, sC);
+      }
+  return (s0 + sA) + (sB + sC);
+}
+
+// record of row (kind; x, y, z)
+template <int P, typename T>
+__host__ __device__ __forceinline__ const T* rec3(const LevelTab3<T>& L, int kind, int x, int y, int z) {
+  using R = Rec3<P>;
+  const int lastp = L.n + P - 1, lastq = L.n + P - 2;
+  int cx = cls1d<P>(x, kind == 0 ? lastp : lastq);
+  int cy = cls1d<P>(y, kind == 1 ? lastp : lastq);
+  int cz = cls1d<P>(z, kind == 2 ? lastp : lastq);
+  int cl = (cz * R::NC + cy) * R::NC + cx;
+  const int* cm = kind == 0 ? L.cm0 : (kind == 1 ? L.cm1 : (kind == 2 ? L.cm2 : L.cm3));
+  const T* rc = kind == 0 ? L.rc0 : (kind == 1 ? L.rc1 : (kind == 2 ? L.rc2 : L.rc3));
+  return rc + (size_t)cm[cl] * R::RU;
+}
+
+// (K U)_g for one row g (not lambda); *m gets the row's mean coefficient (p rows) or 0.
+template <int P, typename T>
+__host__ __device__ __forceinline__ T row3(const LevelTab3<T>& L, const T* __restrict__ U, int g, T* m = nullptr) {
+  using R = Rec3<P>;
+  int kind, x, y, z;
+  decode3(L, g, kind, x, y, z);
+  const T* rc = rec3<P>(L, kind, x, y, z);
+  const bool vel = kind < 3;
+  // box 0: own component (velocity rows) or u_x (pressure rows)
+  T acc = box3<P, 2 * P + 1>(L, rc, U, vel ? kind : 0, vel ? kind : 0, vel ? -P : -(P - 1), x, y, z);
+  // box 1: pressure (velocity rows) or u_y (pressure rows)
+  acc += box3<P, 2 * P>(L, rc + R::B0, U, vel ? 3 : 1, vel ? kind : 1, vel ? -P : -(P - 1), x, y, z);
+  if (!vel) {
+    acc += box3<P, 2 * P>(L, rc + R::B0 + R::B1, U, 2, 2, -(P - 1), x, y, z);
+    acc = fma(rc[R::RU - 1], U[L.n_total - 1], acc);
+    if (m) *m = rc[R::RU - 1];
+  } else if (m) {
+    *m = T(0);
+  }
+  return acc;
+}
+
+// R = F - K U (every row but lambda); per-block partial sums of R^2 and of m.p.
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_residual3(LevelTab3<T> L, const T* __restrict__ U, const T* __restrict__ F,
+                                                   T* __restrict__ R, double* __restrict__ part) {
+  __shared__ double sh[32];
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  double r2 = 0.0, mp = 0.0;
+  if (g < L.n_total - 1) {
+    T m;
+    T r = F[g] - row3<P>(L, U, g, &m);
+    R[g] = r;
+    r2 = (double)r * (double)r;
+    mp = (double)m * (double)U[g];
+  }
+  double s1 = block_sum(r2, sh);
+  double s2 = block_sum(mp, sh);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1; part[2 * blockIdx.x + 1] = s2; }
+}
+
+// One colour of the multiplicative sweep (eq. MSM).  Blocks [0, nb8): four 8-DOF patches
+// per warp, lane = (patch, local row); blocks [nb8, ...): one warp per larger patch.
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_mult_colour3(LevelTab3<T> L, T* __restrict__ U, const T* __restrict__ F,
+                                                      const int* __restrict__ dofs, const int* __restrict__ cls,
+                                                      const T* __restrict__ cinv, const T* __restrict__ cinv8,
+                                                      const int* __restrict__ nloc, int maxl, int first, int n8,
+                                                      int ngen, int nb8) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if ((int)blockIdx.x < nb8) {
+    const int grp = (blockIdx.x * 8 + wib) * 4 + (lane >> 3), row = lane & 7;
+    const bool active = grp < n8;
+    const int patch = first + (active ? grp : 0);
+    const int g = dofs[(size_t)patch * maxl + row];
+    T r = F[g] - row3<P>(L, U, g);
+    const T* A = cinv8 + (size_t)cls[patch] * 64 + row * 8;
+    T d0 = T(0), d1 = T(0);
+#pragma unroll
+    for (int s = 0; s < 8; s += 2) {
+      d0 = fma(A[s], __shfl_sync(0xffffffffu, r, (lane & ~7) + s), d0);
+      d1 = fma(A[s + 1], __shfl_sync(0xffffffffu, r, (lane & ~7) + s + 1), d1);
+    }
+    if (active) U[g] += d0 + d1;
+    return;
+  }
+  extern __shared__ unsigned char smem_raw[];
+  T* r = reinterpret_cast<T*>(smem_raw) + wib * maxl;
+  const int w = ((int)blockIdx.x - nb8) * 8 + wib;
+  if (w >= ngen) return;
+  const int patch = first + n8 + w;
+  const int c = cls[patch], nl = nloc[c];
+  const int* pd = dofs + (size_t)patch * maxl;
+  for (int k = lane; k < nl; k += 32) { int g = pd[k]; r[k] = F[g] - row3<P>(L, U, g); }
+  __syncwarp();
+  const T* A = cinv + (size_t)c * maxl * maxl;
+  for (int k = lane; k < nl; k += 32) U[pd[k]] += dot_n(A + (size_t)k * maxl, r, nl);
+}
+
+// block and local (x, y, z) of entry g (not lambda) on a level
+template <typename T>
+__device__ __forceinline__ void split3(const LevelTab3<T>& L, int g, int& blk, int& x, int& y, int& z, int& dx, int& dy) {
+  blk = (g >= L.n_uc) + (g >= 2 * L.n_uc) + (g >= L.n_u);
+  int r = g - (blk < 3 ? blk * L.n_uc : L.n_u);
+  dx = blk == 0 ? L.ni : L.nq;
+  dy = blk == 1 ? L.ni : L.nq;
+  int t = r / dx;
+  x = r - t * dx;
+  z = t / dy;
+  y = t - z * dy;
+}
+
+// u_f += P u_c: per fine entry, the 3 x 3 x 3 tensor product of 1D knot-insertion weights
+// (degree p along the component's own axis, p-1 across; all p-1 for the pressure).
+template <typename T>
+__global__ void k_prolong_add3(LevelTab3<T> Lf, LevelTab3<T> Lc, Xfer<T> tp, Xfer<T> tq, const T* __restrict__ uc,
+                               T* __restrict__ uf) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Lf.n_total) return;
+  if (g == Lf.n_total - 1) { uf[g] += uc[Lc.n_total - 1]; return; }
+  int blk, x, y, z, dx, dy;
+  split3(Lf, g, blk, x, y, z, dx, dy);
+  const Xfer<T>& X = blk == 0 ? tp : tq;
+  const Xfer<T>& Y = blk == 1 ? tp : tq;
+  const Xfer<T>& Z = blk == 2 ? tp : tq;
+  const int cdx = blk == 0 ? Lc.ni : Lc.nq, cdy = blk == 1 ? Lc.ni : Lc.nq;
+  const T* src = uc + (blk < 3 ? blk * Lc.n_uc : Lc.n_u);
+  const int cx0 = X.c0[x], cy0 = Y.c0[y], cz0 = Z.c0[z];
+  T acc = T(0);
+#pragma unroll
+  for (int kz = 0; kz < kWP; ++kz) {
+    int cz = min(cz0 + kz, Z.nc - 1);            // weights past the end are zero
+    T sy = T(0);
+#pragma unroll
+    for (int ky = 0; ky < kWP; ++ky) {
+      int cy = min(cy0 + ky, Y.nc - 1);
+      const T* rowp = src + ((size_t)cz * cdy + cy) * cdx;
+      T sx = T(0);
+#pragma unroll
+      for (int kx = 0; kx < kWP; ++kx) sx = fma(X.pv[x * kWP + kx], rowp[min(cx0 + kx, X.nc - 1)], sx);
+      sy = fma(Y.pv[y * kWP + ky], sx, sy);
+    }
+    acc = fma(Z.pv[z * kWP + kz], sy, acc);
+  }
+  uf[g] += acc;
+}
+
+// g_c = P^T r_f: per coarse entry, the 5 x 5 x 5 tensor product of the transposed weights.
+template <typename T>
+__global__ void k_restrict3(LevelTab3<T> Lf, LevelTab3<T> Lc, Xfer<T> tp, Xfer<T> tq, const T* __restrict__ rf,
+                            T* __restrict__ gc) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Lc.n_total) return;
+  if (g == Lc.n_total - 1) { gc[g] = rf[Lf.n_total - 1]; return; }
+  int blk, x, y, z, dx, dy;
+  split3(Lc, g, blk, x, y, z, dx, dy);
+  const Xfer<T>& X = blk == 0 ? tp : tq;
+  const Xfer<T>& Y = blk == 1 ? tp : tq;
+  const Xfer<T>& Z = blk == 2 ? tp : tq;
+  const int fdx = blk == 0 ? Lf.ni : Lf.nq, fdy = blk == 1 ? Lf.ni : Lf.nq;
+  const T* src = rf + (blk < 3 ? blk * Lf.n_uc : Lf.n_u);
+  const int fx0 = X.f0[x], fy0 = Y.f0[y], fz0 = Z.f0[z];
+  T acc = T(0);
+#pragma unroll
+  for (int kz = 0; kz < kWR; ++kz) {
+    int fz = min(fz0 + kz, Z.nf - 1);
+    T sy = T(0);
+#pragma unroll
+    for (int ky = 0; ky < kWR; ++ky) {
+      int fy = min(fy0 + ky, Y.nf - 1);
+      const T* rowp = src + ((size_t)fz * fdy + fy) * fdx;
+      T sx = T(0);
+#pragma unroll
+      for (int kx = 0; kx < kWR; ++kx) sx = fma(X.rv[x * kWR + kx], rowp[min(fx0 + kx, X.nf - 1)], sx);
+      sy = fma(Y.rv[y * kWR + ky], sx, sy);
+    }
+    acc = fma(Z.rv[z * kWR + kz], sy, acc);
+  }
+  gc[g] = acc;
+}
+
+}  // namespace dev
+}  // namespace igamg

@@ -16,6 +16,7 @@
 #include <thread>
 #include <utility>
 
+#include "igamg3d.h"
 #include "igamg_internal.h"
 
 namespace igamg {
@@ -29,7 +30,7 @@ void Band::add(int i, int j, double x) {
   v[(size_t)i * (2 * hw + 1) + d] += x;
 }
 
-namespace {
+// ---- shared helpers (also used by the 3D set-up) ----
 
 std::vector<double> knots(int d, int n) {
   std::vector<double> t(n + 2 * d + 1);
@@ -140,7 +141,7 @@ bool invert(std::vector<double> A, int n, std::vector<double>& Ainv) {
   return true;
 }
 
-}  // namespace
+
 
 // 1D factors on n elements (all integrals by (p+2)-point Gauss, exact for these polynomials).
 void build_level1d(int p, int n, double sigma, double nu, double pen_over_nu, Level1D& L) {
@@ -199,7 +200,7 @@ void build_level1d(int p, int n, double sigma, double nu, double pen_over_nu, Le
   for (int k = 1; k <= n + q; ++k) L.dcoef[k - 1] = p / (tp[k + p] - tp[k]);
 }
 
-namespace {
+
 
 // Dense 1D prolongation (fine x coarse) for midpoint refinement, by collocation.
 std::vector<double> prolong_dense(int d, int nc, int& nfb, int& ncb) {
@@ -281,7 +282,7 @@ long long gid(const igamg_sizes& s, int blk, int x, int y) {
   }
 }
 
-}  // namespace
+
 
 double k_entry(const Level1D& L, const igamg_sizes& s, long long g1, long long g2) {
   Dof a = decode(s, g1), b = decode(s, g2);
@@ -622,6 +623,8 @@ igamg_sizes level_sizes(int p, int n) {
   s.n_patches = (n + p - 2) * (n + p - 2);
   s.n_colours = (p + 1) * (p + 1);
   s.n_quad = p + 2;
+  s.dim = 2;
+  s.n_uz = 0;
   return s;
 }
 
@@ -793,6 +796,7 @@ int host_build(const igamg_problem* prob, int level, igamg::HierarchyHost& H) {
 
 extern "C" int igamg_host_level_matrix(const igamg_problem* prob, int level, double* K, size_t cap,
                                        long long* n_out) {
+  if (prob && prob->dim == 3) return igamg::host_level_matrix3(prob, level, K, cap, n_out, false);
   igamg::HierarchyHost H;
   int rc = host_build(prob, level, H);
   if (rc) return rc;
@@ -809,6 +813,7 @@ extern "C" int igamg_host_level_matrix(const igamg_problem* prob, int level, dou
 
 extern "C" int igamg_host_prolongation(const igamg_problem* prob, int level, double* P, size_t cap,
                                        long long* n_rows, long long* n_cols) {
+  if (prob && prob->dim == 3) return igamg::host_prolongation3(prob, level, P, cap, n_rows, n_cols);
   if (level < 1) return IGAMG_EINVAL;
   igamg::HierarchyHost H;
   int rc = host_build(prob, level, H);
@@ -844,6 +849,8 @@ extern "C" int igamg_host_prolongation(const igamg_problem* prob, int level, dou
 
 extern "C" int igamg_host_patches(const igamg_problem* prob, int level, int* colour, int* dofs,
                                   size_t cap_patches, size_t cap_dofs, int* n_patches, int* maxl) {
+  if (prob && prob->dim == 3)
+    return igamg::host_patches3(prob, level, colour, dofs, cap_patches, cap_dofs, n_patches, maxl);
   if (level < 1) return IGAMG_EINVAL;
   igamg::HierarchyHost H;
   int rc = host_build(prob, level, H);

@@ -21,10 +21,11 @@ def _ptr(t):
 
 
 class Solver:
-    """Owns one igamg_handle: the level hierarchy of Sec. 5.1 for a 2D problem."""
+    """Owns one igamg_handle: the level hierarchy of Sec. 5.1 for a 2D (unit square) or
+    3D (unit cube, dim=3) problem."""
 
     def __init__(self, p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.5, nu1=2, nu2=2,
-                 c_penalty=0.0, precision=_lib.IGAMG_FP64, device="cuda", stream=None, beta=None):
+                 c_penalty=0.0, precision=_lib.IGAMG_FP64, device="cuda", stream=None, beta=None, dim=2):
         """beta: advection at the quadrature points (host array (2, nG, nG)) for the
         generalized Oseen problem, or None for generalized Stokes."""
         self.device = torch.device(device)
@@ -33,8 +34,8 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
         self.problem = _lib.make_problem(p, n_fine, n_levels, sigma, nu, smoother, eta, nu1, nu2,
-                                         c_penalty, precision, beta=self._beta)
-        self.p, self.n_fine, self.n_levels = p, n_fine, n_levels
+                                         c_penalty, precision, beta=self._beta, dim=dim)
+        self.p, self.n_fine, self.n_levels, self.dim = p, n_fine, n_levels, dim
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib().igamg_create(ctypes.byref(self.problem), ctypes.c_void_p(self.stream.cuda_stream),
@@ -174,9 +175,9 @@ def solve_batch(solvers, Us, Fs, rtol=1e-8, max_cycles=100, history=False):
 
 
 # ---- host-only inspection (no GPU) ----------------------------------------------------
-def host_level_matrix(p, n_fine, n_levels, sigma, nu, level, c_penalty=0.0, beta=None):
+def host_level_matrix(p, n_fine, n_levels, sigma, nu, level, c_penalty=0.0, beta=None, dim=2):
     beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
-    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, c_penalty=c_penalty, beta=beta)
+    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, c_penalty=c_penalty, beta=beta, dim=dim)
     n = ctypes.c_longlong()
     check(lib().igamg_host_level_matrix(ctypes.byref(pr), level, None, 0, ctypes.byref(n)), "host_level_matrix")
     K = np.zeros((n.value, n.value))
@@ -185,9 +186,9 @@ def host_level_matrix(p, n_fine, n_levels, sigma, nu, level, c_penalty=0.0, beta
     return K
 
 
-def host_operator_rows(p, n_fine, n_levels, sigma, nu, level, beta=None):
+def host_operator_rows(p, n_fine, n_levels, sigma, nu, level, beta=None, dim=2):
     beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
-    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, beta=beta)
+    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, beta=beta, dim=dim)
     n = ctypes.c_longlong()
     check(lib().igamg_host_operator_rows(ctypes.byref(pr), level, None, 0, ctypes.byref(n)), "host_operator_rows")
     K = np.zeros((n.value, n.value))
@@ -196,8 +197,19 @@ def host_operator_rows(p, n_fine, n_levels, sigma, nu, level, beta=None):
     return K
 
 
-def host_prolongation(p, n_fine, n_levels, level):
-    pr = _lib.make_problem(p, n_fine, n_levels, 1.0, 1.0)
+def host_operator_apply(p, n_fine, n_levels, sigma, nu, level, V, beta=None, dim=2):
+    """K_l V through the kernels' row evaluation, on the host (V: float64 numpy vector)."""
+    beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
+    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, beta=beta, dim=dim)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    KV = np.zeros_like(V)
+    check(lib().igamg_host_operator_apply(ctypes.byref(pr), level, V.ctypes.data_as(ctypes.c_void_p),
+                                          KV.ctypes.data_as(ctypes.c_void_p), V.size), "host_operator_apply")
+    return KV
+
+
+def host_prolongation(p, n_fine, n_levels, level, dim=2):
+    pr = _lib.make_problem(p, n_fine, n_levels, 1.0, 1.0, dim=dim)
     r, c = ctypes.c_longlong(), ctypes.c_longlong()
     check(lib().igamg_host_prolongation(ctypes.byref(pr), level, None, 0, ctypes.byref(r), ctypes.byref(c)),
           "host_prolongation")
@@ -207,8 +219,8 @@ def host_prolongation(p, n_fine, n_levels, level):
     return P
 
 
-def host_patches(p, n_fine, n_levels, level):
-    pr = _lib.make_problem(p, n_fine, n_levels, 1.0, 1.0)
+def host_patches(p, n_fine, n_levels, level, dim=2):
+    pr = _lib.make_problem(p, n_fine, n_levels, 1.0, 1.0, dim=dim)
     npat, maxl = ctypes.c_int(), ctypes.c_int()
     check(lib().igamg_host_patches(ctypes.byref(pr), level, None, None, 0, 0, ctypes.byref(npat),
                                    ctypes.byref(maxl)), "host_patches")
