@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -189,7 +190,7 @@ __global__ void k_lift3_chi(int ni, int nq, const double* __restrict__ dcoef, co
 template <typename T>
 struct Lev3T {
   LevelTab3<T> L{};
-  T *cinv = nullptr, *cinv8 = nullptr;
+  T *cinv = nullptr, *cinv8 = nullptr, *cinv_all = nullptr;
   Xfer<T> tp{}, tq{};
   T *U = nullptr, *F = nullptr, *R = nullptr;
 };
@@ -201,9 +202,11 @@ struct Typed3 {
 };
 
 struct Lev3Common {
-  int n_patches = 0, maxl = 0, n_colours = 0;
-  std::vector<int> colour_off, n8;
+  int n_patches = 0, maxl = 0, n_colours = 0, row_slots = 0;
+  std::vector<int> colour_off, n8, colour_blk;
   int *dofs = nullptr, *cls = nullptr, *nloc = nullptr;
+  int *slot_g = nullptr, *slot_c = nullptr;
+  unsigned* slot_kb = nullptr;
   double *dcoef = nullptr, *inv_dcoef = nullptr;
 };
 
@@ -254,6 +257,27 @@ int launch_check() {
   return IGAMG_OK;
 }
 
+// colour kernel: row-parallel (default) or the patch-per-lane-group form (IGAMG_PATCH_KERNEL=lanes)
+bool row_parallel() {
+  static const bool rp = [] {
+    const char* e = std::getenv("IGAMG_PATCH_KERNEL");
+    return !(e && std::strcmp(e, "lanes") == 0);
+  }();
+  return rp;
+}
+
+// Split rows (k_mult_rows3x) where a colour has few rows: IGAMG_ROW_SPLIT = 0 (never),
+// 1 (always), unset (levels whose colours average fewer than kSplitBelow slot blocks).
+constexpr int kSplitBelow = 152;
+bool split_rows(const Lev3Common& lc) {
+  static const int mode = [] {
+    const char* e = std::getenv("IGAMG_ROW_SPLIT");
+    return e ? std::atoi(e) : -1;
+  }();
+  if (mode >= 0) return mode == 1;
+  return lc.colour_blk[lc.n_colours] < kSplitBelow * lc.n_colours;
+}
+
 template <typename T> Typed3<T>& typed(igamg3d_handle* h);
 template <> Typed3<double>& typed<double>(igamg3d_handle* h) { return h->d; }
 template <> Typed3<float>& typed<float>(igamg3d_handle* h) { return h->f; }
@@ -277,7 +301,9 @@ int upload_typed(igamg3d_handle* h, Typed3<T>& ty) {
     Lt.cm0 = cm[0]; Lt.cm1 = cm[1]; Lt.cm2 = cm[2]; Lt.cm3 = cm[3];
     Lt.rc0 = rc4[0]; Lt.rc1 = rc4[1]; Lt.rc2 = rc4[2]; Lt.rc3 = rc4[3];
     if (l >= 1) {
-      if ((rc = upload_as(h, &tl.cinv, hl.pt.cinv)) || (rc = upload_as(h, &tl.cinv8, hl.pt.cinv8))) return rc;
+      if ((rc = upload_as(h, &tl.cinv, hl.pt.cinv)) || (rc = upload_as(h, &tl.cinv8, hl.pt.cinv8)) ||
+          (rc = upload_as(h, &tl.cinv_all, hl.pt.cinv_all)))
+        return rc;
       auto up = [&](const Transfer1D& t, Xfer<T>& x) -> int {
         x.nf = t.nf; x.nc = t.nc;
         int r;
@@ -311,6 +337,28 @@ template <typename T>
 int do_smooth(igamg3d_handle* h, int l, T* U, const T* F, cudaStream_t s) {
   auto& lc = h->lc[l];
   auto& tl = typed<T>(h).lev[l];
+  if (row_parallel() && lc.row_slots) {
+    const int S = lc.row_slots;
+    const int* sg = lc.slot_g; const int* sc = lc.slot_c; const unsigned* sk = lc.slot_kb;
+    if (S == 256 && split_rows(lc)) {
+      for (int c = 0; c < lc.n_colours; ++c) {
+        int b0 = lc.colour_blk[c], nb = lc.colour_blk[c + 1] - b0;
+        if (nb == 0) continue;
+        if (h->prob.p == 2) k_mult_rows3x<2, 256, T><<<nb, 768, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
+        else k_mult_rows3x<3, 256, T><<<nb, 768, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
+      }
+      return launch_check();
+    }
+    for (int c = 0; c < lc.n_colours; ++c) {
+      int b0 = lc.colour_blk[c], nb = lc.colour_blk[c + 1] - b0;
+      if (nb == 0) continue;
+      if (h->prob.p == 2 && S == 256) k_mult_rows3<2, 256, T><<<nb, 256, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
+      else if (h->prob.p == 2) k_mult_rows3<2, 1024, T><<<nb, 1024, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
+      else if (S == 256) k_mult_rows3<3, 256, T><<<nb, 256, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
+      else k_mult_rows3<3, 1024, T><<<nb, 1024, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
+    }
+    return launch_check();
+  }
   size_t shm = (size_t)(kBlock / 32) * lc.maxl * sizeof(T);
   for (int c = 0; c < lc.n_colours; ++c) {
     int first = lc.colour_off[c], count = lc.colour_off[c + 1] - first;
@@ -471,9 +519,10 @@ int h3_create(const igamg_problem* prob, void* cuda_stream, igamg3d_handle** out
     if (l >= 1) {
       const auto& pt = lh.pt;
       lc.n_patches = pt.n_patches; lc.maxl = pt.maxl; lc.n_colours = pt.n_colours;
-      lc.colour_off = pt.colour_off; lc.n8 = pt.n8;
+      lc.colour_off = pt.colour_off; lc.n8 = pt.n8; lc.colour_blk = pt.colour_blk; lc.row_slots = pt.row_slots;
       if ((rc = upload_as(h, &lc.dofs, pt.dofs)) || (rc = upload_as(h, &lc.cls, pt.cls)) ||
-          (rc = upload_as(h, &lc.nloc, pt.nloc)))
+          (rc = upload_as(h, &lc.nloc, pt.nloc)) || (rc = upload_as(h, &lc.slot_g, pt.slot_g)) ||
+          (rc = upload_as(h, &lc.slot_c, pt.slot_c)) || (rc = upload_as(h, &lc.slot_kb, pt.slot_kb)))
         return fail(rc);
     }
   }

@@ -59,7 +59,20 @@ struct PatchTables {
   std::vector<int> n8;         // per colour: patches with 4+4 DOFs, stored first in the colour
   std::vector<int> d2p_off;    // dof -> list of (patch * maxl + local row), CSR over dofs
   std::vector<int> d2p_idx;
+  // Row-flat view for the row-parallel colour kernel: each colour is cut into blocks of
+  // row_slots slots (256, or 1024 on levels whose largest patch has more than 256 rows),
+  // one slot per local row; a patch's rows sit in consecutive slots of one block (blocks
+  // are padded instead of splitting a patch).
+  int row_slots = 0;                // 0: no row-flat view (a patch larger than 1024 rows)
+  std::vector<int> slot_g;          // dof of the slot's row, or -1 (padding)
+  std::vector<int> slot_c;          // the patch's class: its matrix in cinv_all
+  std::vector<unsigned> slot_kb;    // local row k | nl << 10 | (slot of the patch's row 0 in the block) << 20
+  std::vector<int> colour_blk;      // n_colours + 1: first block of each colour
+  std::vector<double> cinv_all;     // every class (8-DOF classes after the others), maxl x maxl
 };
+
+// Fills the row-flat view (slot_*, colour_blk, cinv_all) from dofs / cls / nloc / cinv / cinv8.
+void build_row_slots(PatchTables& pt);
 
 // Row stencils of K_l by row class.  A row's class is the pair of 1D position classes
 // of its two indices (cls1 below): positions within T of either end are their own class,

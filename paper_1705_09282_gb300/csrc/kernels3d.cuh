@@ -186,6 +186,68 @@ __global__ void __launch_bounds__(256) k_mult_colour3(LevelTab3<T> L, T* __restr
   for (int k = lane; k < nl; k += 32) U[pd[k]] += dot_n(A + (size_t)k * maxl, r, nl);
 }
 
+// One colour of the multiplicative sweep, row-parallel: one thread per local row of a
+// patch (slot), patches packed whole into blocks of S slots (S = 256, or 1024 on levels
+// with larger patches).  Each thread forms its row's local residual into shared memory;
+// after the barrier it applies its row of the patch's bordered inverse to the patch's
+// residual and updates its own unknown.
+template <int P, int S, typename T>
+__global__ void __launch_bounds__(S) k_mult_rows3(LevelTab3<T> L, T* __restrict__ U, const T* __restrict__ F,
+                                                  const int* __restrict__ slot_g, const int* __restrict__ slot_c,
+                                                  const unsigned* __restrict__ slot_kb,
+                                                  const T* __restrict__ cinv, int maxl, int first_slot) {
+  __shared__ T r[S];
+  const int s = first_slot + blockIdx.x * S + threadIdx.x;
+  const int g = slot_g[s];
+  T rv = T(0);
+  if (g >= 0) rv = F[g] - row3<P>(L, U, g);
+  r[threadIdx.x] = rv;
+  __syncthreads();
+  if (g < 0) return;
+  const unsigned kb = slot_kb[s];
+  const int k = kb & 0x3ff, nl = (kb >> 10) & 0x3ff, base = kb >> 20;
+  U[g] += dot_n(cinv + ((size_t)slot_c[s] * maxl + k) * maxl, r + base, nl);
+}
+
+// The same colour step with each row's three neighbour boxes evaluated by three different
+// threads (warps [0, S/32) box 0 with F, the next S/32 warps box 1, the last S/32 box 2 and
+// the lambda term), so every thread's chain of loads and multiply-adds is about a third as
+// long: for levels where a colour has too few rows to hide that latency.  Every warp runs
+// one box shape, so no warp diverges; the partial sums meet in shared memory.
+template <int P, int S, typename T>
+__global__ void __launch_bounds__(3 * S) k_mult_rows3x(LevelTab3<T> L, T* __restrict__ U, const T* __restrict__ F,
+                                                       const int* __restrict__ slot_g, const int* __restrict__ slot_c,
+                                                       const unsigned* __restrict__ slot_kb,
+                                                       const T* __restrict__ cinv, int maxl, int first_slot) {
+  using R = Rec3<P>;
+  __shared__ T part[3][S];
+  const int w = threadIdx.x / S, t = threadIdx.x - w * S;
+  const int s = first_slot + blockIdx.x * S + t;
+  const int g = slot_g[s];
+  T acc = T(0);
+  if (g >= 0) {
+    int kind, x, y, z;
+    decode3(L, g, kind, x, y, z);
+    const T* rc = rec3<P>(L, kind, x, y, z);
+    const bool vel = kind < 3;
+    if (w == 0) {
+      acc = F[g] - box3<P, 2 * P + 1>(L, rc, U, vel ? kind : 0, vel ? kind : 0, vel ? -P : -(P - 1), x, y, z);
+    } else if (w == 1) {
+      acc = -box3<P, 2 * P>(L, rc + R::B0, U, vel ? 3 : 1, vel ? kind : 1, vel ? -P : -(P - 1), x, y, z);
+    } else if (!vel) {
+      acc = -fma(rc[R::RU - 1], U[L.n_total - 1], box3<P, 2 * P>(L, rc + R::B0 + R::B1, U, 2, 2, -(P - 1), x, y, z));
+    }
+  }
+  part[w][t] = acc;
+  __syncthreads();
+  if (w == 0) part[0][t] = acc + (part[1][t] + part[2][t]);
+  __syncthreads();
+  if (w != 0 || g < 0) return;
+  const unsigned kb = slot_kb[s];
+  const int k = kb & 0x3ff, nl = (kb >> 10) & 0x3ff, base = kb >> 20;
+  U[g] += dot_n(cinv + ((size_t)slot_c[s] * maxl + k) * maxl, &part[0][0] + base, nl);
+}
+
 // block and local (x, y, z) of entry g (not lambda) on a level
 template <typename T>
 __device__ __forceinline__ void split3(const LevelTab3<T>& L, int g, int& blk, int& x, int& y, int& z, int& dx, int& dy) {

@@ -601,6 +601,41 @@ int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt
 
 }  // namespace
 
+void build_row_slots(PatchTables& pt) {
+  const int maxl = pt.maxl;
+  pt.row_slots = maxl <= 256 ? 256 : (maxl <= 1024 ? 1024 : 0);
+  const int S = pt.row_slots;
+  if (!S) return;
+  pt.cinv_all.assign((size_t)(pt.n_cls + pt.n_cls8) * maxl * maxl, 0.0);
+  std::copy(pt.cinv.begin(), pt.cinv.begin() + (size_t)pt.n_cls * maxl * maxl, pt.cinv_all.begin());
+  for (int c = 0; c < pt.n_cls8; ++c)
+    for (int r = 0; r < 8; ++r)
+      for (int t = 0; t < 8; ++t)
+        pt.cinv_all[((size_t)(pt.n_cls + c) * maxl + r) * maxl + t] = pt.cinv8[(size_t)c * 64 + r * 8 + t];
+  pt.slot_g.clear(); pt.slot_c.clear(); pt.slot_kb.clear();
+  pt.colour_blk.assign(pt.n_colours + 1, 0);
+  auto pad_block = [&]() {
+    while (pt.slot_g.size() % S) { pt.slot_g.push_back(-1); pt.slot_c.push_back(0); pt.slot_kb.push_back(0u); }
+  };
+  for (int col = 0; col < pt.n_colours; ++col) {
+    pt.colour_blk[col] = (int)(pt.slot_g.size() / S);
+    for (int i = pt.colour_off[col]; i < pt.colour_off[col + 1]; ++i) {
+      const bool is8 = i - pt.colour_off[col] < pt.n8[col];
+      const int cls = is8 ? pt.n_cls + pt.cls[i] : pt.cls[i];
+      const int nl = is8 ? 8 : pt.nloc[pt.cls[i]];
+      if ((int)(pt.slot_g.size() % S) + nl > S) pad_block();
+      const unsigned base = (unsigned)(pt.slot_g.size() % S);
+      for (int k = 0; k < nl; ++k) {
+        pt.slot_g.push_back(pt.dofs[(size_t)i * maxl + k]);
+        pt.slot_c.push_back(cls);
+        pt.slot_kb.push_back((unsigned)k | ((unsigned)nl << 10) | (base << 20));
+      }
+    }
+    pad_block();
+  }
+  pt.colour_blk[pt.n_colours] = (int)(pt.slot_g.size() / S);
+}
+
 double k_entry_rows(const LevelHost& lv, int p, long long g1, long long g2) {
   const int q = p - 1, RU = (2 * p + 1) * (2 * q + 1) + 2 * p * (2 * q + 1) + 1;
   Dof a = decode(lv.sz, g1), b = decode(lv.sz, g2);

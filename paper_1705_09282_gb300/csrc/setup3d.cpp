@@ -296,6 +296,7 @@ int build_patches3(int p, const Level1D& L, const Sizes3& s, PatchTables& pt, st
     for (int r = 0; r < 8; ++r)
       for (int t = 0; t < 8; ++t) pt.cinv8[(size_t)c * 64 + r * 8 + t] = inv[(size_t)r * 9 + t];
   }
+  build_row_slots(pt);
   return IGAMG_OK;
 }
 
