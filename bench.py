@@ -54,6 +54,18 @@ def peaks():
     return dict(FALLBACK_PEAKS), "fallback"
 
 
+def max_over_ranks(seconds, device, world):
+    """The job's time: the maximum of the ranks' timed regions (replicas run the same sweep;
+    value = all ranks' work / this time)."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -204,12 +216,7 @@ def run_ours(args):
     clocks = clk.stop()
     lat64, lat64_cyc = single_solve_ms("S")
     lat32, lat32_cyc = single_solve_ms("S32")
-    t_total = sum(ms_steps) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = max_over_ranks(sum(ms_steps) / 1e3, dev, world)
     value = world * dofcyc / t_total / 1e6
     solves = len(problems)
     solve_ms = 1e3 * t_total / (args.steps * solves)

@@ -155,10 +155,14 @@ struct Typed {
   std::vector<TypedLevel<T>> lev;
   T* coarse_inv = nullptr;
   T* delta = nullptr;
-  int fused_lc = -1;            // levels 0..fused_lc run in one block (k_fused_coarse), or -1
-  int fused_max = -1;           // deepest feasible choice (descriptor is built for it)
+  int fused_lc = -1;            // levels 0..fused_lc run in one launch, or -1 (per-level launches)
+  int fused_kind = 1;           // 1: one block (k_fused_coarse); C > 1: one cluster of C blocks
+  int fused_max = -1;           // deepest feasible one-block choice (descriptor is built for it)
   size_t fused_smem = 0;
   FusedDesc<T> fused{};
+  int cluster_max = -1;         // deepest feasible cluster choice
+  size_t cluster_smem = 0;
+  ClusterDesc<T> cdesc{};
 };
 
 struct LevelCommon {
@@ -300,8 +304,29 @@ int do_coarse(igamg_handle* h, const T* G, T* U, cudaStream_t s) {
 }
 
 template <typename T>
+int do_cluster(igamg_handle* h, const T* Fin, T* Uio, int load_u, cudaStream_t s) {
+  auto& ty = typed<T>(h);
+  ty.cdesc.nlev = ty.fused_lc + 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ty.fused_kind);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = ty.cluster_smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)ty.fused_kind; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = h->prob.p == 2 ? cudaLaunchKernelEx(&cfg, k_cluster_coarse<2, T>, ty.cdesc, Fin, Uio, load_u)
+                                 : cudaLaunchKernelEx(&cfg, k_cluster_coarse<3, T>, ty.cdesc, Fin, Uio, load_u);
+  if (e != cudaSuccess) { g_err = cudaGetErrorString(e); return IGAMG_ECUDA; }
+  return IGAMG_OK;
+}
+
+template <typename T>
 int do_fused(igamg_handle* h, const T* Fin, T* Uio, int load_u, cudaStream_t s) {
   auto& ty = typed<T>(h);
+  if (ty.fused_kind > 1) return do_cluster<T>(h, Fin, Uio, load_u, s);
   ty.fused.nlev = ty.fused_lc + 1;
   if (h->prob.p == 2) k_fused_coarse<2, T><<<1, 1024, ty.fused_smem, s>>>(ty.fused, Fin, Uio, load_u);
   else k_fused_coarse<3, T><<<1, 1024, ty.fused_smem, s>>>(ty.fused, Fin, Uio, load_u);
@@ -532,6 +557,50 @@ LevelTab<T> make_tab(const igamg_sizes& sz, int p, const T* sx, const T* sy, con
 // Choose the coarse levels that run in one block (multiplicative smoother only): all
 // levels with at most 32 (FP64) / 64 (FP32) elements per direction whose vectors fit in
 // shared memory, and fill the kernel's level descriptors.
+// Descriptor of the cluster form of the coarse end (k_cluster_coarse): every level below
+// the finest whose colouring fits the descriptor; the depth and the cluster size are picked
+// by the autotuner.
+template <typename T>
+int setup_cluster(igamg_handle* h, Typed<T>& ty) {
+  ty.cluster_max = -1;
+  const int L = h->prob.n_levels;
+  if (h->prob.smoother != IGAMG_MULT || L < 2) return IGAMG_OK;
+  if (std::getenv("IGAMG_NO_CLUSTER")) return IGAMG_OK;
+  int best = -1, maxl = 0;
+  for (int lc = 1; lc < L && lc < kMaxFused; ++lc) {
+    if (h->lc[lc].n_colours > kMaxColours) break;
+    best = lc;
+  }
+  if (best < 1) return IGAMG_OK;
+  ClusterDesc<T>& D = ty.cdesc;
+  D = ClusterDesc<T>{};
+  D.nlev = best + 1; D.nu1 = h->prob.nu1; D.nu2 = h->prob.nu2; D.ndof0 = h->host.ndof0;
+  D.coarse_inv = ty.coarse_inv;
+  int rc = dmalloc(h, (void**)&D.part, 32 * sizeof(double));
+  if (rc) return rc;
+  for (int l = 0; l <= best; ++l) {
+    ClusterLevel<T>& V = D.lev[l];
+    const auto& lc = h->lc[l];
+    V.L = ty.lev[l].L; V.tp = ty.lev[l].tp; V.tq = ty.lev[l].tq; V.cinv = ty.lev[l].cinv; V.cinv8 = ty.lev[l].cinv8;
+    V.dofs = lc.dofs; V.cls = lc.cls; V.nloc = lc.nloc; V.maxl = lc.maxl; V.n_colours = lc.n_colours;
+    for (int k = 0; k <= lc.n_colours && l >= 1; ++k) V.colour_off[k] = lc.colour_off[k];
+    for (int k = 0; k < lc.n_colours && l >= 1; ++k) V.n8[k] = lc.n8[k];
+    V.U = ty.lev[l].U; V.F = ty.lev[l].F; V.R = ty.lev[l].R;
+    maxl = std::max(maxl, lc.maxl);
+  }
+  D.maxl = std::max(maxl, 1);
+  ty.cluster_smem = (size_t)32 * D.maxl * sizeof(T);
+  for (auto fn : {(const void*)k_cluster_coarse<2, T>, (const void*)k_cluster_coarse<3, T>}) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ty.cluster_smem) != cudaSuccess) {
+      cudaGetLastError();
+      return IGAMG_OK;                 // no cluster form on this device: per-level launches
+    }
+  }
+  ty.cluster_max = best;
+  return IGAMG_OK;
+}
+
 template <typename T>
 int setup_fused(igamg_handle* h, Typed<T>& ty) {
   ty.fused_lc = -1;
@@ -595,20 +664,30 @@ struct TuneKey {
     return std::tie(p, n, L, bytes, sm, nu1, nu2) < std::tie(o.p, o.n, o.L, o.bytes, o.sm, o.nu1, o.nu2);
   }
 };
-std::map<TuneKey, int>& tune_cache() { static std::map<TuneKey, int> m; return m; }
+std::map<TuneKey, std::pair<int, int>>& tune_cache() { static std::map<TuneKey, std::pair<int, int>> m; return m; }
 std::mutex& tune_mutex() { static std::mutex m; return m; }
 
 template <typename T>
 int autotune_fused(igamg_handle* h, Typed<T>& ty) {
-  if (ty.fused_max < 1) { ty.fused_lc = -1; return IGAMG_OK; }
+  ty.fused_kind = 1;
+  if (ty.fused_max < 1 && ty.cluster_max < 1) { ty.fused_lc = -1; return IGAMG_OK; }
   const int L = h->prob.n_levels;
   TuneKey key{h->prob.p, h->prob.n_fine, L, (int)sizeof(T), h->prob.smoother, h->prob.nu1, h->prob.nu2};
-  const char* env = std::getenv("IGAMG_FUSED_LEVELS");   // fixed choice (tests, experiments)
-  if (env) { ty.fused_lc = std::min(std::atoi(env), ty.fused_max); if (ty.fused_lc < 1) ty.fused_lc = -1; return IGAMG_OK; }
+  // fixed choices (tests, experiments): IGAMG_FUSED_LEVELS = depth, IGAMG_FUSED_CLUSTER = blocks
+  const char* env = std::getenv("IGAMG_FUSED_LEVELS");
+  if (env) {
+    const char* ec = std::getenv("IGAMG_FUSED_CLUSTER");
+    int kind = ec ? std::atoi(ec) : 1;
+    int lim = kind > 1 ? ty.cluster_max : ty.fused_max;
+    ty.fused_kind = kind > 1 ? kind : 1;
+    ty.fused_lc = std::min(std::atoi(env), lim);
+    if (ty.fused_lc < 1) ty.fused_lc = -1;
+    return IGAMG_OK;
+  }
   {
     std::lock_guard<std::mutex> lk(tune_mutex());
     auto it = tune_cache().find(key);
-    if (it != tune_cache().end()) { ty.fused_lc = it->second; return IGAMG_OK; }
+    if (it != tune_cache().end()) { ty.fused_lc = it->second.first; ty.fused_kind = it->second.second; return IGAMG_OK; }
   }
   T* U = ty.lev[L - 1].U;
   T* F = ty.lev[L - 1].F;
@@ -623,18 +702,34 @@ int autotune_fused(igamg_handle* h, Typed<T>& ty) {
   float best_ms = 1e30f;
   int best = -1;
   const bool verbose = std::getenv("IGAMG_VERBOSE") != nullptr;
-  for (int cand = -1; cand <= ty.fused_max; ++cand) {
-    if (cand == 0) continue;
+  std::vector<std::pair<int, int>> cands{{-1, 1}};
+  for (int d = 1; d <= ty.fused_max; ++d) cands.push_back({d, 1});
+  for (int C : {4, 8, 16})
+    for (int d = 1; d <= ty.cluster_max; ++d) cands.push_back({d, C});
+  int best_kind = 1;
+  for (auto [cand, kind] : cands) {
     ty.fused_lc = cand;
+    ty.fused_kind = kind;
     cudaGraph_t g;
     cudaGraphExec_t ge = nullptr;
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = do_vcycle<T>(h, U, F, h->cap_stream);
     cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc && kind > 1) {                  // this cluster size cannot be launched here: skip it
+      if (ec == cudaSuccess) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (verbose) std::fprintf(stderr, "igamg: cluster %d unavailable (%s)\n", kind, g_err.c_str());
+      continue;
+    }
     if (rc) { if (ec == cudaSuccess) cudaGraphDestroy(g); cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
     CK(ec);
     cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
+    if (ei != cudaSuccess && kind > 1) {
+      cudaGetLastError();
+      if (verbose) std::fprintf(stderr, "igamg: cluster %d graph unavailable (%s)\n", kind, cudaGetErrorString(ei));
+      continue;
+    }
     CK(ei);
     float ms = 0;
     cudaError_t e = cudaGraphLaunch(ge, h->stream);
@@ -645,15 +740,16 @@ int autotune_fused(igamg_handle* h, Typed<T>& ty) {
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     cudaGraphExecDestroy(ge);
     CK(e);
-    if (verbose) std::fprintf(stderr, "igamg: fused coarse levels %d: %.1f us per V-cycle\n", cand, 1e3f * ms / 5);
-    if (ms < best_ms) { best_ms = ms; best = cand; }
+    if (verbose) std::fprintf(stderr, "igamg: fused coarse levels %d (blocks %d): %.1f us per V-cycle\n", cand, kind, 1e3f * ms / 5);
+    if (ms < best_ms) { best_ms = ms; best = cand; best_kind = kind; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ty.fused_lc = best;
-  if (verbose) std::fprintf(stderr, "igamg: chose fused coarse levels %d\n", best);
+  ty.fused_kind = best_kind;
+  if (verbose) std::fprintf(stderr, "igamg: chose fused coarse levels %d (blocks %d)\n", best, best_kind);
   std::lock_guard<std::mutex> lk(tune_mutex());
-  tune_cache()[key] = best;
+  tune_cache()[key] = {best, best_kind};
   return IGAMG_OK;
 }
 
@@ -689,6 +785,7 @@ int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
   }
   if ((rc = upload_as(h, &ty.coarse_inv, h->host.coarse_inv))) return rc;
   if ((rc = dmalloc(h, (void**)&ty.delta, std::max<size_t>(max_delta, 1) * sizeof(T)))) return rc;
+  if ((rc = setup_cluster<T>(h, ty))) return rc;
   return setup_fused<T>(h, ty);
 }
 

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -199,11 +200,16 @@ template <typename T>
 struct Typed3 {
   std::vector<Lev3T<T>> lev;
   T* coarse_inv = nullptr;
+  int fused_lc = -1;                // levels 0..fused_lc run in one cluster launch, or -1
+  int fused_kind = 8;               // cluster size (blocks)
+  int cluster_max = -1;
+  Cluster3Desc<T> cdesc{};
 };
 
 struct Lev3Common {
   int n_patches = 0, maxl = 0, n_colours = 0, row_slots = 0;
   std::vector<int> colour_off, n8, colour_blk;
+  int* colour_blk_dev = nullptr;
   int *dofs = nullptr, *cls = nullptr, *nloc = nullptr;
   int *slot_g = nullptr, *slot_c = nullptr;
   unsigned* slot_kb = nullptr;
@@ -397,11 +403,50 @@ int do_coarse(igamg3d_handle* h, const T* G, T* U, cudaStream_t s) {
 }
 
 template <typename T>
+int do_cluster(igamg3d_handle* h, const T* Fin, T* Uio, int load_u, cudaStream_t s) {
+  auto& ty = typed<T>(h);
+  ty.cdesc.nlev = ty.fused_lc + 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ty.fused_kind);
+  cfg.blockDim = dim3(1024);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)ty.fused_kind; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = h->prob.p == 2 ? cudaLaunchKernelEx(&cfg, k_cluster3<2, T>, ty.cdesc, Fin, Uio, load_u)
+                                 : cudaLaunchKernelEx(&cfg, k_cluster3<3, T>, ty.cdesc, Fin, Uio, load_u);
+  if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return IGAMG_ECUDA; }
+  return IGAMG_OK;
+}
+
+template <typename T>
 int do_vcycle(igamg3d_handle* h, T* U, const T* F, cudaStream_t s) {
   auto& ty = typed<T>(h);
   const int L = (int)ty.lev.size();
   if (L == 1) return do_coarse<T>(h, F, U, s);
   int rc;
+  const int lc = ty.fused_lc;
+  if (lc == L - 1) return do_cluster<T>(h, F, U, 1, s);
+  if (lc >= 1) {
+    for (int l = L - 1; l > lc; --l) {
+      T* Ul = (l == L - 1) ? U : ty.lev[l].U;
+      const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
+      if (l < L - 1) CK3(cudaMemsetAsync(Ul, 0, ty.lev[l].L.n_total * sizeof(T), s));
+      for (int k = 0; k < h->prob.nu1; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+      if ((rc = do_residual<T>(h, l, Ul, Fl, ty.lev[l].R, nullptr, s))) return rc;
+      if ((rc = do_restrict<T>(h, l, ty.lev[l].R, ty.lev[l - 1].F, s))) return rc;
+    }
+    if ((rc = do_cluster<T>(h, ty.lev[lc].F, ty.lev[lc].U, 0, s))) return rc;
+    for (int l = lc + 1; l <= L - 1; ++l) {
+      T* Ul = (l == L - 1) ? U : ty.lev[l].U;
+      const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
+      if ((rc = do_prolong<T>(h, l, ty.lev[l - 1].U, Ul, s))) return rc;
+      for (int k = 0; k < h->prob.nu2; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+    }
+    return IGAMG_OK;
+  }
   for (int l = L - 1; l >= 1; --l) {
     T* Ul = (l == L - 1) ? U : ty.lev[l].U;
     const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
@@ -478,6 +523,101 @@ int read_norm(igamg3d_handle* h, double* out) {
 
 }  // namespace
 
+// Descriptor of the cluster form of the coarse end (k_cluster3) and the choice of its
+// depth and cluster size: every candidate V-cycle is captured into a graph and replayed, the
+// fastest kept (IGAMG_FUSED_LEVELS / IGAMG_FUSED_CLUSTER fix the choice, IGAMG_NO_CLUSTER
+// disables the cluster form).
+template <typename T>
+int setup_cluster3(igamg3d_handle* h, Typed3<T>& ty) {
+  ty.fused_lc = -1;
+  ty.cluster_max = -1;
+  const int L = (int)ty.lev.size();
+  if (L < 2 || std::getenv("IGAMG_NO_CLUSTER")) return IGAMG_OK;
+  int best = -1;
+  for (int l = 1; l < L && l < kMaxFused3; ++l) best = l;
+  if (best < 1) return IGAMG_OK;
+  Cluster3Desc<T>& D = ty.cdesc;
+  D = Cluster3Desc<T>{};
+  D.nlev = best + 1; D.nu1 = h->prob.nu1; D.nu2 = h->prob.nu2; D.ndof0 = h->ndof0;
+  D.coarse_inv = ty.coarse_inv;
+  int rc = dmalloc(h, (void**)&D.part, 32 * sizeof(double));
+  if (rc) return rc;
+  for (int l = 0; l <= best; ++l) {
+    Cluster3Level<T>& V = D.lev[l];
+    const auto& lc = h->lc[l];
+    V.L = ty.lev[l].L; V.tp = ty.lev[l].tp; V.tq = ty.lev[l].tq; V.cinv = ty.lev[l].cinv_all;
+    V.slot_g = lc.slot_g; V.slot_c = lc.slot_c; V.slot_kb = lc.slot_kb; V.colour_blk = lc.colour_blk_dev;
+    V.n_colours = lc.n_colours; V.maxl = lc.maxl; V.row_slots = lc.row_slots;
+    V.U = ty.lev[l].U; V.F = ty.lev[l].F; V.R = ty.lev[l].R;
+    if (l >= 1 && lc.row_slots != 256 && lc.row_slots != 1024) { best = l - 1; break; }
+  }
+  if (best < 1) return IGAMG_OK;
+  for (auto fn : {(const void*)k_cluster3<2, T>, (const void*)k_cluster3<3, T>})
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return IGAMG_OK;
+    }
+  ty.cluster_max = best;
+  const char* env = std::getenv("IGAMG_FUSED_LEVELS");
+  if (env) {
+    const char* ec = std::getenv("IGAMG_FUSED_CLUSTER");
+    ty.fused_kind = ec ? std::max(2, std::atoi(ec)) : 8;
+    ty.fused_lc = std::min(std::atoi(env), best);
+    if (ty.fused_lc < 1) ty.fused_lc = -1;
+    return IGAMG_OK;
+  }
+  // time the candidates on zero vectors of the finest level
+  T* U = ty.lev[L - 1].U;
+  T* F = ty.lev[L - 1].F;
+  size_t nb = (size_t)ty.lev[L - 1].L.n_total * sizeof(T);
+  CK3(cudaMemsetAsync(U, 0, nb, h->stream));
+  CK3(cudaMemsetAsync(F, 0, nb, h->stream));
+  cudaEvent_t e0, e1;
+  CK3(cudaEventCreate(&e0));
+  CK3(cudaEventCreate(&e1));
+  const bool verbose = std::getenv("IGAMG_VERBOSE") != nullptr;
+  std::vector<std::pair<int, int>> cands{{-1, 8}};
+  for (int C : {8, 16})
+    for (int d = 1; d <= best; ++d) cands.push_back({d, C});
+  float best_ms = 1e30f;
+  int best_lc = -1, best_kind = 8;
+  for (auto [cand, kind] : cands) {
+    ty.fused_lc = cand;
+    ty.fused_kind = kind;
+    cudaGraph_t g;
+    cudaGraphExec_t ge = nullptr;
+    CK3(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int r = do_vcycle<T>(h, U, F, h->cap_stream);
+    cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
+    if (r || ec != cudaSuccess) {
+      if (ec == cudaSuccess) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (cand < 0) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r ? r : IGAMG_ECUDA; }
+      continue;
+    }
+    cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) { cudaGetLastError(); continue; }
+    float ms = 0;
+    cudaError_t e = cudaGraphLaunch(ge, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int rr = 0; rr < 3 && e == cudaSuccess; ++rr) e = cudaGraphLaunch(ge, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaGraphExecDestroy(ge);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); set_error(cudaGetErrorString(e)); return IGAMG_ECUDA; }
+    if (verbose) std::fprintf(stderr, "igamg3d: cluster levels %d (blocks %d): %.1f us per V-cycle\n", cand, kind, 1e3f * ms / 3);
+    if (ms < best_ms) { best_ms = ms; best_lc = cand; best_kind = kind; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ty.fused_lc = best_lc;
+  ty.fused_kind = best_kind;
+  if (verbose) std::fprintf(stderr, "igamg3d: chose cluster levels %d (blocks %d)\n", best_lc, best_kind);
+  return IGAMG_OK;
+}
+
 // ---- entry points used by igamg.cu -----------------------------------------------------
 namespace igamg {
 
@@ -522,13 +662,16 @@ int h3_create(const igamg_problem* prob, void* cuda_stream, igamg3d_handle** out
       lc.colour_off = pt.colour_off; lc.n8 = pt.n8; lc.colour_blk = pt.colour_blk; lc.row_slots = pt.row_slots;
       if ((rc = upload_as(h, &lc.dofs, pt.dofs)) || (rc = upload_as(h, &lc.cls, pt.cls)) ||
           (rc = upload_as(h, &lc.nloc, pt.nloc)) || (rc = upload_as(h, &lc.slot_g, pt.slot_g)) ||
-          (rc = upload_as(h, &lc.slot_c, pt.slot_c)) || (rc = upload_as(h, &lc.slot_kb, pt.slot_kb)))
+          (rc = upload_as(h, &lc.slot_c, pt.slot_c)) || (rc = upload_as(h, &lc.slot_kb, pt.slot_kb)) ||
+          (rc = upload_as(h, &lc.colour_blk_dev, pt.colour_blk)))
         return fail(rc);
     }
   }
   h->ndof0 = h->host.ndof0;
   if ((rc = upload_typed<double>(h, h->d))) return fail(rc);
   if (pr.precision == IGAMG_FP32_IR && (rc = upload_typed<float>(h, h->f))) return fail(rc);
+  if ((rc = setup_cluster3<double>(h, h->d))) return fail(rc);
+  if (pr.precision == IGAMG_FP32_IR && (rc = setup_cluster3<float>(h, h->f))) return fail(rc);
   const auto& fs = h->host.lev[L - 1].sz;
   long long nfine = fs.n_total;
   if ((rc = dmalloc(h, (void**)&h->part, 2 * sizeof(double) * (nblk(nfine) + 1)))) return fail(rc);

@@ -460,6 +460,117 @@ __global__ void __launch_bounds__(1024) k_fused_coarse(FusedDesc<T> D, const T* 
   }
 }
 
+// ---- the coarse end of the V-cycle in one thread-block cluster ---------------------------
+// The same phases as k_fused_coarse, but spread over the C blocks of one cluster (C SMs of
+// FP64 throughput instead of one) with the level vectors in global memory (they stay in
+// L2): a phase's work is split over all warps of the cluster and phases are separated by
+// the cluster barrier (hardware barrier with release / acquire semantics at cluster scope),
+// not by kernel launches.
+template <typename T>
+struct ClusterLevel {
+  LevelTab<T> L;
+  Xfer<T> tp, tq;                   // transfer from the level below into this one (l >= 1)
+  const T *cinv, *cinv8;
+  const int *dofs, *cls, *nloc;
+  int maxl, n_colours;
+  int colour_off[kMaxColours + 1], n8[kMaxColours];
+  T *U, *F, *R;
+};
+
+template <typename T>
+struct ClusterDesc {
+  int nlev, nu1, nu2, ndof0, maxl;
+  const T* coarse_inv;
+  double* part;                     // one partial sum per block (lambda row of the residual)
+  ClusterLevel<T> lev[kMaxFused];
+};
+
+template <int P, typename T>
+__global__ void __launch_bounds__(1024) k_cluster_coarse(ClusterDesc<T> D, const T* __restrict__ Ftop, T* __restrict__ Utop,
+                                                         int load_u) {
+  extern __shared__ unsigned char smem_raw[];
+  T* scratch_all = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red[32];
+  const unsigned rank = blockIdx.x, C = gridDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+  const int gtid = rank * nt + tid, gnt = C * nt, gwarp = rank * nwarp + warp, gnwarp = C * nwarp;
+  const int lc = D.nlev - 1;
+  T* scratch = scratch_all + warp * D.maxl;
+  auto csync = []() { asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory"); };
+  auto Uof = [&](int l) { return l == lc ? Utop : D.lev[l].U; };
+  auto Fof = [&](int l) { return l == lc ? Ftop : (const T*)D.lev[l].F; };
+  if (!load_u) {
+    for (int i = gtid; i < D.lev[lc].L.n_total; i += gnt) Utop[i] = T(0);
+    csync();
+  }
+  auto smooth = [&](int l) {
+    const ClusterLevel<T>& V = D.lev[l];
+    T* U = Uof(l); const T* F = Fof(l);
+    for (int c = 0; c < V.n_colours; ++c) {
+      int first = V.colour_off[c], n8 = V.n8[c], ngen = V.colour_off[c + 1] - first - n8;
+      int lanes = ((n8 * 8 + 31) / 32) * 32;
+      for (int t = gtid - lane; t < lanes; t += gnt)           // whole warps (shuffles span the warp)
+        fast_patch_lane<P>(V.L, U, F, V.dofs, V.cls, V.cinv8, V.maxl, first, n8, (t + lane) >> 3, lane);
+      for (int w = gwarp; w < ngen; w += gnwarp)
+        general_patch_warp<P>(V.L, U, F, V.dofs, V.cls, V.cinv, V.nloc, V.maxl, first + n8 + w, lane, scratch);
+      csync();
+    }
+  };
+  for (int l = lc; l >= 1; --l) {
+    for (int k = 0; k < D.nu1; ++k) smooth(l);
+    const ClusterLevel<T>& V = D.lev[l];
+    const ClusterLevel<T>& Cl = D.lev[l - 1];
+    {  // residual (all rows but lambda) and this block's share of m . p
+      const T* U = Uof(l); const T* F = Fof(l); T* R = V.R;
+      const int nu = V.L.n_ux + V.L.n_uy;
+      double mp = 0.0;
+      for (int g = gtid; g < V.L.n_total - 1; g += gnt) {
+        R[g] = F[g] - row_KU<P>(V.L, U, g);
+        if (g >= nu) mp += (double)mean_coef<P>(V.L, g - nu) * (double)U[g];
+      }
+      double sblk = block_sum(mp, red);
+      if (tid == 0) D.part[rank] = sblk;
+      csync();
+      if (gtid == 0) {
+        double sm = 0.0;
+        for (unsigned b = 0; b < C; ++b) sm += D.part[b];
+        R[V.L.n_total - 1] = (T)((double)F[V.L.n_total - 1] - sm);
+      }
+      csync();
+    }
+    {  // restriction into level l-1, and U_{l-1} = 0
+      const T* R = V.R;
+      T* Fc = Cl.F; T* Uc = Cl.U;
+      for (int g = gtid; g < Cl.L.n_total; g += gnt) {
+        Fc[g] = (g == Cl.L.n_total - 1) ? R[V.L.n_total - 1] : restrict_elem(V.L, Cl.L, V.tp, V.tq, R, g);
+        Uc[g] = T(0);
+      }
+      csync();
+    }
+  }
+  {  // exact coarsest solve, one warp per row of K_0^{-1}
+    const T* G = D.lev[0].F; T* U0 = D.lev[0].U;
+    for (int i = gwarp; i < D.ndof0; i += gnwarp) {
+      const T* row = D.coarse_inv + (size_t)i * D.ndof0;
+      T acc = T(0);
+#pragma unroll 4
+      for (int j = lane; j < D.ndof0; j += 32) acc = fma(row[j], G[j], acc);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) U0[i] = acc;
+    }
+    csync();
+  }
+  for (int l = 1; l <= lc; ++l) {
+    const ClusterLevel<T>& V = D.lev[l];
+    const ClusterLevel<T>& Cl = D.lev[l - 1];
+    T* U = Uof(l); const T* Uc = Cl.U;
+    for (int g = gtid; g < V.L.n_total; g += gnt)
+      U[g] += (g == V.L.n_total - 1) ? Uc[Cl.L.n_total - 1] : prolong_elem(V.L, Cl.L, V.tp, V.tq, Uc, g);
+    csync();
+    for (int k = 0; k < D.nu2; ++k) smooth(l);
+  }
+}
+
 // ---- mixed precision helpers ---------------------------------------------------------
 static __global__ void k_to_float(int n, const double* __restrict__ a, float* __restrict__ b) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -261,14 +261,11 @@ __device__ __forceinline__ void split3(const LevelTab3<T>& L, int g, int& blk, i
   y = t - z * dy;
 }
 
-// u_f += P u_c: per fine entry, the 3 x 3 x 3 tensor product of 1D knot-insertion weights
-// (degree p along the component's own axis, p-1 across; all p-1 for the pressure).
+// (P u_c) at fine entry g (not lambda): the 3 x 3 x 3 tensor product of 1D knot-insertion
+// weights (degree p along the component's own axis, p-1 across; all p-1 for the pressure).
 template <typename T>
-__global__ void k_prolong_add3(LevelTab3<T> Lf, LevelTab3<T> Lc, Xfer<T> tp, Xfer<T> tq, const T* __restrict__ uc,
-                               T* __restrict__ uf) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= Lf.n_total) return;
-  if (g == Lf.n_total - 1) { uf[g] += uc[Lc.n_total - 1]; return; }
+__device__ __forceinline__ T prolong3_elem(const LevelTab3<T>& Lf, const LevelTab3<T>& Lc, const Xfer<T>& tp,
+                                           const Xfer<T>& tq, const T* __restrict__ uc, int g) {
   int blk, x, y, z, dx, dy;
   split3(Lf, g, blk, x, y, z, dx, dy);
   const Xfer<T>& X = blk == 0 ? tp : tq;
@@ -293,16 +290,13 @@ __global__ void k_prolong_add3(LevelTab3<T> Lf, LevelTab3<T> Lc, Xfer<T> tp, Xfe
     }
     acc = fma(Z.pv[z * kWP + kz], sy, acc);
   }
-  uf[g] += acc;
+  return acc;
 }
 
-// g_c = P^T r_f: per coarse entry, the 5 x 5 x 5 tensor product of the transposed weights.
+// (P^T r_f) at coarse entry g (not lambda): the 5 x 5 x 5 tensor product of the transposed weights.
 template <typename T>
-__global__ void k_restrict3(LevelTab3<T> Lf, LevelTab3<T> Lc, Xfer<T> tp, Xfer<T> tq, const T* __restrict__ rf,
-                            T* __restrict__ gc) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= Lc.n_total) return;
-  if (g == Lc.n_total - 1) { gc[g] = rf[Lf.n_total - 1]; return; }
+__device__ __forceinline__ T restrict3_elem(const LevelTab3<T>& Lf, const LevelTab3<T>& Lc, const Xfer<T>& tp,
+                                            const Xfer<T>& tq, const T* __restrict__ rf, int g) {
   int blk, x, y, z, dx, dy;
   split3(Lc, g, blk, x, y, z, dx, dy);
   const Xfer<T>& X = blk == 0 ? tp : tq;
@@ -327,7 +321,176 @@ __global__ void k_restrict3(LevelTab3<T> Lf, LevelTab3<T> Lc, Xfer<T> tp, Xfer<T
     }
     acc = fma(Z.rv[z * kWR + kz], sy, acc);
   }
-  gc[g] = acc;
+  return acc;
+}
+
+// u_f += P u_c (lambda added); one thread per fine entry.
+template <typename T>
+__global__ void k_prolong_add3(LevelTab3<T> Lf, LevelTab3<T> Lc, Xfer<T> tp, Xfer<T> tq, const T* __restrict__ uc,
+                               T* __restrict__ uf) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Lf.n_total) return;
+  uf[g] += (g == Lf.n_total - 1) ? uc[Lc.n_total - 1] : prolong3_elem(Lf, Lc, tp, tq, uc, g);
+}
+
+// g_c = P^T r_f (lambda copied); one thread per coarse entry.
+template <typename T>
+__global__ void k_restrict3(LevelTab3<T> Lf, LevelTab3<T> Lc, Xfer<T> tp, Xfer<T> tq, const T* __restrict__ rf,
+                            T* __restrict__ gc) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Lc.n_total) return;
+  gc[g] = (g == Lc.n_total - 1) ? rf[Lf.n_total - 1] : restrict3_elem(Lf, Lc, tp, tq, rf, g);
+}
+
+// ---- the coarse end of the 3D V-cycle in one thread-block cluster -----------------------
+// As k_cluster_coarse (2D): the phases of Algorithm 1 for levels 0..lc spread over the
+// blocks of one cluster, separated by the cluster barrier, vectors in global memory (L2).
+// A colour is processed one slot block (k_mult_rows3's packing) per block iteration: with
+// 256-slot blocks each row's three neighbour boxes go to three groups of 256 threads, as in
+// k_mult_rows3x; with 1024-slot blocks (levels whose patches exceed 256 rows) one thread per row.
+constexpr int kMaxFused3 = 6;
+
+template <typename T>
+struct Cluster3Level {
+  LevelTab3<T> L;
+  Xfer<T> tp, tq;                   // transfer from the level below into this one (l >= 1)
+  const T* cinv;                    // cinv_all of the level
+  const int *slot_g, *slot_c, *colour_blk;
+  const unsigned* slot_kb;
+  int n_colours, maxl, row_slots;
+  T *U, *F, *R;
+};
+
+template <typename T>
+struct Cluster3Desc {
+  int nlev, nu1, nu2, ndof0;
+  const T* coarse_inv;
+  double* part;
+  Cluster3Level<T> lev[kMaxFused3];
+};
+
+template <int P, typename T>
+__global__ void __launch_bounds__(1024) k_cluster3(Cluster3Desc<T> D, const T* __restrict__ Ftop, T* __restrict__ Utop,
+                                                   int load_u) {
+  using R = Rec3<P>;
+  __shared__ T part3[1024];
+  __shared__ double red[32];
+  const unsigned rank = blockIdx.x, C = gridDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+  const int gtid = rank * nt + tid, gnt = C * nt, gwarp = rank * nwarp + warp, gnwarp = C * nwarp;
+  const int lc = D.nlev - 1;
+  auto csync = []() { asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory"); };
+  auto Uof = [&](int l) { return l == lc ? Utop : D.lev[l].U; };
+  auto Fof = [&](int l) { return l == lc ? Ftop : (const T*)D.lev[l].F; };
+  if (!load_u) {
+    for (int i = gtid; i < D.lev[lc].L.n_total; i += gnt) Utop[i] = T(0);
+    csync();
+  }
+  auto smooth = [&](int l) {
+    const Cluster3Level<T>& V = D.lev[l];
+    T* U = Uof(l); const T* F = Fof(l);
+    const int S = V.row_slots;
+    for (int c = 0; c < V.n_colours; ++c) {
+      const int b0 = V.colour_blk[c], b1 = V.colour_blk[c + 1];
+      for (int b = b0 + (int)rank; b < b1; b += (int)C) {
+        if (S == 256) {
+          const int w = tid >> 8, t = tid & 255;
+          const int s = b * 256 + t;
+          const int g = w < 3 ? V.slot_g[s] : -1;
+          T acc = T(0);
+          if (g >= 0) {
+            int kind, x, y, z;
+            decode3(V.L, g, kind, x, y, z);
+            const T* rc = rec3<P>(V.L, kind, x, y, z);
+            const bool vel = kind < 3;
+            if (w == 0)
+              acc = F[g] - box3<P, 2 * P + 1>(V.L, rc, U, vel ? kind : 0, vel ? kind : 0, vel ? -P : -(P - 1), x, y, z);
+            else if (w == 1)
+              acc = -box3<P, 2 * P>(V.L, rc + R::B0, U, vel ? 3 : 1, vel ? kind : 1, vel ? -P : -(P - 1), x, y, z);
+            else if (!vel)
+              acc = -fma(rc[R::RU - 1], U[V.L.n_total - 1], box3<P, 2 * P>(V.L, rc + R::B0 + R::B1, U, 2, 2, -(P - 1), x, y, z));
+          }
+          part3[tid] = acc;
+          __syncthreads();
+          if (w == 0) part3[t] = acc + (part3[256 + t] + part3[512 + t]);
+          __syncthreads();
+          if (w == 0 && g >= 0) {
+            const unsigned kb = V.slot_kb[s];
+            const int k = kb & 0x3ff, nl = (kb >> 10) & 0x3ff, base = kb >> 20;
+            U[g] += dot_n(V.cinv + ((size_t)V.slot_c[s] * V.maxl + k) * V.maxl, part3 + base, nl);
+          }
+          __syncthreads();
+        } else {
+          const int s = b * S + tid;
+          const int g = tid < S ? V.slot_g[s] : -1;
+          T rv = T(0);
+          if (g >= 0) rv = F[g] - row3<P>(V.L, U, g);
+          part3[tid] = rv;
+          __syncthreads();
+          if (g >= 0) {
+            const unsigned kb = V.slot_kb[s];
+            const int k = kb & 0x3ff, nl = (kb >> 10) & 0x3ff, base = kb >> 20;
+            U[g] += dot_n(V.cinv + ((size_t)V.slot_c[s] * V.maxl + k) * V.maxl, part3 + base, nl);
+          }
+          __syncthreads();
+        }
+      }
+      csync();
+    }
+  };
+  for (int l = lc; l >= 1; --l) {
+    for (int k = 0; k < D.nu1; ++k) smooth(l);
+    const Cluster3Level<T>& V = D.lev[l];
+    const Cluster3Level<T>& Cl = D.lev[l - 1];
+    {  // residual (all rows but lambda) and this block's share of m . p
+      const T* U = Uof(l); const T* F = Fof(l); T* Rv = V.R;
+      double mp = 0.0;
+      for (int g = gtid; g < V.L.n_total - 1; g += gnt) {
+        T m;
+        Rv[g] = F[g] - row3<P>(V.L, U, g, &m);
+        mp += (double)m * (double)U[g];
+      }
+      double sblk = block_sum(mp, red);
+      if (tid == 0) D.part[rank] = sblk;
+      csync();
+      if (gtid == 0) {
+        double sm = 0.0;
+        for (unsigned b = 0; b < C; ++b) sm += D.part[b];
+        Rv[V.L.n_total - 1] = (T)((double)F[V.L.n_total - 1] - sm);
+      }
+      csync();
+    }
+    {  // restriction into level l-1, and U_{l-1} = 0
+      const T* Rv = V.R;
+      T* Fc = Cl.F; T* Uc = Cl.U;
+      for (int g = gtid; g < Cl.L.n_total; g += gnt) {
+        Fc[g] = (g == Cl.L.n_total - 1) ? Rv[V.L.n_total - 1] : restrict3_elem(V.L, Cl.L, V.tp, V.tq, Rv, g);
+        Uc[g] = T(0);
+      }
+      csync();
+    }
+  }
+  {  // exact coarsest solve, one warp per row of K_0^{-1}
+    const T* G = D.lev[0].F; T* U0 = D.lev[0].U;
+    for (int i = gwarp; i < D.ndof0; i += gnwarp) {
+      const T* row = D.coarse_inv + (size_t)i * D.ndof0;
+      T acc = T(0);
+#pragma unroll 4
+      for (int j = lane; j < D.ndof0; j += 32) acc = fma(row[j], G[j], acc);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) U0[i] = acc;
+    }
+    csync();
+  }
+  for (int l = 1; l <= lc; ++l) {
+    const Cluster3Level<T>& V = D.lev[l];
+    const Cluster3Level<T>& Cl = D.lev[l - 1];
+    T* U = Uof(l); const T* Uc = Cl.U;
+    for (int g = gtid; g < V.L.n_total; g += gnt)
+      U[g] += (g == V.L.n_total - 1) ? Uc[Cl.L.n_total - 1] : prolong3_elem(V.L, Cl.L, V.tp, V.tq, Uc, g);
+    csync();
+    for (int k = 0; k < D.nu2; ++k) smooth(l);
+  }
 }
 
 }  // namespace dev

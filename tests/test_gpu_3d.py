@@ -221,3 +221,31 @@ def test_full_size_workload_properties():
     # manufactured one at the element corners' Greville points (smooth solution, h = 1/64)
     s = S64.sizes()
     assert s.n_total == 3 * 64 * 65 * 65 + 65 ** 3 + 1
+
+
+@pytest.mark.parametrize("p,n,L,depth,blocks", [(2, 8, 3, "1", "8"), (2, 8, 3, "2", "16"), (3, 4, 2, "1", "8"),
+                                                 (2, 16, 4, "2", "8")])
+def test_cluster_coarse_levels_same_iterates(p, n, L, depth, blocks, monkeypatch):
+    # the coarsest levels in one thread-block cluster (fixed depth and size): the same
+    # iterates as the oracle, and a mixed-precision solve reaching the FP64 solution
+    from paper_1705_09282_gb300 import _lib
+    monkeypatch.setenv("IGAMG_FUSED_LEVELS", depth)
+    monkeypatch.setenv("IGAMG_FUSED_CLUSTER", blocks)
+    S = _solver(p, n, L)
+    S32 = _solver(p, n, L, precision=_lib.IGAMG_FP32_IR)
+    monkeypatch.delenv("IGAMG_FUSED_LEVELS")
+    monkeypatch.delenv("IGAMG_FUSED_CLUSTER")
+    H = _hier(p, n, L)
+    f = inputs.manufactured_forcing_3d(p, n, 1.0, 1.0)
+    F = H.fine.load_vector(f)
+    Ug, Fg = S.empty(), _t(F)
+    Uo = np.zeros_like(F)
+    for k in range(2):
+        S.vcycle(Ug, Fg)
+        H.vcycle(Uo, F)
+        assert _rel(_np(Ug), Uo) < RTOL_IT, k
+    U32 = S32.empty()
+    rep = S32.solve(U32, Fg, rtol=1e-9, max_cycles=60)
+    assert rep["converged"] and rep["div_inf"] <= 1e-11 * np.abs(Uo).max()
+    H.solve(Uo, F, 1e-12, 80)
+    assert _rel(_np(U32), Uo) < 1e-7

@@ -265,3 +265,34 @@ def test_one_block_coarse_levels_same_iterates(depth, p, monkeypatch):
     U = np.zeros_like(F)
     H.solve(U, F, 1e-12, 80)
     assert _rel(_np(U32), U) < 1e-7
+
+
+@pytest.mark.parametrize("depth,blocks", [("1", "4"), ("2", "8"), ("3", "16"), ("5", "8")])
+@pytest.mark.parametrize("p", [2, 3])
+def test_cluster_coarse_levels_same_iterates(depth, blocks, p, monkeypatch):
+    # the coarsest levels run in one thread-block cluster (fixed depth and cluster size);
+    # iterates and the mixed-precision solution must not depend on that choice
+    monkeypatch.setenv("IGAMG_FUSED_LEVELS", depth)
+    monkeypatch.setenv("IGAMG_FUSED_CLUSTER", blocks)
+    n, L = 64, 6
+    S = _solver(p, n, L)
+    S32 = _solver(p, n, L, precision=1)
+    monkeypatch.delenv("IGAMG_FUSED_LEVELS")
+    monkeypatch.delenv("IGAMG_FUSED_CLUSTER")
+    H = o2.Hierarchy(p, n, L, 1.0, 1.0)
+    f = inputs.grf_forcing(p, n, seed=43)
+    F = H.fine.load_vector(f)
+    U = np.zeros_like(F)
+    Fg = S.load_vector(_t(f))
+    Ug = S.empty()
+    for _ in range(2):
+        H.vcycle(U, F)
+        S.vcycle(Ug, Fg)
+        assert _rel(_np(Ug), U) < RTOL_IT
+    rep = S.solve(Ug, Fg, rtol=1e-9, max_cycles=60)
+    assert rep["converged"] and rep["div_inf"] <= 1e-12 * np.abs(_np(Ug)).max()
+    U32 = S32.empty()
+    rep = S32.solve(U32, Fg, rtol=1e-9, max_cycles=60)
+    assert rep["converged"]
+    H.solve(U, F, 1e-12, 80)
+    assert _rel(_np(U32), U) < 1e-7
