@@ -136,7 +136,7 @@ def run_ours(args):
     import torch
 
     from paper_1705_09282_gb300 import inputs
-    from paper_1705_09282_gb300._lib import IGAMG_FP32_IR
+    from paper_1705_09282_gb300._lib import IGAMG_FGMRES_FP32, IGAMG_FGMRES_FP64, IGAMG_FP32_IR
     from paper_1705_09282_gb300.solver import Solver, solve_batch
 
     rank, world, local = dist_env()
@@ -216,6 +216,23 @@ def run_ours(args):
     clocks = clk.stop()
     lat64, lat64_cyc = single_solve_ms("S")
     lat32, lat32_cyc = single_solve_ms("S32")
+    # the Krylov wrapper on the same single solve (FGMRES(20) in FP64, V-cycle preconditioner)
+    krylov = {}
+    pr0 = problems[0]
+    for name, prec in (("fgmres_fp64", IGAMG_FGMRES_FP64), ("fgmres_fp32", IGAMG_FGMRES_FP32)):
+        SK = Solver(pr0["p"], N_FINE, N_LEVELS, pr0["sigma"], 1.0, nu1=2, nu2=2, device=dev, stream=stream,
+                    precision=prec, restart=20)
+        for _ in range(2):
+            pr0["U"].zero_()
+            rk = SK.solve(pr0["U"], pr0["F"], rtol=RTOL, max_cycles=MAXC, history=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pr0["U"].zero_()
+        rk = SK.solve(pr0["U"], pr0["F"], rtol=RTOL, max_cycles=MAXC, history=False)
+        torch.cuda.synchronize()
+        krylov[name] = {"single_solve_ms": 1e3 * (time.perf_counter() - t0), "vcycles": rk["cycles"],
+                        "converged": rk["converged"], "rel_residual": rk["rel_residual"], "div_inf": rk["div_inf"]}
+        SK.close()
     t_total = max_over_ranks(sum(ms_steps) / 1e3, dev, world)
     value = world * dofcyc / t_total / 1e6
     solves = len(problems)
@@ -255,7 +272,7 @@ def run_ours(args):
     achieved = n_patch_colour * flops_patch / launch_s / 1e12
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12    # 152 SMs x 2 DFMA/clk x 2 flops
-    roofline = {"kernel": "k_mult_colour<2,double> (one colour, finest level, p=2)", "bound": "alu",
+    roofline = {"kernel": "k_mult_colour_split<2,double> (one colour, finest level, p=2)", "bound": "alu",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s (FP64)", "frac": achieved / fp64_peak,
                 "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x median SM clock",
                 "avg_launch_us": launch_s * 1e6, "flops_per_launch": n_patch_colour * flops_patch,
@@ -295,6 +312,7 @@ def run_ours(args):
             "single_solve_ms": lat64, "single_solve_case": f"p=2, sigma=1e-4, {lat64_cyc} cycles, alone",
             "cycles": {f"p{pr['p']}_sigma{pr['sigma']:g}": c for pr, c in zip(problems, cyc_list)},
             "roofline": roofline, "e2e": e2e, "clocks": clocks, "mixed_fp32_ir": mixed,
+            "krylov_single_solve": krylov,
             "max_div_inf": div64,
             "gpu_launches": (sum(launches_per_solve(pr["p"], c) for pr, c in zip(problems, cyc_list))
                              + sum(launches_per_solve(pr["p"], c, mixed=True) for pr, c in zip(problems, cyc32))) * args.steps}
@@ -430,14 +448,34 @@ def run_oseen(args):
             ts.append(dt)
             cyc, div = rep["cycles"], rep["div_inf"]
         t = sum(ts) / len(ts)
-        # the FP32 or FP64 colour kernel on the finest level, timed alone
+        # the FP64 colour kernel on the finest level, timed alone
         sz = S.sizes()
         sweeps = 10
         dt_sm, _ = _timed(lambda: S.smooth(U, F, sweeps=sweeps), stream)
+        colour_us = 1e6 * dt_sm / (sweeps * sz.n_colours)
+        # the FP64 operator apply (residual) on the finest level: it streams one 28-coefficient
+        # record per row from HBM (the advection field makes every row different)
+        R = S.empty()
+        reps_r = 20
+        dt_r, _ = _timed(lambda: [S.residual(U, F, out=R) for _ in range(reps_r)], stream)
+        res_us = 1e6 * dt_r / reps_r
+        n = sz.n_total
+        RU = (2 * p + 1) * (2 * p - 1) + 2 * p * (2 * p - 1) + 1   # padded row record (2 boxes + lambda)
+        res_bytes = (n - 1) * (RU * 8 + 3 * 8)                    # records + U, F, R once
+        # colour: per 8-DOF patch 8 records, its own 8x8 inverse, dof ids, class id, F and U rows
+        patches_colour = sz.n_patches / sz.n_colours
+        col_bytes = patches_colour * (8 * RU * 8 + 64 * 8 + 8 * 4 + 4 + 3 * 8 * 8)
         out[name] = {"solve_ms": 1e3 * t, "cycles": cyc, "mdof_per_s_per_cycle": S.ndof() * cyc / t / 1e6,
-                     "div_inf": div, "setup_s": setup, "fp64_colour_launch_us": 1e6 * dt_sm / (sweeps * sz.n_colours)}
+                     "div_inf": div, "setup_s": setup, "fp64_colour_launch_us": colour_us,
+                     "fp64_residual_us": res_us,
+                     "residual_hbm": {"bytes": res_bytes, "achieved_gbs": res_bytes / res_us / 1e3},
+                     "colour_hbm": {"bytes": col_bytes, "achieved_gbs": col_bytes / colour_us / 1e3}}
         S.close()
     pk, src = peaks()
+    for v in out.values():
+        for key in ("residual_hbm", "colour_hbm"):
+            v[key]["peak_gbs"] = pk["hbm_gbs"]
+            v[key]["frac"] = v[key]["achieved_gbs"] / pk["hbm_gbs"]
     line = {"metric": "Oseen solve time to 1e-8 rel. residual (config 3)", "workload": "oseen",
             "config": {"workload": "2D generalized Oseen, unit square, p=2, 512x512, 8 levels, nu=1e-2, sigma=1, "
                                    "max|beta|=0.5 (Re=50, Da=100), GRF forcing seed 1707, V(2,2) multiplicative",
@@ -545,6 +583,47 @@ def run_cube(args):
     print(json.dumps(line), flush=True)
 
 
+def run_smoothers(args):
+    """Additive (eq. ASM) against multiplicative (eq. MSM) Schwarz at the headline size:
+    2D generalized Stokes, 256 x 256, 7 grids, p = 2 and 3, sigma = nu = 1, GRF forcing,
+    FP64, V(2,2), zero guess, to 1e-8 (the trade-off of the paper's Tables 1 and 2: the
+    additive sweep is three launches, the multiplicative one (p+1)^2)."""
+    import torch
+
+    from paper_1705_09282_gb300 import inputs
+    from paper_1705_09282_gb300._lib import IgamgError
+    from paper_1705_09282_gb300.solver import Solver
+    stream = torch.cuda.current_stream()
+    out = {}
+    for p in DEGREES:
+        f = torch.tensor(inputs.grf_forcing(p, N_FINE, seed=SEED), device="cuda")
+        for name, sm, eta in (("mult", "mult", 0.5), ("add_eta0.3", "add", 0.3), ("add_eta0.2", "add", 0.2)):
+            S = Solver(p, N_FINE, N_LEVELS, 1.0, 1.0, smoother=sm, eta=eta, nu1=2, nu2=2)
+            F = S.load_vector(f)
+            U = S.empty()
+            for _ in range(args.warmup):
+                U.zero_()
+                S.solve(U, F, rtol=RTOL, max_cycles=200, history=False)
+            ts = []
+            try:
+                for _ in range(args.steps):
+                    U.zero_()
+                    dt, rep = _timed(lambda: S.solve(U, F, rtol=RTOL, max_cycles=200, history=False), stream)
+                    ts.append(dt)
+            except IgamgError as e:          # eq. ASM can diverge (reading R9): report it
+                out["p%d_%s" % (p, name)] = {"converged": False, "error": str(e)}
+                S.close()
+                continue
+            t = sum(ts) / len(ts)
+            out["p%d_%s" % (p, name)] = {"converged": rep["converged"], "cycles": rep["cycles"], "solve_ms": 1e3 * t,
+                                         "ms_per_cycle": 1e3 * t / max(rep["cycles"], 1), "div_inf": rep["div_inf"]}
+            S.close()
+    line = {"metric": "additive vs multiplicative Schwarz: solve time to 1e-8", "workload": "smoothers",
+            "config": {"workload": "2D generalized Stokes, 256x256, 7 levels, p=2,3, sigma=nu=1, GRF forcing, FP64, V(2,2)"},
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -552,8 +631,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="stokes", choices=["stokes", "oseen", "batch", "cube"],
-                    help="stokes: the headline sweep (default); oseen / batch / cube: extra measurements")
+    ap.add_argument("--workload", default="stokes", choices=["stokes", "oseen", "batch", "cube", "smoothers"],
+                    help="stokes: the headline sweep (default); oseen / batch / cube / smoothers: extra measurements")
     ap.add_argument("--batch-count", type=int, default=1024)
     ap.add_argument("--train-count", type=int, default=384)
     ap.add_argument("--train-steps", type=int, default=6000)
@@ -571,6 +650,8 @@ def main():
         run_batch(args)
     elif args.workload == "cube":
         run_cube(args)
+    elif args.workload == "smoothers":
+        run_smoothers(args)
     else:
         run_ours(args)
 

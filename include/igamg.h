@@ -59,7 +59,14 @@ enum {
 };
 
 enum { IGAMG_MULT = 0, IGAMG_ADD = 1 };          /* eq. MSM / eq. ASM of Sec. 5.2 */
-enum { IGAMG_FP64 = 0, IGAMG_FP32_IR = 1 };      /* precision of the V-cycle */
+/* Precision / wrapper of the solve:
+ *   IGAMG_FP64         plain FP64 V-cycles (Algorithm 1 as the solver)
+ *   IGAMG_FP32_IR      FP32 V-cycles inside FP64 iterative refinement (north star (1))
+ *   IGAMG_FGMRES_FP64  FGMRES(m) in FP64 with one FP64 V-cycle as right preconditioner
+ *   IGAMG_FGMRES_FP32  FGMRES(m) in FP64 with one FP32 V-cycle as right preconditioner
+ * In every mode each update of the velocity is divergence-free to FP64 round-off (the FP32
+ * corrections enter through the FP64 curl of a potential, Sec. 4.3 complex). */
+enum { IGAMG_FP64 = 0, IGAMG_FP32_IR = 1, IGAMG_FGMRES_FP64 = 2, IGAMG_FGMRES_FP32 = 3 };
 
 typedef struct {
   int dim;            /* 2, or 3 (unit cube, see the 3D layout above) */
@@ -73,7 +80,8 @@ typedef struct {
   int smoother;       /* IGAMG_MULT or IGAMG_ADD */
   double eta;         /* additive scaling factor (Sec. 5.2, eq. ASM); <= 0 selects 0.5 */
   int nu1, nu2;       /* pre- / post-smoothing sweeps (Algorithm 1) */
-  int precision;      /* IGAMG_FP64 or IGAMG_FP32_IR */
+  int precision;      /* IGAMG_FP64, IGAMG_FP32_IR, IGAMG_FGMRES_FP64 or IGAMG_FGMRES_FP32 */
+  int restart;        /* FGMRES: Krylov directions per restart cycle; <= 0 selects 20 */
 } igamg_problem;
 
 typedef struct {
@@ -141,6 +149,10 @@ int igamg_vcycle(igamg_handle* h, double* U, const double* F);
 
 /* V-cycles until ||F - K U||_2 <= rtol ||F - K U_0||_2 or max_cycles (Sec. 6 protocol with
  * the tolerance as a parameter).  Synchronises once per cycle to read the norm.
+ * FGMRES modes: max_cycles bounds the preconditioner applications (V-cycles), the report
+ * counts them, its history holds the Krylov residual estimates, and the stopping test uses
+ * the true residual at the end of each restart cycle.  igamg_vcycle on such a handle runs one
+ * V-cycle of the underlying precision (FP64, or one FP32 refinement step).
  * rep may be NULL.  Returns IGAMG_NOT_CONVERGED (U holds the last iterate) if the
  * tolerance was not met, IGAMG_ENONFINITE if a norm was NaN/Inf. */
 int igamg_solve(igamg_handle* h, double* U, const double* F, double rtol, int max_cycles,

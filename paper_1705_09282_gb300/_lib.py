@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(_PKG, "libigamg.so")
 IGAMG_OK = 0
 IGAMG_NOT_CONVERGED = 1
 IGAMG_MULT, IGAMG_ADD = 0, 1
-IGAMG_FP64, IGAMG_FP32_IR = 0, 1
+IGAMG_FP64, IGAMG_FP32_IR, IGAMG_FGMRES_FP64, IGAMG_FGMRES_FP32 = 0, 1, 2, 3
 
 
 class Problem(ctypes.Structure):
@@ -20,7 +20,7 @@ class Problem(ctypes.Structure):
                 ("n_levels", ctypes.c_int), ("sigma", ctypes.c_double), ("nu", ctypes.c_double),
                 ("c_penalty", ctypes.c_double), ("beta_qp", ctypes.c_void_p),
                 ("smoother", ctypes.c_int), ("eta", ctypes.c_double), ("nu1", ctypes.c_int),
-                ("nu2", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("nu2", ctypes.c_int), ("precision", ctypes.c_int), ("restart", ctypes.c_int)]
 
 
 class Sizes(ctypes.Structure):
@@ -115,11 +115,11 @@ def check(code, where):
 
 
 def make_problem(p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.5, nu1=2, nu2=2,
-                 c_penalty=0.0, precision=IGAMG_FP64, beta=None, dim=2):
+                 c_penalty=0.0, precision=IGAMG_FP64, beta=None, dim=2, restart=0):
     pr = Problem()
     pr.dim, pr.p, pr.n_fine, pr.n_levels = dim, p, n_fine, n_levels
     pr.sigma, pr.nu, pr.c_penalty = float(sigma), float(nu), float(c_penalty)
     pr.beta_qp = beta.ctypes.data if beta is not None else None
     pr.smoother = IGAMG_ADD if smoother == "add" else IGAMG_MULT
-    pr.eta, pr.nu1, pr.nu2, pr.precision = float(eta), nu1, nu2, precision
+    pr.eta, pr.nu1, pr.nu2, pr.precision, pr.restart = float(eta), nu1, nu2, precision, restart
     return pr

@@ -23,6 +23,7 @@
 #include "igamg3d.h"
 #include "igamg_internal.h"
 #include "kernels.cuh"
+#include "krylov.h"
 
 using namespace igamg;
 using namespace igamg::dev;
@@ -199,6 +200,8 @@ struct igamg_handle {
   cudaStream_t exec_stream = nullptr;  // used by igamg_solve_batch
   cudaEvent_t ev = nullptr;
   igamg3d_handle* d3 = nullptr;        // dim = 3: everything lives in the 3D driver
+  KrylovWork kw;                       // FGMRES modes
+  double* zeros = nullptr;             // FGMRES: a zero right-hand side (K z = -(0 - K z))
 };
 
 namespace {
@@ -235,6 +238,22 @@ int launch_check() {
   return IGAMG_OK;
 }
 
+// Colour kernel form: one lane per row (k_mult_colour, default) or split rows
+// (k_mult_colour_split, IGAMG_SPLIT_COLOUR=1; measured 10 % slower on the 256^2 sweep).
+// Per-row operator records (Oseen) always use the former.
+bool split_colour(bool per_row_records) {
+  static const int mode = [] {
+    const char* e = std::getenv("IGAMG_SPLIT_COLOUR");
+    return e ? std::atoi(e) : 0;
+  }();
+  return mode == 1 && !per_row_records;
+}
+
+// FP32 V-cycles (refinement step or FGMRES preconditioner) on this handle
+bool fp32_base(const igamg_problem& pr) {
+  return pr.precision == IGAMG_FP32_IR || pr.precision == IGAMG_FGMRES_FP32;
+}
+
 template <typename T> Typed<T>& typed(igamg_handle* h);
 template <> Typed<double>& typed<double>(igamg_handle* h) { return h->d; }
 template <> Typed<float>& typed<float>(igamg_handle* h) { return h->f; }
@@ -255,7 +274,20 @@ int do_smooth(igamg_handle* h, int l, T* U, const T* F, cudaStream_t s) {
   auto& lc = h->lc[l];
   auto& tl = typed<T>(h).lev[l];
   size_t shm = (size_t)(kBlock / 32) * lc.maxl * sizeof(T);
-  if (h->prob.smoother == IGAMG_MULT) {
+  if (h->prob.smoother == IGAMG_MULT && split_colour(tl.L.srow != nullptr)) {
+    size_t shm16 = (size_t)16 * lc.maxl * sizeof(T);
+    for (int c = 0; c < lc.n_colours; ++c) {
+      int first = lc.colour_off[c], count = lc.colour_off[c + 1] - first;
+      if (count == 0) continue;
+      int n8 = lc.n8[c], ngen = count - n8;
+      int nb8 = (n8 + 31) / 32, nbg = (ngen + 15) / 16;
+      unsigned nb = (unsigned)(nb8 + nbg);
+      if (h->prob.p == 2)
+        k_mult_colour_split<2, T><<<nb, 512, shm16, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+      else
+        k_mult_colour_split<3, T><<<nb, 512, shm16, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+    }
+  } else if (h->prob.smoother == IGAMG_MULT) {
     for (int c = 0; c < lc.n_colours; ++c) {
       int first = lc.colour_off[c], count = lc.colour_off[c + 1] - first;
       if (count == 0) continue;
@@ -399,7 +431,7 @@ int do_ir_step(igamg_handle* h, double* U, const double* F, cudaStream_t s) {
 // one solve step: FP64 mode -> V-cycle + residual norm; FP32 mode -> refinement step.
 int do_step(igamg_handle* h, double* U, const double* F, cudaStream_t s) {
   const int L = (int)h->d.lev.size();
-  if (h->prob.precision == IGAMG_FP32_IR) return do_ir_step(h, U, F, s);
+  if (fp32_base(h->prob)) return do_ir_step(h, U, F, s);
   int rc = do_vcycle<double>(h, U, F, s);
   if (rc) return rc;
   return do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, h->norm2, s);
@@ -413,7 +445,7 @@ int ensure_graph(igamg_handle* h, int kind, double* U, const double* F) {
   CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   int L = (int)h->d.lev.size();
   int rc = IGAMG_OK;
-  if (kind == 1 && h->prob.precision == IGAMG_FP32_IR)
+  if (kind == 1 && fp32_base(h->prob))
     rc = do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, nullptr, h->cap_stream);
   if (!rc) rc = do_step(h, U, F, h->cap_stream);
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
@@ -451,8 +483,23 @@ int div_inf_impl(igamg_handle* h, const double* U, double* out) { return div_inf
 // Several independent solves at once, each on its handle's own execution stream: one
 // round launches one captured step per unfinished solve, then reads all their norms.
 // Small solves are latency bound, so running them side by side fills the GPU.
+int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max_cycles, igamg_report* rep,
+               double atol);
+
 int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, double rtol, int max_cycles,
                      igamg_report* reps, int* status, const double* atol = nullptr) {
+  bool krylov = false;
+  for (int i = 0; i < n; ++i) krylov = krylov || hs[i]->prob.precision >= IGAMG_FGMRES_FP64;
+  if (krylov) {   // FGMRES solves are host-driven: run them one after another
+    int worst = IGAMG_OK;
+    for (int i = 0; i < n; ++i) {
+      int st = solve_impl(hs[i], Us[i], Fs[i], rtol, max_cycles, reps ? &reps[i] : nullptr, atol ? atol[i] : -1.0);
+      if (status) status[i] = st;
+      if (st < 0) return st;
+      if (st == IGAMG_NOT_CONVERGED) worst = IGAMG_NOT_CONVERGED;
+    }
+    return worst;
+  }
   std::vector<double> r0(n, 0.0), rk(n, 0.0);
   std::vector<int> k(n, 0), st(n, IGAMG_NOT_CONVERGED);
   int rc;
@@ -513,8 +560,59 @@ int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, d
   return worst;
 }
 
+// ---- FGMRES around the V-cycle (krylov.cu) ---------------------------------------------
+int kr_precond(void* ctx, const double* v, double* z) {
+  auto* h = (igamg_handle*)ctx;
+  cudaStream_t s = h->stream;
+  const int L = (int)h->d.lev.size();
+  const auto& Ld = h->d.lev[L - 1].L;
+  CK(cudaMemsetAsync(z, 0, Ld.n_total * sizeof(double), s));
+  if (h->prob.precision == IGAMG_FGMRES_FP64) return do_vcycle<double>(h, z, v, s);
+  auto& top32 = h->f.lev[L - 1];
+  k_to_float<<<nblk(Ld.n_total), kBlock, 0, s>>>(Ld.n_total, v, top32.F);
+  CK(cudaMemsetAsync(top32.U, 0, Ld.n_total * sizeof(float), s));
+  int rc = do_vcycle<float>(h, top32.U, top32.F, s);
+  if (rc) return rc;
+  k_integrate_psi<<<nblk((long long)Ld.nint * 32, 128), 128, 0, s>>>(Ld.nint, Ld.nxu, h->lc[L - 1].inv_dcoef, top32.U, h->psi);
+  k_curl_update<<<nblk(Ld.n_total), kBlock, 0, s>>>(Ld, h->lc[L - 1].dcoef, h->psi, top32.U, z);
+  return launch_check();
+}
+
+int kr_apply(void* ctx, const double* z, double* w) {
+  auto* h = (igamg_handle*)ctx;
+  const int L = (int)h->d.lev.size();
+  int rc = do_residual<double>(h, L - 1, z, h->zeros, w, nullptr, h->stream);     // w = -K z
+  if (rc) return rc;
+  return krylov_negate(w, h->d.lev[L - 1].L.n_total, h->stream);
+}
+
+int kr_residual(void* ctx, const double* U, const double* F, double* R, double* norm) {
+  auto* h = (igamg_handle*)ctx;
+  const int L = (int)h->d.lev.size();
+  int rc = do_residual<double>(h, L - 1, U, F, R, h->norm2, h->stream);
+  if (rc) return rc;
+  return read_norm(h, norm);
+}
+
+int fgmres_impl(igamg_handle* h, double* U, const double* F, double rtol, int max_cycles, igamg_report* rep,
+                double atol) {
+  KrylovOps ops;
+  ops.ctx = h; ops.stream = h->stream;
+  ops.precond = kr_precond; ops.apply = kr_apply; ops.residual = kr_residual;
+  int st = fgmres_solve(ops, h->kw, U, F, rtol, atol, max_cycles, rep);
+  if (st < 0) return st;
+  if (rep) {
+    double dv = 0.0;
+    int rc = div_inf_impl(h, U, &dv);
+    if (rc) return rc;
+    rep->div_inf = dv;
+  }
+  return st;
+}
+
 int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max_cycles, igamg_report* rep,
-               double atol = -1.0) {
+               double atol) {
+  if (h->prob.precision >= IGAMG_FGMRES_FP64) return fgmres_impl(h, U, F, rtol, max_cycles, rep, atol);
   int L = (int)h->d.lev.size();
   int rc = do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, h->norm2, h->stream);
   if (rc) return rc;
@@ -816,7 +914,7 @@ int validate(const igamg_problem& pr) {
   if (pr.n_fine % (1 << (pr.n_levels - 1))) return IGAMG_EINVAL;
   if (!(pr.sigma > 0) || !(pr.nu > 0) || pr.nu1 < 0 || pr.nu2 < 0) return IGAMG_EINVAL;
   if (pr.smoother != IGAMG_MULT && pr.smoother != IGAMG_ADD) return IGAMG_EINVAL;
-  if (pr.precision != IGAMG_FP64 && pr.precision != IGAMG_FP32_IR) return IGAMG_EUNSUPPORTED;
+  if (pr.precision < IGAMG_FP64 || pr.precision > IGAMG_FGMRES_FP32) return IGAMG_EUNSUPPORTED;
   if (pr.n_fine > 8192) return IGAMG_EINVAL;
   // the coarsest grid is solved with a dense inverse held in shared memory by one block
   if (level_sizes(pr.p, pr.n_fine >> (pr.n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
@@ -892,7 +990,7 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
   }
   h->ndof0 = h->host.ndof0;
   if ((rc = upload_typed<double>(h, h->d, max_delta))) return fail(rc);
-  if (pr.precision == IGAMG_FP32_IR && (rc = upload_typed<float>(h, h->f, max_delta))) return fail(rc);
+  if (fp32_base(pr) && (rc = upload_typed<float>(h, h->f, max_delta))) return fail(rc);
   h->ndof0 = h->host.ndof0;
   long long nfine = h->lc[L - 1].sz.n_total;
   if ((rc = dmalloc(h, (void**)&h->part, 2 * sizeof(double) * (nblk(nfine) + 1)))) return fail(rc);
@@ -907,7 +1005,12 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
   if ((rc = dmalloc(h, (void**)&h->psi, nint * nint * sizeof(double)))) return fail(rc);
   if (cudaMallocHost((void**)&h->h_pinned, 2 * sizeof(double)) != cudaSuccess) return fail(IGAMG_ECUDA);
   if ((rc = autotune_fused<double>(h, h->d))) return fail(rc);
-  if (pr.precision == IGAMG_FP32_IR && (rc = autotune_fused<float>(h, h->f))) return fail(rc);
+  if (fp32_base(pr) && (rc = autotune_fused<float>(h, h->f))) return fail(rc);
+  if (pr.precision >= IGAMG_FGMRES_FP64) {
+    if ((rc = krylov_alloc(h->kw, pr.restart > 0 ? pr.restart : 20, nfine, h->allocs))) return fail(rc);
+    if ((rc = dmalloc(h, (void**)&h->zeros, nfine * sizeof(double)))) return fail(rc);
+    if (cudaMemset(h->zeros, 0, nfine * sizeof(double)) != cudaSuccess) return fail(IGAMG_ECUDA);
+  }
   if (cudaStreamCreateWithFlags(&h->exec_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(IGAMG_ECUDA);
   if (cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess) return fail(IGAMG_ECUDA);
   *out = h;
@@ -917,6 +1020,7 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
 void igamg_destroy(igamg_handle* h) {
   if (!h) return;
   if (h->d3) h3_destroy(h->d3);
+  krylov_free_host(h->kw);
   for (auto& g : h->graph) if (g) cudaGraphExecDestroy(g);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -999,7 +1103,7 @@ int igamg_vcycle(igamg_handle* h, double* U, const double* F) {
 int igamg_solve(igamg_handle* h, double* U, const double* F, double rtol, int max_cycles, igamg_report* rep) {
   if (!h || !U || !F || !(rtol >= 0) || max_cycles < 0) return IGAMG_EINVAL;
   if (h->d3) return h3_solve(h->d3, U, F, rtol, max_cycles, rep, -1.0);
-  return solve_impl(h, U, F, rtol, max_cycles, rep);
+  return solve_impl(h, U, F, rtol, max_cycles, rep, -1.0);
 }
 
 int igamg_solve_host(igamg_handle* h, const double* f_qp_host, double* U_host, double rtol, int max_cycles,
@@ -1012,7 +1116,7 @@ int igamg_solve_host(igamg_handle* h, const double* f_qp_host, double* U_host, d
   CK(cudaMemcpyAsync(h->Uh, U_host, nt * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   int rc = igamg_load_vector(h, h->f_dev, h->Fh);
   if (rc) return rc;
-  int st = solve_impl(h, h->Uh, h->Fh, rtol, max_cycles, rep);
+  int st = solve_impl(h, h->Uh, h->Fh, rtol, max_cycles, rep, -1.0);
   if (st < 0) return st;
   CK(cudaMemcpyAsync(U_host, h->Uh, nt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));

@@ -24,6 +24,7 @@
 #include "igamg3d.h"
 #include "igamg_internal.h"
 #include "kernels3d.cuh"
+#include "krylov.h"
 
 using namespace igamg;
 using namespace igamg::dev;
@@ -235,6 +236,8 @@ struct igamg3d_handle {
   const void* gU[2] = {nullptr, nullptr};
   const void* gF[2] = {nullptr, nullptr};
   std::vector<void*> allocs;
+  KrylovWork kw;                    // FGMRES modes
+  double* zeros = nullptr;
 };
 
 namespace {
@@ -282,6 +285,10 @@ bool split_rows(const Lev3Common& lc) {
   }();
   if (mode >= 0) return mode == 1;
   return lc.colour_blk[lc.n_colours] < kSplitBelow * lc.n_colours;
+}
+
+bool fp32_base3(const igamg_problem& pr) {
+  return pr.precision == IGAMG_FP32_IR || pr.precision == IGAMG_FGMRES_FP32;
 }
 
 template <typename T> Typed3<T>& typed(igamg3d_handle* h);
@@ -488,7 +495,7 @@ int do_ir_step(igamg3d_handle* h, double* U, const double* F, cudaStream_t s) {
 
 int do_step(igamg3d_handle* h, double* U, const double* F, cudaStream_t s) {
   const int L = (int)h->d.lev.size();
-  if (h->prob.precision == IGAMG_FP32_IR) return do_ir_step(h, U, F, s);
+  if (fp32_base3(h->prob)) return do_ir_step(h, U, F, s);
   int rc = do_vcycle<double>(h, U, F, s);
   if (rc) return rc;
   return do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, h->norm2, s);
@@ -501,7 +508,7 @@ int ensure_graph(igamg3d_handle* h, int kind, double* U, const double* F) {
   CK3(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   int L = (int)h->d.lev.size();
   int rc = IGAMG_OK;
-  if (kind == 1 && h->prob.precision == IGAMG_FP32_IR)
+  if (kind == 1 && fp32_base3(h->prob))
     rc = do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, nullptr, h->cap_stream);
   if (!rc) rc = do_step(h, U, F, h->cap_stream);
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
@@ -628,7 +635,7 @@ int validate3(const igamg_problem& pr) {
   if (!(pr.sigma > 0) || !(pr.nu > 0) || pr.nu1 < 0 || pr.nu2 < 0) return IGAMG_EINVAL;
   if (pr.smoother != IGAMG_MULT) return IGAMG_EUNSUPPORTED;   // eq. ASM is not built in 3D
   if (pr.beta_qp) return IGAMG_EUNSUPPORTED;                  // 3D Oseen is not built
-  if (pr.precision != IGAMG_FP64 && pr.precision != IGAMG_FP32_IR) return IGAMG_EUNSUPPORTED;
+  if (pr.precision < IGAMG_FP64 || pr.precision > IGAMG_FGMRES_FP32) return IGAMG_EUNSUPPORTED;
   if (sizes3(pr.p, pr.n_fine).n_total > (1LL << 30)) return IGAMG_EINVAL;   // 32-bit row indices
   if (sizes3(pr.p, pr.n_fine >> (pr.n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
   return IGAMG_OK;
@@ -669,9 +676,7 @@ int h3_create(const igamg_problem* prob, void* cuda_stream, igamg3d_handle** out
   }
   h->ndof0 = h->host.ndof0;
   if ((rc = upload_typed<double>(h, h->d))) return fail(rc);
-  if (pr.precision == IGAMG_FP32_IR && (rc = upload_typed<float>(h, h->f))) return fail(rc);
-  if ((rc = setup_cluster3<double>(h, h->d))) return fail(rc);
-  if (pr.precision == IGAMG_FP32_IR && (rc = setup_cluster3<float>(h, h->f))) return fail(rc);
+  if (fp32_base3(pr) && (rc = upload_typed<float>(h, h->f))) return fail(rc);
   const auto& fs = h->host.lev[L - 1].sz;
   long long nfine = fs.n_total;
   if ((rc = dmalloc(h, (void**)&h->part, 2 * sizeof(double) * (nblk(nfine) + 1)))) return fail(rc);
@@ -700,12 +705,21 @@ int h3_create(const igamg_problem* prob, void* cuda_stream, igamg3d_handle** out
     cudaFuncSetAttribute(k_coarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(h->ndof0 * sizeof(double)));
     cudaFuncSetAttribute(k_coarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(h->ndof0 * sizeof(float)));
   }
+  // the cluster tuner runs V-cycles: only once every workspace above exists
+  if ((rc = setup_cluster3<double>(h, h->d))) return fail(rc);
+  if (fp32_base3(pr) && (rc = setup_cluster3<float>(h, h->f))) return fail(rc);
+  if (pr.precision >= IGAMG_FGMRES_FP64) {
+    if ((rc = krylov_alloc(h->kw, pr.restart > 0 ? pr.restart : 20, nfine, h->allocs))) return fail(rc);
+    if ((rc = dmalloc(h, (void**)&h->zeros, nfine * sizeof(double)))) return fail(rc);
+    if (cudaMemset(h->zeros, 0, nfine * sizeof(double)) != cudaSuccess) return fail(IGAMG_ECUDA);
+  }
   *out = h;
   return IGAMG_OK;
 }
 
 void h3_destroy(igamg3d_handle* h) {
   if (!h) return;
+  krylov_free_host(h->kw);
   for (auto& g : h->graph) if (g) cudaGraphExecDestroy(g);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -776,8 +790,59 @@ int h3_div_inf(igamg3d_handle* h, const double* U, double* out) {
   return IGAMG_OK;
 }
 
+static int kr3_precond(void* ctx, const double* v, double* z) {
+  auto* h = (igamg3d_handle*)ctx;
+  cudaStream_t s = h->stream;
+  const int L = (int)h->d.lev.size();
+  const auto& Ld = h->d.lev[L - 1].L;
+  const auto& lc = h->lc[L - 1];
+  CK3(cudaMemsetAsync(z, 0, Ld.n_total * sizeof(double), s));
+  if (h->prob.precision == IGAMG_FGMRES_FP64) return do_vcycle<double>(h, z, v, s);
+  auto& top32 = h->f.lev[L - 1];
+  k_to_float<<<nblk(Ld.n_total), kBlock, 0, s>>>(Ld.n_total, v, top32.F);
+  CK3(cudaMemsetAsync(top32.U, 0, Ld.n_total * sizeof(float), s));
+  int rc = do_vcycle<float>(h, top32.U, top32.F, s);
+  if (rc) return rc;
+  const int ni = Ld.ni, nq = Ld.nq;
+  CK3(cudaMemsetAsync(h->psi + (size_t)2 * nq * ni * ni, 0, (size_t)nq * ni * ni * sizeof(double), s));
+  k_lift3_z<<<nblk(2LL * ni * nq), kBlock, 0, s>>>(top32.L, lc.inv_dcoef, top32.U, h->psi, h->tot);
+  k_lift3_chi<<<nblk(ni, 128), 128, 0, s>>>(ni, nq, lc.dcoef, lc.inv_dcoef, h->tot, h->psi);
+  k_curl3<true><<<nblk(Ld.n_total), kBlock, 0, s>>>(Ld, lc.dcoef, h->psi, top32.U, z);
+  return launch_check();
+}
+
+static int kr3_apply(void* ctx, const double* z, double* w) {
+  auto* h = (igamg3d_handle*)ctx;
+  const int L = (int)h->d.lev.size();
+  int rc = do_residual<double>(h, L - 1, z, h->zeros, w, nullptr, h->stream);    // w = -K z
+  if (rc) return rc;
+  return krylov_negate(w, h->d.lev[L - 1].L.n_total, h->stream);
+}
+
+static int kr3_residual(void* ctx, const double* U, const double* F, double* R, double* norm) {
+  auto* h = (igamg3d_handle*)ctx;
+  const int L = (int)h->d.lev.size();
+  int rc = do_residual<double>(h, L - 1, U, F, R, h->norm2, h->stream);
+  if (rc) return rc;
+  return read_norm(h, norm);
+}
+
 int h3_solve(igamg3d_handle* h, double* U, const double* F, double rtol, int max_cycles, igamg_report* rep,
              double atol) {
+  if (h->prob.precision >= IGAMG_FGMRES_FP64) {
+    KrylovOps ops;
+    ops.ctx = h; ops.stream = h->stream;
+    ops.precond = kr3_precond; ops.apply = kr3_apply; ops.residual = kr3_residual;
+    int st = fgmres_solve(ops, h->kw, U, F, rtol, atol, max_cycles, rep);
+    if (st < 0) return st;
+    if (rep) {
+      double dv = 0.0;
+      int rc = h3_div_inf(h, U, &dv);
+      if (rc) return rc;
+      rep->div_inf = dv;
+    }
+    return st;
+  }
   int L = (int)h->d.lev.size();
   int rc = do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, h->norm2, h->stream);
   if (rc) return rc;

@@ -60,7 +60,9 @@ __host__ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v
 // over fixed-size, zero-padded stencil records with clamped (always valid) neighbour
 // indices: no lane diverges on the row kind (each FP64 instruction already costs 64 issue
 // cycles per warp on GB300) and every load can be issued ahead of the FMAs.
-template <int P, typename T>
+// PART = 2: the whole row; PART = 0: box 0 only; PART = 1: box 1 and the lambda term (the
+// split form lets two warps share one row's multiply-adds, see k_mult_colour_split).
+template <int P, typename T, int PART = 2>
 __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __restrict__ U, int g) {
   constexpr int Q = P - 1, TC = 2 * P + 1, NC = 2 * TC + 1;
   constexpr int WQ = 2 * Q + 1, WPP = 2 * P + 1;
@@ -87,21 +89,25 @@ __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __re
   const int b1_x0 = is_x ? -P : -Q, b1_y0 = is_x ? -Q : (is_p ? -Q : -P), b1_wy = is_x ? WQ : 2 * P;
   const int b1_ylo = is_p ? 1 : 0, b1_yhi = is_p ? L.nint : L.lastq, b1_ysh = is_p ? 1 : 0;
   T acc = T(0), acc2 = T(0);
+  if (PART != 1) {
 #pragma unroll
-  for (int j = 0; j < B0; ++j) {
-    int dx = j / b0_wy, dy = j - dx * b0_wy;
-    int x = clampi(ix + b0_x0 + dx, b0_xlo, b0_xhi) - b0_xsh;
-    int y = clampi(iy + b0_y0 + dy, b0_ylo, b0_yhi) - b0_ysh;
-    acc = fma(st[j], U[b0_base + y * b0_stride + x], acc);
+    for (int j = 0; j < B0; ++j) {
+      int dx = j / b0_wy, dy = j - dx * b0_wy;
+      int x = clampi(ix + b0_x0 + dx, b0_xlo, b0_xhi) - b0_xsh;
+      int y = clampi(iy + b0_y0 + dy, b0_ylo, b0_yhi) - b0_ysh;
+      acc = fma(st[j], U[b0_base + y * b0_stride + x], acc);
+    }
   }
+  if (PART != 0) {
 #pragma unroll
-  for (int j = 0; j < B1; ++j) {
-    int dx = j / b1_wy, dy = j - dx * b1_wy;
-    int x = clampi(ix + b1_x0 + dx, 0, L.lastq);
-    int y = clampi(iy + b1_y0 + dy, b1_ylo, b1_yhi) - b1_ysh;
-    acc2 = fma(st[B0 + j], U[b1_base + y * L.npd + x], acc2);
+    for (int j = 0; j < B1; ++j) {
+      int dx = j / b1_wy, dy = j - dx * b1_wy;
+      int x = clampi(ix + b1_x0 + dx, 0, L.lastq);
+      int y = clampi(iy + b1_y0 + dy, b1_ylo, b1_yhi) - b1_ysh;
+      acc2 = fma(st[B0 + j], U[b1_base + y * L.npd + x], acc2);
+    }
+    acc = fma(st[RU - 1], U[L.n_total - 1], acc);
   }
-  acc = fma(st[RU - 1], U[L.n_total - 1], acc);
   return acc + acc2;
 }
 
@@ -276,6 +282,52 @@ __global__ void __launch_bounds__(256) k_mult_colour(LevelTab<T> L, T* __restric
   extern __shared__ unsigned char smem_raw[];
   T* sh = reinterpret_cast<T*>(smem_raw);
   int w = ((int)blockIdx.x - nb8) * 8 + wib;
+  if (w >= ngen) return;
+  general_patch_warp<P>(L, U, F, dofs, cls, cinv, nloc, maxl, first + n8 + w, lane, sh + wib * maxl);
+}
+
+// The same colour step with each 8-DOF patch row split over two warps: warps 0-7 of the
+// block sum box 0 of their rows (minus F), warps 8-15 box 1 and the lambda term of the same
+// rows; the halves meet in shared memory, then warps 0-7 apply the local inverses.  Each
+// warp issues about half the FP64 instructions of k_mult_colour's, which shortens the
+// critical path on GB300 (one FP64 instruction per warp every 64 cycles).  Blocks [nb8, ...)
+// hold the larger (wall) patches, one warp each.
+template <int P, typename T>
+__global__ void __launch_bounds__(512) k_mult_colour_split(LevelTab<T> L, T* __restrict__ U, const T* __restrict__ F,
+                                                           const int* __restrict__ dofs, const int* __restrict__ cls,
+                                                           const T* __restrict__ cinv, const T* __restrict__ cinv8,
+                                                           const int* __restrict__ nloc,
+                                                           int maxl, int first, int n8, int ngen, int nb8) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if ((int)blockIdx.x < nb8) {
+    __shared__ T part[2][256];
+    const int half = wib >> 3, w8 = wib & 7;
+    const int slot = w8 * 32 + lane;                    // (patch in block, row)
+    const int grp = (blockIdx.x * 8 + w8) * 4 + (lane >> 3), row = lane & 7;
+    const bool active = grp < n8;
+    const int patch = first + (active ? grp : 0);
+    const int g = dofs[(size_t)patch * maxl + row];
+    T v = half == 0 ? F[g] - row_KU<P, T, 0>(L, U, g) : -row_KU<P, T, 1>(L, U, g);
+    part[half][slot] = v;
+    __syncthreads();
+    if (half) return;
+    const T r = v + part[1][slot];
+    part[0][slot] = r;
+    __syncwarp();
+    const T* A = cinv8 + (size_t)cls[patch] * 64 + row * 8;
+    const T* rp = &part[0][slot - row];
+    T d0 = T(0), d1 = T(0);
+#pragma unroll
+    for (int s = 0; s < 8; s += 2) {
+      d0 = fma(A[s], rp[s], d0);
+      d1 = fma(A[s + 1], rp[s + 1], d1);
+    }
+    if (active) U[g] += d0 + d1;
+    return;
+  }
+  extern __shared__ unsigned char smem_raw[];
+  T* sh = reinterpret_cast<T*>(smem_raw);
+  int w = ((int)blockIdx.x - nb8) * 16 + wib;
   if (w >= ngen) return;
   general_patch_warp<P>(L, U, F, dofs, cls, cinv, nloc, maxl, first + n8 + w, lane, sh + wib * maxl);
 }
