@@ -376,14 +376,23 @@ def run_reference(args):
 
 def profile_case(spec):
     """Untimed workload for profilers: two solves of one case of the sweep.
-    spec = "p<degree>-<fp64|mixed>[-sigma<value>]", e.g. "p2-fp64", or "cube-p2-<fp64|mixed>"
-    (one solve of the 64^3 cube)."""
+    spec = "p<degree>-<fp64|mixed>[-sigma<value>]", e.g. "p2-fp64", "cube-p2-<fp64|mixed>" (one
+    solve of the 64^3 cube) or "oseen-<fp64|mixed>" (one solve of the 512^2 Oseen problem)."""
     import torch
 
     from paper_1705_09282_gb300 import inputs
     from paper_1705_09282_gb300._lib import IGAMG_FP32_IR, IGAMG_FP64
     from paper_1705_09282_gb300.solver import Solver
     parts = spec.split("-")
+    if parts[0] == "oseen":
+        prec = IGAMG_FP32_IR if parts[1] == "mixed" else IGAMG_FP64
+        S = Solver(2, 512, 8, 1.0, 1e-2, beta=inputs.oseen_advection(2, 512, 0.5), precision=prec)
+        F = S.load_vector(torch.tensor(inputs.grf_forcing(2, 512, seed=1707), device="cuda"))
+        U = S.empty()
+        rep = S.solve(U, F, rtol=RTOL, max_cycles=MAXC, history=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": spec, "cycles": rep["cycles"], "rel_residual": rep["rel_residual"]}))
+        return
     if parts[0] == "cube":
         prec = IGAMG_FP32_IR if parts[2] == "mixed" else IGAMG_FP64
         S = Solver(int(parts[1][1:]), 64, 5, 1.0, 1.0, nu1=2, nu2=2, precision=prec, dim=3)
@@ -583,6 +592,50 @@ def run_cube(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cube_oseen(args):
+    """3D generalized Oseen on the unit cube (the regimes of Table 7): p = 2, 64^3 elements,
+    5 grids, beta = the manufactured velocity scaled to max |beta| = 1, (Re, Da) = (1, 1) with
+    nu = 1, sigma = 1 and (100, 1000) with nu = 0.01, sigma = 10; manufactured forcing;
+    FP64 and FP32-in-FP64 solves from zero to 1e-8 (per-row operator records in HBM)."""
+    import torch
+
+    from paper_1705_09282_gb300 import inputs
+    from paper_1705_09282_gb300._lib import IGAMG_FP32_IR, IGAMG_FP64
+    from paper_1705_09282_gb300.solver import Solver
+    p, n, L = 2, 64, 5
+    beta = inputs.oseen_advection_3d(p, n, 1.0)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for re_, da, sigma, nu in ((1, 1, 1.0, 1.0), (100, 1000, 10.0, 0.01)):
+        f = torch.tensor(inputs.oseen_forcing_3d(p, n, sigma, nu, beta), device="cuda")
+        for name, prec in (("fp64", IGAMG_FP64), ("mixed", IGAMG_FP32_IR)):
+            t0 = time.perf_counter()
+            S = Solver(p, n, L, sigma, nu, precision=prec, dim=3, beta=beta)
+            setup = time.perf_counter() - t0
+            F = S.load_vector(f)
+            U = S.empty()
+            for _ in range(args.warmup):
+                U.zero_()
+                S.solve(U, F, rtol=RTOL, max_cycles=MAXC, history=False)
+            ts = []
+            for _ in range(args.steps):
+                U.zero_()
+                dt, rep = _timed(lambda: S.solve(U, F, rtol=RTOL, max_cycles=MAXC, history=False), stream)
+                assert rep["converged"], rep
+                ts.append(dt)
+            t = sum(ts) / len(ts)
+            out["%s_Re%d_Da%d" % (name, re_, da)] = {
+                "solve_ms": 1e3 * t, "cycles": rep["cycles"], "rel_residual": rep["rel_residual"],
+                "mdof_per_s_per_cycle": S.ndof() * rep["cycles"] / t / 1e6, "div_inf": rep["div_inf"],
+                "setup_s": setup}
+            S.close()
+    line = {"metric": "3D Oseen solve time to 1e-8 rel. residual (Table 7 regimes)", "workload": "cube-oseen",
+            "config": {"workload": "3D generalized Oseen, unit cube, p=2, 64^3 elements, 5 levels, max|beta|=1, "
+                                   "(Re, Da) in {(1, 1), (100, 1000)}, manufactured forcing, V(2,2) multiplicative",
+                       "ndof": 3 * 64 * 65 * 65 + 65 ** 3 + 1}, "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_smoothers(args):
     """Additive (eq. ASM) against multiplicative (eq. MSM) Schwarz at the headline size:
     2D generalized Stokes, 256 x 256, 7 grids, p = 2 and 3, sigma = nu = 1, GRF forcing,
@@ -601,11 +654,11 @@ def run_smoothers(args):
             S = Solver(p, N_FINE, N_LEVELS, 1.0, 1.0, smoother=sm, eta=eta, nu1=2, nu2=2)
             F = S.load_vector(f)
             U = S.empty()
-            for _ in range(args.warmup):
-                U.zero_()
-                S.solve(U, F, rtol=RTOL, max_cycles=200, history=False)
             ts = []
             try:
+                for _ in range(args.warmup):
+                    U.zero_()
+                    S.solve(U, F, rtol=RTOL, max_cycles=200, history=False)
                 for _ in range(args.steps):
                     U.zero_()
                     dt, rep = _timed(lambda: S.solve(U, F, rtol=RTOL, max_cycles=200, history=False), stream)
@@ -631,8 +684,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="stokes", choices=["stokes", "oseen", "batch", "cube", "smoothers"],
-                    help="stokes: the headline sweep (default); oseen / batch / cube / smoothers: extra measurements")
+    ap.add_argument("--workload", default="stokes",
+                    choices=["stokes", "oseen", "batch", "cube", "cube-oseen", "smoothers"],
+                    help="stokes: the headline sweep (default); the others: extra measurements")
     ap.add_argument("--batch-count", type=int, default=1024)
     ap.add_argument("--train-count", type=int, default=384)
     ap.add_argument("--train-steps", type=int, default=6000)
@@ -652,6 +706,8 @@ def main():
         run_cube(args)
     elif args.workload == "smoothers":
         run_smoothers(args)
+    elif args.workload == "cube-oseen":
+        run_cube_oseen(args)
     else:
         run_ours(args)
 

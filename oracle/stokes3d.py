@@ -12,6 +12,7 @@ Follows (3D versions of the 2D oracle's steps):
   * K_l = R K P with tensor-product knot-insertion prolongations                -- Sec. 5.1
   * subdomains = supports of vector-potential basis functions
     Psi = S^{q,p,p} x S^{p,q,p} x S^{p,p,q} with psi x n = 0 on the boundary     -- Sec. 5.2
+  * generalized Oseen: + (beta . grad u, v) componentwise; coarse levels = R K P   -- Sec. 3.1, Sec. 5.1
   * Algorithm 1 with the multiplicative Schwarz smoother (eq. MSM), exact
     coarsest solve (the paper's 3D results use the multiplicative smoother only)  -- Sec. 5.1-5.2, Sec. 6.3
 Readings: local pressure bordered with m (zero-mean local pressure); multiplicative order
@@ -35,7 +36,10 @@ class Stokes3D:
     """Layout of U: [u_x (z, y, x interior), u_y (z, y interior, x), u_z (z interior, y, x),
     p (z, y, x), lambda], x fastest; interior = indices 1..n+p-2 of the degree-p direction."""
 
-    def __init__(self, p, n, sigma, nu, c_pen=None, h_pen=None, assemble=True):
+    def __init__(self, p, n, sigma, nu, c_pen=None, h_pen=None, assemble=True, beta=None):
+        """beta: advection at the quadrature points, (3, nG, nG, nG) [component, z, y, x], for
+        the generalized Oseen problem (Sec. 3.1), or None for generalized Stokes."""
+        self.beta = beta
         self.p, self.q, self.n = p, p - 1, n
         self.sigma, self.nu = float(sigma), float(nu)
         self.c_pen = 4.0 * (p - 1) if c_pen is None else float(c_pen)
@@ -149,6 +153,11 @@ class Stokes3D:
             M = sig * np.einsum("zyxaghk,zyxbghk,ghk->zyxab", v, v, W3)
             for d in (dx, dy, dz):
                 M += nu * np.einsum("zyxaghk,zyxbghk,ghk->zyxab", d, d, W3)
+            if self.beta is not None:
+                # Oseen: + int v_c (beta . grad u_c), componentwise (Sec. 3.1)
+                bq = [np.asarray(self.beta[a]).reshape(n, G, n, G, n, G).transpose(0, 2, 4, 1, 3, 5) for a in range(3)]
+                adv = bq[0][:, :, :, None] * dx + bq[1][:, :, :, None] * dy + bq[2][:, :, :, None] * dz
+                M += np.einsum("zyxaghk,zyxbghk,ghk->zyxab", v, adv, W3)
             add(idc, idc, M)
             dv = (dx, dy, dz)[c]                                        # d u_c / d x_c
             Bl = np.einsum("zyxaghk,zyxbghk,ghk->zyxab", dv, pv, W3)
@@ -353,9 +362,9 @@ class Level3D:
 
 
 class Hierarchy3D:
-    def __init__(self, p, n_fine, n_levels, sigma, nu, nu1=2, nu2=2):
+    def __init__(self, p, n_fine, n_levels, sigma, nu, nu1=2, nu2=2, beta=None):
         self.p, self.n_levels, self.nu1, self.nu2 = p, n_levels, nu1, nu2
-        fine = Stokes3D(p, n_fine, sigma, nu)
+        fine = Stokes3D(p, n_fine, sigma, nu, beta=beta)
         self.fine = fine
         levels, Ps = [None] * n_levels, [None] * n_levels
         K, m = fine.K, fine.m

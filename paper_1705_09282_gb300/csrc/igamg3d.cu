@@ -214,6 +214,7 @@ struct Lev3Common {
   int *dofs = nullptr, *cls = nullptr, *nloc = nullptr;
   int *slot_g = nullptr, *slot_c = nullptr;
   unsigned* slot_kb = nullptr;
+  long long* cinv_off = nullptr;
   double *dcoef = nullptr, *inv_dcoef = nullptr;
 };
 
@@ -313,10 +314,17 @@ int upload_typed(igamg3d_handle* h, Typed3<T>& ty) {
     }
     Lt.cm0 = cm[0]; Lt.cm1 = cm[1]; Lt.cm2 = cm[2]; Lt.cm3 = cm[3];
     Lt.rc0 = rc4[0]; Lt.rc1 = rc4[1]; Lt.rc2 = rc4[2]; Lt.rc3 = rc4[3];
+    Lt.srow = nullptr;
+    if (!hl.rows.empty()) {
+      T* sr = nullptr;
+      if ((rc = upload_as(h, &sr, hl.rows))) return rc;
+      Lt.srow = sr;
+    }
     if (l >= 1) {
-      if ((rc = upload_as(h, &tl.cinv, hl.pt.cinv)) || (rc = upload_as(h, &tl.cinv8, hl.pt.cinv8)) ||
-          (rc = upload_as(h, &tl.cinv_all, hl.pt.cinv_all)))
+      // the lane-group kernel's tables (maxl-stride inverses) only for class-record levels
+      if (hl.rows.empty() && ((rc = upload_as(h, &tl.cinv, hl.pt.cinv)) || (rc = upload_as(h, &tl.cinv8, hl.pt.cinv8))))
         return rc;
+      if ((rc = upload_as(h, &tl.cinv_all, hl.pt.cinv_all))) return rc;
       auto up = [&](const Transfer1D& t, Xfer<T>& x) -> int {
         x.nf = t.nf; x.nc = t.nc;
         int r;
@@ -350,25 +358,25 @@ template <typename T>
 int do_smooth(igamg3d_handle* h, int l, T* U, const T* F, cudaStream_t s) {
   auto& lc = h->lc[l];
   auto& tl = typed<T>(h).lev[l];
-  if (row_parallel() && lc.row_slots) {
+  if ((row_parallel() || tl.L.srow) && lc.row_slots) {
     const int S = lc.row_slots;
     const int* sg = lc.slot_g; const int* sc = lc.slot_c; const unsigned* sk = lc.slot_kb;
     if (S == 256 && split_rows(lc)) {
       for (int c = 0; c < lc.n_colours; ++c) {
         int b0 = lc.colour_blk[c], nb = lc.colour_blk[c + 1] - b0;
         if (nb == 0) continue;
-        if (h->prob.p == 2) k_mult_rows3x<2, 256, T><<<nb, 768, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
-        else k_mult_rows3x<3, 256, T><<<nb, 768, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
+        if (h->prob.p == 2) k_mult_rows3x<2, 256, T><<<nb, 768, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
+        else k_mult_rows3x<3, 256, T><<<nb, 768, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
       }
       return launch_check();
     }
     for (int c = 0; c < lc.n_colours; ++c) {
       int b0 = lc.colour_blk[c], nb = lc.colour_blk[c + 1] - b0;
       if (nb == 0) continue;
-      if (h->prob.p == 2 && S == 256) k_mult_rows3<2, 256, T><<<nb, 256, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
-      else if (h->prob.p == 2) k_mult_rows3<2, 1024, T><<<nb, 1024, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
-      else if (S == 256) k_mult_rows3<3, 256, T><<<nb, 256, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
-      else k_mult_rows3<3, 1024, T><<<nb, 1024, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.maxl, b0 * S);
+      if (h->prob.p == 2 && S == 256) k_mult_rows3<2, 256, T><<<nb, 256, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
+      else if (h->prob.p == 2) k_mult_rows3<2, 1024, T><<<nb, 1024, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
+      else if (S == 256) k_mult_rows3<3, 256, T><<<nb, 256, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
+      else k_mult_rows3<3, 1024, T><<<nb, 1024, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
     }
     return launch_check();
   }
@@ -552,7 +560,7 @@ int setup_cluster3(igamg3d_handle* h, Typed3<T>& ty) {
   for (int l = 0; l <= best; ++l) {
     Cluster3Level<T>& V = D.lev[l];
     const auto& lc = h->lc[l];
-    V.L = ty.lev[l].L; V.tp = ty.lev[l].tp; V.tq = ty.lev[l].tq; V.cinv = ty.lev[l].cinv_all;
+    V.L = ty.lev[l].L; V.tp = ty.lev[l].tp; V.tq = ty.lev[l].tq; V.cinv = ty.lev[l].cinv_all; V.cinv_off = lc.cinv_off;
     V.slot_g = lc.slot_g; V.slot_c = lc.slot_c; V.slot_kb = lc.slot_kb; V.colour_blk = lc.colour_blk_dev;
     V.n_colours = lc.n_colours; V.maxl = lc.maxl; V.row_slots = lc.row_slots;
     V.U = ty.lev[l].U; V.F = ty.lev[l].F; V.R = ty.lev[l].R;
@@ -634,7 +642,6 @@ int validate3(const igamg_problem& pr) {
   if (pr.n_fine % (1 << (pr.n_levels - 1))) return IGAMG_EINVAL;
   if (!(pr.sigma > 0) || !(pr.nu > 0) || pr.nu1 < 0 || pr.nu2 < 0) return IGAMG_EINVAL;
   if (pr.smoother != IGAMG_MULT) return IGAMG_EUNSUPPORTED;   // eq. ASM is not built in 3D
-  if (pr.beta_qp) return IGAMG_EUNSUPPORTED;                  // 3D Oseen is not built
   if (pr.precision < IGAMG_FP64 || pr.precision > IGAMG_FGMRES_FP32) return IGAMG_EUNSUPPORTED;
   if (sizes3(pr.p, pr.n_fine).n_total > (1LL << 30)) return IGAMG_EINVAL;   // 32-bit row indices
   if (sizes3(pr.p, pr.n_fine >> (pr.n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
@@ -670,7 +677,7 @@ int h3_create(const igamg_problem* prob, void* cuda_stream, igamg3d_handle** out
       if ((rc = upload_as(h, &lc.dofs, pt.dofs)) || (rc = upload_as(h, &lc.cls, pt.cls)) ||
           (rc = upload_as(h, &lc.nloc, pt.nloc)) || (rc = upload_as(h, &lc.slot_g, pt.slot_g)) ||
           (rc = upload_as(h, &lc.slot_c, pt.slot_c)) || (rc = upload_as(h, &lc.slot_kb, pt.slot_kb)) ||
-          (rc = upload_as(h, &lc.colour_blk_dev, pt.colour_blk)))
+          (rc = upload_as(h, &lc.colour_blk_dev, pt.colour_blk)) || (rc = upload_as(h, &lc.cinv_off, pt.cinv_off)))
         return fail(rc);
     }
   }
@@ -909,13 +916,16 @@ int host_operator_rows3(const igamg_problem* prob, int level, double* K, size_t 
   one.n_levels = 1;
   one.c_penalty = prob->c_penalty > 0 ? prob->c_penalty : 4.0 * (prob->p - 1);
   one.c_penalty *= (double)prob->n_fine / one.n_fine;   // keep C_I / h_fine
-  if ((rc = build_level_only3(one, H, err))) return rc;
-  const auto& lh = H.lev[0];
+  // Stokes: only this level's records (one-level build of this mesh); Oseen: the level of the
+  // full operator hierarchy (coarse levels are Galerkin products)
+  if ((rc = prob->beta_qp ? build_operators3(*prob, H, err) : build_level_only3(one, H, err))) return rc;
+  const auto& lh = prob->beta_qp ? H.lev[level] : H.lev[0];
   LevelTab3<double> L{};
   L.n = lh.sz.n; L.ni = lh.sz.ni; L.nq = lh.sz.nq;
   L.n_uc = (int)lh.sz.n_uc; L.n_u = (int)lh.sz.n_u; L.n_p = (int)lh.sz.n_p; L.n_total = (int)lh.sz.n_total;
   L.cm0 = lh.st.cmap[0].data(); L.cm1 = lh.st.cmap[1].data(); L.cm2 = lh.st.cmap[2].data(); L.cm3 = lh.st.cmap[3].data();
   L.rc0 = lh.st.rec[0].data(); L.rc1 = lh.st.rec[1].data(); L.rc2 = lh.st.rec[2].data(); L.rc3 = lh.st.rec[3].data();
+  L.srow = lh.rows.empty() ? nullptr : lh.rows.data();
   long long n = lh.sz.n_total;
   if (n_out) *n_out = n;
   if (!K) return IGAMG_OK;
@@ -946,14 +956,17 @@ int host_operator_apply3(const igamg_problem* prob, int level, const double* V, 
   one.c_penalty = (prob->c_penalty > 0 ? prob->c_penalty : 4.0 * (prob->p - 1)) * prob->n_fine / one.n_fine;
   HierarchyHost3 H;
   std::string err;
-  if ((rc = build_level_only3(one, H, err))) return rc;
-  const auto& lh = H.lev[0];
+  // Stokes: only this level's records (one-level build of this mesh); Oseen: the level of the
+  // full operator hierarchy (coarse levels are Galerkin products)
+  if ((rc = prob->beta_qp ? build_operators3(*prob, H, err) : build_level_only3(one, H, err))) return rc;
+  const auto& lh = prob->beta_qp ? H.lev[level] : H.lev[0];
   if (n != (size_t)lh.sz.n_total) return IGAMG_EINVAL;
   LevelTab3<double> L{};
   L.n = lh.sz.n; L.ni = lh.sz.ni; L.nq = lh.sz.nq;
   L.n_uc = (int)lh.sz.n_uc; L.n_u = (int)lh.sz.n_u; L.n_p = (int)lh.sz.n_p; L.n_total = (int)lh.sz.n_total;
   L.cm0 = lh.st.cmap[0].data(); L.cm1 = lh.st.cmap[1].data(); L.cm2 = lh.st.cmap[2].data(); L.cm3 = lh.st.cmap[3].data();
   L.rc0 = lh.st.rec[0].data(); L.rc1 = lh.st.rec[1].data(); L.rc2 = lh.st.rec[2].data(); L.rc3 = lh.st.rec[3].data();
+  L.srow = lh.rows.empty() ? nullptr : lh.rows.data();
   double lam = 0.0;
   for (size_t i = 0; i + 1 < n; ++i) {
     double m = 0.0;

@@ -68,7 +68,8 @@ struct PatchTables {
   std::vector<int> slot_c;          // the patch's class: its matrix in cinv_all
   std::vector<unsigned> slot_kb;    // local row k | nl << 10 | (slot of the patch's row 0 in the block) << 20
   std::vector<int> colour_blk;      // n_colours + 1: first block of each colour
-  std::vector<double> cinv_all;     // every class (8-DOF classes after the others), maxl x maxl
+  std::vector<double> cinv_all;     // every class (8-DOF classes after the others), nl x nl packed
+  std::vector<long long> cinv_off;  // offset of each class's matrix in cinv_all
 };
 
 // Fills the row-flat view (slot_*, colour_blk, cinv_all) from dofs / cls / nloc / cinv / cinv8.
@@ -133,6 +134,7 @@ void build_stencils(int p, const Level1D& L, const igamg_sizes& s, Stencils& st)
 // helpers of setup.cpp shared with the 3D set-up
 std::vector<double> knots(int d, int n);
 void span_values(const std::vector<double>& t, int d, int s, double x, double* N);
+void span_derivs(const std::vector<double>& t, int d, int s, double x, double* dN);
 void gauss01(int m, std::vector<double>& x, std::vector<double>& w);
 bool invert(std::vector<double> A, int n, std::vector<double>& Ainv);
 std::vector<double> prolong_dense(int d, int nc, int& nfb, int& ncb);
@@ -171,6 +173,11 @@ struct LevelHost3 {
   igamg_sizes pub{};
   PatchTables pt;
   Stencils3 st;
+  // generalized Oseen only (empty otherwise): per velocity row, box 0 of the advection part
+  // (fine level: assembled; coarse levels: R A P of the level above), and per row (all rows
+  // but lambda) the full record = class record + advection, as the kernels read it
+  std::vector<double> adv;
+  std::vector<double> rows;
 };
 
 struct HierarchyHost3 {
@@ -190,5 +197,7 @@ int build_level_only3(const igamg_problem& pr, HierarchyHost3& H, std::string& e
 double k_entry3(const Level1D& L, const Sizes3& s, long long g1, long long g2);
 // entry (g1, g2) evaluated from the row records, as the GPU kernels do
 double k_entry3_records(const LevelHost3& lv, int p, long long g1, long long g2);
+// the full hierarchy without patch tables and coarse inverse (host inspection of operators)
+int build_operators3(const igamg_problem& pr, HierarchyHost3& H, std::string& err);
 
 }  // namespace igamg

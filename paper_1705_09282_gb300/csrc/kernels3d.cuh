@@ -19,6 +19,7 @@ struct LevelTab3 {
   int n_uc, n_u, n_p, n_total;
   const int *cm0, *cm1, *cm2, *cm3;      // class -> record, per row kind
   const T *rc0, *rc1, *rc2, *rc3;        // records, per row kind
+  const T* srow;                         // per-row records (generalized Oseen), or null
 };
 
 template <int P>
@@ -93,10 +94,11 @@ __host__ __device__ __forceinline__ T box3(const LevelTab3<T>& L, const T* __res
   return (s0 + sA) + (sB + sC);
 }
 
-// record of row (kind; x, y, z)
+// record of row g = (kind; x, y, z)
 template <int P, typename T>
-__host__ __device__ __forceinline__ const T* rec3(const LevelTab3<T>& L, int kind, int x, int y, int z) {
+__host__ __device__ __forceinline__ const T* rec3(const LevelTab3<T>& L, int kind, int x, int y, int z, int g) {
   using R = Rec3<P>;
+  if (L.srow) return L.srow + (size_t)g * R::RU;
   const int lastp = L.n + P - 1, lastq = L.n + P - 2;
   int cx = cls1d<P>(x, kind == 0 ? lastp : lastq);
   int cy = cls1d<P>(y, kind == 1 ? lastp : lastq);
@@ -113,7 +115,7 @@ __host__ __device__ __forceinline__ T row3(const LevelTab3<T>& L, const T* __res
   using R = Rec3<P>;
   int kind, x, y, z;
   decode3(L, g, kind, x, y, z);
-  const T* rc = rec3<P>(L, kind, x, y, z);
+  const T* rc = rec3<P>(L, kind, x, y, z, g);
   const bool vel = kind < 3;
   // box 0: own component (velocity rows) or u_x (pressure rows)
   T acc = box3<P, 2 * P + 1>(L, rc, U, vel ? kind : 0, vel ? kind : 0, vel ? -P : -(P - 1), x, y, z);
@@ -195,7 +197,8 @@ template <int P, int S, typename T>
 __global__ void __launch_bounds__(S) k_mult_rows3(LevelTab3<T> L, T* __restrict__ U, const T* __restrict__ F,
                                                   const int* __restrict__ slot_g, const int* __restrict__ slot_c,
                                                   const unsigned* __restrict__ slot_kb,
-                                                  const T* __restrict__ cinv, int maxl, int first_slot) {
+                                                  const T* __restrict__ cinv, const long long* __restrict__ cinv_off,
+                                                  int first_slot) {
   __shared__ T r[S];
   const int s = first_slot + blockIdx.x * S + threadIdx.x;
   const int g = slot_g[s];
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(S) k_mult_rows3(LevelTab3<T> L, T* __restrict_
   if (g < 0) return;
   const unsigned kb = slot_kb[s];
   const int k = kb & 0x3ff, nl = (kb >> 10) & 0x3ff, base = kb >> 20;
-  U[g] += dot_n(cinv + ((size_t)slot_c[s] * maxl + k) * maxl, r + base, nl);
+  U[g] += dot_n(cinv + cinv_off[slot_c[s]] + (size_t)k * nl, r + base, nl);
 }
 
 // The same colour step with each row's three neighbour boxes evaluated by three different
@@ -218,7 +221,8 @@ template <int P, int S, typename T>
 __global__ void __launch_bounds__(3 * S) k_mult_rows3x(LevelTab3<T> L, T* __restrict__ U, const T* __restrict__ F,
                                                        const int* __restrict__ slot_g, const int* __restrict__ slot_c,
                                                        const unsigned* __restrict__ slot_kb,
-                                                       const T* __restrict__ cinv, int maxl, int first_slot) {
+                                                       const T* __restrict__ cinv, const long long* __restrict__ cinv_off,
+                                                       int first_slot) {
   using R = Rec3<P>;
   __shared__ T part[3][S];
   const int w = threadIdx.x / S, t = threadIdx.x - w * S;
@@ -228,7 +232,7 @@ __global__ void __launch_bounds__(3 * S) k_mult_rows3x(LevelTab3<T> L, T* __rest
   if (g >= 0) {
     int kind, x, y, z;
     decode3(L, g, kind, x, y, z);
-    const T* rc = rec3<P>(L, kind, x, y, z);
+    const T* rc = rec3<P>(L, kind, x, y, z, g);
     const bool vel = kind < 3;
     if (w == 0) {
       acc = F[g] - box3<P, 2 * P + 1>(L, rc, U, vel ? kind : 0, vel ? kind : 0, vel ? -P : -(P - 1), x, y, z);
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(3 * S) k_mult_rows3x(LevelTab3<T> L, T* __rest
   if (w != 0 || g < 0) return;
   const unsigned kb = slot_kb[s];
   const int k = kb & 0x3ff, nl = (kb >> 10) & 0x3ff, base = kb >> 20;
-  U[g] += dot_n(cinv + ((size_t)slot_c[s] * maxl + k) * maxl, &part[0][0] + base, nl);
+  U[g] += dot_n(cinv + cinv_off[slot_c[s]] + (size_t)k * nl, &part[0][0] + base, nl);
 }
 
 // block and local (x, y, z) of entry g (not lambda) on a level
@@ -355,6 +359,7 @@ struct Cluster3Level {
   LevelTab3<T> L;
   Xfer<T> tp, tq;                   // transfer from the level below into this one (l >= 1)
   const T* cinv;                    // cinv_all of the level
+  const long long* cinv_off;
   const int *slot_g, *slot_c, *colour_blk;
   const unsigned* slot_kb;
   int n_colours, maxl, row_slots;
@@ -401,7 +406,7 @@ __global__ void __launch_bounds__(1024) k_cluster3(Cluster3Desc<T> D, const T* _
           if (g >= 0) {
             int kind, x, y, z;
             decode3(V.L, g, kind, x, y, z);
-            const T* rc = rec3<P>(V.L, kind, x, y, z);
+            const T* rc = rec3<P>(V.L, kind, x, y, z, g);
             const bool vel = kind < 3;
             if (w == 0)
               acc = F[g] - box3<P, 2 * P + 1>(V.L, rc, U, vel ? kind : 0, vel ? kind : 0, vel ? -P : -(P - 1), x, y, z);
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(1024) k_cluster3(Cluster3Desc<T> D, const T* _
           if (w == 0 && g >= 0) {
             const unsigned kb = V.slot_kb[s];
             const int k = kb & 0x3ff, nl = (kb >> 10) & 0x3ff, base = kb >> 20;
-            U[g] += dot_n(V.cinv + ((size_t)V.slot_c[s] * V.maxl + k) * V.maxl, part3 + base, nl);
+            U[g] += dot_n(V.cinv + V.cinv_off[V.slot_c[s]] + (size_t)k * nl, part3 + base, nl);
           }
           __syncthreads();
         } else {
@@ -430,7 +435,7 @@ __global__ void __launch_bounds__(1024) k_cluster3(Cluster3Desc<T> D, const T* _
           if (g >= 0) {
             const unsigned kb = V.slot_kb[s];
             const int k = kb & 0x3ff, nl = (kb >> 10) & 0x3ff, base = kb >> 20;
-            U[g] += dot_n(V.cinv + ((size_t)V.slot_c[s] * V.maxl + k) * V.maxl, part3 + base, nl);
+            U[g] += dot_n(V.cinv + V.cinv_off[V.slot_c[s]] + (size_t)k * nl, part3 + base, nl);
           }
           __syncthreads();
         }

@@ -606,12 +606,20 @@ void build_row_slots(PatchTables& pt) {
   pt.row_slots = maxl <= 256 ? 256 : (maxl <= 1024 ? 1024 : 0);
   const int S = pt.row_slots;
   if (!S) return;
-  pt.cinv_all.assign((size_t)(pt.n_cls + pt.n_cls8) * maxl * maxl, 0.0);
-  std::copy(pt.cinv.begin(), pt.cinv.begin() + (size_t)pt.n_cls * maxl * maxl, pt.cinv_all.begin());
+  // classes packed nl x nl: general classes first (their nl from nloc), then the 8-DOF ones
+  pt.cinv_off.assign(pt.n_cls + pt.n_cls8 + 1, 0);
+  for (int c = 0; c < pt.n_cls; ++c) pt.cinv_off[c + 1] = pt.cinv_off[c] + (long long)pt.nloc[c] * pt.nloc[c];
+  for (int c = 0; c < pt.n_cls8; ++c) pt.cinv_off[pt.n_cls + c + 1] = pt.cinv_off[pt.n_cls + c] + 64;
+  pt.cinv_all.assign((size_t)pt.cinv_off.back(), 0.0);
+  for (int c = 0; c < pt.n_cls; ++c) {
+    const int nl = pt.nloc[c];
+    for (int r = 0; r < nl; ++r)
+      for (int t = 0; t < nl; ++t)
+        pt.cinv_all[pt.cinv_off[c] + (size_t)r * nl + t] = pt.cinv[((size_t)c * maxl + r) * maxl + t];
+  }
   for (int c = 0; c < pt.n_cls8; ++c)
-    for (int r = 0; r < 8; ++r)
-      for (int t = 0; t < 8; ++t)
-        pt.cinv_all[((size_t)(pt.n_cls + c) * maxl + r) * maxl + t] = pt.cinv8[(size_t)c * 64 + r * 8 + t];
+    std::copy(pt.cinv8.begin() + (size_t)c * 64, pt.cinv8.begin() + (size_t)(c + 1) * 64,
+              pt.cinv_all.begin() + pt.cinv_off[pt.n_cls + c]);
   pt.slot_g.clear(); pt.slot_c.clear(); pt.slot_kb.clear();
   pt.colour_blk.assign(pt.n_colours + 1, 0);
   auto pad_block = [&]() {

@@ -178,7 +178,9 @@ int pos_class3(int a, int lo, int hi, int p) {
   return 2 * T;
 }
 
-int build_patches3(int p, const Level1D& L, const Sizes3& s, PatchTables& pt, std::string& err) {
+template <typename Entry>
+int build_patches3(int p, const Level1D& L, const Sizes3& s, PatchTables& pt, std::string& err, Entry kent,
+                   bool per_patch) {
   const int n = s.n, q = p - 1;
   auto sup = [&](int i, int d) { return std::make_pair(std::max(0, i - d), std::min(n - 1, i)); };
   auto inside = [](std::pair<int, int> a, std::pair<int, int> box) { return box.first <= a.first && a.second <= box.second; };
@@ -220,8 +222,9 @@ int build_patches3(int p, const Level1D& L, const Sizes3& s, PatchTables& pt, st
           collect(0); collect(1); collect(2);
           P_.nv = (int)P_.dofs.size();
           collect(3);
-          P_.key = std::make_tuple(fam, pos_class3(i, lo[0], hi[0], p), pos_class3(j, lo[1], hi[1], p),
-                                   pos_class3(k, lo[2], hi[2], p));
+          P_.key = per_patch ? std::make_tuple(fam, i, j, k)
+                             : std::make_tuple(fam, pos_class3(i, lo[0], hi[0], p), pos_class3(j, lo[1], hi[1], p),
+                                               pos_class3(k, lo[2], hi[2], p));
           all.push_back(std::move(P_));
         }
   }
@@ -257,7 +260,7 @@ int build_patches3(int p, const Level1D& L, const Sizes3& s, PatchTables& pt, st
     int nl = (int)P_.dofs.size(), nb = nl + 1;
     std::vector<double> Kb((size_t)nb * nb, 0.0);
     for (int r = 0; r < nl; ++r)
-      for (int t = 0; t < nl; ++t) Kb[(size_t)r * nb + t] = k_entry3(L, s, P_.dofs[r], P_.dofs[t]);
+      for (int t = 0; t < nl; ++t) Kb[(size_t)r * nb + t] = kent(P_.dofs[r], P_.dofs[t]);
     for (int r = P_.nv; r < nl; ++r) {
       Dof3 d = decode3(s, P_.dofs[r]);
       double m = L.mq[d.i[0]] * L.mq[d.i[1]] * L.mq[d.i[2]];
@@ -290,17 +293,259 @@ int build_patches3(int p, const Level1D& L, const Sizes3& s, PatchTables& pt, st
   for (int t = 0; t < nth; ++t) th.emplace_back(work);
   for (auto& t : th) t.join();
   if (bad) { err = "singular local patch matrix"; return IGAMG_ESINGULAR; }
-  for (int c = 0; c < pt.n_cls8; ++c) {
-    std::vector<double> inv;
-    if (!local_inverse(all[rep8[c]], inv)) { err = "singular local patch matrix"; return IGAMG_ESINGULAR; }
-    for (int r = 0; r < 8; ++r)
-      for (int t = 0; t < 8; ++t) pt.cinv8[(size_t)c * 64 + r * 8 + t] = inv[(size_t)r * 9 + t];
-  }
+  std::atomic<int> next8{0};
+  auto work8 = [&]() {
+    for (;;) {
+      int c = next8.fetch_add(1);
+      if (c >= pt.n_cls8) break;
+      std::vector<double> inv;
+      if (!local_inverse(all[rep8[c]], inv)) { bad = 1; continue; }
+      for (int r = 0; r < 8; ++r)
+        for (int t = 0; t < 8; ++t) pt.cinv8[(size_t)c * 64 + r * 8 + t] = inv[(size_t)r * 9 + t];
+    }
+  };
+  th.clear();
+  for (int t = 0; t < nth; ++t) th.emplace_back(work8);
+  for (auto& t : th) t.join();
+  if (bad) { err = "singular local patch matrix"; return IGAMG_ESINGULAR; }
   build_row_slots(pt);
+  if (per_patch) { std::vector<double>().swap(pt.cinv); std::vector<double>().swap(pt.cinv8); }
   return IGAMG_OK;
 }
 
+// ---- generalized Oseen (Sec. 3.1): the advection block (beta . grad u, v), componentwise ----
+// Stored per velocity row as box 0 of the row record (B0 entries: long axis = the component's
+// own axis, offsets -p..p; -q..q across).  Position of column j in the box of row i:
+int adv_pos(int p, int c, const int* i, const int* j) {
+  const int q = p - 1, W = 2 * q + 1;
+  const int o1 = (c + 1) % 3, o2 = (c + 2) % 3;
+  int a = j[c] - i[c] + p, e1 = j[o1] - i[o1] + q, e2 = j[o2] - i[o2] + q;
+  if (a < 0 || a > 2 * p || e1 < 0 || e1 >= W || e2 < 0 || e2 >= W) return -1;
+  return (a * W + e1) * W + e2;
+}
+
+// Fine level: element-by-element Gauss quadrature ((p+2)^3 points) of int v (beta . grad u)
+// for every component, beta sampled at the quadrature points (3, nG, nG, nG).  Elements are
+// processed in z-slabs coloured by ez mod (p+1), so slabs of one colour touch disjoint rows.
+void add_advection3(int p, const Sizes3& s, const double* beta, std::vector<double>& adv) {
+  const int q = p - 1, n = s.n, G = p + 2, nG = n * G;
+  const int W = 2 * q + 1, B0 = (2 * p + 1) * W * W;
+  adv.assign((size_t)s.n_u * B0, 0.0);
+  auto tp = knots(p, n), tq = knots(q, n);
+  std::vector<double> gx, gw;
+  gauss01(G, gx, gw);
+  // per element and degree: values and derivatives at the G points, (d+1) x G
+  auto table = [&](int d, std::vector<double>& V, std::vector<double>& D) {
+    const auto& t = d == p ? tp : tq;
+    V.assign((size_t)n * (d + 1) * G, 0.0);
+    D.assign((size_t)n * (d + 1) * G, 0.0);
+    for (int e = 0; e < n; ++e)
+      for (int g = 0; g < G; ++g) {
+        double x = (e + gx[g]) / n, N[8], dN[8];
+        span_values(t, d, e + d, x, N);
+        span_derivs(t, d, e + d, x, dN);
+        for (int k = 0; k <= d; ++k) {
+          V[((size_t)e * (d + 1) + k) * G + g] = N[k];
+          D[((size_t)e * (d + 1) + k) * G + g] = dN[k];
+        }
+      }
+  };
+  std::vector<double> Vp, Dp, Vq, Dq;
+  table(p, Vp, Dp);
+  table(q, Vq, Dq);
+  const int nth = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+  for (int colour = 0; colour <= p; ++colour) {
+    std::atomic<int> next{0};
+    auto work = [&]() {
+      std::vector<double> A, Bm, M;
+      for (;;) {
+        int slab = colour + (p + 1) * next.fetch_add(1);
+        if (slab >= n) break;
+        const int ez = slab;
+        for (int ey = 0; ey < n; ++ey)
+          for (int ex = 0; ex < n; ++ex) {
+            const int e[3] = {ex, ey, ez};
+            for (int c = 0; c < 3; ++c) {
+              int d[3];
+              const double *V[3], *D[3];
+              for (int ax = 0; ax < 3; ++ax) {
+                d[ax] = ax == c ? p : q;
+                V[ax] = (ax == c ? Vp.data() : Vq.data()) + (size_t)e[ax] * (d[ax] + 1) * G;
+                D[ax] = (ax == c ? Dp.data() : Dq.data()) + (size_t)e[ax] * (d[ax] + 1) * G;
+              }
+              const int nl = (d[0] + 1) * (d[1] + 1) * (d[2] + 1), ng = G * G * G;
+              A.assign((size_t)nl * ng, 0.0);
+              Bm.assign((size_t)nl * ng, 0.0);
+              for (int kz = 0; kz <= d[2]; ++kz)
+                for (int ky = 0; ky <= d[1]; ++ky)
+                  for (int kx = 0; kx <= d[0]; ++kx) {
+                    const int a = (kz * (d[1] + 1) + ky) * (d[0] + 1) + kx;
+                    for (int gz = 0; gz < G; ++gz)
+                      for (int gy = 0; gy < G; ++gy)
+                        for (int gxx = 0; gxx < G; ++gxx) {
+                          const int g = (gz * G + gy) * G + gxx;
+                          const double w = gw[gz] * gw[gy] * gw[gxx] / ((double)n * n * n);
+                          const double vx = V[0][kx * G + gxx], vy = V[1][ky * G + gy], vz = V[2][kz * G + gz];
+                          const size_t qi = ((size_t)(ez * G + gz) * nG + (ey * G + gy)) * nG + (ex * G + gxx);
+                          const double b0 = beta[qi], b1 = beta[(size_t)nG * nG * nG + qi],
+                                       b2 = beta[(size_t)2 * nG * nG * nG + qi];
+                          A[(size_t)a * ng + g] = w * vx * vy * vz;
+                          Bm[(size_t)a * ng + g] = b0 * D[0][kx * G + gxx] * vy * vz + b1 * vx * D[1][ky * G + gy] * vz +
+                                                   b2 * vx * vy * D[2][kz * G + gz];
+                        }
+                  }
+              for (int a = 0; a < nl; ++a) {
+                int ia[3] = {e[0] + a % (d[0] + 1), e[1] + (a / (d[0] + 1)) % (d[1] + 1), e[2] + a / ((d[0] + 1) * (d[1] + 1))};
+                long long gi = gid3(s, c, ia);
+                if (gi < 0) continue;
+                for (int b = 0; b < nl; ++b) {
+                  int ib[3] = {e[0] + b % (d[0] + 1), e[1] + (b / (d[0] + 1)) % (d[1] + 1), e[2] + b / ((d[0] + 1) * (d[1] + 1))};
+                  if (gid3(s, c, ib) < 0) continue;
+                  double v = 0.0;
+                  for (int g = 0; g < ng; ++g) v += A[(size_t)a * ng + g] * Bm[(size_t)b * ng + g];
+                  int pos = adv_pos(p, c, ia, ib);
+                  if (pos >= 0) adv[(size_t)gi * B0 + pos] += v;
+                }
+              }
+            }
+          }
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t) th.emplace_back(work);
+    for (auto& t : th) t.join();
+  }
+}
+
+// Coarse level: the advection block of R K P (Sec. 5.1), C_c = P_c^T A_c P_c per component,
+// with P_c the tensor product of the 1D knot-insertion bands (degree p along c, p-1 across).
+// Rows of the coarse level are independent: spread over host threads.
+void galerkin_adv3(int p, const Sizes3& sf, const Sizes3& sc, const std::vector<double>& advf,
+                   const Transfer1D& tp, const Transfer1D& tq, std::vector<double>& advc) {
+  const int q = p - 1, W = 2 * q + 1, B0 = (2 * p + 1) * W * W;
+  constexpr int WP = Transfer1D::WP, WR = Transfer1D::WR;
+  advc.assign((size_t)sc.n_u * B0, 0.0);
+  const int nth = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+  std::atomic<long long> next{0};
+  auto work = [&]() {
+    for (;;) {
+      long long i0 = next.fetch_add(256);
+      if (i0 >= sc.n_u) break;
+      for (long long gi = i0; gi < std::min(sc.n_u, i0 + 256); ++gi) {
+        Dof3 ci = decode3(sc, gi);
+        const int c = ci.blk;
+        const Transfer1D* T[3];
+        for (int ax = 0; ax < 3; ++ax) T[ax] = ax == c ? &tp : &tq;
+        // local (view) index of coarse row along each axis: the p-axis view drops index 0
+        int li[3];
+        for (int ax = 0; ax < 3; ++ax) li[ax] = ci.i[ax] - (ax == c ? 1 : 0);
+        double* out = &advc[(size_t)gi * B0];
+        for (int rz = 0; rz < WR; ++rz)
+          for (int ry = 0; ry < WR; ++ry)
+            for (int rx = 0; rx < WR; ++rx) {
+              const int r[3] = {rx, ry, rz};
+              int fa[3];
+              double wa = 1.0;
+              bool ok = true;
+              for (int ax = 0; ax < 3 && ok; ++ax) {
+                int f = T[ax]->f0[li[ax]] + r[ax];
+                if (f >= T[ax]->nf) { ok = false; break; }
+                double w = T[ax]->rv[(size_t)li[ax] * WR + r[ax]];
+                if (w == 0.0) { ok = false; break; }
+                wa *= w;
+                fa[ax] = f + (ax == c ? 1 : 0);                 // full fine index
+              }
+              if (!ok) continue;
+              long long ga = gid3(sf, c, fa);
+              if (ga < 0) continue;
+              const double* arow = &advf[(size_t)ga * B0];
+              for (int a = 0; a <= 2 * p; ++a)
+                for (int e1 = 0; e1 < W; ++e1)
+                  for (int e2 = 0; e2 < W; ++e2) {
+                    const double v = arow[(a * W + e1) * W + e2];
+                    if (v == 0.0) continue;
+                    const int o1 = (c + 1) % 3, o2 = (c + 2) % 3;
+                    int fb[3];
+                    fb[c] = fa[c] - p + a; fb[o1] = fa[o1] - q + e1; fb[o2] = fa[o2] - q + e2;
+                    int lb[3];
+                    bool okb = true;
+                    for (int ax = 0; ax < 3; ++ax) {
+                      lb[ax] = fb[ax] - (ax == c ? 1 : 0);
+                      if (lb[ax] < 0 || lb[ax] >= T[ax]->nf) okb = false;
+                    }
+                    if (!okb) continue;
+                    for (int kz = 0; kz < WP; ++kz)
+                      for (int ky = 0; ky < WP; ++ky)
+                        for (int kx = 0; kx < WP; ++kx) {
+                          const int k[3] = {kx, ky, kz};
+                          int cj[3];
+                          double wb = v * wa;
+                          bool okj = true;
+                          for (int ax = 0; ax < 3 && okj; ++ax) {
+                            int cc = T[ax]->c0[lb[ax]] + k[ax];
+                            double w = T[ax]->pv[(size_t)lb[ax] * WP + k[ax]];
+                            if (cc >= T[ax]->nc || w == 0.0) { okj = false; break; }
+                            wb *= w;
+                            cj[ax] = cc + (ax == c ? 1 : 0);
+                          }
+                          if (!okj) continue;
+                          int pos = adv_pos(p, c, ci.i, cj);
+                          if (pos >= 0) out[pos] += wb;
+                        }
+                  }
+            }
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < nth; ++t) th.emplace_back(work);
+  for (auto& t : th) t.join();
+}
+
+// Per-row records of a level: class record of the row plus the advection box (velocity rows).
+void rows_with_advection3(int p, const LevelHost3& lv, std::vector<double>& rows) {
+  const auto& s = lv.sz;
+  const auto& st = lv.st;
+  const int q = p - 1, RU = st.RU, W = 2 * q + 1, B0 = (2 * p + 1) * W * W;
+  rows.assign((size_t)(s.n_total - 1) * RU, 0.0);
+  const int lastp = s.n + p - 1, lastq = s.n + q - 1;
+  for (long long g = 0; g < s.n_total - 1; ++g) {
+    Dof3 d = decode3(s, g);
+    int last[3];
+    for (int x = 0; x < 3; ++x) last[x] = (d.blk < 3 && x == d.blk) ? lastp : lastq;
+    int cl = (cls1(d.i[2], last[2], st.T) * st.NC + cls1(d.i[1], last[1], st.T)) * st.NC + cls1(d.i[0], last[0], st.T);
+    const double* r = &st.rec[d.blk][(size_t)st.cmap[d.blk][cl] * RU];
+    double* o = &rows[(size_t)g * RU];
+    std::copy(r, r + RU, o);
+    if (d.blk < 3)
+      for (int k = 0; k < B0; ++k) o[k] += lv.adv[(size_t)g * B0 + k];
+  }
+}
+
 }  // namespace
+
+// entry (g1, g2) from the per-row records (generalized Oseen)
+double k_entry3_rows(const LevelHost3& lv, int p, long long g1, long long g2) {
+  const auto& s = lv.sz;
+  const int q = p - 1, W = 2 * q + 1, RU = lv.st.RU;
+  Dof3 a = decode3(s, g1), b = decode3(s, g2);
+  if (a.blk == 4) {
+    if (b.blk != 3) return 0.0;
+    return lv.rows[(size_t)g2 * RU + RU - 1];
+  }
+  const double* r = &lv.rows[(size_t)g1 * RU];
+  if (b.blk == 4) return a.blk == 3 ? r[RU - 1] : 0.0;
+  const int nbox = a.blk < 3 ? 2 : 3;
+  for (int k = 0; k < nbox; ++k) {
+    Box3 bx = box_of(p, a.blk, k);
+    if (bx.blk != b.blk) continue;
+    int c = bx.axis, o1 = (c + 1) % 3, o2 = (c + 2) % 3;
+    int da = b.i[c] - a.i[c] - bx.org, e1 = b.i[o1] - a.i[o1] + q, e2 = b.i[o2] - a.i[o2] + q;
+    if (da < 0 || da >= bx.len || e1 < 0 || e1 >= W || e2 < 0 || e2 >= W) return 0.0;
+    return r[box_start(p, k) + (da * W + e1) * W + e2];
+  }
+  return 0.0;
+}
 
 double k_entry3_records(const LevelHost3& lv, int p, long long g1, long long g2) {
   const auto& s = lv.sz;
@@ -343,7 +588,15 @@ int build_level_only3(const igamg_problem& pr, HierarchyHost3& H, std::string& e
   return IGAMG_OK;
 }
 
-int build_hierarchy3(const igamg_problem& pr, HierarchyHost3& H, std::string& err) {
+namespace {
+int build3(const igamg_problem& pr, HierarchyHost3& H, std::string& err, bool full);
+}
+
+int build_hierarchy3(const igamg_problem& pr, HierarchyHost3& H, std::string& err) { return build3(pr, H, err, true); }
+int build_operators3(const igamg_problem& pr, HierarchyHost3& H, std::string& err) { return build3(pr, H, err, false); }
+
+namespace {
+int build3(const igamg_problem& pr, HierarchyHost3& H, std::string& err, bool full) {
   const int p = pr.p, L = pr.n_levels, nf = pr.n_fine;
   H.p = p; H.L = L; H.n_fine = nf; H.sigma = pr.sigma; H.nu = pr.nu;
   H.cpen = pr.c_penalty > 0 ? pr.c_penalty : 4.0 * (p - 1);
@@ -376,9 +629,20 @@ int build_hierarchy3(const igamg_problem& pr, HierarchyHost3& H, std::string& er
     auto Pq = prolong_dense(p - 1, nc, a, b);
     if (Pq.empty() || !make_transfer(Pq, a, b, 0, H.tq[l])) { err = "degree-(p-1) prolongation"; return IGAMG_ESINGULAR; }
   }
+  const bool general = pr.beta_qp != nullptr;     // generalized Oseen: per-row records
+  if (general) {
+    add_advection3(p, H.lev[L - 1].sz, pr.beta_qp, H.lev[L - 1].adv);
+    for (int l = L - 2; l >= 0; --l)
+      galerkin_adv3(p, H.lev[l + 1].sz, H.lev[l].sz, H.lev[l + 1].adv, H.tp_free[l + 1], H.tq[l + 1], H.lev[l].adv);
+    for (int l = 0; l < L; ++l) rows_with_advection3(p, H.lev[l], H.lev[l].rows);
+  }
+  if (!full) return IGAMG_OK;
   for (int l = 1; l < L; ++l) {
     auto& lv = H.lev[l];
-    int rc = build_patches3(p, lv.f, lv.sz, lv.pt, err);
+    int rc = general ? build_patches3(p, lv.f, lv.sz, lv.pt, err,
+                                      [&](long long a, long long b) { return k_entry3_rows(lv, p, a, b); }, true)
+                     : build_patches3(p, lv.f, lv.sz, lv.pt, err,
+                                      [&](long long a, long long b) { return k_entry3(lv.f, lv.sz, a, b); }, false);
     if (rc) return rc;
   }
   {
@@ -386,7 +650,8 @@ int build_hierarchy3(const igamg_problem& pr, HierarchyHost3& H, std::string& er
     int nd = (int)lv.sz.n_total;
     std::vector<double> K((size_t)nd * nd);
     for (int i = 0; i < nd; ++i)
-      for (int j = 0; j < nd; ++j) K[(size_t)i * nd + j] = k_entry3(lv.f, lv.sz, i, j);
+      for (int j = 0; j < nd; ++j)
+        K[(size_t)i * nd + j] = general ? k_entry3_rows(lv, p, i, j) : k_entry3(lv.f, lv.sz, i, j);
     if (!invert(K, nd, H.coarse_inv)) { err = "singular coarsest matrix"; return IGAMG_ESINGULAR; }
     H.ndof0 = nd;
   }
@@ -412,18 +677,19 @@ int build_hierarchy3(const igamg_problem& pr, HierarchyHost3& H, std::string& er
   }
   return IGAMG_OK;
 }
+}  // namespace
 
 }  // namespace igamg
 
 // ---- host-only inspection (3D): the same entry points dispatch here for dim = 3 --------
 namespace {
-int host_build3(const igamg_problem* prob, int level, igamg::HierarchyHost3& H) {
+int host_build3(const igamg_problem* prob, int level, igamg::HierarchyHost3& H, bool full = true) {
   if (!(prob->sigma > 0) || !(prob->nu > 0)) return IGAMG_EINVAL;
   if (prob->n_levels < 1 || prob->n_fine < 1 || prob->n_fine % (1 << (prob->n_levels - 1))) return IGAMG_EINVAL;
   if (level < 0 || level >= prob->n_levels) return IGAMG_EINVAL;
   if (igamg::sizes3(prob->p, prob->n_fine >> (prob->n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
   std::string err;
-  return igamg::build_hierarchy3(*prob, H, err);
+  return full ? igamg::build_hierarchy3(*prob, H, err) : igamg::build_operators3(*prob, H, err);
 }
 }  // namespace
 
@@ -431,7 +697,7 @@ namespace igamg {
 
 int host_level_matrix3(const igamg_problem* prob, int level, double* K, size_t cap, long long* n_out, bool records) {
   HierarchyHost3 H;
-  int rc = host_build3(prob, level, H);
+  int rc = host_build3(prob, level, H, false);
   if (rc) return rc;
   const auto& lv = H.lev[level];
   long long n = lv.sz.n_total;
@@ -440,7 +706,8 @@ int host_level_matrix3(const igamg_problem* prob, int level, double* K, size_t c
   if (cap < (size_t)(n * n)) return IGAMG_EINVAL;
   for (long long i = 0; i < n; ++i)
     for (long long j = 0; j < n; ++j)
-      K[i * n + j] = records ? k_entry3_records(lv, prob->p, i, j) : k_entry3(lv.f, lv.sz, i, j);
+      K[i * n + j] = !lv.rows.empty() ? k_entry3_rows(lv, prob->p, i, j)
+                     : (records ? k_entry3_records(lv, prob->p, i, j) : k_entry3(lv.f, lv.sz, i, j));
   return IGAMG_OK;
 }
 

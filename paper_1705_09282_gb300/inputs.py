@@ -230,3 +230,29 @@ def random_divfree_guess_3d(p, n, seed):
     psi = 2.0 * rng.uniform(3 * (n + p - 1) * (n + p - 2) ** 2) - 1.0
     pr = 2.0 * rng.uniform((n + p - 1) ** 3) - 1.0
     return psi, pr
+
+
+def oseen_advection_3d(p, n, max_speed=1.0):
+    """beta = the cube's manufactured velocity (divergence-free, zero on the boundary),
+    scaled so that max |beta| = max_speed; layout (3, nG, nG, nG) [component, z, y, x]."""
+    x = quad_points_1d(p, n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    terms = _poly_terms_3d()
+    b = np.stack([_eval_terms(t, X, Y, Z) for t in terms])
+    s = np.linspace(0, 1, 81)
+    S3 = np.meshgrid(s, s, s, indexing="ij")
+    vmax = np.sqrt(sum(_eval_terms(t, S3[2], S3[1], S3[0]) ** 2 for t in terms)).max()
+    return np.ascontiguousarray(b * (max_speed / vmax))
+
+
+def oseen_forcing_3d(p, n, sigma, nu, beta):
+    """f = sigma u - nu Lap u + beta . grad u + grad p for the cube's manufactured solution,
+    beta given at the quadrature points (3, nG, nG, nG)."""
+    x = quad_points_1d(p, n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    f = manufactured_forcing_3d(p, n, sigma, nu)
+    for c, terms in enumerate(_poly_terms_3d()):
+        for coef, fx, fy, fz in terms:
+            f[c] += coef * (beta[0] * fx.deriv()(X) * fy(Y) * fz(Z) + beta[1] * fx(X) * fy.deriv()(Y) * fz(Z)
+                            + beta[2] * fx(X) * fy(Y) * fz.deriv()(Z))
+    return np.ascontiguousarray(f)

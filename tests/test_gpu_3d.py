@@ -249,3 +249,35 @@ def test_cluster_coarse_levels_same_iterates(p, n, L, depth, blocks, monkeypatch
     assert rep["converged"] and rep["div_inf"] <= 1e-11 * np.abs(Uo).max()
     H.solve(Uo, F, 1e-12, 80)
     assert _rel(_np(U32), Uo) < 1e-7
+
+
+@pytest.mark.parametrize("vmax,sigma,nu", [(0.5, 1.0, 0.01), (1.0, 10.0, 0.01), (1.0, 1.0, 1.0)])
+def test_oseen_3d_iterates_and_solve(vmax, sigma, nu):
+    # 3D generalized Oseen (per-row operator records, Galerkin coarse levels, per-patch
+    # inverses): V-cycle iterates and cycle counts equal to the oracle's; divergence-free
+    from paper_1705_09282_gb300 import _lib
+    p, n, L = 2, 8, 3
+    beta = inputs.oseen_advection_3d(p, n, vmax)
+    S = _solver(p, n, L, sigma, nu, beta=beta)
+    H = o3.Hierarchy3D(p, n, L, sigma, nu, beta=beta)
+    f = inputs.oseen_forcing_3d(p, n, sigma, nu, beta)
+    F = H.fine.load_vector(f)
+    assert _rel(_np(S.load_vector(_t(f))), F) < RTOL_OP
+    Ug, Fg = S.empty(), _t(F)
+    Uo = np.zeros_like(F)
+    for k in range(2):
+        S.vcycle(Ug, Fg)
+        H.vcycle(Uo, F)
+        assert _rel(_np(Ug), Uo) < RTOL_IT, k
+    Uo = np.zeros_like(F)
+    ko, hist = H.solve(Uo, F, 1e-8, 60)
+    Ug = S.empty()
+    rep = S.solve(Ug, Fg, rtol=1e-8, max_cycles=60)
+    assert rep["converged"] and rep["cycles"] == ko
+    assert _rel(_np(Ug), Uo) < RTOL_IT
+    assert rep["div_inf"] <= 1e-11 * np.abs(Uo).max()
+    S32 = _solver(p, n, L, sigma, nu, beta=beta, precision=_lib.IGAMG_FP32_IR)
+    U32 = S32.empty()
+    r32 = S32.solve(U32, Fg, rtol=1e-8, max_cycles=60)
+    assert r32["converged"] and r32["div_inf"] <= 1e-11 * np.abs(Uo).max()
+    assert _rel(_np(U32), Uo) < 1e-6

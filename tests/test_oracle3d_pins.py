@@ -300,3 +300,43 @@ def test_paper_table4_cycle_counts_loosely():
             assert k <= bound, (nl, sigma, k)
             if nl == 1:
                 assert k == tab[1][2]
+
+
+def test_oseen_manufactured_convergence_3d():
+    # generalized Oseen with beta = the (scaled) manufactured velocity: rate ~ h^2 for p = 2,
+    # divergence-free discrete solution, and a non-symmetric operator
+    p, sigma, nu = 2, 1.0, 0.1
+    errs = []
+    for n in (4, 8):
+        beta = inputs.oseen_advection_3d(p, n, 1.0)
+        S = o3.Stokes3D(p, n, sigma, nu, beta=beta)
+        U = spla.spsolve(S.K.tocsc(), S.load_vector(inputs.oseen_forcing_3d(p, n, sigma, nu, beta)))
+        x, w = o3.quad_points_1d(p, n)
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        uh = _eval(S, U, np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1))
+        ue = inputs.manufactured_solution_3d(p, n)
+        W = np.einsum("a,b,c->abc", w, w, w).ravel()
+        errs.append(np.sqrt(sum(np.sum(W * (uh[c] - ue[c].ravel()) ** 2) for c in range(3))))
+        assert S.div_inf(U) < 1e-10
+    rate = np.log2(errs[0] / errs[1])
+    assert 1.5 <= rate <= 3.0, (rate, errs)
+    K = S.K.toarray()
+    assert np.abs(K - K.T).max() > 1e-6 * np.abs(K).max()
+
+
+def test_oseen_forcing_matches_closed_form_derivatives():
+    # beta . grad u from the polynomial terms against central differences
+    p, n, h = 2, 1, 1e-4
+    beta = inputs.oseen_advection_3d(p, n, 1.0)
+    f0 = inputs.manufactured_forcing_3d(p, n, 1.0, 1.0)
+    f1 = inputs.oseen_forcing_3d(p, n, 1.0, 1.0, beta)
+    x = inputs.quad_points_1d(p, n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    u = lambda X, Y, Z: [inputs._eval_terms(t, X, Y, Z) for t in inputs._poly_terms_3d()]
+    for c in range(3):
+        grad = [(u(*(v + h * e for v, e in zip((X, Y, Z), d)))[c] - u(*(v - h * e for v, e in zip((X, Y, Z), d)))[c])
+                / (2 * h) for d in np.eye(3)]
+        adv = beta[0] * grad[0] + beta[1] * grad[1] + beta[2] * grad[2]
+        assert np.allclose(f1[c] - f0[c], adv, atol=1e-7)
+    # beta is divergence-free, zero on the boundary, max |beta| = 1
+    assert np.sqrt((beta ** 2).sum(axis=0)).max() <= 1.0 + 1e-12
