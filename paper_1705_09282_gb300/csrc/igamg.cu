@@ -238,6 +238,18 @@ int launch_check() {
   return IGAMG_OK;
 }
 
+// Threads per block of the colour kernel: 128 (default; a colour's blocks then spread evenly
+// over the 152 SMs: ~455 blocks of 16 patches on a 256^2 level instead of ~228 of 32), or
+// IGAMG_COLOUR_BLOCK = 32 .. 256.
+int colour_block() {
+  static const int tpb = [] {
+    const char* e = std::getenv("IGAMG_COLOUR_BLOCK");
+    int v = e ? std::atoi(e) : 128;
+    return (v >= 32 && v <= 256 && v % 32 == 0) ? v : 128;   // launch bounds: 256
+  }();
+  return tpb;
+}
+
 // Colour kernel form: one lane per row (k_mult_colour, default) or split rows
 // (k_mult_colour_split, IGAMG_SPLIT_COLOUR=1; measured 10 % slower on the 256^2 sweep).
 // Per-row operator records (Oseen) always use the former.
@@ -288,16 +300,18 @@ int do_smooth(igamg_handle* h, int l, T* U, const T* F, cudaStream_t s) {
         k_mult_colour_split<3, T><<<nb, 512, shm16, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
     }
   } else if (h->prob.smoother == IGAMG_MULT) {
+    const int tpb = colour_block(), wpb = tpb / 32;
+    const size_t shmc = (size_t)wpb * lc.maxl * sizeof(T);
     for (int c = 0; c < lc.n_colours; ++c) {
       int first = lc.colour_off[c], count = lc.colour_off[c + 1] - first;
       if (count == 0) continue;
       int n8 = lc.n8[c], ngen = count - n8;
-      int nb8 = (n8 + 31) / 32, nbg = (ngen + 7) / 8;
+      int nb8 = (n8 + 4 * wpb - 1) / (4 * wpb), nbg = (ngen + wpb - 1) / wpb;
       unsigned nb = (unsigned)(nb8 + nbg);
       if (h->prob.p == 2)
-        k_mult_colour<2, T><<<nb, kBlock, shm, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+        k_mult_colour<2, T><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
       else
-        k_mult_colour<3, T><<<nb, kBlock, shm, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+        k_mult_colour<3, T><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
     }
   } else {
     int rc = do_residual<T>(h, l, U, F, tl.R, nullptr, s);

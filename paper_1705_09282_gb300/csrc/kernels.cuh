@@ -266,7 +266,9 @@ __device__ __forceinline__ T prolong_elem(const LevelTab<T>& Lf, const LevelTab<
 }
 
 // One colour of the multiplicative Schwarz sweep (eq. MSM).  Blocks [0, nb8): four 8-DOF
-// patches per warp.  Blocks [nb8, ...): one warp per larger (wall) patch.  Same-colour
+// patches per warp.  Blocks [nb8, ...): one warp per larger (wall) patch.  Any block size
+// that is a multiple of 32 (the launch picks 128 threads so that a colour's blocks spread
+// evenly over the SMs).  Same-colour
 // patches share no DOF and are not coupled by K, so they may be solved in any order.
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_mult_colour(LevelTab<T> L, T* __restrict__ U, const T* __restrict__ F,
@@ -274,14 +276,14 @@ __global__ void __launch_bounds__(256) k_mult_colour(LevelTab<T> L, T* __restric
                                                      const T* __restrict__ cinv, const T* __restrict__ cinv8,
                                                      const int* __restrict__ nloc,
                                                      int maxl, int first, int n8, int ngen, int nb8) {
-  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   if ((int)blockIdx.x < nb8) {
-    fast_patch_lane<P>(L, U, F, dofs, cls, cinv8, maxl, first, n8, (blockIdx.x * 8 + wib) * 4 + (lane >> 3), lane);
+    fast_patch_lane<P>(L, U, F, dofs, cls, cinv8, maxl, first, n8, (blockIdx.x * wpb + wib) * 4 + (lane >> 3), lane);
     return;
   }
   extern __shared__ unsigned char smem_raw[];
   T* sh = reinterpret_cast<T*>(smem_raw);
-  int w = ((int)blockIdx.x - nb8) * 8 + wib;
+  int w = ((int)blockIdx.x - nb8) * wpb + wib;
   if (w >= ngen) return;
   general_patch_warp<P>(L, U, F, dofs, cls, cinv, nloc, maxl, first + n8 + w, lane, sh + wib * maxl);
 }
