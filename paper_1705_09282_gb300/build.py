@@ -16,9 +16,11 @@ LIB = os.path.join(PKG, "libigamg.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-              "-I", INCLUDE, "-I", CSRC] + ARCH
-CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", CSRC]
+# -ffp-contract=off for host code: the host set-up rounds the same way on x86-64 and aarch64
+# (gcc contracts a*b+c into fused multiply-adds on aarch64 by default); device code keeps FMA
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC] + ARCH
+CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-pthread", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
 
 
 def _nvcc():

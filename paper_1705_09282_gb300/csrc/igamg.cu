@@ -977,7 +977,11 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
   h->prob = pr;
   h->stream = (cudaStream_t)cuda_stream;
   rc = build_hierarchy(pr, h->host, g_err);
-  if (rc) { delete h; return rc; }
+  if (rc) {
+    if (std::getenv("IGAMG_VERBOSE")) std::fprintf(stderr, "igamg: set-up failed (%d): %s\n", rc, g_err.c_str());
+    delete h;
+    return rc;
+  }
   auto fail = [&](int code) { igamg_destroy(h); return code; };
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(IGAMG_ECUDA);
   const int L = pr.n_levels, p = pr.p;

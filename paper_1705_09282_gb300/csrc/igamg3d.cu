@@ -285,7 +285,7 @@ bool split_rows(const Lev3Common& lc) {
     return e ? std::atoi(e) : -1;
   }();
   if (mode >= 0) return mode == 1;
-  return lc.colour_blk[lc.n_colours] < kSplitBelow * lc.n_colours;
+  return (long long)lc.colour_blk[lc.n_colours] * lc.row_slots < 256LL * kSplitBelow * lc.n_colours;
 }
 
 bool fp32_base3(const igamg_problem& pr) {
@@ -361,11 +361,13 @@ int do_smooth(igamg3d_handle* h, int l, T* U, const T* F, cudaStream_t s) {
   if ((row_parallel() || tl.L.srow) && lc.row_slots) {
     const int S = lc.row_slots;
     const int* sg = lc.slot_g; const int* sc = lc.slot_c; const unsigned* sk = lc.slot_kb;
-    if (S == 256 && split_rows(lc)) {
+    if (S <= 256 && split_rows(lc)) {
       for (int c = 0; c < lc.n_colours; ++c) {
         int b0 = lc.colour_blk[c], nb = lc.colour_blk[c + 1] - b0;
         if (nb == 0) continue;
-        if (h->prob.p == 2) k_mult_rows3x<2, 256, T><<<nb, 768, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
+        if (h->prob.p == 2 && S == 128) k_mult_rows3x<2, 128, T><<<nb, 384, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
+        else if (h->prob.p == 2) k_mult_rows3x<2, 256, T><<<nb, 768, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
+        else if (S == 128) k_mult_rows3x<3, 128, T><<<nb, 384, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
         else k_mult_rows3x<3, 256, T><<<nb, 768, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
       }
       return launch_check();
@@ -373,7 +375,9 @@ int do_smooth(igamg3d_handle* h, int l, T* U, const T* F, cudaStream_t s) {
     for (int c = 0; c < lc.n_colours; ++c) {
       int b0 = lc.colour_blk[c], nb = lc.colour_blk[c + 1] - b0;
       if (nb == 0) continue;
-      if (h->prob.p == 2 && S == 256) k_mult_rows3<2, 256, T><<<nb, 256, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
+      if (h->prob.p == 2 && S == 128) k_mult_rows3<2, 128, T><<<nb, 128, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
+      else if (h->prob.p == 3 && S == 128) k_mult_rows3<3, 128, T><<<nb, 128, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
+      else if (h->prob.p == 2 && S == 256) k_mult_rows3<2, 256, T><<<nb, 256, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
       else if (h->prob.p == 2) k_mult_rows3<2, 1024, T><<<nb, 1024, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
       else if (S == 256) k_mult_rows3<3, 256, T><<<nb, 256, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
       else k_mult_rows3<3, 1024, T><<<nb, 1024, 0, s>>>(tl.L, U, F, sg, sc, sk, tl.cinv_all, lc.cinv_off, b0 * S);
@@ -564,7 +568,7 @@ int setup_cluster3(igamg3d_handle* h, Typed3<T>& ty) {
     V.slot_g = lc.slot_g; V.slot_c = lc.slot_c; V.slot_kb = lc.slot_kb; V.colour_blk = lc.colour_blk_dev;
     V.n_colours = lc.n_colours; V.maxl = lc.maxl; V.row_slots = lc.row_slots;
     V.U = ty.lev[l].U; V.F = ty.lev[l].F; V.R = ty.lev[l].R;
-    if (l >= 1 && lc.row_slots != 256 && lc.row_slots != 1024) { best = l - 1; break; }
+    if (l >= 1 && lc.row_slots != 128 && lc.row_slots != 256 && lc.row_slots != 1024) { best = l - 1; break; }
   }
   if (best < 1) return IGAMG_OK;
   for (auto fn : {(const void*)k_cluster3<2, T>, (const void*)k_cluster3<3, T>})

@@ -60,7 +60,7 @@ struct PatchTables {
   std::vector<int> d2p_off;    // dof -> list of (patch * maxl + local row), CSR over dofs
   std::vector<int> d2p_idx;
   // Row-flat view for the row-parallel colour kernel: each colour is cut into blocks of
-  // row_slots slots (256, or 1024 on levels whose largest patch has more than 256 rows),
+  // row_slots slots (128, 256, or 1024 on levels whose largest patch has more than 256 rows),
   // one slot per local row; a patch's rows sit in consecutive slots of one block (blocks
   // are padded instead of splitting a patch).
   int row_slots = 0;                // 0: no row-flat view (a patch larger than 1024 rows)

@@ -350,8 +350,8 @@ __global__ void k_restrict3(LevelTab3<T> Lf, LevelTab3<T> Lc, Xfer<T> tp, Xfer<T
 // As k_cluster_coarse (2D): the phases of Algorithm 1 for levels 0..lc spread over the
 // blocks of one cluster, separated by the cluster barrier, vectors in global memory (L2).
 // A colour is processed one slot block (k_mult_rows3's packing) per block iteration: with
-// 256-slot blocks each row's three neighbour boxes go to three groups of 256 threads, as in
-// k_mult_rows3x; with 1024-slot blocks (levels whose patches exceed 256 rows) one thread per row.
+// 128- or 256-slot blocks each row's three neighbour boxes go to three groups of S threads, as
+// in k_mult_rows3x; with 1024-slot blocks (levels whose patches exceed 256 rows) one thread per row.
 constexpr int kMaxFused3 = 6;
 
 template <typename T>
@@ -398,9 +398,9 @@ __global__ void __launch_bounds__(1024) k_cluster3(Cluster3Desc<T> D, const T* _
     for (int c = 0; c < V.n_colours; ++c) {
       const int b0 = V.colour_blk[c], b1 = V.colour_blk[c + 1];
       for (int b = b0 + (int)rank; b < b1; b += (int)C) {
-        if (S == 256) {
-          const int w = tid >> 8, t = tid & 255;
-          const int s = b * 256 + t;
+        if (S <= 256) {
+          const int w = tid / S, t = tid - w * S;
+          const int s = b * S + t;
           const int g = w < 3 ? V.slot_g[s] : -1;
           T acc = T(0);
           if (g >= 0) {
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(1024) k_cluster3(Cluster3Desc<T> D, const T* _
           }
           part3[tid] = acc;
           __syncthreads();
-          if (w == 0) part3[t] = acc + (part3[256 + t] + part3[512 + t]);
+          if (w == 0) part3[t] = acc + (part3[S + t] + part3[2 * S + t]);
           __syncthreads();
           if (w == 0 && g >= 0) {
             const unsigned kb = V.slot_kb[s];

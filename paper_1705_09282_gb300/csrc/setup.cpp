@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <atomic>
 #include <map>
 #include <thread>
@@ -611,7 +612,11 @@ int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt
 
 void build_row_slots(PatchTables& pt) {
   const int maxl = pt.maxl;
-  pt.row_slots = maxl <= 256 ? 256 : (maxl <= 1024 ? 1024 : 0);
+  // 128-slot blocks where the patches allow (twice the blocks: a colour spreads more evenly
+  // over the SMs); IGAMG_ROW_SLOTS = 256 keeps 256
+  const char* env = std::getenv("IGAMG_ROW_SLOTS");
+  const int smin = env && std::atoi(env) == 256 ? 256 : 128;
+  pt.row_slots = maxl <= smin ? smin : (maxl <= 256 ? 256 : (maxl <= 1024 ? 1024 : 0));
   const int S = pt.row_slots;
   if (!S) return;
   // classes packed nl x nl: general classes first (their nl from nloc), then the 8-DOF ones

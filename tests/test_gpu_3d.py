@@ -281,3 +281,21 @@ def test_oseen_3d_iterates_and_solve(vmax, sigma, nu):
     r32 = S32.solve(U32, Fg, rtol=1e-8, max_cycles=60)
     assert r32["converged"] and r32["div_inf"] <= 1e-11 * np.abs(Uo).max()
     assert _rel(_np(U32), Uo) < 1e-6
+
+
+@pytest.mark.parametrize("p,n,L", [(2, 2, 2), (3, 2, 2), (2, 4, 3)])
+def test_degenerate_small_meshes(p, n, L):
+    # smallest hierarchies (coarsest mesh of one element; p = 3 on two elements, where every
+    # vector-potential support is the whole cube): iterates equal to the oracle's
+    S = _solver(p, n, L)
+    H = _hier(p, n, L)
+    F = H.fine.load_vector(inputs.manufactured_forcing_3d(p, n, 1.0, 1.0))
+    Ug, Fg = S.empty(), _t(F)
+    Uo = np.zeros_like(F)
+    for k in range(2):
+        S.vcycle(Ug, Fg)
+        H.vcycle(Uo, F)
+        assert _rel(_np(Ug), Uo) < RTOL_IT, k
+    if (p, n) == (3, 2):
+        import scipy.sparse.linalg as spla
+        assert _rel(_np(Ug), spla.spsolve(H.levels[-1].K.tocsc(), F)) < 1e-11

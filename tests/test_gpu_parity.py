@@ -296,3 +296,22 @@ def test_cluster_coarse_levels_same_iterates(depth, blocks, p, monkeypatch):
     assert rep["converged"]
     H.solve(U, F, 1e-12, 80)
     assert _rel(_np(U32), U) < 1e-7
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_manufactured_16x16_three_levels(p):
+    # the small workload: 16 x 16 elements, 3 grids, sigma = nu = 1, forcing from the
+    # manufactured solution u = curl sin^2(pi x) sin^2(pi y), FP64, V(2,2) to 1e-8: same
+    # cycle count and iterate as the oracle, divergence-free at round-off
+    n, L = 16, 3
+    S = _solver(p, n, L)
+    H = o2.Hierarchy(p, n, L, 1.0, 1.0)
+    f = inputs.manufactured_forcing(p, n, 1.0, 1.0)
+    F = H.fine.load_vector(f)
+    U = np.zeros_like(F)
+    k, _ = H.solve(U, F, 1e-8, 50)
+    Ug = S.empty()
+    rep = S.solve(Ug, S.load_vector(_t(f)), rtol=1e-8, max_cycles=50)
+    assert rep["converged"] and rep["cycles"] == k
+    assert _rel(_np(Ug), U) < RTOL_IT
+    assert rep["div_inf"] <= 1e-12 * np.abs(U).max()
