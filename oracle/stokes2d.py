@@ -14,6 +14,8 @@ What it follows, step by step:
   * C_I = 4(p-1), p = streamfunction degree, maximal smoothness, uniform knots -- Sec. 6 preamble
   * prolongation by knot insertion, R = P^T, K_l = R K_{l+1} P                 -- Sec. 5.1
   * Algorithm 1 (MGV), exact coarsest solve                                    -- Sec. 5.1, Algorithm 1
+  * W-cycle (gamma = 2 coarse cycles per level) and full multigrid (nested
+    iteration), the settings Sec. 5's opening paragraph names besides the V-cycle
   * subdomains = supports of streamfunction basis functions; local spaces are
     the basis functions supported inside; additive (eq. ASM) and
     multiplicative (eq. MSM) Schwarz smoothers                                  -- Sec. 5.2
@@ -415,9 +417,10 @@ class Hierarchy:
     """Nested levels l = 0 (coarsest) .. L-1 (finest) with Galerkin coarse operators."""
 
     def __init__(self, p, n_fine, n_levels, sigma, nu, c_pen=None, beta=None,
-                 smoother="mult", eta=0.5, nu1=2, nu2=2):
+                 smoother="mult", eta=0.5, nu1=2, nu2=2, gamma=1):
         self.p, self.n_levels = p, n_levels
         self.smoother, self.eta, self.nu1, self.nu2 = smoother, eta, nu1, nu2
+        self.gamma = gamma
         assert n_fine % (1 << (n_levels - 1)) == 0
         fine = Stokes2D(p, n_fine, sigma, nu, c_pen=c_pen, beta=beta)
         self.fine = fine
@@ -448,7 +451,11 @@ class Hierarchy:
             lev.sweep_additive(U, F, self.eta)
 
     def mgv(self, l, U, F):
-        """Algorithm 1, applied in place to U."""
+        """Algorithm 1, applied in place to U.  With gamma = 1 this is the V-cycle of
+        Algorithm 1.  With gamma = 2 (the W-cycle that Sec. 5's opening paragraph names as
+        another setting for the method) the coarse correction dU comes from two cycles on
+        level l-1 for the same coarse right-hand side G, the second starting from the
+        first's result."""
         if l == 0:
             U[:] = sla.lu_solve(self.coarse_lu, F)
             return
@@ -457,7 +464,8 @@ class Hierarchy:
             self.smooth(l, U, F)
         G = self.P[l - 1].T @ (F - K @ U)
         dU = np.zeros(self.levels[l - 1].K.shape[0])
-        self.mgv(l - 1, dU, G)
+        for _ in range(self.gamma):
+            self.mgv(l - 1, dU, G)
         U += self.P[l - 1] @ dU
         for _ in range(self.nu2):
             self.smooth(l, U, F)
@@ -465,18 +473,40 @@ class Hierarchy:
     def vcycle(self, U, F):
         self.mgv(self.n_levels - 1, U, F)
 
+    def fmg(self, F):
+        """Full multigrid (nested iteration), the other setting that Sec. 5's opening
+        paragraph names: F restricted to every level (F_{l-1} = P_{l-1}^T F_l), the coarsest
+        problem solved exactly, then on each finer level l the prolongated solution of level
+        l-1 taken as the initial guess of one cycle (mgv) for F_l.  Returns the finest
+        level's approximation of K^{-1} F."""
+        L = self.n_levels
+        Fs = [None] * L
+        Fs[-1] = np.asarray(F, dtype=float)
+        for l in range(L - 1, 0, -1):
+            Fs[l - 1] = self.P[l - 1].T @ Fs[l]
+        U = sla.lu_solve(self.coarse_lu, Fs[0])
+        for l in range(1, L):
+            U = self.P[l - 1] @ U
+            self.mgv(l, U, Fs[l])
+        return U
+
     def residual(self, U, F):
         return F - self.levels[-1].K @ U
 
-    def solve(self, U, F, rtol, max_cycles):
-        """V-cycles until ||F - K U||_2 <= rtol ||F - K U_0||_2 (Sec. 6 protocol with the
-        relative tolerance as a parameter).  Returns (cycles, history)."""
+    def solve(self, U, F, rtol, max_cycles, fmg=False):
+        """Cycles until ||F - K U||_2 <= rtol ||F - K U_0||_2 (Sec. 6 protocol with the
+        relative tolerance as a parameter).  With fmg the first step is U += fmg(F - K U)
+        (one full-multigrid pass on the residual equation), counted as one cycle.
+        Returns (cycles, history)."""
         r0 = np.linalg.norm(self.residual(U, F))
         hist = [r0]
         if r0 == 0.0:
             return 0, hist
         for k in range(1, max_cycles + 1):
-            self.vcycle(U, F)
+            if fmg and k == 1:
+                U += self.fmg(self.residual(U, F))
+            else:
+                self.vcycle(U, F)
             rk = np.linalg.norm(self.residual(U, F))
             hist.append(rk)
             if rk <= rtol * r0:

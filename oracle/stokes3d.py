@@ -362,8 +362,9 @@ class Level3D:
 
 
 class Hierarchy3D:
-    def __init__(self, p, n_fine, n_levels, sigma, nu, nu1=2, nu2=2, beta=None):
+    def __init__(self, p, n_fine, n_levels, sigma, nu, nu1=2, nu2=2, beta=None, gamma=1):
         self.p, self.n_levels, self.nu1, self.nu2 = p, n_levels, nu1, nu2
+        self.gamma = gamma
         fine = Stokes3D(p, n_fine, sigma, nu, beta=beta)
         self.fine = fine
         levels, Ps = [None] * n_levels, [None] * n_levels
@@ -384,6 +385,8 @@ class Hierarchy3D:
         self.coarse_lu = sla.lu_factor(levels[0].K.toarray())
 
     def mgv(self, l, U, F):
+        """Algorithm 1 in place on U; gamma = 2 takes the coarse correction from two cycles
+        on level l-1, the second starting from the first (W-cycle, Sec. 5 opening paragraph)."""
         if l == 0:
             U[:] = sla.lu_solve(self.coarse_lu, F)
             return
@@ -392,7 +395,8 @@ class Hierarchy3D:
             self.smooth(l, U, F)
         G = self.P[l - 1].T @ (F - lev.K @ U)
         dU = np.zeros(self.levels[l - 1].K.shape[0])
-        self.mgv(l - 1, dU, G)
+        for _ in range(self.gamma):
+            self.mgv(l - 1, dU, G)
         U += self.P[l - 1] @ dU
         for _ in range(self.nu2):
             self.smooth(l, U, F)
@@ -403,14 +407,33 @@ class Hierarchy3D:
     def vcycle(self, U, F):
         self.mgv(self.n_levels - 1, U, F)
 
-    def solve(self, U, F, rtol, max_cycles):
+    def fmg(self, F):
+        """Full multigrid (nested iteration, Sec. 5 opening paragraph): F restricted to every
+        level, the coarsest solved exactly, then on each finer level one cycle from the
+        prolongated coarser solution.  Returns the finest level's approximation of K^{-1} F."""
+        L = self.n_levels
+        Fs = [None] * L
+        Fs[-1] = np.asarray(F, dtype=float)
+        for l in range(L - 1, 0, -1):
+            Fs[l - 1] = self.P[l - 1].T @ Fs[l]
+        U = sla.lu_solve(self.coarse_lu, Fs[0])
+        for l in range(1, L):
+            U = self.P[l - 1] @ U
+            self.mgv(l, U, Fs[l])
+        return U
+
+    def solve(self, U, F, rtol, max_cycles, fmg=False):
+        """Cycles to rtol; with fmg the first step is U += fmg(F - K U), counted as one cycle."""
         K = self.levels[-1].K
         r0 = np.linalg.norm(F - K @ U)
         hist = [r0]
         if r0 == 0.0:
             return 0, hist
         for k in range(1, max_cycles + 1):
-            self.vcycle(U, F)
+            if fmg and k == 1:
+                U += self.fmg(F - K @ U)
+            else:
+                self.vcycle(U, F)
             hist.append(np.linalg.norm(F - K @ U))
             if hist[-1] <= rtol * r0:
                 return k, hist

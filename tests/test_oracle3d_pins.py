@@ -340,3 +340,38 @@ def test_oseen_forcing_matches_closed_form_derivatives():
         assert np.allclose(f1[c] - f0[c], adv, atol=1e-7)
     # beta is divergence-free, zero on the boundary, max |beta| = 1
     assert np.sqrt((beta ** 2).sum(axis=0)).max() <= 1.0 + 1e-12
+
+
+# ---- W-cycle and full multigrid (Sec. 5 opening paragraph) ------------------------------
+
+def test_w_cycle_on_two_grids_is_the_v_cycle_3d():
+    p, n = 2, 4
+    HV = o3.Hierarchy3D(p, n, 2, 1.0, 1.0, gamma=1)
+    HW = o3.Hierarchy3D(p, n, 2, 1.0, 1.0, gamma=2)
+    F = HV.fine.load_vector(inputs.manufactured_forcing_3d(p, n, 1.0, 1.0))
+    UV, UW = np.zeros_like(F), np.zeros_like(F)
+    HV.vcycle(UV, F)
+    HW.vcycle(UW, F)
+    assert np.abs(UV - UW).max() <= 1e-13 * np.abs(UV).max()
+
+
+def test_fmg_is_exact_on_prolongated_solutions_3d():
+    p, n = 2, 8
+    H = o3.Hierarchy3D(p, n, 3, 1.0, 1.0)
+    rng = np.random.default_rng(6)
+    u = rng.uniform(-1, 1, H.levels[0].K.shape[0])
+    for l in range(1, 3):
+        u = H.P[l - 1] @ u
+    F = H.levels[-1].K @ u
+    U = H.fmg(F)
+    assert np.abs(U - u).max() <= 1e-11 * np.abs(u).max()
+
+
+def test_w_and_fmg_solves_converge_to_direct_solve_3d():
+    p, n = 2, 8
+    H = o3.Hierarchy3D(p, n, 3, 1.0, 1.0, gamma=2)
+    F = H.fine.load_vector(inputs.manufactured_forcing_3d(p, n, 1.0, 1.0))
+    Ux = spla.spsolve(H.levels[-1].K.tocsc(), F)
+    U = np.zeros_like(F)
+    H.solve(U, F, 1e-13, 60, fmg=True)
+    assert np.abs(U - Ux).max() <= 1e-10 * np.abs(Ux).max()

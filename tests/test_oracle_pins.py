@@ -357,3 +357,93 @@ def test_mesh_independent_contraction():
     # (the paper's Tables 1-7 report mesh-independent cycle counts)
     assert max(rates) < 0.35
     assert abs(rates[0] - rates[1]) < 0.1
+
+
+# ----------------------------------------------- W-cycle and full multigrid --
+# Sec. 5's opening paragraph: the method also applies inside a W-cycle or a full
+# multigrid (nested iteration) framework.
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_w_cycle_on_two_grids_is_the_v_cycle(p):
+    # with two grids the coarse correction is an exact solve; repeating it from its own
+    # result changes nothing (a second correction added on top would double it)
+    n = 8
+    F = o2.Hierarchy(p, n, 2, 1.0, 1.0).fine.load_vector(inputs.grf_forcing(p, n, seed=21))
+    HV = o2.Hierarchy(p, n, 2, 1.0, 1.0, gamma=1)
+    HW = o2.Hierarchy(p, n, 2, 1.0, 1.0, gamma=2)
+    UV, UW = np.zeros_like(F), np.zeros_like(F)
+    HV.vcycle(UV, F)
+    HW.vcycle(UW, F)
+    assert np.abs(UV - UW).max() <= 1e-13 * np.abs(UV).max()
+
+
+def test_many_coarse_cycles_tend_to_the_exact_two_grid_cycle():
+    # gamma coarse cycles per level, each continuing from the last, converge to the exact
+    # coarse correction: three grids with large gamma = two grids (same coarse operator
+    # K_1 = P^T K_2 P) to round-off
+    p, n = 2, 8
+    H3 = o2.Hierarchy(p, n, 3, 1.0, 1.0, gamma=30)
+    H2 = o2.Hierarchy(p, n, 2, 1.0, 1.0)
+    assert np.abs((H3.levels[1].K - H2.levels[0].K).toarray()).max() <= 1e-12
+    F = H2.fine.load_vector(inputs.grf_forcing(p, n, seed=22))
+    U3, U2 = np.zeros_like(F), np.zeros_like(F)
+    H3.vcycle(U3, F)
+    H2.vcycle(U2, F)
+    assert np.abs(U3 - U2).max() <= 1e-11 * np.abs(U2).max()
+    # and gamma = 2 is a different, better-converging cycle than gamma = 1 there
+    HV = o2.Hierarchy(p, n, 3, 1.0, 1.0, gamma=1)
+    UV = np.zeros_like(F)
+    HV.vcycle(UV, F)
+    Ux = spla.spsolve(H2.fine.K.tocsc(), F)
+    HW = o2.Hierarchy(p, n, 3, 1.0, 1.0, gamma=2)
+    UW = np.zeros_like(F)
+    HW.vcycle(UW, F)
+    assert np.linalg.norm(UW - Ux) < np.linalg.norm(UV - Ux)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_fmg_is_exact_on_prolongated_solutions(p):
+    # if U* = P_2 P_1 P_0 u_0 then every restricted right-hand side is K_l of the matching
+    # prolongation (Galerkin operators), the coarsest solve recovers u_0 and every cycle
+    # starts from an exact solution, so FMG returns U* to round-off
+    n = 16
+    H = o2.Hierarchy(p, n, 4, 1.0, 1.0)
+    rng = np.random.default_rng(5)
+    u = rng.uniform(-1, 1, H.levels[0].K.shape[0])
+    for l in range(1, 4):
+        u = H.P[l - 1] @ u
+    F = H.levels[-1].K @ u
+    U = H.fmg(F)
+    assert np.abs(U - u).max() <= 1e-11 * np.abs(u).max()
+
+
+def test_fmg_on_one_grid_is_the_direct_solve():
+    H = o2.Hierarchy(2, 4, 1, 1.0, 1.0)
+    F = H.fine.load_vector(inputs.grf_forcing(2, 4, seed=23))
+    assert np.allclose(H.fmg(F), spla.spsolve(H.fine.K.tocsc(), F), atol=1e-13)
+
+
+@pytest.mark.parametrize("p,gamma,fmg", [(2, 2, False), (3, 2, False), (2, 1, True), (3, 2, True)])
+def test_w_and_fmg_solves_converge_to_direct_solve(p, gamma, fmg):
+    n = 8
+    H = o2.Hierarchy(p, n, 3, 1.0, 1.0, gamma=gamma)
+    F = H.fine.load_vector(inputs.grf_forcing(p, n, seed=24))
+    Ux = spla.spsolve(H.levels[-1].K.tocsc(), F)
+    U = np.zeros_like(F)
+    k, hist = H.solve(U, F, 1e-14, 80, fmg=fmg)
+    assert np.abs(U - Ux).max() <= 1e-12 * np.abs(Ux).max()
+    assert all(b < a for a, b in zip(hist[:3], hist[1:4]))
+
+
+def test_fmg_first_step_beats_one_v_cycle_from_zero():
+    # nested iteration starts the finest cycle from the interpolated coarse solution: on a
+    # smooth forcing its first residual is far below that of one V-cycle from zero
+    p, n = 2, 32
+    H = o2.Hierarchy(p, n, 4, 1.0, 1.0)
+    F = H.fine.load_vector(inputs.manufactured_forcing(p, n, 1.0, 1.0))
+    UV = np.zeros_like(F)
+    H.vcycle(UV, F)
+    UF = H.fmg(F)
+    rv = np.linalg.norm(F - H.fine.K @ UV)
+    rf = np.linalg.norm(F - H.fine.K @ UF)
+    assert rf < 0.5 * rv, (rf, rv)
