@@ -82,6 +82,14 @@ typedef struct {
   int nu1, nu2;       /* pre- / post-smoothing sweeps (Algorithm 1) */
   int precision;      /* IGAMG_FP64, IGAMG_FP32_IR, IGAMG_FGMRES_FP64 or IGAMG_FGMRES_FP32 */
   int restart;        /* FGMRES: Krylov directions per restart cycle; <= 0 selects 20 */
+  int gamma;          /* coarse cycles per level: <= 1 the V-cycle of Algorithm 1, 2 the
+                         W-cycle (the second coarse cycle continues from the first); Sec. 5
+                         opening paragraph.  At most 4. */
+  int fmg;            /* 1: every solve's first step is one full-multigrid pass (nested
+                         iteration: the residual restricted to all levels, the coarsest
+                         solved exactly, one cycle per finer level from the prolongated
+                         coarser solution), U += its result; it counts as one cycle.
+                         Not with the FGMRES precisions (IGAMG_EUNSUPPORTED). */
 } igamg_problem;
 
 typedef struct {
@@ -191,6 +199,18 @@ int igamg_streamfunction(igamg_handle* h, const double* U, double* psi);
  * ignored) and the pressure coefficients = p_scale * channel 1 on its leading
  * (n+p-1) x (n+p-1) points.  The velocity is exactly divergence-free (north star (4)). */
 int igamg_warm_start(igamg_handle* h, const float* grid, double psi_scale, double p_scale, double* U);
+
+/* The same guess with its two predicted fields scaled against F (device, the load vector):
+ * U = (alpha curl psi, beta p), u = curl(psi_scale * channel 0) and p = p_scale * channel 1
+ * as above.  (alpha, beta) minimise ||F - K U||_2, the residual that an absolute stopping
+ * test measures (Eq. (3.1)'s matrix K, Sec. 3): a 2 x 2 least-squares problem from five
+ * inner products.  alpha = beta = 0 is admissible, so the first residual is never larger
+ * than that of the zero guess; an exact solution direction is reproduced exactly.  The
+ * velocity stays exactly divergence-free.  Synchronises; alpha, beta (host) may be NULL.
+ * Uses the handle's host-solve and residual workspaces: not concurrent with its solves.
+ * Errors: IGAMG_EINVAL (null pointer), IGAMG_EUNSUPPORTED (3D handle), IGAMG_ENONFINITE. */
+int igamg_warm_start_minres(igamg_handle* h, const float* grid, double psi_scale, double p_scale,
+                            const double* F, double* U, double* alpha, double* beta);
 
 /* ---- the warm-start network ------------------------------------------------------------
  * 3x3 convolutions in_channels -> width -> width -> width -> 2, GELU after the first three

@@ -20,7 +20,8 @@ class Problem(ctypes.Structure):
                 ("n_levels", ctypes.c_int), ("sigma", ctypes.c_double), ("nu", ctypes.c_double),
                 ("c_penalty", ctypes.c_double), ("beta_qp", ctypes.c_void_p),
                 ("smoother", ctypes.c_int), ("eta", ctypes.c_double), ("nu1", ctypes.c_int),
-                ("nu2", ctypes.c_int), ("precision", ctypes.c_int), ("restart", ctypes.c_int)]
+                ("nu2", ctypes.c_int), ("precision", ctypes.c_int), ("restart", ctypes.c_int),
+                ("gamma", ctypes.c_int), ("fmg", ctypes.c_int)]
 
 
 class Sizes(ctypes.Structure):
@@ -62,6 +63,7 @@ SIGNATURES = {
                                    ctypes.POINTER(_D), _I, ctypes.POINTER(Report), ctypes.POINTER(_I)]),
     "igamg_streamfunction": (_I, [_P, _P, _P]),
     "igamg_warm_start": (_I, [_P, _P, _D, _D, _P]),
+    "igamg_warm_start_minres": (_I, [_P, _P, _D, _D, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "igamg_nn_create": (_I, [_I, _I, ctypes.POINTER(_I), ctypes.c_ulonglong, _P, ctypes.POINTER(_P)]),
     "igamg_nn_destroy": (None, [_P]),
     "igamg_nn_num_params": (_I, [_P]),
@@ -115,11 +117,12 @@ def check(code, where):
 
 
 def make_problem(p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.5, nu1=2, nu2=2,
-                 c_penalty=0.0, precision=IGAMG_FP64, beta=None, dim=2, restart=0):
+                 c_penalty=0.0, precision=IGAMG_FP64, beta=None, dim=2, restart=0, gamma=1, fmg=False):
     pr = Problem()
     pr.dim, pr.p, pr.n_fine, pr.n_levels = dim, p, n_fine, n_levels
     pr.sigma, pr.nu, pr.c_penalty = float(sigma), float(nu), float(c_penalty)
     pr.beta_qp = beta.ctypes.data if beta is not None else None
     pr.smoother = IGAMG_ADD if smoother == "add" else IGAMG_MULT
     pr.eta, pr.nu1, pr.nu2, pr.precision, pr.restart = float(eta), nu1, nu2, precision, restart
+    pr.gamma, pr.fmg = gamma, int(bool(fmg))
     return pr

@@ -92,6 +92,39 @@ __global__ void k_grid_to_pressure(int npd, const float* __restrict__ grid, int 
   pr[i] = scale * (double)grid[y * H + x];
 }
 
+// Five dot products x_k . y_k at once (grid-stride, fixed-order block partials part[k][b]).
+constexpr int kDotGrid = 304;
+__global__ void __launch_bounds__(256) k_dots5(int n, const double* __restrict__ x0, const double* __restrict__ y0,
+                                               const double* __restrict__ x1, const double* __restrict__ y1,
+                                               const double* __restrict__ x2, const double* __restrict__ y2,
+                                               const double* __restrict__ x3, const double* __restrict__ y3,
+                                               const double* __restrict__ x4, const double* __restrict__ y4,
+                                               double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s[5] = {0, 0, 0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    s[0] = fma(x0[i], y0[i], s[0]); s[1] = fma(x1[i], y1[i], s[1]); s[2] = fma(x2[i], y2[i], s[2]);
+    s[3] = fma(x3[i], y3[i], s[3]); s[4] = fma(x4[i], y4[i], s[4]);
+  }
+  for (int k = 0; k < 5; ++k) {
+    double t = block_sum(s[k], sh);
+    if (threadIdx.x == 0) part[k * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_dots5_finish(int nb, const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x >= 5) return;
+  double t = 0.0;
+  for (int b = 0; b < nb; ++b) t += part[threadIdx.x * nb + b];
+  out[threadIdx.x] = t;
+}
+
+// U = a U + b Z
+__global__ void k_axpby(int n, double a, double b, const double* __restrict__ Z, double* __restrict__ U) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) U[i] = a * U[i] + b * Z[i];
+}
+
 // velocity = curl psi, psi on the (n+p-2)^2 interior streamfunction coefficients.
 __global__ void k_curl(LevelTab<double> L, const double* __restrict__ dcoef, const double* __restrict__ psi,
                        double* __restrict__ U) {
@@ -193,15 +226,16 @@ struct igamg_handle {
   double *f_dev = nullptr, *Fh = nullptr, *Uh = nullptr;   // host-buffer solve workspaces
   double* psi = nullptr;       // FP32 mode: streamfunction of the correction (fine interior)
   // captured graphs: [0] solve step, [1] public V-cycle (starts with the residual in FP32 mode)
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  const void* gU[2] = {nullptr, nullptr};
-  const void* gF[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  const void* gU[3] = {nullptr, nullptr, nullptr};
+  const void* gF[3] = {nullptr, nullptr, nullptr};
   std::vector<void*> allocs;
   cudaStream_t exec_stream = nullptr;  // used by igamg_solve_batch
   cudaEvent_t ev = nullptr;
   igamg3d_handle* d3 = nullptr;        // dim = 3: everything lives in the 3D driver
   KrylovWork kw;                       // FGMRES modes
-  double* zeros = nullptr;             // FGMRES: a zero right-hand side (K z = -(0 - K z))
+  double* zeros = nullptr;             // a zero right-hand side (K z = -(0 - K z))
+  double* dots = nullptr;              // warm-start scalings: 5 x kDotGrid partials, then 5 sums
 };
 
 namespace {
@@ -379,6 +413,26 @@ int do_fused(igamg_handle* h, const T* Fin, T* Uio, int load_u, cudaStream_t s) 
   return launch_check();
 }
 
+// Algorithm 1 from level l, recursively, in place on Ul (zeroed first if zero): gamma
+// coarse cycles per level, the second and later ones continuing from the previous result
+// (gamma = 2: the W-cycle).  Per-level launches throughout.
+template <typename T>
+int do_cycle(igamg_handle* h, int l, T* Ul, const T* Fl, bool zero, cudaStream_t s) {
+  auto& ty = typed<T>(h);
+  if (l == 0) return do_coarse<T>(h, Fl, Ul, s);
+  int rc;
+  if (zero) CK(cudaMemsetAsync(Ul, 0, ty.lev[l].L.n_total * sizeof(T), s));
+  for (int k = 0; k < h->prob.nu1; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+  if ((rc = do_residual<T>(h, l, Ul, Fl, ty.lev[l].R, nullptr, s))) return rc;
+  if ((rc = do_restrict<T>(h, l, ty.lev[l].R, ty.lev[l - 1].F, s))) return rc;
+  const int gamma = std::max(1, h->prob.gamma);
+  for (int g = 0; g < gamma; ++g)
+    if ((rc = do_cycle<T>(h, l - 1, ty.lev[l - 1].U, ty.lev[l - 1].F, g == 0, s))) return rc;
+  if ((rc = do_prolong<T>(h, l, ty.lev[l - 1].U, Ul, s))) return rc;
+  for (int k = 0; k < h->prob.nu2; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+  return IGAMG_OK;
+}
+
 // Algorithm 1 (MGV) from the finest level, unrolled into launches; the coarsest levels
 // (0 .. fused_lc) run inside one block when they fit in its shared memory.
 template <typename T>
@@ -386,6 +440,7 @@ int do_vcycle(igamg_handle* h, T* U, const T* F, cudaStream_t s) {
   auto& ty = typed<T>(h);
   const int L = (int)ty.lev.size();
   if (L == 1) return do_coarse<T>(h, F, U, s);
+  if (h->prob.gamma > 1) return do_cycle<T>(h, L - 1, U, F, false, s);
   int rc;
   const int lc = ty.fused_lc;
   if (lc == L - 1) return do_fused<T>(h, F, U, 1, s);
@@ -425,17 +480,41 @@ int do_vcycle(igamg_handle* h, T* U, const T* F, cudaStream_t s) {
   return IGAMG_OK;
 }
 
-// FP32 mode, one refinement step: given R64 = F - K U (FP64), an FP32 V-cycle on K e = R64,
-// then U += (curl psi(e), e_p, e_lambda) in FP64 and R64 = F - K U with its norm.
-int do_ir_step(igamg_handle* h, double* U, const double* F, cudaStream_t s) {
+// Full multigrid (nested iteration) on K e = r with r in the finest level's F workspace and
+// e written to its U workspace: r restricted to every level, the coarsest solved exactly,
+// then on each finer level one cycle from the prolongated coarser solution.
+template <typename T>
+int do_fmg(igamg_handle* h, cudaStream_t s) {
+  auto& ty = typed<T>(h);
+  const int L = (int)ty.lev.size();
+  int rc;
+  for (int l = L - 1; l >= 1; --l)
+    if ((rc = do_restrict<T>(h, l, ty.lev[l].F, ty.lev[l - 1].F, s))) return rc;
+  if ((rc = do_coarse<T>(h, ty.lev[0].F, ty.lev[0].U, s))) return rc;
+  for (int l = 1; l <= L - 1; ++l) {
+    CK(cudaMemsetAsync(ty.lev[l].U, 0, ty.lev[l].L.n_total * sizeof(T), s));
+    if ((rc = do_prolong<T>(h, l, ty.lev[l - 1].U, ty.lev[l].U, s))) return rc;
+    if ((rc = do_cycle<T>(h, l, ty.lev[l].U, ty.lev[l].F, false, s))) return rc;
+  }
+  return IGAMG_OK;
+}
+
+// FP32 mode, one refinement step: given R64 = F - K U (FP64), an FP32 V-cycle (or, with
+// fmg, an FP32 full-multigrid pass) on K e = R64, then U += (curl psi(e), e_p, e_lambda) in
+// FP64 and R64 = F - K U with its norm.
+int do_ir_step(igamg_handle* h, double* U, const double* F, cudaStream_t s, bool fmg = false) {
   const int L = (int)h->d.lev.size();
   auto& top32 = h->f.lev[L - 1];
   double* R64 = h->d.lev[L - 1].R;
   const auto& Ld = h->d.lev[L - 1].L;
   k_to_float<<<nblk(Ld.n_total), kBlock, 0, s>>>(Ld.n_total, R64, top32.F);
-  CK(cudaMemsetAsync(top32.U, 0, Ld.n_total * sizeof(float), s));
-  int rc = do_vcycle<float>(h, top32.U, top32.F, s);
-  if (rc) return rc;
+  int rc;
+  if (fmg) {
+    if ((rc = do_fmg<float>(h, s))) return rc;
+  } else {
+    CK(cudaMemsetAsync(top32.U, 0, Ld.n_total * sizeof(float), s));
+    if ((rc = do_vcycle<float>(h, top32.U, top32.F, s))) return rc;
+  }
   k_integrate_psi<<<nblk((long long)Ld.nint * 32, 128), 128, 0, s>>>(Ld.nint, Ld.nxu, h->lc[L - 1].inv_dcoef, top32.U, h->psi);
   k_curl_update<<<nblk(Ld.n_total), kBlock, 0, s>>>(Ld, h->lc[L - 1].dcoef, h->psi, top32.U, U);
   if ((rc = launch_check())) return rc;
@@ -451,7 +530,22 @@ int do_step(igamg_handle* h, double* U, const double* F, cudaStream_t s) {
   return do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, h->norm2, s);
 }
 
-// kind 0: solve step; kind 1: public V-cycle (FP32 mode starts by forming R64)
+// first solve step with fmg (R64 = F - K U on entry): U += FMG(R64), then R64 and its norm.
+int do_fmg_step(igamg_handle* h, double* U, const double* F, cudaStream_t s) {
+  const int L = (int)h->d.lev.size();
+  if (fp32_base(h->prob)) return do_ir_step(h, U, F, s, true);
+  auto& top = h->d.lev[L - 1];
+  const int n = top.L.n_total;
+  CK(cudaMemcpyAsync(top.F, top.R, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  int rc = do_fmg<double>(h, s);
+  if (rc) return rc;
+  k_axpby<<<nblk(n), kBlock, 0, s>>>(n, 1.0, 1.0, top.U, U);
+  if ((rc = launch_check())) return rc;
+  return do_residual<double>(h, L - 1, U, F, top.R, h->norm2, s);
+}
+
+// kind 0: solve step; kind 1: public V-cycle (FP32 mode starts by forming R64); kind 2:
+// the full-multigrid first step
 int ensure_graph(igamg_handle* h, int kind, double* U, const double* F) {
   if (h->graph[kind] && h->gU[kind] == U && h->gF[kind] == F) return IGAMG_OK;
   if (h->graph[kind]) { cudaGraphExecDestroy(h->graph[kind]); h->graph[kind] = nullptr; }
@@ -461,7 +555,7 @@ int ensure_graph(igamg_handle* h, int kind, double* U, const double* F) {
   int rc = IGAMG_OK;
   if (kind == 1 && fp32_base(h->prob))
     rc = do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, nullptr, h->cap_stream);
-  if (!rc) rc = do_step(h, U, F, h->cap_stream);
+  if (!rc) rc = kind == 2 ? do_fmg_step(h, U, F, h->cap_stream) : do_step(h, U, F, h->cap_stream);
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
   if (rc) { if (e == cudaSuccess) cudaGraphDestroy(g); return rc; }
   CK(e);
@@ -531,13 +625,14 @@ int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, d
     if (!std::isfinite(r0[i])) st[i] = IGAMG_ENONFINITE;
     else if (r0[i] == 0.0 || (atol && r0[i] <= atol[i])) st[i] = IGAMG_OK;
     if ((rc = ensure_graph(hs[i], 0, Us[i], Fs[i]))) return rc;
+    if (hs[i]->prob.fmg && (rc = ensure_graph(hs[i], 2, Us[i], Fs[i]))) return rc;
   }
   for (;;) {
     int active = 0;
     for (int i = 0; i < n; ++i) {
       if (st[i] != IGAMG_NOT_CONVERGED || k[i] >= max_cycles) continue;
       igamg_handle* h = hs[i];
-      CK(cudaGraphLaunch(h->graph[0], h->exec_stream));
+      CK(cudaGraphLaunch(h->graph[(k[i] == 0 && h->prob.fmg) ? 2 : 0], h->exec_stream));
       CK(cudaMemcpyAsync(h->h_pinned, h->norm2, sizeof(double), cudaMemcpyDeviceToHost, h->exec_stream));
       ++k[i];
       ++active;
@@ -634,12 +729,13 @@ int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max
   if ((rc = read_norm(h, &r0))) return rc;
   if (!std::isfinite(r0)) return IGAMG_ENONFINITE;
   if ((rc = ensure_graph(h, 0, U, F))) return rc;
+  if (h->prob.fmg && (rc = ensure_graph(h, 2, U, F))) return rc;
   int k = 0;
   double rk = r0;
   int status = IGAMG_NOT_CONVERGED;
   if (r0 == 0.0 || (atol >= 0 && r0 <= atol)) status = IGAMG_OK;
   while (status == IGAMG_NOT_CONVERGED && k < max_cycles) {
-    CK(cudaGraphLaunch(h->graph[0], h->stream));
+    CK(cudaGraphLaunch(h->graph[(k == 0 && h->prob.fmg) ? 2 : 0], h->stream));
     ++k;
     if ((rc = read_norm(h, &rk))) return rc;
     if (!std::isfinite(rk)) { status = IGAMG_ENONFINITE; break; }
@@ -783,6 +879,7 @@ template <typename T>
 int autotune_fused(igamg_handle* h, Typed<T>& ty) {
   ty.fused_kind = 1;
   if (ty.fused_max < 1 && ty.cluster_max < 1) { ty.fused_lc = -1; return IGAMG_OK; }
+  if (h->prob.gamma > 1) { ty.fused_lc = -1; return IGAMG_OK; }   // W-cycles run level by level
   const int L = h->prob.n_levels;
   TuneKey key{h->prob.p, h->prob.n_fine, L, (int)sizeof(T), h->prob.smoother, h->prob.nu1, h->prob.nu2};
   // fixed choices (tests, experiments): IGAMG_FUSED_LEVELS = depth, IGAMG_FUSED_CLUSTER = blocks
@@ -929,6 +1026,8 @@ int validate(const igamg_problem& pr) {
   if (!(pr.sigma > 0) || !(pr.nu > 0) || pr.nu1 < 0 || pr.nu2 < 0) return IGAMG_EINVAL;
   if (pr.smoother != IGAMG_MULT && pr.smoother != IGAMG_ADD) return IGAMG_EINVAL;
   if (pr.precision < IGAMG_FP64 || pr.precision > IGAMG_FGMRES_FP32) return IGAMG_EUNSUPPORTED;
+  if (pr.gamma < 0 || pr.gamma > 4 || pr.fmg < 0 || pr.fmg > 1) return IGAMG_EINVAL;
+  if (pr.fmg && pr.precision >= IGAMG_FGMRES_FP64) return IGAMG_EUNSUPPORTED;
   if (pr.n_fine > 8192) return IGAMG_EINVAL;
   // the coarsest grid is solved with a dense inverse held in shared memory by one block
   if (level_sizes(pr.p, pr.n_fine >> (pr.n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
@@ -982,7 +1081,12 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
     delete h;
     return rc;
   }
-  auto fail = [&](int code) { igamg_destroy(h); return code; };
+  auto fail_at = [&](int code, int line) {
+    if (std::getenv("IGAMG_VERBOSE")) std::fprintf(stderr, "igamg: create failed (%d) at igamg.cu:%d: %s\n", code, line, g_err.c_str());
+    igamg_destroy(h);
+    return code;
+  };
+#define fail(code) fail_at((code), __LINE__)
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(IGAMG_ECUDA);
   const int L = pr.n_levels, p = pr.p;
   h->lc.resize(L);
@@ -1024,15 +1128,17 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
   if (cudaMallocHost((void**)&h->h_pinned, 2 * sizeof(double)) != cudaSuccess) return fail(IGAMG_ECUDA);
   if ((rc = autotune_fused<double>(h, h->d))) return fail(rc);
   if (fp32_base(pr) && (rc = autotune_fused<float>(h, h->f))) return fail(rc);
-  if (pr.precision >= IGAMG_FGMRES_FP64) {
-    if ((rc = krylov_alloc(h->kw, pr.restart > 0 ? pr.restart : 20, nfine, h->allocs))) return fail(rc);
-    if ((rc = dmalloc(h, (void**)&h->zeros, nfine * sizeof(double)))) return fail(rc);
-    if (cudaMemset(h->zeros, 0, nfine * sizeof(double)) != cudaSuccess) return fail(IGAMG_ECUDA);
-  }
+  if (pr.precision >= IGAMG_FGMRES_FP64 &&
+      (rc = krylov_alloc(h->kw, pr.restart > 0 ? pr.restart : 20, nfine, h->allocs)))
+    return fail(rc);
+  if ((rc = dmalloc(h, (void**)&h->zeros, nfine * sizeof(double)))) return fail(rc);
+  if (cudaMemset(h->zeros, 0, nfine * sizeof(double)) != cudaSuccess) return fail(IGAMG_ECUDA);
+  if ((rc = dmalloc(h, (void**)&h->dots, (5 * kDotGrid + 8) * sizeof(double)))) return fail(rc);
   if (cudaStreamCreateWithFlags(&h->exec_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(IGAMG_ECUDA);
   if (cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess) return fail(IGAMG_ECUDA);
   *out = h;
   return IGAMG_OK;
+#undef fail
 }
 
 void igamg_destroy(igamg_handle* h) {
@@ -1194,6 +1300,53 @@ int igamg_warm_start(igamg_handle* h, const float* grid, double psi_scale, doubl
   k_grid_to_pressure<<<nblk(Lt.n_p), kBlock, 0, h->stream>>>(Lt.npd, grid + (size_t)H * H, H, p_scale,
                                                               U + Lt.n_ux + Lt.n_uy);
   return launch_check();
+}
+
+int igamg_warm_start_minres(igamg_handle* h, const float* grid, double psi_scale, double p_scale, const double* F,
+                            double* U, double* alpha_out, double* beta_out) {
+  if (!h || !grid || !F || !U) return IGAMG_EINVAL;
+  if (h->d3) return IGAMG_EUNSUPPORTED;
+  const int L = (int)h->d.lev.size();
+  auto& Lt = h->d.lev.back().L;
+  cudaStream_t s = h->stream;
+  const int n = Lt.n_total, nu = Lt.n_ux + Lt.n_uy;
+  double* Z = h->Fh;                    // the predicted pressure as a vector (velocity 0)
+  double* W1 = h->Uh;                   // -K u
+  double* W2 = h->d.lev[L - 1].R;       // -K Z
+  k_grid_to_psi<<<nblk((long long)Lt.nint * Lt.nint), kBlock, 0, s>>>(Lt.nint, grid, psi_scale, h->psi);
+  CK(cudaMemsetAsync(U, 0, n * sizeof(double), s));
+  k_curl<<<nblk(nu), kBlock, 0, s>>>(Lt, h->lc.back().dcoef, h->psi, U);
+  CK(cudaMemsetAsync(Z, 0, n * sizeof(double), s));
+  const int H = Lt.nint + 2;
+  k_grid_to_pressure<<<nblk(Lt.n_p), kBlock, 0, s>>>(Lt.npd, grid + (size_t)H * H, H, p_scale, Z + nu);
+  int rc = launch_check();
+  if (rc) return rc;
+  if ((rc = do_residual<double>(h, L - 1, U, h->zeros, W1, nullptr, s))) return rc;
+  if ((rc = do_residual<double>(h, L - 1, Z, h->zeros, W2, nullptr, s))) return rc;
+  k_dots5<<<kDotGrid, 256, 0, s>>>(n, F, W1, W1, W1, F, W2, W1, W2, W2, W2, h->dots);
+  k_dots5_finish<<<1, 32, 0, s>>>(kDotGrid, h->dots, h->dots + 5 * kDotGrid);
+  if ((rc = launch_check())) return rc;
+  double d[5];
+  CK(cudaMemcpyAsync(d, h->dots + 5 * kDotGrid, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // (alpha, beta) minimise |F + alpha W1 + beta W2|^2 = |F - K(alpha u + beta Z)|^2:
+  // normal equations [W1.W1 W1.W2; W1.W2 W2.W2] (alpha, beta) = -(F.W1, F.W2).
+  // alpha = beta = 0 is admissible, so the first residual is never larger than |F|.
+  const double a11 = d[1], a12 = d[3], a22 = d[4], r1 = -d[0], r2 = -d[2];
+  const double det = a11 * a22 - a12 * a12;
+  double alpha = 0.0, beta = 0.0;
+  if (det > 1e-14 * a11 * a22) {
+    alpha = (r1 * a22 - r2 * a12) / det;
+    beta = (a11 * r2 - a12 * r1) / det;
+  } else if (a11 > 0.0) {               // the two directions are (nearly) parallel
+    alpha = r1 / a11;
+  }
+  if (!std::isfinite(alpha) || !std::isfinite(beta)) return IGAMG_ENONFINITE;
+  k_axpby<<<nblk(n), kBlock, 0, s>>>(n, alpha, beta, Z, U);
+  if ((rc = launch_check())) return rc;
+  if (alpha_out) *alpha_out = alpha;
+  if (beta_out) *beta_out = beta;
+  return IGAMG_OK;
 }
 
 int igamg_curl(igamg_handle* h, const double* psi, double* U) {

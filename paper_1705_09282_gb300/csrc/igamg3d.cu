@@ -233,9 +233,9 @@ struct igamg3d_handle {
   double *lv_p = nullptr, *lv_q = nullptr, *h_pinned = nullptr;
   double *f_dev = nullptr, *Fh = nullptr, *Uh = nullptr;
   double *psi = nullptr, *tot = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  const void* gU[2] = {nullptr, nullptr};
-  const void* gF[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  const void* gU[3] = {nullptr, nullptr, nullptr};
+  const void* gF[3] = {nullptr, nullptr, nullptr};
   std::vector<void*> allocs;
   KrylovWork kw;                    // FGMRES modes
   double* zeros = nullptr;
@@ -440,11 +440,31 @@ int do_cluster(igamg3d_handle* h, const T* Fin, T* Uio, int load_u, cudaStream_t
   return IGAMG_OK;
 }
 
+// Algorithm 1 from level l, recursively, in place on Ul (zeroed first if zero), with gamma
+// coarse cycles per level (gamma = 2: the W-cycle); per-level launches throughout.
+template <typename T>
+int do_cycle(igamg3d_handle* h, int l, T* Ul, const T* Fl, bool zero, cudaStream_t s) {
+  auto& ty = typed<T>(h);
+  if (l == 0) return do_coarse<T>(h, Fl, Ul, s);
+  int rc;
+  if (zero) CK3(cudaMemsetAsync(Ul, 0, ty.lev[l].L.n_total * sizeof(T), s));
+  for (int k = 0; k < h->prob.nu1; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+  if ((rc = do_residual<T>(h, l, Ul, Fl, ty.lev[l].R, nullptr, s))) return rc;
+  if ((rc = do_restrict<T>(h, l, ty.lev[l].R, ty.lev[l - 1].F, s))) return rc;
+  const int gamma = std::max(1, h->prob.gamma);
+  for (int g = 0; g < gamma; ++g)
+    if ((rc = do_cycle<T>(h, l - 1, ty.lev[l - 1].U, ty.lev[l - 1].F, g == 0, s))) return rc;
+  if ((rc = do_prolong<T>(h, l, ty.lev[l - 1].U, Ul, s))) return rc;
+  for (int k = 0; k < h->prob.nu2; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+  return IGAMG_OK;
+}
+
 template <typename T>
 int do_vcycle(igamg3d_handle* h, T* U, const T* F, cudaStream_t s) {
   auto& ty = typed<T>(h);
   const int L = (int)ty.lev.size();
   if (L == 1) return do_coarse<T>(h, F, U, s);
+  if (h->prob.gamma > 1) return do_cycle<T>(h, L - 1, U, F, false, s);
   int rc;
   const int lc = ty.fused_lc;
   if (lc == L - 1) return do_cluster<T>(h, F, U, 1, s);
@@ -484,18 +504,47 @@ int do_vcycle(igamg3d_handle* h, T* U, const T* F, cudaStream_t s) {
   return IGAMG_OK;
 }
 
-// FP32 mode, one refinement step (R64 = F - K U on entry): FP32 V-cycle on K e = R64, then
-// U += (curl psi(e), e_p, e_lambda) in FP64 and R64 = F - K U with its norm.
-int do_ir_step(igamg3d_handle* h, double* U, const double* F, cudaStream_t s) {
+// Full multigrid (nested iteration) on K e = r, r in the finest level's F workspace, e
+// written to its U workspace: r restricted to every level, the coarsest solved exactly, then
+// on each finer level one cycle from the prolongated coarser solution.
+template <typename T>
+int do_fmg(igamg3d_handle* h, cudaStream_t s) {
+  auto& ty = typed<T>(h);
+  const int L = (int)ty.lev.size();
+  int rc;
+  for (int l = L - 1; l >= 1; --l)
+    if ((rc = do_restrict<T>(h, l, ty.lev[l].F, ty.lev[l - 1].F, s))) return rc;
+  if ((rc = do_coarse<T>(h, ty.lev[0].F, ty.lev[0].U, s))) return rc;
+  for (int l = 1; l <= L - 1; ++l) {
+    CK3(cudaMemsetAsync(ty.lev[l].U, 0, ty.lev[l].L.n_total * sizeof(T), s));
+    if ((rc = do_prolong<T>(h, l, ty.lev[l - 1].U, ty.lev[l].U, s))) return rc;
+    if ((rc = do_cycle<T>(h, l, ty.lev[l].U, ty.lev[l].F, false, s))) return rc;
+  }
+  return IGAMG_OK;
+}
+
+static __global__ void k_add_to3(int n, const double* __restrict__ E, double* __restrict__ U) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) U[i] += E[i];
+}
+
+// FP32 mode, one refinement step (R64 = F - K U on entry): FP32 V-cycle (with fmg: an FP32
+// full-multigrid pass) on K e = R64, then U += (curl psi(e), e_p, e_lambda) in FP64 and
+// R64 = F - K U with its norm.
+int do_ir_step(igamg3d_handle* h, double* U, const double* F, cudaStream_t s, bool fmg = false) {
   const int L = (int)h->d.lev.size();
   auto& top32 = h->f.lev[L - 1];
   double* R64 = h->d.lev[L - 1].R;
   const auto& Ld = h->d.lev[L - 1].L;
   const auto& lc = h->lc[L - 1];
   k_to_float<<<nblk(Ld.n_total), kBlock, 0, s>>>(Ld.n_total, R64, top32.F);
-  CK3(cudaMemsetAsync(top32.U, 0, Ld.n_total * sizeof(float), s));
-  int rc = do_vcycle<float>(h, top32.U, top32.F, s);
-  if (rc) return rc;
+  int rc;
+  if (fmg) {
+    if ((rc = do_fmg<float>(h, s))) return rc;
+  } else {
+    CK3(cudaMemsetAsync(top32.U, 0, Ld.n_total * sizeof(float), s));
+    if ((rc = do_vcycle<float>(h, top32.U, top32.F, s))) return rc;
+  }
   const int ni = Ld.ni, nq = Ld.nq;
   CK3(cudaMemsetAsync(h->psi + (size_t)2 * nq * ni * ni, 0, (size_t)nq * ni * ni * sizeof(double), s));
   k_lift3_z<<<nblk(2LL * ni * nq), kBlock, 0, s>>>(top32.L, lc.inv_dcoef, top32.U, h->psi, h->tot);
@@ -513,6 +562,20 @@ int do_step(igamg3d_handle* h, double* U, const double* F, cudaStream_t s) {
   return do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, h->norm2, s);
 }
 
+// first solve step with fmg (R64 = F - K U on entry): U += FMG(R64), then R64 and its norm.
+int do_fmg_step(igamg3d_handle* h, double* U, const double* F, cudaStream_t s) {
+  const int L = (int)h->d.lev.size();
+  if (fp32_base3(h->prob)) return do_ir_step(h, U, F, s, true);
+  auto& top = h->d.lev[L - 1];
+  const int n = top.L.n_total;
+  CK3(cudaMemcpyAsync(top.F, top.R, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  int rc = do_fmg<double>(h, s);
+  if (rc) return rc;
+  k_add_to3<<<nblk(n), kBlock, 0, s>>>(n, top.U, U);
+  if ((rc = launch_check())) return rc;
+  return do_residual<double>(h, L - 1, U, F, top.R, h->norm2, s);
+}
+
 int ensure_graph(igamg3d_handle* h, int kind, double* U, const double* F) {
   if (h->graph[kind] && h->gU[kind] == U && h->gF[kind] == F) return IGAMG_OK;
   if (h->graph[kind]) { cudaGraphExecDestroy(h->graph[kind]); h->graph[kind] = nullptr; }
@@ -522,7 +585,7 @@ int ensure_graph(igamg3d_handle* h, int kind, double* U, const double* F) {
   int rc = IGAMG_OK;
   if (kind == 1 && fp32_base3(h->prob))
     rc = do_residual<double>(h, L - 1, U, F, h->d.lev[L - 1].R, nullptr, h->cap_stream);
-  if (!rc) rc = do_step(h, U, F, h->cap_stream);
+  if (!rc) rc = kind == 2 ? do_fmg_step(h, U, F, h->cap_stream) : do_step(h, U, F, h->cap_stream);
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
   if (rc) { if (e == cudaSuccess) cudaGraphDestroy(g); return rc; }
   CK3(e);
@@ -552,6 +615,7 @@ int setup_cluster3(igamg3d_handle* h, Typed3<T>& ty) {
   ty.cluster_max = -1;
   const int L = (int)ty.lev.size();
   if (L < 2 || std::getenv("IGAMG_NO_CLUSTER")) return IGAMG_OK;
+  if (h->prob.gamma > 1) return IGAMG_OK;     // W-cycles run level by level
   int best = -1;
   for (int l = 1; l < L && l < kMaxFused3; ++l) best = l;
   if (best < 1) return IGAMG_OK;
@@ -647,6 +711,8 @@ int validate3(const igamg_problem& pr) {
   if (!(pr.sigma > 0) || !(pr.nu > 0) || pr.nu1 < 0 || pr.nu2 < 0) return IGAMG_EINVAL;
   if (pr.smoother != IGAMG_MULT) return IGAMG_EUNSUPPORTED;   // eq. ASM is not built in 3D
   if (pr.precision < IGAMG_FP64 || pr.precision > IGAMG_FGMRES_FP32) return IGAMG_EUNSUPPORTED;
+  if (pr.gamma < 0 || pr.gamma > 4 || pr.fmg < 0 || pr.fmg > 1) return IGAMG_EINVAL;
+  if (pr.fmg && pr.precision >= IGAMG_FGMRES_FP64) return IGAMG_EUNSUPPORTED;
   if (sizes3(pr.p, pr.n_fine).n_total > (1LL << 30)) return IGAMG_EINVAL;   // 32-bit row indices
   if (sizes3(pr.p, pr.n_fine >> (pr.n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
   return IGAMG_OK;
@@ -861,12 +927,13 @@ int h3_solve(igamg3d_handle* h, double* U, const double* F, double rtol, int max
   if ((rc = read_norm(h, &r0))) return rc;
   if (!std::isfinite(r0)) return IGAMG_ENONFINITE;
   if ((rc = ensure_graph(h, 0, U, F))) return rc;
+  if (h->prob.fmg && (rc = ensure_graph(h, 2, U, F))) return rc;
   int k = 0;
   double rk = r0;
   int status = IGAMG_NOT_CONVERGED;
   if (r0 == 0.0 || (atol >= 0 && r0 <= atol)) status = IGAMG_OK;
   while (status == IGAMG_NOT_CONVERGED && k < max_cycles) {
-    CK3(cudaGraphLaunch(h->graph[0], h->stream));
+    CK3(cudaGraphLaunch(h->graph[(k == 0 && h->prob.fmg) ? 2 : 0], h->stream));
     ++k;
     if ((rc = read_norm(h, &rk))) return rc;
     if (!std::isfinite(rk)) { status = IGAMG_ENONFINITE; break; }

@@ -26,16 +26,18 @@ class Solver:
 
     def __init__(self, p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.5, nu1=2, nu2=2,
                  c_penalty=0.0, precision=_lib.IGAMG_FP64, device="cuda", stream=None, beta=None, dim=2,
-                 restart=0):
+                 restart=0, gamma=1, fmg=False):
         """beta: advection at the quadrature points (host array (2, nG, nG)) for the
-        generalized Oseen problem, or None for generalized Stokes."""
+        generalized Oseen problem, or None for generalized Stokes.  gamma = 2 selects the
+        W-cycle; fmg starts every solve with one full-multigrid pass."""
         self.device = torch.device(device)
         if self.device.type != "cuda":
             raise RuntimeError("the igamg solver runs on a CUDA device only")
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
         self.problem = _lib.make_problem(p, n_fine, n_levels, sigma, nu, smoother, eta, nu1, nu2,
-                                         c_penalty, precision, beta=self._beta, dim=dim, restart=restart)
+                                         c_penalty, precision, beta=self._beta, dim=dim, restart=restart,
+                                         gamma=gamma, fmg=fmg)
         self.p, self.n_fine, self.n_levels, self.dim = p, n_fine, n_levels, dim
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

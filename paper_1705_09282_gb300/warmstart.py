@@ -99,6 +99,17 @@ def warm_start(solver, grid, psi_scale, p_scale, out=None):
     return U
 
 
+def warm_start_minres(solver, grid, psi_scale, p_scale, F, out=None):
+    """As warm_start, with the velocity and pressure fields scaled by the pair of factors
+    that minimises ||F - K U|| (igamg_warm_start_minres); returns (U, alpha, beta)."""
+    U = solver.empty() if out is None else out
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(lib().igamg_warm_start_minres(solver._h, _fptr(grid.contiguous()), float(psi_scale), float(p_scale),
+                                        ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(U.data_ptr()),
+                                        ctypes.byref(a), ctypes.byref(b)), "igamg_warm_start_minres")
+    return U, a.value, b.value
+
+
 def solve_abs(solver, U, F, atol, max_cycles=100):
     rep, hist = Solver._report(max_cycles)
     rc = check(lib().igamg_solve_abs(solver._h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(F.data_ptr()),
@@ -184,8 +195,12 @@ def train(net, problems, grids, steps, batch=8, lr=2e-3, seed=0, lr_final=None):
     return losses
 
 
-def predict_guesses(net, problems):
-    """Warm-start initial guesses U0 (written into each problem's U)."""
+def predict_guesses(net, problems, scaled=False):
+    """Warm-start initial guesses U0 (written into each problem's U); with scaled the two
+    predicted fields are rescaled against each problem's F (igamg_warm_start_minres)."""
     for pr in problems:
         g = net.forward(pr.x.unsqueeze(0).contiguous())[0]
-        warm_start(pr.solver, g, pr.scale, pr.p_scale, out=pr.U)
+        if scaled:
+            warm_start_minres(pr.solver, g, pr.scale, pr.p_scale, pr.F, out=pr.U)
+        else:
+            warm_start(pr.solver, g, pr.scale, pr.p_scale, out=pr.U)

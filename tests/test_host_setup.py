@@ -51,6 +51,12 @@ def test_bad_arguments_rejected_on_host():
     assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -2
     pr = _lib().make_problem(2, 8, 2, -1.0, 1.0)      # sigma <= 0
     assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -1
+    for dim in (2, 3):
+        pr = _lib().make_problem(2, 8, 2, 1.0, 1.0, dim=dim, gamma=5)   # at most 4 coarse cycles
+        assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -1
+        pr = _lib().make_problem(2, 8, 2, 1.0, 1.0, dim=dim, fmg=True,  # FMG is not an FGMRES option
+                                 precision=_lib().IGAMG_FGMRES_FP64)
+        assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -2
 
 
 @pytest.mark.parametrize("p,sigma,nu", [(2, 1.0, 1.0), (3, 100.0, 0.3), (2, 1e-4, 1.0)])
