@@ -696,6 +696,67 @@ def run_smoothers(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cycles(args):
+    """Cycle forms on the harder cases (the W-cycle and full multigrid that Sec. 5's opening
+    paragraph names, and FGMRES around the V-cycle): 2D generalized Stokes at 256 x 256,
+    7 grids, p = 2, 3, sigma/nu = 1e-4 and 1e4; generalized Oseen at 512 x 512, 8 grids,
+    nu = 1e-2, sigma = 1, max|beta| = 0.5 and 1 (Re = 50 and 100); GRF forcing, V(2,2)
+    multiplicative, FP64, zero guess, to 1e-8.  Set-up is not timed."""
+    import torch
+
+    from paper_1705_09282_gb300 import inputs
+    from paper_1705_09282_gb300._lib import IGAMG_FGMRES_FP64, IGAMG_FP32_IR, IGAMG_FP64, IgamgError
+    from paper_1705_09282_gb300.solver import Solver
+    stream = torch.cuda.current_stream()
+    forms = (("V", dict(gamma=1, fmg=False, precision=IGAMG_FP64)),
+             ("W", dict(gamma=2, fmg=False, precision=IGAMG_FP64)),
+             ("FMG+V", dict(gamma=1, fmg=True, precision=IGAMG_FP64)),
+             ("FMG+W", dict(gamma=2, fmg=True, precision=IGAMG_FP64)),
+             ("FGMRES(V)", dict(gamma=1, fmg=False, precision=IGAMG_FGMRES_FP64)),
+             ("FMG+V fp32-in-fp64", dict(gamma=1, fmg=True, precision=IGAMG_FP32_IR)))
+    cases = [("stokes p2 sigma1e-4", 2, N_FINE, N_LEVELS, 1e-4, 1.0, None, SEED),
+             ("stokes p3 sigma1e-4", 3, N_FINE, N_LEVELS, 1e-4, 1.0, None, SEED),
+             ("stokes p3 sigma1e4", 3, N_FINE, N_LEVELS, 1e4, 1.0, None, SEED),
+             ("oseen Re50", 2, 512, 8, 1.0, 1e-2, 0.5, 1707),
+             ("oseen Re100", 2, 512, 8, 1.0, 1e-2, 1.0, 1707)]
+    out = {}
+    for name, p, n, L, sigma, nu, bmax, seed in cases:
+        beta = inputs.oseen_advection(p, n, bmax) if bmax else None
+        f = torch.tensor(inputs.grf_forcing(p, n, seed=seed), device="cuda")
+        res = {}
+        for fname, kw in forms:
+            try:
+                S = Solver(p, n, L, sigma, nu, beta=beta, **kw)
+            except IgamgError as e:
+                res[fname] = {"error": str(e)}
+                continue
+            F = S.load_vector(f)
+            U = S.empty()
+            try:
+                for _ in range(args.warmup):
+                    U.zero_()
+                    S.solve(U, F, rtol=RTOL, max_cycles=100, history=False)
+                ts = []
+                for _ in range(args.steps):
+                    U.zero_()
+                    dt, rep = _timed(lambda: S.solve(U, F, rtol=RTOL, max_cycles=100, history=False), stream)
+                    ts.append(dt)
+                t = sum(ts) / len(ts)
+                res[fname] = {"converged": rep["converged"], "cycles": rep["cycles"], "solve_ms": 1e3 * t,
+                              "rel_residual": rep["rel_residual"], "div_inf": rep["div_inf"]}
+            except IgamgError as e:          # a divergent form reports a non-finite residual
+                res[fname] = {"converged": False, "error": str(e)}
+            S.close()
+        out[name] = res
+    line = {"metric": "solve time and cycles to 1e-8 for the V-, W- and full-multigrid cycles and FGMRES",
+            "workload": "cycles",
+            "config": {"workload": "2D generalized Stokes 256x256 (7 levels, p=2,3, sigma/nu=1e-4,1e4) and Oseen "
+                                   "512x512 (8 levels, nu=1e-2, sigma=1, max|beta|=0.5,1), GRF forcing, V(2,2) "
+                                   "multiplicative, zero guess, to 1e-8, set-up not timed"},
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -704,7 +765,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="stokes",
-                    choices=["stokes", "oseen", "batch", "cube", "cube-oseen", "smoothers"],
+                    choices=["stokes", "oseen", "batch", "cube", "cube-oseen", "smoothers", "cycles"],
                     help="stokes: the headline sweep (default); the others: extra measurements")
     ap.add_argument("--batch-count", type=int, default=1024)
     ap.add_argument("--train-count", type=int, default=384)
@@ -727,6 +788,8 @@ def main():
         run_smoothers(args)
     elif args.workload == "cube-oseen":
         run_cube_oseen(args)
+    elif args.workload == "cycles":
+        run_cycles(args)
     else:
         run_ours(args)
 

@@ -417,12 +417,15 @@ class Hierarchy:
     """Nested levels l = 0 (coarsest) .. L-1 (finest) with Galerkin coarse operators."""
 
     def __init__(self, p, n_fine, n_levels, sigma, nu, c_pen=None, beta=None,
-                 smoother="mult", eta=0.5, nu1=2, nu2=2, gamma=1):
+                 smoother="mult", eta=0.5, nu1=2, nu2=2, gamma=1, fine=None):
+        """fine: a prebuilt finest-level discretization (e.g. on a mapped domain) in place
+        of the unit square's; the coarse levels are its Galerkin products either way."""
         self.p, self.n_levels = p, n_levels
         self.smoother, self.eta, self.nu1, self.nu2 = smoother, eta, nu1, nu2
         self.gamma = gamma
         assert n_fine % (1 << (n_levels - 1)) == 0
-        fine = Stokes2D(p, n_fine, sigma, nu, c_pen=c_pen, beta=beta)
+        if fine is None:
+            fine = Stokes2D(p, n_fine, sigma, nu, c_pen=c_pen, beta=beta)
         self.fine = fine
         levels = [None] * n_levels
         Ps = [None] * n_levels

@@ -256,3 +256,59 @@ def oseen_forcing_3d(p, n, sigma, nu, beta):
             f[c] += coef * (beta[0] * fx.deriv()(X) * fy(Y) * fz(Z) + beta[1] * fx(X) * fy.deriv()(Y) * fz(Z)
                             + beta[2] * fx(X) * fy(Y) * fz.deriv()(Z))
     return np.ascontiguousarray(f)
+
+
+# ---- quarter annulus (Sec. 6.2's domain: r_i = 0.075, r_o = 0.225) ------------------------
+# Manufactured solution given directly in physical coordinates: u = curl psi with the
+# polynomial psi = c (x y g1 g2)^2, g1 = x^2 + y^2 - r_i^2, g2 = r_o^2 - x^2 - y^2, which
+# vanishes with its gradient on all four walls (so u = 0 there and div u = 0), and the
+# zero-mean pressure p = x y - (r_i^2 + r_o^2) / (2 pi).  Fields are evaluated at given
+# physical points (x, y arrays of any shape).
+
+ANNULUS_RI, ANNULUS_RO = 0.075, 0.225
+
+
+def _pmul(a, b):
+    out = np.zeros((a.shape[0] + b.shape[0] - 1, a.shape[1] + b.shape[1] - 1))
+    for i in range(a.shape[0]):
+        for j in range(a.shape[1]):
+            if a[i, j] != 0.0:
+                out[i: i + b.shape[0], j: j + b.shape[1]] += a[i, j] * b
+    return out
+
+
+def _annulus_psi_coeffs(r_i, r_o):
+    """Coefficients c[i, j] of x^i y^j of psi, scaled so that max |u| is about 1."""
+    xy = np.zeros((2, 2)); xy[1, 1] = 1.0
+    g1 = np.zeros((3, 3)); g1[2, 0] = g1[0, 2] = 1.0; g1[0, 0] = -r_i * r_i
+    g2 = np.zeros((3, 3)); g2[2, 0] = g2[0, 2] = -1.0; g2[0, 0] = r_o * r_o
+    b = _pmul(_pmul(xy, g1), g2)
+    c = _pmul(b, b)
+    return c / (r_o ** 12) * 8.0
+
+
+def _pder(c, axis, k=1):
+    from numpy.polynomial import polynomial as P
+    return P.polyder(c, m=k, axis=axis)
+
+
+def _pval(c, x, y):
+    from numpy.polynomial import polynomial as P
+    return P.polyval2d(x, y, c)
+
+
+def annulus_solution(x, y, r_i=ANNULUS_RI, r_o=ANNULUS_RO):
+    """(u (2, ...), p (...)) of the manufactured quarter-annulus solution at (x, y)."""
+    c = _annulus_psi_coeffs(r_i, r_o)
+    u = np.stack([_pval(_pder(c, 1), x, y), -_pval(_pder(c, 0), x, y)])
+    p = x * y - (r_i * r_i + r_o * r_o) / (2.0 * np.pi)
+    return u, p
+
+
+def annulus_forcing(x, y, sigma, nu, r_i=ANNULUS_RI, r_o=ANNULUS_RO):
+    """f = sigma u - nu lap u + grad p (generalized Stokes, Sec. 3.1) at (x, y): (2, ...)."""
+    c = _annulus_psi_coeffs(r_i, r_o)
+    ux, uy = _pder(c, 1), -_pder(c, 0)
+    fx = sigma * _pval(ux, x, y) - nu * (_pval(_pder(ux, 0, 2), x, y) + _pval(_pder(ux, 1, 2), x, y)) + y
+    fy = sigma * _pval(uy, x, y) - nu * (_pval(_pder(uy, 0, 2), x, y) + _pval(_pder(uy, 1, 2), x, y)) + x
+    return np.stack([fx, fy])

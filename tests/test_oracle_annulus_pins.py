@@ -1,0 +1,146 @@
+"""Pins for the mapped-domain oracle (Sec. 4.4 push-forwards, Sec. 6.2 quarter annulus):
+the identity map reproduces the unit-square oracle, the map is the quarter annulus, the
+pushed-forward spaces keep the discrete complex, the discrete solution converges to a
+closed-form solution at the expected rates, and the V-cycle counts follow the paper's
+quarter-annulus table."""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import annulus2d as A
+from oracle import bspline as bs
+from oracle import stokes2d as o2
+from paper_1705_09282_gb300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.txt")
+
+
+def _table(name):
+    rows, cur = {}, None
+    for line in open(GOLD):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.isalpha() or line.startswith("table"):
+            cur = line
+            rows[cur] = []
+            continue
+        rows[cur].append([int(v) for v in line.split()])
+    return rows[name]
+
+
+GEOM = A.QuarterAnnulus()
+
+
+def test_map_is_the_quarter_annulus():
+    t = np.linspace(0, 1, 41)
+    for xi, r in ((0.0, 0.075), (1.0, 0.225), (0.5, 0.15)):
+        X, _, _ = GEOM.eval(np.full_like(t, xi), t)
+        assert np.allclose(np.hypot(X[:, 0], X[:, 1]), r, atol=1e-15)
+        assert X[0, 1] == 0.0 and abs(X[-1, 0]) < 1e-16          # eta = 0: x axis, eta = 1: y axis
+        ang = np.arctan2(X[:, 1], X[:, 0])
+        assert np.all(np.diff(ang) > 0) and abs(ang[-1] - np.pi / 2) < 1e-15
+    # first and second derivatives against central differences
+    rng = np.random.default_rng(0)
+    xi, eta = rng.uniform(0.1, 0.9, 20), rng.uniform(0.1, 0.9, 20)
+    X, DF, dDF = GEOM.eval(xi, eta)
+    h = 1e-6
+    for k, (dxi, deta) in enumerate(((h, 0.0), (0.0, h))):
+        Xp, DFp, _ = GEOM.eval(xi + dxi, eta + deta)
+        Xm, DFm, _ = GEOM.eval(xi - dxi, eta - deta)
+        assert np.allclose((Xp - Xm) / (2 * h), DF[:, :, k], atol=1e-8)
+        assert np.allclose((DFp - DFm) / (2 * h), dDF[:, :, :, k], atol=1e-7)
+    assert np.all(np.linalg.det(DF) > 0)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_identity_map_reproduces_the_unit_square(p):
+    n = 6
+    S0 = o2.Stokes2D(p, n, 1.3, 0.7)
+    S1 = A.MappedStokes2D(p, n, 1.3, 0.7, A.IdentityMap())
+    assert abs(S0.K - S1.K).max() <= 1e-14 * abs(S0.K).max()
+    f = np.random.default_rng(1).standard_normal((2, n * (p + 2), n * (p + 2)))
+    assert np.abs(S0.load_vector(f) - S1.load_vector(f)).max() <= 1e-15
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_pushed_forward_spaces_keep_the_complex(p):
+    # div of the Piola map of a curl is (1/det J) divhat curlhat = 0, so B curl psi = 0;
+    # the velocity block is symmetric and the divergence pairing is -B / B^T
+    n = 6
+    S = A.MappedStokes2D(p, n, 1.0, 1.0, GEOM)
+    psi = np.random.default_rng(2).standard_normal(S.n_psi_interior())
+    Uc = S.curl(psi)
+    assert np.abs((S.K @ Uc)[S.n_u: S.n_u + S.n_p]).max() <= 1e-13 * np.abs(Uc).max()
+    Au = S.K[: S.n_u, : S.n_u]
+    assert abs(Au - Au.T).max() <= 1e-13 * abs(Au).max()
+    Bup = S.K[: S.n_u, S.n_u: S.n_u + S.n_p]
+    Bpu = S.K[S.n_u: S.n_u + S.n_p, : S.n_u]
+    assert abs(Bup + Bpu.T).max() <= 1e-14 * abs(Bup).max()
+    # positive definite on divergence-free velocities
+    A_ = Au.toarray()
+    C = np.stack([S.curl(np.eye(S.n_psi_interior())[k])[: S.n_u] for k in range(S.n_psi_interior())], 1)
+    assert np.linalg.eigvalsh(C.T @ A_ @ C).min() > 0
+
+
+def _l2_velocity_error(S, U):
+    p, n = S.p, S.n
+    g, w = bs.gauss_legendre(p + 4)
+    xs = ((np.arange(n)[:, None] + g[None, :]) / n).ravel()
+    ws = np.tile(w / n, n)
+    XI, ETA = np.meshgrid(xs, xs, indexing="xy")
+    uh, X = S.velocity_at(U, XI.ravel(), ETA.ravel())
+    ue, _ = inputs.annulus_solution(X[:, 0], X[:, 1])
+    _, DF, _ = GEOM.eval(XI.ravel(), ETA.ravel())
+    W = (ws[None, :] * ws[:, None]).ravel() * np.linalg.det(DF)
+    return np.sqrt(np.sum(W * np.sum((uh - ue.T) ** 2, axis=1)) / np.sum(W * np.sum(ue.T ** 2, axis=1)))
+
+
+@pytest.mark.parametrize("p,sigma,nu", [(2, 1.0, 1.0), (3, 1.0, 1.0), (2, 1000.0, 1.0)])
+def test_manufactured_convergence_on_the_annulus(p, sigma, nu):
+    errs = []
+    for n in (8, 16):
+        S = A.MappedStokes2D(p, n, sigma, nu, GEOM)
+        X = S.quad_points_xy()
+        F = S.load_vector(inputs.annulus_forcing(X[0], X[1], sigma, nu))
+        U = spla.spsolve(S.K.tocsc(), F)
+        errs.append(_l2_velocity_error(S, U))
+        assert S.div_inf(U) <= 1e-10 * np.abs(U[: S.n_u]).max()
+        assert abs(S.m @ U) <= 1e-12                           # zero-mean pressure
+    rate = np.log2(errs[0] / errs[1])
+    assert p - 0.35 <= rate <= p + 0.6, (rate, errs)
+    assert errs[1] < 0.1
+
+
+def test_paper_annulus_cycle_counts_loosely():
+    # Sec. 6.2's quarter-annulus table: V(1,2), multiplicative, random divergence-free guess,
+    # 1e6 reduction, coarsest mesh one element.  The paper leaves the map's parametrisation,
+    # the Nitsche length on curved walls and the guess open; the counts grow with the levels
+    # as printed (2 -> 24 over n_l = 1..5) and stay within 3 of them
+    for row in _table("tableannulus")[1:5]:
+        nl, da1, da1000 = row[0], row[2], row[3]
+        n = 2 ** nl
+        for sigma, want in ((1.0, da1), (1000.0, da1000)):
+            fine = A.MappedStokes2D(2, n, sigma, 1.0, GEOM)
+            H = o2.Hierarchy(2, n, nl + 1, sigma, 1.0, nu1=1, nu2=2, fine=fine)
+            psi, pr = inputs.random_divfree_guess(2, n, seed=nl)
+            U = fine.curl(psi)
+            U[fine.n_u: fine.n_u + fine.n_p] = pr
+            X = fine.quad_points_xy()
+            F = fine.load_vector(inputs.annulus_forcing(X[0], X[1], sigma, 1.0))
+            k, _ = H.solve(U, F, 1e-6, 60)
+            assert abs(k - want) <= 3, (nl, sigma, k, want)
+
+
+def test_vcycles_on_the_annulus_converge_to_direct_solve():
+    p, n = 2, 8
+    fine = A.MappedStokes2D(p, n, 1.0, 1.0, GEOM)
+    H = o2.Hierarchy(p, n, 3, 1.0, 1.0, fine=fine)
+    X = fine.quad_points_xy()
+    F = fine.load_vector(inputs.annulus_forcing(X[0], X[1], 1.0, 1.0))
+    Ux = spla.spsolve(fine.K.tocsc(), F)
+    U = np.zeros_like(F)
+    H.solve(U, F, 1e-14, 120)
+    assert np.abs(U - Ux).max() <= 1e-11 * np.abs(Ux).max()
