@@ -90,7 +90,22 @@ typedef struct {
                          solved exactly, one cycle per finer level from the prolongated
                          coarser solution), U += its result; it counts as one cycle.
                          Not with the FGMRES precisions (IGAMG_EUNSUPPORTED). */
+  int geometry;       /* IGAMG_GEOM_SQUARE (unit square / cube) or, 2D generalized Stokes
+                         only, IGAMG_GEOM_QUARTER_ANNULUS (Sec. 6.2's domain) */
+  double r_inner, r_outer; /* quarter annulus radii; <= 0 selects 0.075 and 0.225 */
 } igamg_problem;
+
+/* Domains.  The quarter annulus {r_inner <= |x| <= r_outer, x, y >= 0} is the image of the
+ * unit square under F(xi, eta) = (r_inner + (r_outer - r_inner) xi) C(eta), C the rational
+ * quadratic Bezier quarter circle (control points (1,0), (1,1), (0,1), weights 1, 1/sqrt(2),
+ * 1): xi is radial, eta angular.  The discrete spaces are the push-forwards of Sec. 4.4
+ * (velocity by the contravariant Piola map, pressure by 1/det J), so U keeps the unit
+ * square's layout of parametric coefficients, div u = (1/det J) div_hat u_hat stays exactly
+ * zero, and the curl / streamfunction entry points act on the same coefficients.  The
+ * operator has variable coefficients and couples u_x with u_y; it is assembled on the host
+ * at creation (Nitsche terms on all four walls with h = the element height normal to the
+ * wall), the coarse operators are Galerkin products and every patch has its own inverse. */
+enum { IGAMG_GEOM_SQUARE = 0, IGAMG_GEOM_QUARTER_ANNULUS = 1 };
 
 typedef struct {
   int n;              /* elements per direction on this level */
@@ -132,7 +147,15 @@ int igamg_get_sizes(const igamg_handle* h, int level, igamg_sizes* out);
  * f and beta are sampled at their tensor products, layout (2, n*G, n*G) [comp][y][x]. */
 int igamg_quad_points(const igamg_handle* h, double* x, size_t cap, size_t* n_out);
 
-/* F = (l(v), 0, 0), l(v) = int v.f (Sec. 3.1), f at the quadrature points (device). */
+/* Physical coordinates of the finest level's quadrature points, (2, n*G, n*G) [x or y][eta
+ * point][xi point] (host, capacity cap >= *n_out = 2 (n*G)^2): on the unit square the tensor
+ * products of igamg_quad_points, on the quarter annulus their images under the map.  2D only
+ * (IGAMG_EUNSUPPORTED for a 3D handle). */
+int igamg_quad_points_xy(const igamg_handle* h, double* xy, size_t cap, size_t* n_out);
+
+/* F = (l(v), 0, 0), l(v) = int v.f (Sec. 3.1), f at the quadrature points (device), layout
+ * (2, n*G, n*G).  On the quarter annulus f is the physical field at the points of
+ * igamg_quad_points_xy and l(v) = int (J^T f) . v_hat dxi (Sec. 4.4 push-forward). */
 int igamg_load_vector(igamg_handle* h, const double* f_qp, double* F);
 
 /* R = F - K_l U on level l (Sec. 3.4; coarse K_l = R K P, Sec. 5.1).  If norm_out is

@@ -13,6 +13,7 @@ IGAMG_OK = 0
 IGAMG_NOT_CONVERGED = 1
 IGAMG_MULT, IGAMG_ADD = 0, 1
 IGAMG_FP64, IGAMG_FP32_IR, IGAMG_FGMRES_FP64, IGAMG_FGMRES_FP32 = 0, 1, 2, 3
+IGAMG_GEOM_SQUARE, IGAMG_GEOM_QUARTER_ANNULUS = 0, 1
 
 
 class Problem(ctypes.Structure):
@@ -21,7 +22,8 @@ class Problem(ctypes.Structure):
                 ("c_penalty", ctypes.c_double), ("beta_qp", ctypes.c_void_p),
                 ("smoother", ctypes.c_int), ("eta", ctypes.c_double), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("precision", ctypes.c_int), ("restart", ctypes.c_int),
-                ("gamma", ctypes.c_int), ("fmg", ctypes.c_int)]
+                ("gamma", ctypes.c_int), ("fmg", ctypes.c_int), ("geometry", ctypes.c_int),
+                ("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double)]
 
 
 class Sizes(ctypes.Structure):
@@ -47,6 +49,7 @@ SIGNATURES = {
     "igamg_strerror": (ctypes.c_char_p, [_I]),
     "igamg_get_sizes": (_I, [_P, _I, ctypes.POINTER(Sizes)]),
     "igamg_quad_points": (_I, [_P, _P, _SZ, ctypes.POINTER(_SZ)]),
+    "igamg_quad_points_xy": (_I, [_P, _P, _SZ, ctypes.POINTER(_SZ)]),
     "igamg_load_vector": (_I, [_P, _P, _P]),
     "igamg_residual": (_I, [_P, _I, _P, _P, _P, _P]),
     "igamg_smooth": (_I, [_P, _I, _P, _P, _I]),
@@ -117,7 +120,8 @@ def check(code, where):
 
 
 def make_problem(p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.5, nu1=2, nu2=2,
-                 c_penalty=0.0, precision=IGAMG_FP64, beta=None, dim=2, restart=0, gamma=1, fmg=False):
+                 c_penalty=0.0, precision=IGAMG_FP64, beta=None, dim=2, restart=0, gamma=1, fmg=False,
+                 geometry=IGAMG_GEOM_SQUARE, r_inner=0.0, r_outer=0.0):
     pr = Problem()
     pr.dim, pr.p, pr.n_fine, pr.n_levels = dim, p, n_fine, n_levels
     pr.sigma, pr.nu, pr.c_penalty = float(sigma), float(nu), float(c_penalty)
@@ -125,4 +129,5 @@ def make_problem(p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.5, nu1=2
     pr.smoother = IGAMG_ADD if smoother == "add" else IGAMG_MULT
     pr.eta, pr.nu1, pr.nu2, pr.precision, pr.restart = float(eta), nu1, nu2, precision, restart
     pr.gamma, pr.fmg = gamma, int(bool(fmg))
+    pr.geometry, pr.r_inner, pr.r_outer = geometry, float(r_inner), float(r_outer)
     return pr

@@ -119,6 +119,16 @@ __global__ void k_dots5_finish(int nb, const double* __restrict__ part, double* 
   out[threadIdx.x] = t;
 }
 
+// mapped domains: the parametric load J^T f at every quadrature point (f and fh may alias)
+__global__ void k_pullback(int npts, const double* __restrict__ jt, const double* f, double* fh) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npts) return;
+  const double fx = f[i], fy = f[npts + i];
+  const double* t = jt + (size_t)4 * i;              // t[2k + c] = dX_c / dxi_k
+  fh[i] = t[0] * fx + t[1] * fy;
+  fh[npts + i] = t[2] * fx + t[3] * fy;
+}
+
 // U = a U + b Z
 __global__ void k_axpby(int n, double a, double b, const double* __restrict__ Z, double* __restrict__ U) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -235,6 +245,7 @@ struct igamg_handle {
   igamg3d_handle* d3 = nullptr;        // dim = 3: everything lives in the 3D driver
   KrylovWork kw;                       // FGMRES modes
   double* zeros = nullptr;             // a zero right-hand side (K z = -(0 - K z))
+  double* jt = nullptr;                // mapped domains: J^T at the finest quadrature points
   double* dots = nullptr;              // warm-start scalings: 5 x kDotGrid partials, then 5 sums
 };
 
@@ -752,9 +763,11 @@ int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max
 }
 
 template <typename T>
-LevelTab<T> make_tab(const igamg_sizes& sz, int p, const T* sx, const T* sy, const T* sp, const T* srow = nullptr) {
+LevelTab<T> make_tab(const igamg_sizes& sz, int p, const T* sx, const T* sy, const T* sp, const T* srow = nullptr,
+                     const T* sext = nullptr) {
   LevelTab<T> L{};
   L.srow = srow;
+  L.sext = sext;
   int n = sz.n;
   L.n = n; L.nxu = n + p - 2; L.npd = n + p - 1; L.nint = n + p - 2; L.lastp = n + p - 1; L.lastq = n + p - 2;
   L.n_ux = (int)sz.n_ux; L.n_uy = (int)sz.n_uy; L.n_p = (int)sz.n_p; L.n_total = (int)sz.n_total;
@@ -971,10 +984,11 @@ int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
   for (int l = 0; l < L; ++l) {
     auto& lh = h->host.lev[l];
     auto& tl = ty.lev[l];
-    T *sx, *sy, *sp, *srow = nullptr;
+    T *sx, *sy, *sp, *srow = nullptr, *sext = nullptr;
     if ((rc = upload_as(h, &sx, lh.st.sx)) || (rc = upload_as(h, &sy, lh.st.sy)) || (rc = upload_as(h, &sp, lh.st.sp))) return rc;
     if (!lh.rows.empty() && (rc = upload_as(h, &srow, lh.rows))) return rc;
-    tl.L = make_tab<T>(lh.sz, p, sx, sy, sp, srow);
+    if (!lh.ext.empty() && (rc = upload_as(h, &sext, lh.ext))) return rc;
+    tl.L = make_tab<T>(lh.sz, p, sx, sy, sp, srow, sext);
     if (l >= 1) {
       if ((rc = upload_as(h, &tl.cinv, lh.pt.cinv))) return rc;
       if ((rc = upload_as(h, &tl.cinv8, lh.pt.cinv8))) return rc;
@@ -1028,6 +1042,12 @@ int validate(const igamg_problem& pr) {
   if (pr.precision < IGAMG_FP64 || pr.precision > IGAMG_FGMRES_FP32) return IGAMG_EUNSUPPORTED;
   if (pr.gamma < 0 || pr.gamma > 4 || pr.fmg < 0 || pr.fmg > 1) return IGAMG_EINVAL;
   if (pr.fmg && pr.precision >= IGAMG_FGMRES_FP64) return IGAMG_EUNSUPPORTED;
+  if (pr.geometry < IGAMG_GEOM_SQUARE || pr.geometry > IGAMG_GEOM_QUARTER_ANNULUS) return IGAMG_EINVAL;
+  if (pr.geometry == IGAMG_GEOM_QUARTER_ANNULUS) {
+    if (pr.beta_qp) return IGAMG_EUNSUPPORTED;                 // generalized Stokes only
+    const double ri = pr.r_inner > 0 ? pr.r_inner : 0.075, ro = pr.r_outer > 0 ? pr.r_outer : 0.225;
+    if (!(ri > 0) || !(ro > ri) || !std::isfinite(ro)) return IGAMG_EINVAL;
+  }
   if (pr.n_fine > 8192) return IGAMG_EINVAL;
   // the coarsest grid is solved with a dense inverse held in shared memory by one block
   if (level_sizes(pr.p, pr.n_fine >> (pr.n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
@@ -1126,6 +1146,7 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
   size_t nint = (size_t)(pr.n_fine + p - 2);
   if ((rc = dmalloc(h, (void**)&h->psi, nint * nint * sizeof(double)))) return fail(rc);
   if (cudaMallocHost((void**)&h->h_pinned, 2 * sizeof(double)) != cudaSuccess) return fail(IGAMG_ECUDA);
+  if (!h->host.jt.empty() && (rc = upload_as(h, &h->jt, h->host.jt))) return fail(rc);
   if ((rc = autotune_fused<double>(h, h->d))) return fail(rc);
   if (fp32_base(pr) && (rc = autotune_fused<float>(h, h->f))) return fail(rc);
   if (pr.precision >= IGAMG_FGMRES_FP64 &&
@@ -1176,9 +1197,31 @@ int igamg_load_vector(igamg_handle* h, const double* f_qp, double* F) {
   if (!h || !f_qp || !F) return IGAMG_EINVAL;
   if (h->d3) return h3_load_vector(h->d3, f_qp, F);
   auto& Lt = h->d.lev.back().L;
+  if (h->jt) {                                       // mapped domain: load J^T f
+    const int npts = h->prob.n_fine * (h->prob.p + 2) * h->prob.n_fine * (h->prob.p + 2);
+    k_pullback<<<nblk(npts), kBlock, 0, h->stream>>>(npts, h->jt, f_qp, h->f_dev);
+    f_qp = h->f_dev;
+  }
   if (h->prob.p == 2) k_load<2><<<nblk(Lt.n_total), kBlock, 0, h->stream>>>(Lt, h->lv_p, h->lv_q, f_qp, F);
   else k_load<3><<<nblk(Lt.n_total), kBlock, 0, h->stream>>>(Lt, h->lv_p, h->lv_q, f_qp, F);
   return launch_check();
+}
+
+int igamg_quad_points_xy(const igamg_handle* h, double* xy, size_t cap, size_t* n_out) {
+  if (!h || !n_out) return IGAMG_EINVAL;
+  if (h->d3) return IGAMG_EUNSUPPORTED;
+  const std::vector<double>& qx = h->host.quad_x;
+  const size_t nG = qx.size();
+  *n_out = 2 * nG * nG;
+  if (!xy) return IGAMG_OK;
+  if (cap < 2 * nG * nG) return IGAMG_EINVAL;
+  if (!h->host.quad_xy.empty()) {
+    std::memcpy(xy, h->host.quad_xy.data(), 2 * nG * nG * sizeof(double));
+  } else {
+    for (size_t iy = 0; iy < nG; ++iy)
+      for (size_t ix = 0; ix < nG; ++ix) { xy[iy * nG + ix] = qx[ix]; xy[nG * nG + iy * nG + ix] = qx[iy]; }
+  }
+  return IGAMG_OK;
 }
 
 int igamg_residual(igamg_handle* h, int level, const double* U, const double* F, double* R, double* norm_out) {
@@ -1384,7 +1427,8 @@ extern "C" int igamg_residual_static(const igamg_problem* prob, int level, const
                                      void* cuda_stream) {
   if (!prob || !U || !F || !R) return IGAMG_EINVAL;
   const igamg_problem& pr = *prob;
-  if (pr.dim != 2 || (pr.p != 2 && pr.p != 3) || pr.beta_qp) return IGAMG_EUNSUPPORTED;  // Stokes only
+  if (pr.dim != 2 || (pr.p != 2 && pr.p != 3) || pr.beta_qp || pr.geometry != IGAMG_GEOM_SQUARE)
+    return IGAMG_EUNSUPPORTED;                                // Stokes on the unit square only
   if (pr.n_levels < 1 || pr.n_levels > 16 || pr.n_fine < 1 || pr.n_fine > 8192) return IGAMG_EINVAL;
   if (pr.n_fine % (1 << (pr.n_levels - 1))) return IGAMG_EINVAL;
   if (level < 0 || level >= pr.n_levels || !(pr.sigma > 0) || !(pr.nu > 0)) return IGAMG_EINVAL;
@@ -1459,7 +1503,8 @@ extern "C" int igamg_host_operator_rows(const igamg_problem* prob, int level, do
   if ((rc = build_hierarchy(*prob, H, err))) return rc;
   const auto& lh = H.lev[level];
   LevelTab<double> L = make_tab<double>(lh.sz, prob->p, lh.st.sx.data(), lh.st.sy.data(), lh.st.sp.data(),
-                                        lh.rows.empty() ? nullptr : lh.rows.data());
+                                        lh.rows.empty() ? nullptr : lh.rows.data(),
+                                        lh.ext.empty() ? nullptr : lh.ext.data());
   long long n = lh.sz.n_total;
   if (n_out) *n_out = n;
   if (!K) return IGAMG_OK;
@@ -1495,7 +1540,8 @@ extern "C" int igamg_host_operator_apply(const igamg_problem* prob, int level, c
   const auto& lh = H.lev[level];
   if (n != (size_t)lh.sz.n_total) return IGAMG_EINVAL;
   LevelTab<double> L = make_tab<double>(lh.sz, prob->p, lh.st.sx.data(), lh.st.sy.data(), lh.st.sp.data(),
-                                        lh.rows.empty() ? nullptr : lh.rows.data());
+                                        lh.rows.empty() ? nullptr : lh.rows.data(),
+                                        lh.ext.empty() ? nullptr : lh.ext.data());
   double lam = 0.0;
   for (size_t i = 0; i + 1 < n; ++i) {
     KV[i] = prob->p == 2 ? row_KU<2, double>(L, V, (int)i) : row_KU<3, double>(L, V, (int)i);

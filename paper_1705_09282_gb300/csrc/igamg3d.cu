@@ -712,6 +712,7 @@ int validate3(const igamg_problem& pr) {
   if (pr.smoother != IGAMG_MULT) return IGAMG_EUNSUPPORTED;   // eq. ASM is not built in 3D
   if (pr.precision < IGAMG_FP64 || pr.precision > IGAMG_FGMRES_FP32) return IGAMG_EUNSUPPORTED;
   if (pr.gamma < 0 || pr.gamma > 4 || pr.fmg < 0 || pr.fmg > 1) return IGAMG_EINVAL;
+  if (pr.geometry != IGAMG_GEOM_SQUARE) return IGAMG_EUNSUPPORTED;   // the unit cube only
   if (pr.fmg && pr.precision >= IGAMG_FGMRES_FP64) return IGAMG_EUNSUPPORTED;
   if (sizes3(pr.p, pr.n_fine).n_total > (1LL << 30)) return IGAMG_EINVAL;   // 32-bit row indices
   if (sizes3(pr.p, pr.n_fine >> (pr.n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;

@@ -104,6 +104,9 @@ struct LevelHost {
   // coefficients per row (rows 0 .. n_total-2, same layout as the class records); empty
   // when the class stencils describe the level.
   std::vector<double> rows;
+  // Mapped domains only (empty otherwise): per velocity row (0 .. n_ux+n_uy-1) the 2p x 2p
+  // coefficients coupling it to the other velocity component (the third box of the record).
+  std::vector<double> ext;
 };
 
 struct HierarchyHost {
@@ -119,6 +122,11 @@ struct HierarchyHost {
   int G = 0;
   std::vector<double> lv_p, lv_q;      // (n+p)*(p+1)*G and (n+q)*(q+1)*G
   std::vector<double> quad_x;          // n*G abscissae (finest level)
+  // mapped domains: the finest level's quadrature points in physical coordinates, (2, nG, nG)
+  // [component][eta point][xi point], and J^T there, (nG, nG, 2, 2) [.][.][k][i] = dX_i/dxi_k,
+  // which turns f into the parametric load (J^T f)
+  int geometry = 0;
+  std::vector<double> quad_xy, jt;
 };
 
 // Builds everything; returns IGAMG_OK or an error code with a message in err.

@@ -19,6 +19,8 @@ struct LevelTab {
   int n_ux, n_uy, n_p, n_total;
   const T *sx, *sy, *sp;                 // class stencils (see Stencils in igamg_internal.h)
   const T* srow;                         // per-row records (general operators), or null
+  const T* sext;                         // mapped domains: per velocity row, the 2p x 2p
+                                         // coefficients on the other velocity component, or null
 };
 
 template <typename T>
@@ -107,6 +109,21 @@ __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __re
       acc2 = fma(st[B0 + j], U[b1_base + y * L.npd + x], acc2);
     }
     acc = fma(st[RU - 1], U[L.n_total - 1], acc);
+    if (L.sext && !is_p) {
+      // third box (mapped domains): u_x row -> u_y columns (x - P .. x + Q, y - Q .. y + P),
+      // u_y row -> u_x columns (x - Q .. x + P, y - P .. y + Q); clamped positions carry 0
+      constexpr int W2 = 2 * P;
+      const T* se = L.sext + (size_t)g * (W2 * W2);
+      const int ox = is_x ? -P : -Q, oy = is_x ? -Q : -P;
+#pragma unroll
+      for (int j = 0; j < W2 * W2; ++j) {
+        int dx = j / W2, dy = j - dx * W2;
+        int cx = ix + ox + dx, cy = iy + oy + dy;
+        int idx = is_x ? L.n_ux + (clampi(cy, 1, L.nint) - 1) * L.npd + clampi(cx, 0, L.lastq)
+                       : clampi(cy, 0, L.lastq) * L.nxu + clampi(cx, 1, L.nint) - 1;
+        acc2 = fma(se[j], U[idx], acc2);
+      }
+    }
   }
   return acc + acc2;
 }

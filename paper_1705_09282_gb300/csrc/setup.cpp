@@ -409,14 +409,266 @@ void add_advection(int p, const LevelHost& lv, const double* beta, std::vector<d
         }
 }
 
+// ---- mapped domains (Sec. 4.4 push-forwards; Sec. 6.2's quarter annulus) ----------------
+// Third record box of a velocity row: its coupling to the other velocity component,
+// 2p x 2p entries.  u_x row (x, y) -> u_y column (x + dx, y + dy), dx in [-p, q],
+// dy in [-q, p]; u_y row -> u_x column, dx in [-q, p], dy in [-p, q].
+int ext_index(int p, const Dof& r, const Dof& c) {
+  const int q = p - 1, W = 2 * p;
+  const int dx = c.x - r.x, dy = c.y - r.y;
+  if (r.blk == 0 && c.blk == 1 && dx >= -p && dx <= q && dy >= -q && dy <= p) return (dx + p) * W + dy + q;
+  if (r.blk == 1 && c.blk == 0 && dx >= -q && dx <= p && dy >= -p && dy <= q) return (dx + q) * W + dy + p;
+  return -1;
+}
+
+Dof ext_col(const igamg_sizes& s, int p, const Dof& r, int e) {
+  const int q = p - 1, W = 2 * p, nint = s.n + p - 2, lastq = s.n + q - 1;
+  Dof c{-1, 0, 0};
+  if (r.blk == 0) {
+    c = {1, r.x + e / W - p, r.y + e % W - q};
+    if (c.x < 0 || c.x > lastq || c.y < 1 || c.y > nint) c.blk = -1;
+  } else if (r.blk == 1) {
+    c = {0, r.x + e / W - q, r.y + e % W - p};
+    if (c.x < 1 || c.x > nint || c.y < 0 || c.y > lastq) c.blk = -1;
+  }
+  return c;
+}
+
+// F(xi, eta) = r(xi) C(eta), r = ri + (ro - ri) xi, C the rational quadratic Bezier quarter
+// circle (control points (1,0), (1,1), (0,1), weights 1, 1/sqrt(2), 1).  X[i], DF[i][k] =
+// dX_i/dxi_k, D2[i][k][l] = d^2 X_i / dxi_k dxi_l.
+void annulus_map(double ri, double ro, double xi, double eta, double X[2], double DF[2][2], double D2[2][2][2]) {
+  const double w = std::sqrt(0.5), t = eta, u = 1.0 - eta;
+  // homogeneous numerator N(t) and weight W(t) with their derivatives
+  const double Nx = u * u + w * 2 * t * u, Ny = w * 2 * t * u + t * t;
+  const double dNx = -2 * u + w * (2 - 4 * t), dNy = w * (2 - 4 * t) + 2 * t;
+  const double ddNx = 2 - 4 * w, ddNy = -4 * w + 2;
+  const double Wt = u * u + w * 2 * t * u + t * t, dW = -2 * u + w * (2 - 4 * t) + 2 * t, ddW = 4 - 4 * w;
+  const double C[2] = {Nx / Wt, Ny / Wt};
+  const double A[2] = {dNx * Wt - Nx * dW, dNy * Wt - Ny * dW};          // C' = A / W^2
+  const double dA[2] = {ddNx * Wt - Nx * ddW, ddNy * Wt - Ny * ddW};
+  double dC[2], ddC[2];
+  for (int i = 0; i < 2; ++i) {
+    dC[i] = A[i] / (Wt * Wt);
+    ddC[i] = dA[i] / (Wt * Wt) - 2 * A[i] * dW / (Wt * Wt * Wt);
+  }
+  const double dr = ro - ri, r = ri + dr * xi;
+  for (int i = 0; i < 2; ++i) {
+    X[i] = r * C[i];
+    DF[i][0] = dr * C[i];
+    DF[i][1] = r * dC[i];
+    D2[i][0][0] = 0.0;
+    D2[i][0][1] = D2[i][1][0] = dr * dC[i];
+    D2[i][1][1] = r * ddC[i];
+  }
+}
+
+namespace {
+// Values and physical gradients of the pushed-forward velocity basis v = N a_c / det J
+// (a_c = column c of DF) from the parametric value N and gradient (N_xi, N_eta).
+struct Pushed { double v[2], g[2][2], divh; };
+
+inline Pushed push_velocity(double N, double Nxi, double Neta, int c, const double DF[2][2], const double D2[2][2][2],
+                            double J, const double dJ[2], const double inv[2][2]) {
+  Pushed o;
+  const double dN[2] = {Nxi, Neta};
+  double G[2][2];                                     // d v_i / d xi_k
+  for (int i = 0; i < 2; ++i) {
+    const double a = DF[i][c];
+    o.v[i] = N * a / J;
+    for (int k = 0; k < 2; ++k) G[i][k] = dN[k] * a / J + N * D2[i][c][k] / J - N * a * dJ[k] / (J * J);
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) o.g[i][j] = G[i][0] * inv[0][j] + G[i][1] * inv[1][j];
+  o.divh = dN[c];
+  return o;
+}
+
+struct Geo { double X[2], DF[2][2], D2[2][2][2], J, dJ[2], inv[2][2]; };
+
+inline Geo geo_at(double ri, double ro, double xi, double eta) {
+  Geo g;
+  annulus_map(ri, ro, xi, eta, g.X, g.DF, g.D2);
+  g.J = g.DF[0][0] * g.DF[1][1] - g.DF[0][1] * g.DF[1][0];
+  for (int k = 0; k < 2; ++k)
+    g.dJ[k] = g.D2[0][0][k] * g.DF[1][1] + g.DF[0][0] * g.D2[1][1][k] - g.D2[0][1][k] * g.DF[1][0] - g.DF[0][1] * g.D2[1][0][k];
+  g.inv[0][0] = g.DF[1][1] / g.J; g.inv[0][1] = -g.DF[0][1] / g.J;
+  g.inv[1][0] = -g.DF[1][0] / g.J; g.inv[1][1] = g.DF[0][0] / g.J;
+  return g;
+}
+
+// free velocity functions of element (ex, ey) at one point: global ids and pushed values
+struct LocalVel { int n = 0; long long gid[32]; Dof d[32]; Pushed f[32]; };
+
+void local_velocity(const igamg_sizes& sz, int p, int ex, int ey, const std::vector<double>& tp,
+                    const std::vector<double>& tq, double xi, double eta, const Geo& G, LocalVel& out) {
+  const int q = p - 1;
+  double Npx[8], dNpx[8], Nqx[8], dNqx[8], Npy[8], dNpy[8], Nqy[8], dNqy[8];
+  span_values(tp, p, ex + p, xi, Npx); span_derivs(tp, p, ex + p, xi, dNpx);
+  span_values(tq, q, ex + q, xi, Nqx); span_derivs(tq, q, ex + q, xi, dNqx);
+  span_values(tp, p, ey + p, eta, Npy); span_derivs(tp, p, ey + p, eta, dNpy);
+  span_values(tq, q, ey + q, eta, Nqy); span_derivs(tq, q, ey + q, eta, dNqy);
+  out.n = 0;
+  for (int a = 0; a <= p; ++a)                        // u_x: degree p in xi, q in eta
+    for (int b = 0; b <= q; ++b) {
+      long long g = gid(sz, 0, ex + a, ey + b);
+      if (g < 0) continue;
+      out.gid[out.n] = g; out.d[out.n] = {0, ex + a, ey + b};
+      out.f[out.n++] = push_velocity(Npx[a] * Nqy[b], dNpx[a] * Nqy[b], Npx[a] * dNqy[b], 0, G.DF, G.D2, G.J, G.dJ, G.inv);
+    }
+  for (int a = 0; a <= q; ++a)                        // u_y: degree q in xi, p in eta
+    for (int b = 0; b <= p; ++b) {
+      long long g = gid(sz, 1, ex + a, ey + b);
+      if (g < 0) continue;
+      out.gid[out.n] = g; out.d[out.n] = {1, ex + a, ey + b};
+      out.f[out.n++] = push_velocity(Nqx[a] * Npy[b], dNqx[a] * Npy[b], Nqx[a] * dNpy[b], 1, G.DF, G.D2, G.J, G.dJ, G.inv);
+    }
+}
+}  // namespace
+
+// Adds K(row = test gid ti, column = trial gid tj) += val into the level's records.
+static void put_entry(int p, const igamg_sizes& sz, std::vector<double>& rows, std::vector<double>& ext,
+                      const Dof& r, long long ti, const Dof& c, double val) {
+  const int q = p - 1, RU = (2 * p + 1) * (2 * q + 1) + 2 * p * (2 * q + 1) + 1, BX = 4 * p * p;
+  int idx = box_index(p, r, c);
+  if (idx >= 0) { rows[(size_t)ti * RU + idx] += val; return; }
+  idx = ext_index(p, r, c);
+  if (idx >= 0) ext[(size_t)ti * BX + idx] += val;
+  (void)sz;
+}
+
+// Fine-level operator of generalized Stokes on the quarter annulus, in record form:
+// sigma (u, v) + nu (grad u, grad v) - (div v, p) + (div u, q) on the physical domain,
+// integrated over the parametric square with (p+2)-point Gauss rules; Nitsche terms
+// -nu (grad u n).v - nu (grad v n).u + C_I nu / h u.v on the four walls, h = det J /
+// (|tangent| n); the multiplier column m_j = int q_j dx = int q_hat_j dxi.  Also fills the
+// physical quadrature points and J^T there for the load vector.
+void assemble_mapped(int p, LevelHost& lv, double sigma, double nu, double cpen, double ri, double ro,
+                     HierarchyHost& H) {
+  const int q = p - 1, n = lv.sz.n, G = p + 2, nG = n * G;
+  const int RU = (2 * p + 1) * (2 * q + 1) + 2 * p * (2 * q + 1) + 1, BX = 4 * p * p;
+  const long long nu_rows = lv.sz.n_ux + lv.sz.n_uy, nr = lv.sz.n_total - 1;
+  lv.rows.assign((size_t)nr * RU, 0.0);
+  lv.ext.assign((size_t)nu_rows * BX, 0.0);
+  std::vector<double> gx, gw;
+  gauss01(G, gx, gw);
+  auto tp = knots(p, n), tq = knots(q, n);
+  auto& rows = lv.rows;
+  auto& ext = lv.ext;
+  // volume terms: an element row ey writes only the records of functions with y index in
+  // [ey, ey + p], so element rows p + 2 apart never share a record; p + 2 sequential phases,
+  // each spreading its element rows (ey = phase mod p + 2) over the threads
+  unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  const int phases = p + 2;
+  for (int ph = 0; ph < phases; ++ph) {
+    std::vector<int> eys;
+    for (int ey = ph; ey < n; ey += phases) eys.push_back(ey);
+    auto work = [&](size_t i0, size_t i1) {
+      LocalVel lvv;
+      for (size_t ii = i0; ii < i1; ++ii) {
+        const int ey = eys[ii];
+        for (int ex = 0; ex < n; ++ex)
+          for (int gyi = 0; gyi < G; ++gyi)
+            for (int gxi = 0; gxi < G; ++gxi) {
+              const double xi = (ex + gx[gxi]) / n, eta = (ey + gx[gyi]) / n;
+              const double w = gw[gxi] * gw[gyi] / ((double)n * n);
+              Geo g = geo_at(ri, ro, xi, eta);
+              local_velocity(lv.sz, p, ex, ey, tp, tq, xi, eta, g, lvv);
+              double Nqx[8], Nqy[8];
+              span_values(tq, q, ex + q, xi, Nqx);
+              span_values(tq, q, ey + q, eta, Nqy);
+              const double wJ = w * g.J;
+              for (int i = 0; i < lvv.n; ++i) {
+                const Pushed& a = lvv.f[i];
+                for (int j = 0; j < lvv.n; ++j) {
+                  const Pushed& b = lvv.f[j];
+                  double m = sigma * (a.v[0] * b.v[0] + a.v[1] * b.v[1]);
+                  double k = a.g[0][0] * b.g[0][0] + a.g[0][1] * b.g[0][1] + a.g[1][0] * b.g[1][0] + a.g[1][1] * b.g[1][1];
+                  put_entry(p, lv.sz, rows, ext, lvv.d[i], lvv.gid[i], lvv.d[j], wJ * (m + nu * k));
+                }
+                // b(v, q) = int div v q dx = int divhat vhat qhat / det J dxi
+                for (int ka = 0; ka <= q; ++ka)
+                  for (int kb = 0; kb <= q; ++kb) {
+                    const long long gq = gid(lv.sz, 2, ex + ka, ey + kb);
+                    const Dof dq{2, ex + ka, ey + kb};
+                    const double bval = w * a.divh * Nqx[ka] * Nqy[kb] / g.J;
+                    put_entry(p, lv.sz, rows, ext, lvv.d[i], lvv.gid[i], dq, -bval);
+                    put_entry(p, lv.sz, rows, ext, dq, gq, lvv.d[i], bval);
+                  }
+              }
+            }
+      }
+    };
+    std::vector<std::thread> th;
+    size_t chunk = (eys.size() + nth - 1) / nth;
+    for (unsigned t = 0; t < nth; ++t) {
+      size_t i0 = t * chunk, i1 = std::min(eys.size(), i0 + chunk);
+      if (i0 < i1) th.emplace_back(work, i0, i1);
+    }
+    for (auto& t : th) t.join();
+  }
+  // Nitsche terms on the four walls (k = 0: xi = const walls, k = 1: eta = const walls)
+  const double pen_c = cpen * nu;
+  LocalVel lvv;
+  for (int wall = 0; wall < 4; ++wall) {
+    const int k = wall / 2, side = wall % 2;
+    for (int e = 0; e < n; ++e)
+      for (int gi = 0; gi < G; ++gi) {
+        const double t = (e + gx[gi]) / n, wt = gw[gi] / n;
+        const double xi = k == 0 ? (double)side : t, eta = k == 0 ? t : (double)side;
+        const int ex = k == 0 ? (side ? n - 1 : 0) : e, ey = k == 0 ? e : (side ? n - 1 : 0);
+        Geo g = geo_at(ri, ro, xi, eta);
+        local_velocity(lv.sz, p, ex, ey, tp, tq, xi, eta, g, lvv);
+        double nv[2] = {g.inv[k][0], g.inv[k][1]};    // gradient of xi_k
+        double nn = std::sqrt(nv[0] * nv[0] + nv[1] * nv[1]);
+        const double sgn = side ? 1.0 : -1.0;
+        nv[0] *= sgn / nn; nv[1] *= sgn / nn;
+        const double tl = std::sqrt(g.DF[0][1 - k] * g.DF[0][1 - k] + g.DF[1][1 - k] * g.DF[1][1 - k]);
+        const double ds = wt * tl, h = g.J / (tl * n);
+        for (int i = 0; i < lvv.n; ++i) {
+          const Pushed& a = lvv.f[i];
+          const double dna[2] = {a.g[0][0] * nv[0] + a.g[0][1] * nv[1], a.g[1][0] * nv[0] + a.g[1][1] * nv[1]};
+          for (int j = 0; j < lvv.n; ++j) {
+            const Pushed& b = lvv.f[j];
+            const double dnb[2] = {b.g[0][0] * nv[0] + b.g[0][1] * nv[1], b.g[1][0] * nv[0] + b.g[1][1] * nv[1]};
+            const double val = ds * (-nu * (dnb[0] * a.v[0] + dnb[1] * a.v[1]) - nu * (dna[0] * b.v[0] + dna[1] * b.v[1])
+                                     + pen_c / h * (a.v[0] * b.v[0] + a.v[1] * b.v[1]));
+            put_entry(p, lv.sz, rows, ext, lvv.d[i], lvv.gid[i], lvv.d[j], val);
+          }
+        }
+      }
+  }
+  // multiplier column of the pressure rows
+  for (long long g = lv.sz.n_ux + lv.sz.n_uy; g < nr; ++g) {
+    Dof d = decode(lv.sz, g);
+    rows[(size_t)g * RU + RU - 1] = lv.f.mq[d.x] * lv.f.mq[d.y];
+  }
+  // physical quadrature points and J^T for the load vector
+  H.quad_xy.assign((size_t)2 * nG * nG, 0.0);
+  H.jt.assign((size_t)4 * nG * nG, 0.0);
+  for (int iy = 0; iy < nG; ++iy)
+    for (int ix = 0; ix < nG; ++ix) {
+      const double xi = (ix / G + gx[ix % G]) / n, eta = (iy / G + gx[iy % G]) / n;
+      double X[2], DF[2][2], D2[2][2][2];
+      annulus_map(ri, ro, xi, eta, X, DF, D2);
+      const size_t o = (size_t)iy * nG + ix;
+      H.quad_xy[o] = X[0];
+      H.quad_xy[(size_t)nG * nG + o] = X[1];
+      for (int kk = 0; kk < 2; ++kk)
+        for (int i = 0; i < 2; ++i) H.jt[o * 4 + kk * 2 + i] = DF[i][kk];
+    }
+}
+
 // K_c = P^T K_f P (Sec. 5.1) in per-row stencil form.  P is block diagonal with tensor
 // products of the 1D knot-insertion views tp (degree p, interior indices) and tq.
 int galerkin_rows(int p, const LevelHost& F, const LevelHost& C, const Transfer1D& tp, const Transfer1D& tq,
-                  std::vector<double>& out, std::string& err) {
-  const int q = p - 1, RU = (2 * p + 1) * (2 * q + 1) + 2 * p * (2 * q + 1) + 1;
+                  std::vector<double>& out, std::string& err, std::vector<double>* out_ext = nullptr) {
+  const int q = p - 1, RU = (2 * p + 1) * (2 * q + 1) + 2 * p * (2 * q + 1) + 1, BX = 4 * p * p;
   const int WR = Transfer1D::WR, WP = Transfer1D::WP;
   long long nC = C.sz.n_total - 1;
   out.assign((size_t)nC * RU, 0.0);
+  const bool has_ext = !F.ext.empty() && out_ext;
+  if (has_ext) out_ext->assign((size_t)(C.sz.n_ux + C.sz.n_uy) * BX, 0.0);
   std::atomic<int> bad{0};
   auto work = [&](long long i0, long long i1) {
     for (long long i = i0; i < i1; ++i) {
@@ -426,6 +678,7 @@ int galerkin_rows(int p, const LevelHost& F, const LevelHost& C, const Transfer1
       int sx = ri.blk == 0 ? 1 : 0, sy = ri.blk == 1 ? 1 : 0;   // view index = full - shift
       int cxv = ri.x - sx, cyv = ri.y - sy;
       double* orow = &out[(size_t)i * RU];
+      double* oext = (has_ext && ri.blk < 2) ? &(*out_ext)[(size_t)i * BX] : nullptr;
       for (int kx = 0; kx < WR; ++kx) {
         int fxv = TX.f0[cxv] + kx;
         double wx = TX.rv[(size_t)cxv * WR + kx];
@@ -437,13 +690,16 @@ int galerkin_rows(int p, const LevelHost& F, const LevelHost& C, const Transfer1
           long long a = gid(F.sz, ri.blk, fxv + sx, fyv + sy);
           Dof ra = decode(F.sz, a);
           const double* frow = &F.rows[(size_t)a * RU];
+          const double* fext = (has_ext && ra.blk < 2) ? &F.ext[(size_t)a * BX] : nullptr;
           double wa = wx * wy;
           double fscale = 0.0;
           for (int e = 0; e < RU; ++e) fscale = std::max(fscale, std::fabs(frow[e]));
-          for (int e = 0; e < RU; ++e) {
-            double val = frow[e];
+          if (fext) for (int e = 0; e < BX; ++e) fscale = std::max(fscale, std::fabs(fext[e]));
+          const int ne = fext ? RU + BX : RU;
+          for (int e = 0; e < ne; ++e) {
+            double val = e < RU ? frow[e] : fext[e - RU];
             if (val == 0.0) continue;
-            Dof cb = box_col(F.sz, p, ra, e);
+            Dof cb = e < RU ? box_col(F.sz, p, ra, e) : ext_col(F.sz, p, ra, e - RU);
             if (cb.blk < 0) continue;
             if (cb.blk == 3) { orow[RU - 1] += wa * val; continue; }
             const Transfer1D& JX = cb.blk == 0 ? tp : tq;
@@ -460,6 +716,10 @@ int galerkin_rows(int p, const LevelHost& F, const LevelHost& C, const Transfer1
                 if (wjy == 0.0 || cjy >= JY.nc) continue;
                 Dof cj{cb.blk, cjx + jsx, cjy + jsy};
                 int idx = box_index(p, ri, cj);
+                if (idx < 0 && oext) {
+                  int ie = ext_index(p, ri, cj);
+                  if (ie >= 0) { oext[ie] += wa * val * wjx * wjy; continue; }
+                }
                 if (idx < 0) {
                   // only round-off may fall outside the pattern (exact zeros in exact
                   // arithmetic can come out as tiny numbers where the compiler contracts
@@ -658,11 +918,16 @@ void build_row_slots(PatchTables& pt) {
 }
 
 double k_entry_rows(const LevelHost& lv, int p, long long g1, long long g2) {
-  const int q = p - 1, RU = (2 * p + 1) * (2 * q + 1) + 2 * p * (2 * q + 1) + 1;
+  const int q = p - 1, RU = (2 * p + 1) * (2 * q + 1) + 2 * p * (2 * q + 1) + 1, BX = 4 * p * p;
   Dof a = decode(lv.sz, g1), b = decode(lv.sz, g2);
   if (a.blk == 3) return b.blk == 2 ? lv.rows[(size_t)g2 * RU + RU - 1] : 0.0;
   int idx = box_index(p, a, b);
-  return idx < 0 ? 0.0 : lv.rows[(size_t)g1 * RU + idx];
+  if (idx >= 0) return lv.rows[(size_t)g1 * RU + idx];
+  if (!lv.ext.empty()) {
+    idx = ext_index(p, a, b);
+    if (idx >= 0) return lv.ext[(size_t)g1 * BX + idx];
+  }
+  return 0.0;
 }
 
 igamg_sizes level_sizes(int p, int n) {
@@ -765,7 +1030,9 @@ int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err)
   H.cpen = pr.c_penalty > 0 ? pr.c_penalty : 4.0 * (p - 1);
   const double pen_over_nu = H.cpen * nf;  // C_I / h_fine on every level
   H.lev.resize(L);
-  const bool general = pr.beta_qp != nullptr;     // generalized Oseen: per-row operators
+  const bool mapped = pr.geometry == IGAMG_GEOM_QUARTER_ANNULUS;
+  const bool general = pr.beta_qp != nullptr || mapped;   // Oseen, mapped: per-row operators
+  H.geometry = pr.geometry;
   for (int l = 0; l < L; ++l) {
     int n = nf >> (L - 1 - l);
     auto& lv = H.lev[l];
@@ -783,13 +1050,19 @@ int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err)
     if (Pq.empty() || !make_transfer(Pq, a, b, 0, H.tq[l])) { err = "degree-(p-1) prolongation"; return IGAMG_ESINGULAR; }
   }
   if (general) {
-    // fine level: the Stokes part from the class stencils plus the advection term; coarse
-    // levels: Galerkin products (the advection field is not polynomial, so re-assembly
-    // would not equal R K P)
-    rows_from_classes(p, H.lev[L - 1], H.lev[L - 1].rows);
-    add_advection(p, H.lev[L - 1], pr.beta_qp, H.lev[L - 1].rows);
+    // fine level: the Stokes part from the class stencils plus the advection term, or the
+    // operator on the mapped domain; coarse levels: Galerkin products (neither the advection
+    // field nor the map is polynomial, so re-assembly would not equal R K P)
+    if (mapped) {
+      const double ri = pr.r_inner > 0 ? pr.r_inner : 0.075, ro = pr.r_outer > 0 ? pr.r_outer : 0.225;
+      assemble_mapped(p, H.lev[L - 1], pr.sigma, pr.nu, H.cpen, ri, ro, H);
+    } else {
+      rows_from_classes(p, H.lev[L - 1], H.lev[L - 1].rows);
+      add_advection(p, H.lev[L - 1], pr.beta_qp, H.lev[L - 1].rows);
+    }
     for (int l = L - 2; l >= 0; --l) {
-      int rc = galerkin_rows(p, H.lev[l + 1], H.lev[l], H.tp_free[l + 1], H.tq[l + 1], H.lev[l].rows, err);
+      int rc = galerkin_rows(p, H.lev[l + 1], H.lev[l], H.tp_free[l + 1], H.tq[l + 1], H.lev[l].rows, err,
+                             mapped ? &H.lev[l].ext : nullptr);
       if (rc) return rc;
     }
   }
@@ -844,6 +1117,8 @@ int host_build(const igamg_problem* prob, int level, igamg::HierarchyHost& H) {
   if (!(prob->sigma > 0) || !(prob->nu > 0)) return IGAMG_EINVAL;
   if (prob->n_levels < 1 || prob->n_fine < 1 || prob->n_fine % (1 << (prob->n_levels - 1))) return IGAMG_EINVAL;
   if (level < 0 || level >= prob->n_levels) return IGAMG_EINVAL;
+  if (prob->geometry < IGAMG_GEOM_SQUARE || prob->geometry > IGAMG_GEOM_QUARTER_ANNULUS) return IGAMG_EINVAL;
+  if (prob->geometry == IGAMG_GEOM_QUARTER_ANNULUS && prob->beta_qp) return IGAMG_EUNSUPPORTED;
   if (igamg::level_sizes(prob->p, prob->n_fine >> (prob->n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
   std::string err;
   return igamg::build_hierarchy(*prob, H, err);

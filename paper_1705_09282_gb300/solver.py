@@ -26,10 +26,11 @@ class Solver:
 
     def __init__(self, p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.5, nu1=2, nu2=2,
                  c_penalty=0.0, precision=_lib.IGAMG_FP64, device="cuda", stream=None, beta=None, dim=2,
-                 restart=0, gamma=1, fmg=False):
+                 restart=0, gamma=1, fmg=False, geometry=_lib.IGAMG_GEOM_SQUARE, r_inner=0.0, r_outer=0.0):
         """beta: advection at the quadrature points (host array (2, nG, nG)) for the
         generalized Oseen problem, or None for generalized Stokes.  gamma = 2 selects the
-        W-cycle; fmg starts every solve with one full-multigrid pass."""
+        W-cycle; fmg starts every solve with one full-multigrid pass.  geometry =
+        IGAMG_GEOM_QUARTER_ANNULUS solves on the quarter annulus (2D Stokes)."""
         self.device = torch.device(device)
         if self.device.type != "cuda":
             raise RuntimeError("the igamg solver runs on a CUDA device only")
@@ -37,7 +38,8 @@ class Solver:
         self._beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
         self.problem = _lib.make_problem(p, n_fine, n_levels, sigma, nu, smoother, eta, nu1, nu2,
                                          c_penalty, precision, beta=self._beta, dim=dim, restart=restart,
-                                         gamma=gamma, fmg=fmg)
+                                         gamma=gamma, fmg=fmg, geometry=geometry, r_inner=r_inner,
+                                         r_outer=r_outer)
         self.p, self.n_fine, self.n_levels, self.dim = p, n_fine, n_levels, dim
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -73,6 +75,16 @@ class Solver:
         check(lib().igamg_quad_points(self._h, x.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)),
               "igamg_quad_points")
         return x
+
+    def quad_points_xy(self):
+        """Physical quadrature points (2, nG, nG) [x or y][eta point][xi point]."""
+        n = ctypes.c_size_t()
+        check(lib().igamg_quad_points_xy(self._h, None, 0, ctypes.byref(n)), "igamg_quad_points_xy")
+        xy = np.zeros(n.value)
+        check(lib().igamg_quad_points_xy(self._h, xy.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)),
+              "igamg_quad_points_xy")
+        nG = int(round(np.sqrt(n.value // 2)))
+        return xy.reshape(2, nG, nG)
 
     def empty(self, level=None):
         return torch.zeros(self.ndof(level), dtype=torch.float64, device=self.device)
@@ -178,9 +190,10 @@ def solve_batch(solvers, Us, Fs, rtol=1e-8, max_cycles=100, history=False):
 
 
 # ---- host-only inspection (no GPU) ----------------------------------------------------
-def host_level_matrix(p, n_fine, n_levels, sigma, nu, level, c_penalty=0.0, beta=None, dim=2):
+def host_level_matrix(p, n_fine, n_levels, sigma, nu, level, c_penalty=0.0, beta=None, dim=2, geometry=0):
     beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
-    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, c_penalty=c_penalty, beta=beta, dim=dim)
+    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, c_penalty=c_penalty, beta=beta, dim=dim,
+                           geometry=geometry)
     n = ctypes.c_longlong()
     check(lib().igamg_host_level_matrix(ctypes.byref(pr), level, None, 0, ctypes.byref(n)), "host_level_matrix")
     K = np.zeros((n.value, n.value))
@@ -189,9 +202,9 @@ def host_level_matrix(p, n_fine, n_levels, sigma, nu, level, c_penalty=0.0, beta
     return K
 
 
-def host_operator_rows(p, n_fine, n_levels, sigma, nu, level, beta=None, dim=2):
+def host_operator_rows(p, n_fine, n_levels, sigma, nu, level, beta=None, dim=2, geometry=0):
     beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
-    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, beta=beta, dim=dim)
+    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, beta=beta, dim=dim, geometry=geometry)
     n = ctypes.c_longlong()
     check(lib().igamg_host_operator_rows(ctypes.byref(pr), level, None, 0, ctypes.byref(n)), "host_operator_rows")
     K = np.zeros((n.value, n.value))
@@ -200,10 +213,10 @@ def host_operator_rows(p, n_fine, n_levels, sigma, nu, level, beta=None, dim=2):
     return K
 
 
-def host_operator_apply(p, n_fine, n_levels, sigma, nu, level, V, beta=None, dim=2):
+def host_operator_apply(p, n_fine, n_levels, sigma, nu, level, V, beta=None, dim=2, geometry=0):
     """K_l V through the kernels' row evaluation, on the host (V: float64 numpy vector)."""
     beta = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
-    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, beta=beta, dim=dim)
+    pr = _lib.make_problem(p, n_fine, n_levels, sigma, nu, beta=beta, dim=dim, geometry=geometry)
     V = np.ascontiguousarray(V, dtype=np.float64)
     KV = np.zeros_like(V)
     check(lib().igamg_host_operator_apply(ctypes.byref(pr), level, V.ctypes.data_as(ctypes.c_void_p),

@@ -129,3 +129,35 @@ def test_oseen_operators_match_oracle_galerkin(p, n, L):
     # and the operator is not symmetric (the advection term is present)
     K = H.levels[-1].K.toarray()
     assert np.abs(K - K.T).max() > 1e-6 * np.abs(K).max()
+
+
+# ---- quarter annulus (Sec. 4.4 push-forwards, Sec. 6.2) ----------------------------------
+
+@pytest.mark.parametrize("p,n,L,sigma,nu", [(2, 8, 3, 1.3, 0.7), (3, 8, 2, 1.0, 1.0), (2, 12, 2, 1e3, 1.0)])
+def test_annulus_operators_match_oracle(p, n, L, sigma, nu):
+    # the host assembly on the mapped domain (third record box for the u_x - u_y coupling)
+    # and its Galerkin coarse levels, entry by entry and through the kernels' row evaluation
+    from oracle import annulus2d as A
+    from paper_1705_09282_gb300.solver import host_level_matrix, host_operator_rows
+    fine = A.MappedStokes2D(p, n, sigma, nu, A.QuarterAnnulus())
+    H = o2.Hierarchy(p, n, L, sigma, nu, fine=fine)
+    for lev in range(L):
+        Ko = H.levels[lev].K.toarray()
+        scale = np.abs(Ko).max()
+        assert np.abs(host_level_matrix(p, n, L, sigma, nu, lev, geometry=1) - Ko).max() <= 1e-13 * scale, lev
+        assert np.abs(host_operator_rows(p, n, L, sigma, nu, lev, geometry=1) - Ko).max() <= 1e-13 * scale, lev
+
+
+def test_annulus_arguments_rejected_on_host():
+    import ctypes
+    L = _lib().lib()
+    h = ctypes.c_void_p()
+    pr = _lib().make_problem(2, 8, 2, 1.0, 1.0, geometry=2)                       # no such domain
+    assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -1
+    pr = _lib().make_problem(2, 8, 2, 1.0, 1.0, geometry=1, r_inner=0.3, r_outer=0.2)
+    assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -1
+    beta = np.zeros((2, 32, 32))
+    pr = _lib().make_problem(2, 8, 2, 1.0, 1.0, geometry=1, beta=beta)           # Stokes only
+    assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -2
+    pr = _lib().make_problem(2, 8, 2, 1.0, 1.0, geometry=1, dim=3)               # 2D only
+    assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -2
