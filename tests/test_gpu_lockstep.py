@@ -1,0 +1,86 @@
+"""Lockstep batches (igamg_solve_batch): FP64 handles of one structure step their V-cycles
+together, each colour / residual / transfer / coarse solve one launch over up to 24 solves,
+larger groups as parallel graph branches, converged solves switched off by a device flag.
+Per solve the arithmetic is the single solve's, so with per-level launches on every level
+(IGAMG_FUSED_LEVELS=-1 for the single solves) iterates, cycle counts and histories are
+identical bit for bit."""
+import numpy as np
+import pytest
+
+from paper_1705_09282_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _run(cases, monkeypatch, abs_tol=False, zero=()):
+    torch = _torch()
+    from paper_1705_09282_gb300 import warmstart as ws
+    from paper_1705_09282_gb300.solver import Solver, solve_batch
+    monkeypatch.setenv("IGAMG_FUSED_LEVELS", "-1")
+    monkeypatch.setenv("IGAMG_LOCKSTEP_MIN", "2")       # small groups too (default: 8 or more)
+    solvers, Fs, Us, singles, atol = [], [], [], [], []
+    for j, (p, n, L, sigma, kw) in enumerate(cases):
+        S = Solver(p, n, L, sigma, 1.0, **kw)
+        if kw.get("geometry", 0) == 1:
+            X = S.quad_points_xy()
+            f = inputs.annulus_forcing(X[0], X[1], sigma, 1.0)
+        else:
+            f = inputs.grf_forcing(p, n, seed=300 + j)
+        F = S.load_vector(torch.tensor(f, device="cuda"))
+        if j in zero:
+            F.zero_()
+        a = 1e-8 * float(torch.linalg.norm(F)) if abs_tol else None
+        U1 = S.empty()
+        if abs_tol:
+            r1 = ws.solve_abs(S, U1, F, a, 80)
+        else:
+            r1 = S.solve(U1, F, rtol=1e-8, max_cycles=80)
+        singles.append((r1, U1.cpu().numpy()))
+        solvers.append(S); Fs.append(F); Us.append(S.empty()); atol.append(a)
+    if abs_tol:
+        reps = ws.solve_batch_abs(solvers, Us, Fs, atol, 80)
+    else:
+        reps = solve_batch(solvers, Us, Fs, rtol=1e-8, max_cycles=80, history=True)
+    for j, ((r1, U1), rep, U) in enumerate(zip(singles, reps, Us)):
+        assert rep["converged"] == r1["converged"] and rep["cycles"] == r1["cycles"], j
+        assert np.array_equal(U.cpu().numpy(), U1), j
+        if not abs_tol:
+            assert rep["history"] == pytest.approx(r1["history"], rel=0, abs=0), j
+        assert rep["div_inf"] == r1["div_inf"], j
+    return reps
+
+
+def test_mixed_groups_and_stragglers(monkeypatch):
+    from paper_1705_09282_gb300._lib import IGAMG_FP32_IR
+    cases = [(2, 32, 4, s, {}) for s in (1e-4, 1e-2, 1.0, 1e2, 1e4)]            # one group of 5
+    cases += [(3, 32, 4, s, {}) for s in (1e-2, 1e2)]                          # a second group
+    cases += [(2, 16, 3, 1.0, {})]                                             # a singleton
+    cases += [(2, 32, 4, 1.0, {"precision": IGAMG_FP32_IR})]                   # not batched (FP32)
+    cases += [(2, 32, 4, 3.0, {"gamma": 2})]                                   # not batched (W-cycle)
+    _run(cases, monkeypatch)
+
+
+def test_group_larger_than_one_launch(monkeypatch):
+    # 30 solves: two chunks (24 + 6) as parallel branches of the batch graph
+    rng = np.random.default_rng(5)
+    cases = [(2, 16, 3, float(10 ** rng.uniform(-2, 4)), {}) for _ in range(30)]
+    reps = _run(cases, monkeypatch)
+    assert len({r["cycles"] for r in reps}) >= 1
+
+
+def test_absolute_tolerance_and_zero_rhs(monkeypatch):
+    cases = [(2, 32, 4, s, {}) for s in (1e-2, 1.0, 1e3)] + [(3, 16, 3, s, {}) for s in (1.0, 10.0)]
+    reps = _run(cases, monkeypatch, abs_tol=True, zero=(1,))
+    assert reps[1]["cycles"] == 0 and reps[1]["converged"]
+
+
+def test_annulus_group(monkeypatch):
+    cases = [(2, 16, 3, s, {"geometry": 1}) for s in (1.0, 1e3, 1e-2)]
+    _run(cases, monkeypatch)
