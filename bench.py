@@ -381,13 +381,31 @@ def run_reference(args):
 def profile_case(spec):
     """Untimed workload for profilers: two solves of one case of the sweep.
     spec = "p<degree>-<fp64|mixed>[-sigma<value>]", e.g. "p2-fp64", "cube-p2-<fp64|mixed>" (one
-    solve of the 64^3 cube) or "oseen-<fp64|mixed>" (one solve of the 512^2 Oseen problem)."""
+    solve of the 64^3 cube), "oseen-<fp64|mixed>" (one solve of the 512^2 Oseen problem) or
+    "batch128" (two lockstep batches of 24 solves of 128^2)."""
+    import numpy as np
     import torch
 
     from paper_1705_09282_gb300 import inputs
     from paper_1705_09282_gb300._lib import IGAMG_FP32_IR, IGAMG_FP64
     from paper_1705_09282_gb300.solver import Solver
     parts = spec.split("-")
+    if parts[0] == "batch128":
+        # 24 solves of 128^2 (p = 2, 6 grids, sigma/nu spread over [1e-2, 1e4]) in one lockstep group
+        from paper_1705_09282_gb300.solver import solve_batch
+        solvers, Us, Fs = [], [], []
+        for j, sig in enumerate(np.logspace(-2, 4, 24)):
+            S = Solver(2, 128, 6, float(sig), 1.0)
+            Fs.append(S.load_vector(torch.tensor(inputs.grf_forcing(2, 128, seed=1709 + j), device="cuda")))
+            Us.append(S.empty())
+            solvers.append(S)
+        for _ in range(2):
+            for U in Us:
+                U.zero_()
+            reps = solve_batch(solvers, Us, Fs, rtol=RTOL, max_cycles=MAXC)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": spec, "cycles": [r["cycles"] for r in reps]}))
+        return
     if parts[0] == "oseen":
         prec = IGAMG_FP32_IR if parts[1] == "mixed" else IGAMG_FP64
         S = Solver(2, 512, 8, 1.0, 1e-2, beta=inputs.oseen_advection(2, 512, 0.5), precision=prec)

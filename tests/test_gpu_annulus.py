@@ -161,3 +161,28 @@ def test_solve_host_on_the_annulus():
     rep_d = S.solve(Ud, S.load_vector(_t(f)), rtol=1e-8, max_cycles=80)
     assert rep_h["cycles"] == rep_d["cycles"]
     assert np.array_equal(Uh, _np(Ud))
+
+
+@pytest.mark.parametrize("p,n,L", [(2, 12, 3), (3, 8, 2)])
+def test_additive_smoother_and_vcycle_on_the_annulus(p, n, L):
+    # eq. ASM with per-patch inverses on the mapped operator
+    S = _solver(p, n, L, smoother="add", eta=0.3)
+    fine = A.MappedStokes2D(p, n, 1.0, 1.0, GEOM)
+    H = o2.Hierarchy(p, n, L, 1.0, 1.0, smoother="add", eta=0.3, fine=fine)
+    for lev in range(1, L):
+        nd = H.levels[lev].K.shape[0]
+        U = inputs.random_vector(nd, seed=11 * lev)
+        F = inputs.random_vector(nd, seed=11 * lev + 1)
+        Ug = _t(U)
+        S.smooth(Ug, _t(F), level=lev, sweeps=1)
+        Uo = U.copy()
+        H.smooth(lev, Uo, F)
+        assert _rel(_np(Ug), Uo) < 1e-12, lev
+    f = _forcing(S)
+    F = fine.load_vector(f)
+    Fg = S.load_vector(_t(f))
+    U, Ug = np.zeros_like(F), S.empty()
+    for k in range(2):
+        H.vcycle(U, F)
+        S.vcycle(Ug, Fg)
+        assert _rel(_np(Ug), U) < RTOL_IT, k
