@@ -500,9 +500,15 @@ def run_oseen(args):
         # colour: per 8-DOF patch 8 records, its own 8x8 inverse, dof ids, class id, F and U rows
         patches_colour = sz.n_patches / sz.n_colours
         col_bytes = patches_colour * (8 * RU * 8 + 64 * 8 + 8 * 4 + 4 + 3 * 8 * 8)
+        # the same residual against the FP64 pipe: one multiply-add per record coefficient
+        res_flops = 2.0 * (ntot - 1) * RU
+        fp64_peak = 152 * 2 * 2 * 2070e6 / 1e12
         out[name] = {"solve_ms": 1e3 * t, "cycles": cyc, "mdof_per_s_per_cycle": S.ndof() * cyc / t / 1e6,
                      "div_inf": div, "setup_s": setup, "fp64_colour_launch_us": colour_us,
                      "fp64_residual_us": res_us,
+                     "residual_fp64": {"flops": res_flops, "achieved_tflops": res_flops / res_us / 1e6,
+                                       "peak_tflops": fp64_peak, "frac": res_flops / res_us / 1e6 / fp64_peak,
+                                       "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz"},
                      "residual_hbm": {"bytes": res_bytes, "achieved_gbs": res_bytes / res_us / 1e3},
                      "colour_hbm": {"bytes": col_bytes, "achieved_gbs": col_bytes / colour_us / 1e3}}
         S.close()
