@@ -789,7 +789,8 @@ def run_annulus(args):
 
 def run_cycles(args):
     """Cycle forms on the harder cases (the W-cycle and full multigrid that Sec. 5's opening
-    paragraph names, and FGMRES around the V-cycle): 2D generalized Stokes at 256 x 256,
+    paragraph names, and FGMRES around the V-cycle): 3D generalized Stokes on the 64^3 cube;
+    2D generalized Stokes at 256 x 256,
     7 grids, p = 2, 3, sigma/nu = 1e-4 and 1e4; generalized Oseen at 512 x 512, 8 grids,
     nu = 1e-2, sigma = 1, max|beta| = 0.5 and 1 (Re = 50 and 100); GRF forcing, V(2,2)
     multiplicative, FP64, zero guess, to 1e-8.  Set-up is not timed."""
@@ -805,19 +806,22 @@ def run_cycles(args):
              ("FMG+W", dict(gamma=2, fmg=True, precision=IGAMG_FP64)),
              ("FGMRES(V)", dict(gamma=1, fmg=False, precision=IGAMG_FGMRES_FP64)),
              ("FMG+V fp32-in-fp64", dict(gamma=1, fmg=True, precision=IGAMG_FP32_IR)))
-    cases = [("stokes p2 sigma1e-4", 2, N_FINE, N_LEVELS, 1e-4, 1.0, None, SEED),
+    cases = [("cube p2 sigma1", 2, 64, 5, 1.0, 1.0, "cube", None),
+             ("stokes p2 sigma1e-4", 2, N_FINE, N_LEVELS, 1e-4, 1.0, None, SEED),
              ("stokes p3 sigma1e-4", 3, N_FINE, N_LEVELS, 1e-4, 1.0, None, SEED),
              ("stokes p3 sigma1e4", 3, N_FINE, N_LEVELS, 1e4, 1.0, None, SEED),
              ("oseen Re50", 2, 512, 8, 1.0, 1e-2, 0.5, 1707),
              ("oseen Re100", 2, 512, 8, 1.0, 1e-2, 1.0, 1707)]
     out = {}
     for name, p, n, L, sigma, nu, bmax, seed in cases:
-        beta = inputs.oseen_advection(p, n, bmax) if bmax else None
-        f = torch.tensor(inputs.grf_forcing(p, n, seed=seed), device="cuda")
+        cube = bmax == "cube"
+        beta = inputs.oseen_advection(p, n, bmax) if (bmax and not cube) else None
+        f = torch.tensor(inputs.manufactured_forcing_3d(p, n, sigma, nu) if cube else inputs.grf_forcing(p, n, seed=seed),
+                         device="cuda")
         res = {}
         for fname, kw in forms:
             try:
-                S = Solver(p, n, L, sigma, nu, beta=beta, **kw)
+                S = Solver(p, n, L, sigma, nu, beta=beta, dim=3 if cube else 2, **kw)
             except IgamgError as e:
                 res[fname] = {"error": str(e)}
                 continue
@@ -841,7 +845,8 @@ def run_cycles(args):
         out[name] = res
     line = {"metric": "solve time and cycles to 1e-8 for the V-, W- and full-multigrid cycles and FGMRES",
             "workload": "cycles",
-            "config": {"workload": "2D generalized Stokes 256x256 (7 levels, p=2,3, sigma/nu=1e-4,1e4) and Oseen "
+            "config": {"workload": "3D generalized Stokes 64^3 (5 levels, p=2, sigma=nu=1, manufactured forcing), "
+                                   "2D generalized Stokes 256x256 (7 levels, p=2,3, sigma/nu=1e-4,1e4) and Oseen "
                                    "512x512 (8 levels, nu=1e-2, sigma=1, max|beta|=0.5,1), GRF forcing, V(2,2) "
                                    "multiplicative, zero guess, to 1e-8, set-up not timed"},
             "results": out}

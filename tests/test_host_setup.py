@@ -161,3 +161,17 @@ def test_annulus_arguments_rejected_on_host():
     assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -2
     pr = _lib().make_problem(2, 8, 2, 1.0, 1.0, geometry=1, dim=3)               # 2D only
     assert L.igamg_create(ctypes.byref(pr), None, ctypes.byref(h)) == -2
+
+
+def test_batch_entry_points_reject_bad_lists_on_host():
+    # argument checks of the batch entry points run before any device work
+    import ctypes
+    L = _lib().lib()
+    assert L.igamg_solve_batch(0, None, None, None, 1e-8, 10, None, None) == 0          # empty batch
+    assert L.igamg_solve_batch(-1, None, None, None, 1e-8, 10, None, None) == -1
+    hs = (ctypes.c_void_p * 2)(None, None)
+    us = (ctypes.c_void_p * 2)(None, None)
+    assert L.igamg_solve_batch(2, hs, us, us, 1e-8, 10, None, None) == -1              # null handles
+    assert L.igamg_solve_batch(0, None, None, None, -1.0, 10, None, None) == -1        # rtol < 0
+    at = (ctypes.c_double * 1)(1e-8)
+    assert L.igamg_solve_batch_abs(0, None, None, None, at, 10, None, None) == 0
