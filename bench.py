@@ -521,7 +521,7 @@ def run_oseen(args):
         for key in ("residual_hbm", "colour_hbm"):
             v[key]["peak_gbs"] = pk["hbm_gbs"]
             v[key]["frac"] = v[key]["achieved_gbs"] / pk["hbm_gbs"]
-    line = {"metric": "Oseen solve time to 1e-8 rel. residual (config 3)", "workload": "oseen",
+    line = {"metric": "Oseen solve time to 1e-8 rel. residual (2D, 512^2)", "workload": "oseen",
             "config": {"workload": "2D generalized Oseen, unit square, p=2, 512x512, 8 levels, nu=1e-2, sigma=1, "
                                    "max|beta|=0.5 (Re=50, Da=100), GRF forcing seed 1707, V(2,2) multiplicative",
                        "ndof": None}, "results": out, "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_source": src}
@@ -529,7 +529,7 @@ def run_oseen(args):
 
 
 def run_batch(args):
-    """Config 5 style batch: independent 2D generalized Stokes solves of sizes 64/96/128
+    """The 1024-solve batch: independent 2D generalized Stokes solves of sizes 64/96/128
     (round-robin), sigma/nu log-uniform in [1e-2, 1e4], GRF forcing, side by side; zero
     initial guess versus the learned warm start (network trained on separate problems
     solved by the same multigrid), both to the absolute residual 1e-8 ||F||."""
@@ -573,7 +573,7 @@ def run_batch(args):
     cc = np.array([r["cycles"] for r in rc])
     cw = np.array([r["cycles"] for r in rw])
     cs = np.array([r["cycles"] for r in rs])
-    line = {"metric": "batched solve time to 1e-8 ||F|| and MDOF/s per V-cycle (config 5)", "workload": "batch",
+    line = {"metric": "batched solve time to 1e-8 ||F|| and MDOF/s per V-cycle (1024 solves of 64^2..128^2)", "workload": "batch",
             "config": {"solves": count, "sizes": [64, 96, 128], "p": p, "sigma_over_nu": "log-uniform [1e-2, 1e4]",
                        "train_problems": args.train_count, "train_steps": args.train_steps},
             "zero_guess": {"seconds": tc, "mean_cycles": float(cc.mean()), "mdof_per_s_per_cycle": float((ndof * cc).sum() / tc / 1e6)},
@@ -629,7 +629,7 @@ def run_cube(args):
                 "mdof_per_s_per_cycle": S.ndof() * rep["cycles"] / t / 1e6, "div_inf": rep["div_inf"],
                 "setup_s": setup, "fine_sweep_ms": 1e3 * dt_sm / sweeps, "colours": sz.n_colours}
             S.close()
-    line = {"metric": "3D solve time to 1e-8 rel. residual & MDOF/s per V-cycle (config 4)", "workload": "cube",
+    line = {"metric": "3D solve time to 1e-8 rel. residual & MDOF/s per V-cycle (64^3 cube)", "workload": "cube",
             "config": {"workload": "3D generalized Stokes, unit cube, p=2 (velocity S^{2,1,1} x S^{1,2,1} x S^{1,1,2}), "
                                    "64^3 elements, 5 levels, sigma/nu in {1, 1e3}, manufactured forcing of Sec. 6.3, "
                                    "V(2,2) multiplicative vector-potential Schwarz, zero initial guess, to 1e-8",

@@ -61,7 +61,7 @@ enum {
 enum { IGAMG_MULT = 0, IGAMG_ADD = 1 };          /* eq. MSM / eq. ASM of Sec. 5.2 */
 /* Precision / wrapper of the solve:
  *   IGAMG_FP64         plain FP64 V-cycles (Algorithm 1 as the solver)
- *   IGAMG_FP32_IR      FP32 V-cycles inside FP64 iterative refinement (north star (1))
+ *   IGAMG_FP32_IR      FP32 V-cycles inside FP64 iterative refinement
  *   IGAMG_FGMRES_FP64  FGMRES(m) in FP64 with one FP64 V-cycle as right preconditioner
  *   IGAMG_FGMRES_FP32  FGMRES(m) in FP64 with one FP32 V-cycle as right preconditioner
  * In every mode each update of the velocity is divergence-free to FP64 round-off (the FP32
@@ -220,7 +220,7 @@ int igamg_streamfunction(igamg_handle* h, const double* U, double* psi);
 /* Learned warm start from a two-channel network output grid (float, (2, n+p, n+p), device):
  * U = (curl psi, p, 0) with psi = psi_scale * channel 0 on the interior (boundary ring
  * ignored) and the pressure coefficients = p_scale * channel 1 on its leading
- * (n+p-1) x (n+p-1) points.  The velocity is exactly divergence-free (north star (4)). */
+ * (n+p-1) x (n+p-1) points.  The velocity is exactly divergence-free. */
 int igamg_warm_start(igamg_handle* h, const float* grid, double psi_scale, double p_scale, double* U);
 
 /* The same guess with its two predicted fields scaled against F (device, the load vector):
