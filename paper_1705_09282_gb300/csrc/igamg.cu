@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cstdint>
 #include <cmath>
 #include <cstdlib>
 #include <map>
@@ -222,7 +224,9 @@ struct LevelCommon {
 
 // Workspace and captured graphs of one lockstep batch (a fixed list of handles and vectors).
 struct BatchCache {
-  std::vector<const void*> key;        // handles, then U and F of every solve
+  // creation serials of the handles, then the U and F addresses of every solve (serials, not
+  // handle addresses: a handle destroyed and re-created at the same address must not match)
+  std::vector<unsigned long long> key;
   int count = 0;
   int* flags = nullptr;                // device: 1 while a solve is active
   double* norms = nullptr;             // device: ||F - K U||^2 per solve
@@ -235,6 +239,11 @@ struct BatchCache {
   cudaGraphExec_t g_res = nullptr;     // residual norms of all active solves
   cudaGraphExec_t g_cycle = nullptr;   // one V-cycle, then the residual norms
 };
+
+static unsigned long long next_serial() {
+  static std::atomic<unsigned long long> counter{0};
+  return ++counter;
+}
 
 static void batch_cache_free(BatchCache* c) {
   if (!c) return;
@@ -279,6 +288,7 @@ struct igamg_handle {
   double* jt = nullptr;                // mapped domains: J^T at the finest quadrature points
   double* dots = nullptr;              // warm-start scalings: 5 x kDotGrid partials, then 5 sums
   BatchCache* bc = nullptr;            // lockstep batches led by this handle (igamg_solve_batch)
+  unsigned long long serial = next_serial();   // unique per handle created in this process
 };
 
 namespace {
@@ -765,9 +775,12 @@ int batch_capture(igamg_handle** hs, double** Us, const double** Fs, BatchCache&
 }
 
 int batch_prepare(int n, igamg_handle** hs, double** Us, const double** Fs, BatchCache*& bcr) {
-  std::vector<const void*> key;
-  for (int i = 0; i < n; ++i) key.push_back(hs[i]);
-  for (int i = 0; i < n; ++i) { key.push_back(Us[i]); key.push_back(Fs[i]); }
+  std::vector<unsigned long long> key;
+  for (int i = 0; i < n; ++i) key.push_back(hs[i]->serial);
+  for (int i = 0; i < n; ++i) {
+    key.push_back((unsigned long long)(uintptr_t)Us[i]);
+    key.push_back((unsigned long long)(uintptr_t)Fs[i]);
+  }
   igamg_handle* h0 = hs[0];
   if (h0->bc && h0->bc->key == key) { bcr = h0->bc; return IGAMG_OK; }
   batch_cache_free(h0->bc);

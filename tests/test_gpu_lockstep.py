@@ -84,3 +84,32 @@ def test_absolute_tolerance_and_zero_rhs(monkeypatch):
 def test_annulus_group(monkeypatch):
     cases = [(2, 16, 3, s, {"geometry": 1}) for s in (1.0, 1e3, 1e-2)]
     _run(cases, monkeypatch)
+
+
+def test_member_handle_recreated_between_batches(monkeypatch):
+    # the group's captured graphs belong to the batch's list of handles; a member destroyed and
+    # replaced (possibly at the same address) must not reuse them
+    torch = _torch()
+    from paper_1705_09282_gb300.solver import Solver, solve_batch
+    monkeypatch.setenv("IGAMG_FUSED_LEVELS", "-1")
+    monkeypatch.setenv("IGAMG_LOCKSTEP_MIN", "2")
+    p, n, L = 2, 16, 3
+    f = torch.tensor(inputs.grf_forcing(p, n, seed=77), device="cuda")
+    A = Solver(p, n, L, 1.0, 1.0)
+    B = Solver(p, n, L, 10.0, 1.0)
+    FA, FB = A.load_vector(f), B.load_vector(f)
+    UA, UB = A.empty(), B.empty()
+    solve_batch([A, B], [UA, UB], [FA, FB], rtol=1e-8, max_cycles=60)
+    B.close()
+    del B
+    C = Solver(p, n, L, 1e3, 1.0)                     # same structure, other operator
+    FC = C.load_vector(f)
+    UA.zero_()
+    UC = UB                                          # the same vector buffers as before
+    UC.zero_()
+    FB.copy_(FC)
+    reps = solve_batch([A, C], [UA, UC], [FA, FB], rtol=1e-8, max_cycles=60)
+    U1 = C.empty()
+    r1 = C.solve(U1, FC, rtol=1e-8, max_cycles=60)
+    assert reps[1]["cycles"] == r1["cycles"]
+    assert np.array_equal(UC.cpu().numpy(), U1.cpu().numpy())
