@@ -724,7 +724,7 @@ def run_smoothers(args):
 
 def run_annulus(args):
     """Generalized Stokes on the quarter annulus (Sec. 6.2's domain, r = 0.075 .. 0.225,
-    push-forward spaces of Sec. 4.4): p = 2, 256 x 256 elements, 7 grids, sigma/nu in
+    push-forward spaces of Sec. 4.3): p = 2, 256 x 256 elements, 7 grids, sigma/nu in
     {1, 1e3}, the closed-form manufactured forcing, V(2,2) multiplicative, zero guess, to
     1e-8; FP64, FP32-in-FP64 and FGMRES.  The operator is stored per row (three boxes,
     u_x - u_y coupled) and every patch has its own inverse, so the sweeps stream their

@@ -98,7 +98,7 @@ typedef struct {
 /* Domains.  The quarter annulus {r_inner <= |x| <= r_outer, x, y >= 0} is the image of the
  * unit square under F(xi, eta) = (r_inner + (r_outer - r_inner) xi) C(eta), C the rational
  * quadratic Bezier quarter circle (control points (1,0), (1,1), (0,1), weights 1, 1/sqrt(2),
- * 1): xi is radial, eta angular.  The discrete spaces are the push-forwards of Sec. 4.4
+ * 1): xi is radial, eta angular.  The discrete spaces are the push-forwards of Sec. 4.3
  * (velocity by the contravariant Piola map, pressure by 1/det J), so U keeps the unit
  * square's layout of parametric coefficients, div u = (1/det J) div_hat u_hat stays exactly
  * zero, and the curl / streamfunction entry points act on the same coefficients.  The
@@ -155,7 +155,7 @@ int igamg_quad_points_xy(const igamg_handle* h, double* xy, size_t cap, size_t* 
 
 /* F = (l(v), 0, 0), l(v) = int v.f (Sec. 3.1), f at the quadrature points (device), layout
  * (2, n*G, n*G).  On the quarter annulus f is the physical field at the points of
- * igamg_quad_points_xy and l(v) = int (J^T f) . v_hat dxi (Sec. 4.4 push-forward). */
+ * igamg_quad_points_xy and l(v) = int (J^T f) . v_hat dxi (Sec. 4.3 push-forward). */
 int igamg_load_vector(igamg_handle* h, const double* f_qp, double* F);
 
 /* R = F - K_l U on level l (Sec. 3.4; coarse K_l = R K P, Sec. 5.1).  If norm_out is

@@ -1,12 +1,12 @@
 """Generalized Stokes on a mapped 2D domain: isogeometric compatible B-splines defined
-through push-forwards of the parametric spaces (Sec. 4.4), on the quarter annulus of
+through push-forwards of the parametric spaces (Sec. 4.3), on the quarter annulus of
 Sec. 6.2 (inner radius 0.075, outer radius 0.225, quadratic rational Bezier map).
 
 TEST INFRASTRUCTURE ONLY (the oracle).  Only tests/, __graft_entry__.smoke() and
 bench.py's CPU legs may import it; the product path never does.
 
 What it follows:
-  * physical spaces by push-forward (Sec. 4.4): psi = psi_hat o F^-1,
+  * physical spaces by push-forward (Sec. 4.3): psi = psi_hat o F^-1,
     v = (1/det J) J v_hat o F^-1 (contravariant Piola), q = (1/det J) q_hat o F^-1;
     so div v = (1/det J) div_hat v_hat and the discrete complex is kept
   * weak form of Sec. 3.1 / 3.3 on the physical domain, integrated over the parametric

@@ -7,7 +7,7 @@ Everything here is written for clarity, in FP64, following the paper:
   * open knot vectors, first/last knot repeated p+1 times, domain (0,1)  -- Sec. 4.2
   * maximally smooth B-splines on uniform knot vectors                    -- Sec. 6 preamble
   * Cox-de Boor recursion for the basis                                   -- Sec. 4.2
-  * knot insertion transformation matrix T (N_i = sum_j T_ij N~_j)        -- Sec. 4.5
+  * knot insertion transformation matrix T (N_i = sum_j T_ij N~_j)        -- Sec. 4.4
     built here with Boehm's single-knot insertion (a textbook algorithm;
     the paper defers the construction to its references).
 """
@@ -126,7 +126,7 @@ def boehm_insert(knots, degree, xbar):
 
 def refinement_matrix(knots, degree, new_knots_inserted):
     """Prolongation of coefficients (fine x coarse) for inserting the given knots
-    one at a time.  In the notation of Sec. 4.5 this is T transposed:
+    one at a time.  In the notation of Sec. 4.4 this is T transposed:
     u~_j = sum_i T_ij u_i."""
     t = np.array(knots, dtype=np.float64)
     P = np.eye(n_basis(t, degree))

@@ -362,10 +362,13 @@ class Level3D:
 
 
 class Hierarchy3D:
-    def __init__(self, p, n_fine, n_levels, sigma, nu, nu1=2, nu2=2, beta=None, gamma=1):
+    def __init__(self, p, n_fine, n_levels, sigma, nu, nu1=2, nu2=2, beta=None, gamma=1, fine=None):
+        """fine: a prebuilt finest-level discretization (e.g. on a mapped domain) in place of
+        the unit cube's; the coarse levels are its Galerkin products either way."""
         self.p, self.n_levels, self.nu1, self.nu2 = p, n_levels, nu1, nu2
         self.gamma = gamma
-        fine = Stokes3D(p, n_fine, sigma, nu, beta=beta)
+        if fine is None:
+            fine = Stokes3D(p, n_fine, sigma, nu, beta=beta)
         self.fine = fine
         levels, Ps = [None] * n_levels, [None] * n_levels
         K, m = fine.K, fine.m

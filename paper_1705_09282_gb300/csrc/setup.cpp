@@ -6,7 +6,7 @@
 // products R K P of Sec. 5.1; for this bilinear form they equal the same form on the
 // coarse spline space with the Nitsche penalty of the finest mesh (the coarse space is a
 // subspace of the fine one and every integral is exact), which is how they are built.
-// Knot-insertion prolongations (Sec. 4.5) are obtained by collocation at the fine
+// Knot-insertion prolongations (Sec. 4.4) are obtained by collocation at the fine
 // Greville abscissae (Schoenberg-Whitney), not by inserting knots one at a time.
 #include <algorithm>
 #include <cmath>
@@ -409,7 +409,7 @@ void add_advection(int p, const LevelHost& lv, const double* beta, std::vector<d
         }
 }
 
-// ---- mapped domains (Sec. 4.4 push-forwards; Sec. 6.2's quarter annulus) ----------------
+// ---- mapped domains (Sec. 4.3 push-forwards; Sec. 6.2's quarter annulus) ----------------
 // Third record box of a velocity row: its coupling to the other velocity component,
 // 2p x 2p entries.  u_x row (x, y) -> u_y column (x + dx, y + dy), dx in [-p, q],
 // dy in [-q, p]; u_y row -> u_x column, dx in [-q, p], dy in [-p, q].

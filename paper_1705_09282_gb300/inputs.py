@@ -312,3 +312,38 @@ def annulus_forcing(x, y, sigma, nu, r_i=ANNULUS_RI, r_o=ANNULUS_RO):
     fx = sigma * _pval(ux, x, y) - nu * (_pval(_pder(ux, 0, 2), x, y) + _pval(_pder(ux, 1, 2), x, y)) + y
     fy = sigma * _pval(uy, x, y) - nu * (_pval(_pder(uy, 0, 2), x, y) + _pval(_pder(uy, 1, 2), x, y)) + x
     return np.stack([fx, fy])
+
+
+# ---- hollow cylinder section (the quarter annulus extruded by a depth of 0.1) ---------------
+# u = g(z) (d psi/dy, -d psi/dx, 0) with the quarter-annulus psi above and g(z) =
+# 16 (z (d - z))^2 / d^4, which vanishes on all six walls and is divergence-free;
+# p = x y - (r_i^2 + r_o^2) / (2 pi) (zero mean over the section).
+
+CYLINDER_DEPTH = 0.1
+
+
+def _cyl_g(z, d):
+    h = (z * (d - z)) ** 2
+    h2 = 2 * (d - z) ** 2 - 8 * z * (d - z) + 2 * z ** 2
+    return 16.0 * h / d ** 4, 16.0 * h2 / d ** 4
+
+
+def cylinder_solution(x, y, z, r_i=ANNULUS_RI, r_o=ANNULUS_RO, depth=CYLINDER_DEPTH):
+    """(u (3, ...), p (...)) of the manufactured hollow-cylinder solution at (x, y, z)."""
+    c = _annulus_psi_coeffs(r_i, r_o)
+    g, _ = _cyl_g(z, depth)
+    u = np.stack([g * _pval(_pder(c, 1), x, y), -g * _pval(_pder(c, 0), x, y), 0.0 * x])
+    p = x * y - (r_i * r_i + r_o * r_o) / (2.0 * np.pi)
+    return u, p
+
+
+def cylinder_forcing(x, y, z, sigma, nu, r_i=ANNULUS_RI, r_o=ANNULUS_RO, depth=CYLINDER_DEPTH):
+    """f = sigma u - nu lap u + grad p (generalized Stokes, Sec. 3.1) at (x, y, z): (3, ...)."""
+    c = _annulus_psi_coeffs(r_i, r_o)
+    g, g2 = _cyl_g(z, depth)
+    comps = []
+    for a, sgn in ((_pder(c, 1), 1.0), (_pder(c, 0), -1.0)):
+        val = _pval(a, x, y)
+        lap = _pval(_pder(a, 0, 2), x, y) + _pval(_pder(a, 1, 2), x, y)
+        comps.append(sgn * (sigma * g * val - nu * (g * lap + g2 * val)))
+    return np.stack([comps[0] + y, comps[1] + x, 0.0 * x])

@@ -1,4 +1,4 @@
-"""GPU parity on the quarter annulus (Sec. 4.4 push-forwards, Sec. 6.2): quadrature points,
+"""GPU parity on the quarter annulus (Sec. 4.3 push-forwards, Sec. 6.2): quadrature points,
 load vector, level operators, smoother, V-cycles and whole solves against the mapped-domain
 oracle, on the same seeded inputs.  Tolerances as for the unit square: single operator
 applications 1e-13 relative, V-cycle and solve iterates 1e-10 with identical cycle counts."""

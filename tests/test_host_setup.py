@@ -131,7 +131,7 @@ def test_oseen_operators_match_oracle_galerkin(p, n, L):
     assert np.abs(K - K.T).max() > 1e-6 * np.abs(K).max()
 
 
-# ---- quarter annulus (Sec. 4.4 push-forwards, Sec. 6.2) ----------------------------------
+# ---- quarter annulus (Sec. 4.3 push-forwards, Sec. 6.2) ----------------------------------
 
 @pytest.mark.parametrize("p,n,L,sigma,nu", [(2, 8, 3, 1.3, 0.7), (3, 8, 2, 1.0, 1.0), (2, 12, 2, 1e3, 1.0)])
 def test_annulus_operators_match_oracle(p, n, L, sigma, nu):

@@ -1,4 +1,4 @@
-"""Pins for the mapped-domain oracle (Sec. 4.4 push-forwards, Sec. 6.2 quarter annulus):
+"""Pins for the mapped-domain oracle (Sec. 4.3 push-forwards, Sec. 6.2 quarter annulus):
 the identity map reproduces the unit-square oracle, the map is the quarter annulus, the
 pushed-forward spaces keep the discrete complex, the discrete solution converges to a
 closed-form solution at the expected rates, and the V-cycle counts follow the paper's

@@ -70,7 +70,7 @@ def test_cardinal_quadratic_mass_and_stiffness_rows():
 
 
 def test_knot_insertion_figure_example():
-    # Sec. 4.5 figure: Xi = (0,0,0,.2,.4,.6,.8,1,1,1) refined at the midpoints gives
+    # Sec. 4.4 figure: Xi = (0,0,0,.2,.4,.6,.8,1,1,1) refined at the midpoints gives
     # (0,0,0,.1,...,.9,1,1,1); the function is the same before and after.
     t = np.array([0, 0, 0, .2, .4, .6, .8, 1, 1, 1.0])
     tf, P = bs.refinement_matrix(t, 2, [.1, .3, .5, .7, .9])
