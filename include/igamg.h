@@ -90,8 +90,9 @@ typedef struct {
                          solved exactly, one cycle per finer level from the prolongated
                          coarser solution), U += its result; it counts as one cycle.
                          Not with the FGMRES precisions (IGAMG_EUNSUPPORTED). */
-  int geometry;       /* IGAMG_GEOM_SQUARE (unit square / cube) or, 2D generalized Stokes
-                         only, IGAMG_GEOM_QUARTER_ANNULUS (Sec. 6.2's domain) */
+  int geometry;       /* IGAMG_GEOM_SQUARE (unit square / cube); generalized Stokes only:
+                         IGAMG_GEOM_QUARTER_ANNULUS (2D, Sec. 6.2's domain) or
+                         IGAMG_GEOM_HOLLOW_CYLINDER (3D, Sec. 6.4: the annulus extruded by 0.1) */
   double r_inner, r_outer; /* quarter annulus radii; <= 0 selects 0.075 and 0.225 */
 } igamg_problem;
 
@@ -105,7 +106,10 @@ typedef struct {
  * operator has variable coefficients and couples u_x with u_y; it is assembled on the host
  * at creation (Nitsche terms on all four walls with h = the element height normal to the
  * wall), the coarse operators are Galerkin products and every patch has its own inverse. */
-enum { IGAMG_GEOM_SQUARE = 0, IGAMG_GEOM_QUARTER_ANNULUS = 1 };
+/* The hollow cylinder section is that map extruded: F(xi, eta, zeta) = (quarter-annulus map
+ * of (xi, eta), 0.1 zeta); its operator couples u_x with u_y (an extra record box per row of
+ * those two), u_z only with itself and the pressure. */
+enum { IGAMG_GEOM_SQUARE = 0, IGAMG_GEOM_QUARTER_ANNULUS = 1, IGAMG_GEOM_HOLLOW_CYLINDER = 2 };
 
 typedef struct {
   int n;              /* elements per direction on this level */
@@ -147,15 +151,15 @@ int igamg_get_sizes(const igamg_handle* h, int level, igamg_sizes* out);
  * f and beta are sampled at their tensor products, layout (2, n*G, n*G) [comp][y][x]. */
 int igamg_quad_points(const igamg_handle* h, double* x, size_t cap, size_t* n_out);
 
-/* Physical coordinates of the finest level's quadrature points, (2, n*G, n*G) [x or y][eta
- * point][xi point] (host, capacity cap >= *n_out = 2 (n*G)^2): on the unit square the tensor
- * products of igamg_quad_points, on the quarter annulus their images under the map.  2D only
- * (IGAMG_EUNSUPPORTED for a 3D handle). */
+/* Physical coordinates of the finest level's quadrature points (host, capacity cap >= *n_out):
+ * 2D (2, n*G, n*G) [x or y][eta point][xi point], 3D (3, n*G, n*G, n*G) [x, y or z][zeta][eta]
+ * [xi]; on the unit square / cube the tensor products of igamg_quad_points, on a mapped
+ * domain their images under the map. */
 int igamg_quad_points_xy(const igamg_handle* h, double* xy, size_t cap, size_t* n_out);
 
 /* F = (l(v), 0, 0), l(v) = int v.f (Sec. 3.1), f at the quadrature points (device), layout
- * (2, n*G, n*G).  On the quarter annulus f is the physical field at the points of
- * igamg_quad_points_xy and l(v) = int (J^T f) . v_hat dxi (Sec. 4.3 push-forward). */
+ * (2, n*G, n*G) (3D: (3, n*G, n*G, n*G)).  On a mapped domain f is the physical field at the
+ * points of igamg_quad_points_xy and l(v) = int (J^T f) . v_hat dxi (Sec. 4.3 push-forward). */
 int igamg_load_vector(igamg_handle* h, const double* f_qp, double* F);
 
 /* R = F - K_l U on level l (Sec. 3.4; coarse K_l = R K P, Sec. 5.1).  If norm_out is

@@ -13,7 +13,7 @@ IGAMG_OK = 0
 IGAMG_NOT_CONVERGED = 1
 IGAMG_MULT, IGAMG_ADD = 0, 1
 IGAMG_FP64, IGAMG_FP32_IR, IGAMG_FGMRES_FP64, IGAMG_FGMRES_FP32 = 0, 1, 2, 3
-IGAMG_GEOM_SQUARE, IGAMG_GEOM_QUARTER_ANNULUS = 0, 1
+IGAMG_GEOM_SQUARE, IGAMG_GEOM_QUARTER_ANNULUS, IGAMG_GEOM_HOLLOW_CYLINDER = 0, 1, 2
 
 
 class Problem(ctypes.Structure):

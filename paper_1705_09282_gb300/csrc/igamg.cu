@@ -1577,7 +1577,22 @@ int igamg_load_vector(igamg_handle* h, const double* f_qp, double* F) {
 
 int igamg_quad_points_xy(const igamg_handle* h, double* xy, size_t cap, size_t* n_out) {
   if (!h || !n_out) return IGAMG_EINVAL;
-  if (h->d3) return IGAMG_EUNSUPPORTED;
+  if (h->d3) {                                       // (3, nG, nG, nG) [x, y or z][z][y][x]
+    const std::vector<double>& qx = h3_quad_x(h->d3);
+    const std::vector<double>& q3 = h3_quad_xyz(h->d3);
+    const size_t nG = qx.size(), np = nG * nG * nG;
+    *n_out = 3 * np;
+    if (!xy) return IGAMG_OK;
+    if (cap < 3 * np) return IGAMG_EINVAL;
+    if (!q3.empty()) { std::memcpy(xy, q3.data(), 3 * np * sizeof(double)); return IGAMG_OK; }
+    for (size_t iz = 0; iz < nG; ++iz)
+      for (size_t iy = 0; iy < nG; ++iy)
+        for (size_t ix = 0; ix < nG; ++ix) {
+          const size_t o = (iz * nG + iy) * nG + ix;
+          xy[o] = qx[ix]; xy[np + o] = qx[iy]; xy[2 * np + o] = qx[iz];
+        }
+    return IGAMG_OK;
+  }
   const std::vector<double>& qx = h->host.quad_x;
   const size_t nG = qx.size();
   *n_out = 2 * nG * nG;

@@ -239,6 +239,7 @@ struct igamg3d_handle {
   std::vector<void*> allocs;
   KrylovWork kw;                    // FGMRES modes
   double* zeros = nullptr;
+  double* jt = nullptr;              // mapped domains: J^T at the finest quadrature points
 };
 
 namespace {
@@ -315,10 +316,16 @@ int upload_typed(igamg3d_handle* h, Typed3<T>& ty) {
     Lt.cm0 = cm[0]; Lt.cm1 = cm[1]; Lt.cm2 = cm[2]; Lt.cm3 = cm[3];
     Lt.rc0 = rc4[0]; Lt.rc1 = rc4[1]; Lt.rc2 = rc4[2]; Lt.rc3 = rc4[3];
     Lt.srow = nullptr;
+    Lt.sext = nullptr;
     if (!hl.rows.empty()) {
       T* sr = nullptr;
       if ((rc = upload_as(h, &sr, hl.rows))) return rc;
       Lt.srow = sr;
+    }
+    if (!hl.ext.empty()) {
+      T* se = nullptr;
+      if ((rc = upload_as(h, &se, hl.ext))) return rc;
+      Lt.sext = se;
     }
     if (l >= 1) {
       // the lane-group kernel's tables (maxl-stride inverses) only for class-record levels
@@ -523,6 +530,17 @@ int do_fmg(igamg3d_handle* h, cudaStream_t s) {
   return IGAMG_OK;
 }
 
+// mapped domains: the parametric load J^T f at every quadrature point (f and fh may alias)
+static __global__ void k_pullback3(int npts, const double* __restrict__ jt, const double* f, double* fh) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npts) return;
+  const double fx = f[i], fy = f[(size_t)npts + i], fz = f[(size_t)2 * npts + i];
+  const double* t = jt + (size_t)9 * i;              // t[3k + c] = dX_c / dxi_k
+  fh[i] = t[0] * fx + t[1] * fy + t[2] * fz;
+  fh[(size_t)npts + i] = t[3] * fx + t[4] * fy + t[5] * fz;
+  fh[(size_t)2 * npts + i] = t[6] * fx + t[7] * fy + t[8] * fz;
+}
+
 static __global__ void k_add_to3(int n, const double* __restrict__ E, double* __restrict__ U) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) U[i] += E[i];
@@ -712,7 +730,12 @@ int validate3(const igamg_problem& pr) {
   if (pr.smoother != IGAMG_MULT) return IGAMG_EUNSUPPORTED;   // eq. ASM is not built in 3D
   if (pr.precision < IGAMG_FP64 || pr.precision > IGAMG_FGMRES_FP32) return IGAMG_EUNSUPPORTED;
   if (pr.gamma < 0 || pr.gamma > 4 || pr.fmg < 0 || pr.fmg > 1) return IGAMG_EINVAL;
-  if (pr.geometry != IGAMG_GEOM_SQUARE) return IGAMG_EUNSUPPORTED;   // the unit cube only
+  if (pr.geometry != IGAMG_GEOM_SQUARE && pr.geometry != IGAMG_GEOM_HOLLOW_CYLINDER) return IGAMG_EUNSUPPORTED;
+  if (pr.geometry == IGAMG_GEOM_HOLLOW_CYLINDER) {
+    if (pr.beta_qp) return IGAMG_EUNSUPPORTED;                          // generalized Stokes only
+    const double ri = pr.r_inner > 0 ? pr.r_inner : 0.075, ro = pr.r_outer > 0 ? pr.r_outer : 0.225;
+    if (!(ri > 0) || !(ro > ri) || !std::isfinite(ro)) return IGAMG_EINVAL;
+  }
   if (pr.fmg && pr.precision >= IGAMG_FGMRES_FP64) return IGAMG_EUNSUPPORTED;
   if (sizes3(pr.p, pr.n_fine).n_total > (1LL << 30)) return IGAMG_EINVAL;   // 32-bit row indices
   if (sizes3(pr.p, pr.n_fine >> (pr.n_levels - 1)).n_total > 4096) return IGAMG_EINVAL;
@@ -763,6 +786,7 @@ int h3_create(const igamg_problem* prob, void* cuda_stream, igamg3d_handle** out
   if ((rc = upload_as(h, &h->lv_p, h->host.lv_p)) || (rc = upload_as(h, &h->lv_q, h->host.lv_q))) return fail(rc);
   size_t nG = (size_t)pr.n_fine * (p + 2);
   if ((rc = dmalloc(h, (void**)&h->f_dev, 3 * nG * nG * nG * sizeof(double)))) return fail(rc);
+  if (!h->host.jt.empty() && (rc = upload_as(h, &h->jt, h->host.jt))) return fail(rc);
   if ((rc = dmalloc(h, (void**)&h->Fh, nfine * sizeof(double)))) return fail(rc);
   if ((rc = dmalloc(h, (void**)&h->Uh, nfine * sizeof(double)))) return fail(rc);
   size_t npsi = (size_t)3 * fs.nq * fs.ni * fs.ni;
@@ -814,9 +838,16 @@ int h3_sizes(const igamg3d_handle* h, int level, igamg_sizes* out) {
 }
 
 const std::vector<double>& h3_quad_x(const igamg3d_handle* h) { return h->host.quad_x; }
+const std::vector<double>& h3_quad_xyz(const igamg3d_handle* h) { return h->host.quad_xyz; }
 
 int h3_load_vector(igamg3d_handle* h, const double* f_qp, double* F) {
   auto& Lt = h->d.lev.back().L;
+  if (h->jt) {                                      // mapped domain: load J^T f
+    const int nG = h->prob.n_fine * (h->prob.p + 2);
+    const int npts = nG * nG * nG;
+    k_pullback3<<<nblk(npts), kBlock, 0, h->stream>>>(npts, h->jt, f_qp, h->f_dev);
+    f_qp = h->f_dev;
+  }
   if (h->prob.p == 2) k_load3<2><<<nblk(Lt.n_total), kBlock, 0, h->stream>>>(Lt, h->lv_p, h->lv_q, f_qp, F);
   else k_load3<3><<<nblk(Lt.n_total), kBlock, 0, h->stream>>>(Lt, h->lv_p, h->lv_q, f_qp, F);
   return launch_check();
@@ -990,14 +1021,16 @@ int host_operator_rows3(const igamg_problem* prob, int level, double* K, size_t 
   one.c_penalty *= (double)prob->n_fine / one.n_fine;   // keep C_I / h_fine
   // Stokes: only this level's records (one-level build of this mesh); Oseen: the level of the
   // full operator hierarchy (coarse levels are Galerkin products)
-  if ((rc = prob->beta_qp ? build_operators3(*prob, H, err) : build_level_only3(one, H, err))) return rc;
-  const auto& lh = prob->beta_qp ? H.lev[level] : H.lev[0];
+  const bool whole = prob->beta_qp || prob->geometry == IGAMG_GEOM_HOLLOW_CYLINDER;
+  if ((rc = whole ? build_operators3(*prob, H, err) : build_level_only3(one, H, err))) return rc;
+  const auto& lh = whole ? H.lev[level] : H.lev[0];
   LevelTab3<double> L{};
   L.n = lh.sz.n; L.ni = lh.sz.ni; L.nq = lh.sz.nq;
   L.n_uc = (int)lh.sz.n_uc; L.n_u = (int)lh.sz.n_u; L.n_p = (int)lh.sz.n_p; L.n_total = (int)lh.sz.n_total;
   L.cm0 = lh.st.cmap[0].data(); L.cm1 = lh.st.cmap[1].data(); L.cm2 = lh.st.cmap[2].data(); L.cm3 = lh.st.cmap[3].data();
   L.rc0 = lh.st.rec[0].data(); L.rc1 = lh.st.rec[1].data(); L.rc2 = lh.st.rec[2].data(); L.rc3 = lh.st.rec[3].data();
   L.srow = lh.rows.empty() ? nullptr : lh.rows.data();
+  L.sext = lh.ext.empty() ? nullptr : lh.ext.data();
   long long n = lh.sz.n_total;
   if (n_out) *n_out = n;
   if (!K) return IGAMG_OK;
@@ -1030,8 +1063,9 @@ int host_operator_apply3(const igamg_problem* prob, int level, const double* V, 
   std::string err;
   // Stokes: only this level's records (one-level build of this mesh); Oseen: the level of the
   // full operator hierarchy (coarse levels are Galerkin products)
-  if ((rc = prob->beta_qp ? build_operators3(*prob, H, err) : build_level_only3(one, H, err))) return rc;
-  const auto& lh = prob->beta_qp ? H.lev[level] : H.lev[0];
+  const bool whole = prob->beta_qp || prob->geometry == IGAMG_GEOM_HOLLOW_CYLINDER;
+  if ((rc = whole ? build_operators3(*prob, H, err) : build_level_only3(one, H, err))) return rc;
+  const auto& lh = whole ? H.lev[level] : H.lev[0];
   if (n != (size_t)lh.sz.n_total) return IGAMG_EINVAL;
   LevelTab3<double> L{};
   L.n = lh.sz.n; L.ni = lh.sz.ni; L.nq = lh.sz.nq;
@@ -1039,6 +1073,7 @@ int host_operator_apply3(const igamg_problem* prob, int level, const double* V, 
   L.cm0 = lh.st.cmap[0].data(); L.cm1 = lh.st.cmap[1].data(); L.cm2 = lh.st.cmap[2].data(); L.cm3 = lh.st.cmap[3].data();
   L.rc0 = lh.st.rec[0].data(); L.rc1 = lh.st.rec[1].data(); L.rc2 = lh.st.rec[2].data(); L.rc3 = lh.st.rec[3].data();
   L.srow = lh.rows.empty() ? nullptr : lh.rows.data();
+  L.sext = lh.ext.empty() ? nullptr : lh.ext.data();
   double lam = 0.0;
   for (size_t i = 0; i + 1 < n; ++i) {
     double m = 0.0;

@@ -17,6 +17,7 @@ void h3_destroy(igamg3d_handle* h);
 int h3_levels(const igamg3d_handle* h);
 int h3_sizes(const igamg3d_handle* h, int level, igamg_sizes* out);
 const std::vector<double>& h3_quad_x(const igamg3d_handle* h);
+const std::vector<double>& h3_quad_xyz(const igamg3d_handle* h);   // mapped domains, else empty
 int h3_load_vector(igamg3d_handle* h, const double* f_qp, double* F);
 int h3_residual(igamg3d_handle* h, int level, const double* U, const double* F, double* R, double* norm_out);
 int h3_smooth(igamg3d_handle* h, int level, double* U, const double* F, int sweeps);

@@ -186,6 +186,9 @@ struct LevelHost3 {
   // but lambda) the full record = class record + advection, as the kernels read it
   std::vector<double> adv;
   std::vector<double> rows;
+  // mapped domains only (empty otherwise): per u_x / u_y row (0 .. 2 n_uc - 1) the
+  // 2p x 2p x (2p-1) coefficients coupling it to the other of the two components
+  std::vector<double> ext;
 };
 
 struct HierarchyHost3 {
@@ -197,6 +200,10 @@ struct HierarchyHost3 {
   int ndof0 = 0;
   int G = 0;
   std::vector<double> lv_p, lv_q, quad_x;
+  // mapped domains: physical quadrature points (3, nG, nG, nG) [component][z][y][x] and
+  // J^T there, (nG^3, 3, 3) [.][k][i] = dX_i/dxi_k (the load is int (J^T f) . v_hat)
+  int geometry = 0;
+  std::vector<double> quad_xyz, jt;
 };
 
 int build_hierarchy3(const igamg_problem& pr, HierarchyHost3& H, std::string& err);

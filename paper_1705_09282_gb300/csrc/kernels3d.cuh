@@ -20,6 +20,8 @@ struct LevelTab3 {
   const int *cm0, *cm1, *cm2, *cm3;      // class -> record, per row kind
   const T *rc0, *rc1, *rc2, *rc3;        // records, per row kind
   const T* srow;                         // per-row records (generalized Oseen), or null
+  const T* sext;                         // mapped domains: per u_x / u_y row the 2P x 2P x (2Q+1)
+                                         // coefficients on the other of the two, or null
 };
 
 template <int P>
@@ -94,6 +96,47 @@ __host__ __device__ __forceinline__ T box3(const LevelTab3<T>& L, const T* __res
   return (s0 + sA) + (sB + sC);
 }
 
+// extra box of a u_x (kind 0) or u_y (kind 1) row on a mapped domain: the other component's
+// columns x + ox .. x + ox + 2P - 1, y + oy .. y + oy + 2P - 1, z - Q .. z + Q (ox, oy = -P, -Q
+// for u_x rows, -Q, -P for u_y rows), coefficients se[(a 2P + b) W + c]; clamped positions
+// carry zero coefficients
+template <int P, typename T>
+__host__ __device__ __forceinline__ T ext3(const LevelTab3<T>& L, const T* __restrict__ se, const T* __restrict__ U,
+                                  int kind, int x, int y, int z) {
+  constexpr int Q = P - 1, W = 2 * Q + 1, L2 = 2 * P;
+  const int ob = 1 - kind;
+  const int ox = kind == 0 ? -P : -Q, oy = kind == 0 ? -Q : -P;
+  int lo0, hi0, s0, lo1, hi1, s1, lo2, hi2, s2;
+  axis3(L, ob, 0, lo0, hi0, s0);
+  axis3(L, ob, 1, lo1, hi1, s1);
+  axis3(L, ob, 2, lo2, hi2, s2);
+  const T* base = U + ob * L.n_uc;
+  int A[L2], B[L2], Cz[W];
+#pragma unroll
+  for (int a = 0; a < L2; ++a) {
+    A[a] = (clampi(x + ox + a, lo0, hi0) - lo0) * s0;
+    B[a] = (clampi(y + oy + a, lo1, hi1) - lo1) * s1;
+  }
+#pragma unroll
+  for (int c = 0; c < W; ++c) Cz[c] = (clampi(z - Q + c, lo2, hi2) - lo2) * s2;
+  T sa = T(0), sb = T(0);
+#pragma unroll
+  for (int a = 0; a < L2; ++a)
+#pragma unroll
+    for (int b = 0; b < L2; ++b)
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const int j = (a * L2 + b) * W + c;
+        const T v = base[A[a] + B[b] + Cz[c]];
+        if (j & 1) sb = fma(se[j], v, sb);
+        else sa = fma(se[j], v, sa);
+      }
+  return sa + sb;
+}
+
+template <int P>
+__host__ __device__ constexpr int ext3_len() { return 4 * P * P * (2 * P - 1); }
+
 // record of row g = (kind; x, y, z)
 template <int P, typename T>
 __host__ __device__ __forceinline__ const T* rec3(const LevelTab3<T>& L, int kind, int x, int y, int z, int g) {
@@ -125,8 +168,9 @@ __host__ __device__ __forceinline__ T row3(const LevelTab3<T>& L, const T* __res
     acc += box3<P, 2 * P>(L, rc + R::B0 + R::B1, U, 2, 2, -(P - 1), x, y, z);
     acc = fma(rc[R::RU - 1], U[L.n_total - 1], acc);
     if (m) *m = rc[R::RU - 1];
-  } else if (m) {
-    *m = T(0);
+  } else {
+    if (L.sext && kind < 2) acc += ext3<P>(L, L.sext + (size_t)g * ext3_len<P>(), U, kind, x, y, z);
+    if (m) *m = T(0);
   }
   return acc;
 }
@@ -240,6 +284,8 @@ __global__ void __launch_bounds__(3 * S) k_mult_rows3x(LevelTab3<T> L, T* __rest
       acc = -box3<P, 2 * P>(L, rc + R::B0, U, vel ? 3 : 1, vel ? kind : 1, vel ? -P : -(P - 1), x, y, z);
     } else if (!vel) {
       acc = -fma(rc[R::RU - 1], U[L.n_total - 1], box3<P, 2 * P>(L, rc + R::B0 + R::B1, U, 2, 2, -(P - 1), x, y, z));
+    } else if (L.sext && kind < 2) {
+      acc = -ext3<P>(L, L.sext + (size_t)g * ext3_len<P>(), U, kind, x, y, z);
     }
   }
   part[w][t] = acc;
@@ -414,6 +460,8 @@ __global__ void __launch_bounds__(1024) k_cluster3(Cluster3Desc<T> D, const T* _
               acc = -box3<P, 2 * P>(V.L, rc + R::B0, U, vel ? 3 : 1, vel ? kind : 1, vel ? -P : -(P - 1), x, y, z);
             else if (!vel)
               acc = -fma(rc[R::RU - 1], U[V.L.n_total - 1], box3<P, 2 * P>(V.L, rc + R::B0 + R::B1, U, 2, 2, -(P - 1), x, y, z));
+            else if (V.L.sext && kind < 2)
+              acc = -ext3<P>(V.L, V.L.sext + (size_t)g * ext3_len<P>(), U, kind, x, y, z);
           }
           part3[tid] = acc;
           __syncthreads();

@@ -522,6 +522,424 @@ void rows_with_advection3(int p, const LevelHost3& lv, std::vector<double>& rows
   }
 }
 
+// ---- mapped domains (Sec. 4.3 push-forwards; Sec. 6.4's hollow cylinder section) ----------
+// Position of column b in the record of row a (boxes 0..2), or -1.
+int rec_pos3(int p, const Dof3& a, const Dof3& b) {
+  const int q = p - 1, W = 2 * q + 1;
+  const int nbox = a.blk < 3 ? 2 : 3;
+  for (int k = 0; k < nbox; ++k) {
+    Box3 bx = box_of(p, a.blk, k);
+    if (bx.blk != b.blk) continue;
+    const int c = bx.axis, o1 = (c + 1) % 3, o2 = (c + 2) % 3;
+    const int da = b.i[c] - a.i[c] - bx.org, e1 = b.i[o1] - a.i[o1] + q, e2 = b.i[o2] - a.i[o2] + q;
+    if (da < 0 || da >= bx.len || e1 < 0 || e1 >= W || e2 < 0 || e2 >= W) return -1;
+    return box_start(p, k) + (da * W + e1) * W + e2;
+  }
+  return -1;
+}
+
+// Column of record entry e of row a (blk = -1 outside the free ranges; 4 = lambda).
+Dof3 rec_col3(const Sizes3& s, int p, const Dof3& a, int e) {
+  const int q = p - 1, W = 2 * q + 1, RU = (2 * p + 1) * W * W + 2 * 2 * p * W * W + 1;
+  Dof3 c{-1, {0, 0, 0}};
+  if (e == RU - 1) { if (a.blk == 3) c.blk = 4; return c; }
+  const int nbox = a.blk < 3 ? 2 : 3;
+  for (int k = nbox - 1; k >= 0; --k) {
+    const int st = box_start(p, k);
+    if (e < st) continue;
+    Box3 bx = box_of(p, a.blk, k);
+    const int f = e - st, da = f / (W * W), e1 = (f / W) % W, e2 = f % W;
+    if (da >= bx.len) return c;
+    const int ax = bx.axis, o1 = (ax + 1) % 3, o2 = (ax + 2) % 3;
+    c.blk = bx.blk;
+    c.i[ax] = a.i[ax] + bx.org + da; c.i[o1] = a.i[o1] - q + e1; c.i[o2] = a.i[o2] - q + e2;
+    if (gid3(s, c.blk, c.i) < 0) c.blk = -1;
+    return c;
+  }
+  return c;
+}
+
+// Extra box of a u_x or u_y row (mapped domains): its coupling to the other of the two,
+// 2p x 2p x (2q+1) entries [x][y][z]; u_x row -> u_y columns x - p .. x + q, y - q .. y + p;
+// u_y row -> u_x columns x - q .. x + p, y - p .. y + q; z - q .. z + q for both.
+int ext_pos3(int p, const Dof3& a, const Dof3& b) {
+  const int q = p - 1, W = 2 * q + 1, L2 = 2 * p;
+  if (!((a.blk == 0 && b.blk == 1) || (a.blk == 1 && b.blk == 0))) return -1;
+  const int ox = a.blk == 0 ? -p : -q, oy = a.blk == 0 ? -q : -p;
+  const int ix = b.i[0] - a.i[0] - ox, iy = b.i[1] - a.i[1] - oy, iz = b.i[2] - a.i[2] + q;
+  if (ix < 0 || ix >= L2 || iy < 0 || iy >= L2 || iz < 0 || iz >= W) return -1;
+  return (ix * L2 + iy) * W + iz;
+}
+
+Dof3 ext_col3(const Sizes3& s, int p, const Dof3& a, int e) {
+  const int q = p - 1, W = 2 * q + 1, L2 = 2 * p;
+  Dof3 c{-1, {0, 0, 0}};
+  if (a.blk != 0 && a.blk != 1) return c;
+  const int ox = a.blk == 0 ? -p : -q, oy = a.blk == 0 ? -q : -p;
+  c.blk = 1 - a.blk;
+  c.i[0] = a.i[0] + ox + e / (L2 * W);
+  c.i[1] = a.i[1] + oy + (e / W) % L2;
+  c.i[2] = a.i[2] - q + e % W;
+  if (gid3(s, c.blk, c.i) < 0) c.blk = -1;
+  return c;
+}
+
+// F(xi, eta, zeta) = (r(xi) C(eta), d zeta): the quarter annulus (rational quadratic
+// Bezier quarter circle C, radius r = ri + (ro - ri) xi) extruded by the depth d.
+void cylinder_map(double ri, double ro, double d, const double xi3[3], double X[3], double DF[3][3],
+                  double D2[3][3][3]) {
+  const double xi = xi3[0], eta = xi3[1], zeta = xi3[2];
+  const double w = std::sqrt(0.5), t = eta, u = 1.0 - eta;
+  const double Nx = u * u + w * 2 * t * u, Ny = w * 2 * t * u + t * t;
+  const double dNx = -2 * u + w * (2 - 4 * t), dNy = w * (2 - 4 * t) + 2 * t;
+  const double ddNx = 2 - 4 * w, ddNy = -4 * w + 2;
+  const double Wt = u * u + w * 2 * t * u + t * t, dW = -2 * u + w * (2 - 4 * t) + 2 * t, ddW = 4 - 4 * w;
+  const double C[2] = {Nx / Wt, Ny / Wt};
+  const double A[2] = {dNx * Wt - Nx * dW, dNy * Wt - Ny * dW};
+  const double dA[2] = {ddNx * Wt - Nx * ddW, ddNy * Wt - Ny * ddW};
+  const double dr = ro - ri, r = ri + dr * xi;
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) {
+      DF[i][k] = 0.0;
+      for (int l = 0; l < 3; ++l) D2[i][k][l] = 0.0;
+    }
+  for (int i = 0; i < 2; ++i) {
+    const double dC = A[i] / (Wt * Wt), ddC = dA[i] / (Wt * Wt) - 2 * A[i] * dW / (Wt * Wt * Wt);
+    X[i] = r * C[i];
+    DF[i][0] = dr * C[i];
+    DF[i][1] = r * dC;
+    D2[i][0][1] = D2[i][1][0] = dr * dC;
+    D2[i][1][1] = r * ddC;
+  }
+  X[2] = d * zeta;
+  DF[2][2] = d;
+}
+
+struct Geo3 { double X[3], DF[3][3], D2[3][3][3], J, dJ[3], inv[3][3]; };
+
+Geo3 geo3_at(double ri, double ro, double d, const double xi3[3]) {
+  Geo3 g;
+  cylinder_map(ri, ro, d, xi3, g.X, g.DF, g.D2);
+  const auto& M = g.DF;
+  g.inv[0][0] = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+  g.inv[0][1] = M[0][2] * M[2][1] - M[0][1] * M[2][2];
+  g.inv[0][2] = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+  g.inv[1][0] = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+  g.inv[1][1] = M[0][0] * M[2][2] - M[0][2] * M[2][0];
+  g.inv[1][2] = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+  g.inv[2][0] = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+  g.inv[2][1] = M[0][1] * M[2][0] - M[0][0] * M[2][1];
+  g.inv[2][2] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+  g.J = M[0][0] * g.inv[0][0] + M[0][1] * g.inv[1][0] + M[0][2] * g.inv[2][0];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) g.inv[i][j] /= g.J;
+  // d det J / dxi_k = det J tr(J^-1 dJ/dxi_k) (Jacobi's formula)
+  for (int k = 0; k < 3; ++k) {
+    double tr = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) tr += g.inv[i][j] * g.D2[j][i][k];
+    g.dJ[k] = g.J * tr;
+  }
+  return g;
+}
+
+struct Pushed3 { double v[3], g[3][3], divh; };
+
+// v = N a_c / det J (contravariant Piola, a_c = column c of DF) with its physical gradient
+Pushed3 push3(double N, const double dN[3], int c, const Geo3& G) {
+  Pushed3 o;
+  double Gk[3][3];
+  for (int i = 0; i < 3; ++i) {
+    const double a = G.DF[i][c];
+    o.v[i] = N * a / G.J;
+    for (int k = 0; k < 3; ++k) Gk[i][k] = dN[k] * a / G.J + N * G.D2[i][c][k] / G.J - N * a * G.dJ[k] / (G.J * G.J);
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) o.g[i][j] = Gk[i][0] * G.inv[0][j] + Gk[i][1] * G.inv[1][j] + Gk[i][2] * G.inv[2][j];
+  o.divh = dN[c];
+  return o;
+}
+
+struct LocalVel3 { int n = 0; long long gid[128]; Dof3 d[128]; Pushed3 f[128]; };
+
+// free velocity functions of element e at parametric point xi3
+void local_velocity3(const Sizes3& s, int p, const int e[3], const std::vector<double>& tp,
+                     const std::vector<double>& tq, const double xi3[3], const Geo3& G, LocalVel3& out) {
+  const int q = p - 1;
+  double Np[3][8], dNp[3][8], Nq[3][8], dNq[3][8];
+  for (int ax = 0; ax < 3; ++ax) {
+    span_values(tp, p, e[ax] + p, xi3[ax], Np[ax]); span_derivs(tp, p, e[ax] + p, xi3[ax], dNp[ax]);
+    span_values(tq, q, e[ax] + q, xi3[ax], Nq[ax]); span_derivs(tq, q, e[ax] + q, xi3[ax], dNq[ax]);
+  }
+  out.n = 0;
+  for (int c = 0; c < 3; ++c) {
+    int deg[3] = {q, q, q};
+    deg[c] = p;
+    for (int kz = 0; kz <= deg[2]; ++kz)
+      for (int ky = 0; ky <= deg[1]; ++ky)
+        for (int kx = 0; kx <= deg[0]; ++kx) {
+          const int k[3] = {kx, ky, kz};
+          Dof3 d{c, {e[0] + kx, e[1] + ky, e[2] + kz}};
+          const long long g = gid3(s, c, d.i);
+          if (g < 0) continue;
+          double val[3], der[3];
+          for (int ax = 0; ax < 3; ++ax) {
+            val[ax] = ax == c ? Np[ax][k[ax]] : Nq[ax][k[ax]];
+            der[ax] = ax == c ? dNp[ax][k[ax]] : dNq[ax][k[ax]];
+          }
+          const double N = val[0] * val[1] * val[2];
+          const double dN[3] = {der[0] * val[1] * val[2], val[0] * der[1] * val[2], val[0] * val[1] * der[2]};
+          out.gid[out.n] = g; out.d[out.n] = d;
+          out.f[out.n++] = push3(N, dN, c, G);
+        }
+  }
+}
+
+// K(row a, column b) += val into the level's records; returns |val| when (a, b) lies outside
+// the record pattern (then nothing is stored).
+double put3(int p, std::vector<double>& rows, std::vector<double>& ext, const Dof3& a, long long ga, const Dof3& b,
+            double val) {
+  const int q = p - 1, W = 2 * q + 1, RU = (2 * p + 1) * W * W + 4 * p * W * W + 1, BX = 4 * p * p * W;
+  int pos = rec_pos3(p, a, b);
+  if (pos >= 0) { rows[(size_t)ga * RU + pos] += val; return 0.0; }
+  pos = ext_pos3(p, a, b);
+  if (pos >= 0) { ext[(size_t)ga * BX + pos] += val; return 0.0; }
+  return std::fabs(val);
+}
+
+// Fine-level operator of generalized Stokes on the hollow cylinder section, in record form:
+// sigma (u, v) + nu (grad u, grad v) - (div v, p) + (div u, q) on the physical domain with
+// (p+2)-point Gauss rules per direction; Nitsche terms on the six faces, h = det J /
+// (|t1 x t2| n); the multiplier column m_j = int q_hat_j dxi.  Also fills the physical
+// quadrature points and J^T for the load vector.
+int assemble_mapped3(int p, LevelHost3& lv, double sigma, double nu, double cpen, double ri, double ro, double depth,
+                     HierarchyHost3& H, std::string& err) {
+  const int q = p - 1, W = 2 * q + 1, n = lv.sz.n, G = p + 2, nG = n * G;
+  const int RU = (2 * p + 1) * W * W + 4 * p * W * W + 1, BX = 4 * p * p * W;
+  const auto& sz = lv.sz;
+  lv.rows.assign((size_t)(sz.n_total - 1) * RU, 0.0);
+  lv.ext.assign((size_t)2 * sz.n_uc * BX, 0.0);
+  std::vector<double> gx, gw;
+  gauss01(G, gx, gw);
+  auto tp = knots(p, n), tq = knots(q, n);
+  double outside = 0.0, scale = 0.0;
+  // an element slab ez writes only the records of functions with z index in [ez, ez + p],
+  // so slabs p + 2 apart never share a record: p + 2 sequential phases
+  const unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<double> out_max(nth, 0.0), sc_max(nth, 0.0);
+  for (int ph = 0; ph < p + 2; ++ph) {
+    std::vector<int> ezs;
+    for (int ez = ph; ez < n; ez += p + 2) ezs.push_back(ez);
+    auto work = [&](unsigned t, size_t i0, size_t i1) {
+      LocalVel3 lvv;
+      for (size_t ii = i0; ii < i1; ++ii) {
+        const int ez = ezs[ii];
+        for (int ey = 0; ey < n; ++ey)
+          for (int ex = 0; ex < n; ++ex)
+            for (int gzi = 0; gzi < G; ++gzi)
+              for (int gyi = 0; gyi < G; ++gyi)
+                for (int gxi = 0; gxi < G; ++gxi) {
+                  const int e[3] = {ex, ey, ez};
+                  const double xi3[3] = {(ex + gx[gxi]) / n, (ey + gx[gyi]) / n, (ez + gx[gzi]) / n};
+                  const double w = gw[gxi] * gw[gyi] * gw[gzi] / ((double)n * n * n);
+                  Geo3 g = geo3_at(ri, ro, depth, xi3);
+                  local_velocity3(sz, p, e, tp, tq, xi3, g, lvv);
+                  double Nq[3][8];
+                  for (int ax = 0; ax < 3; ++ax) span_values(tq, q, e[ax] + q, xi3[ax], Nq[ax]);
+                  const double wJ = w * g.J;
+                  for (int i = 0; i < lvv.n; ++i) {
+                    const Pushed3& a = lvv.f[i];
+                    for (int j = 0; j < lvv.n; ++j) {
+                      const Pushed3& b = lvv.f[j];
+                      double m = a.v[0] * b.v[0] + a.v[1] * b.v[1] + a.v[2] * b.v[2];
+                      double k = 0.0;
+                      for (int r = 0; r < 3; ++r)
+                        for (int c = 0; c < 3; ++c) k += a.g[r][c] * b.g[r][c];
+                      const double val = wJ * (sigma * m + nu * k);
+                      sc_max[t] = std::max(sc_max[t], std::fabs(val));
+                      out_max[t] = std::max(out_max[t], put3(p, lv.rows, lv.ext, lvv.d[i], lvv.gid[i], lvv.d[j], val));
+                    }
+                    // b(v, q) = int divhat vhat qhat / det J dxi
+                    for (int kz = 0; kz <= q; ++kz)
+                      for (int ky = 0; ky <= q; ++ky)
+                        for (int kx = 0; kx <= q; ++kx) {
+                          const Dof3 dq{3, {ex + kx, ey + ky, ez + kz}};
+                          const long long gq = gid3(sz, 3, dq.i);
+                          const double bval = w * a.divh * Nq[0][kx] * Nq[1][ky] * Nq[2][kz] / g.J;
+                          put3(p, lv.rows, lv.ext, lvv.d[i], lvv.gid[i], dq, -bval);
+                          put3(p, lv.rows, lv.ext, dq, gq, lvv.d[i], bval);
+                        }
+                  }
+                }
+      }
+    };
+    std::vector<std::thread> th;
+    const size_t chunk = (ezs.size() + nth - 1) / nth;
+    for (unsigned t = 0; t < nth; ++t) {
+      const size_t i0 = t * chunk, i1 = std::min(ezs.size(), i0 + chunk);
+      if (i0 < i1) th.emplace_back(work, t, i0, i1);
+    }
+    for (auto& t : th) t.join();
+  }
+  for (unsigned t = 0; t < nth; ++t) { outside = std::max(outside, out_max[t]); scale = std::max(scale, sc_max[t]); }
+  // Nitsche terms on the six faces
+  const double pen_c = cpen * nu;
+  LocalVel3 lvv;
+  for (int k = 0; k < 3; ++k) {
+    const int a1 = (k + 1) % 3, a2 = (k + 2) % 3;
+    for (int side = 0; side < 2; ++side)
+      for (int e1 = 0; e1 < n; ++e1)
+        for (int e2 = 0; e2 < n; ++e2)
+          for (int g1 = 0; g1 < G; ++g1)
+            for (int g2 = 0; g2 < G; ++g2) {
+              int e[3];
+              double xi3[3];
+              e[k] = side ? n - 1 : 0; xi3[k] = side;
+              e[a1] = e1; xi3[a1] = (e1 + gx[g1]) / n;
+              e[a2] = e2; xi3[a2] = (e2 + gx[g2]) / n;
+              const double wt = gw[g1] * gw[g2] / ((double)n * n);
+              Geo3 g = geo3_at(ri, ro, depth, xi3);
+              local_velocity3(sz, p, e, tp, tq, xi3, g, lvv);
+              double nv[3] = {g.inv[k][0], g.inv[k][1], g.inv[k][2]};     // gradient of xi_k
+              const double nn = std::sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+              for (int c = 0; c < 3; ++c) nv[c] *= (side ? 1.0 : -1.0) / nn;
+              const double t1[3] = {g.DF[0][a1], g.DF[1][a1], g.DF[2][a1]};
+              const double t2[3] = {g.DF[0][a2], g.DF[1][a2], g.DF[2][a2]};
+              const double cr[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2], t1[0] * t2[1] - t1[1] * t2[0]};
+              const double area = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+              const double ds = wt * area, h = g.J / (area * n);
+              for (int i = 0; i < lvv.n; ++i) {
+                const Pushed3& a = lvv.f[i];
+                double dna[3];
+                for (int r = 0; r < 3; ++r) dna[r] = a.g[r][0] * nv[0] + a.g[r][1] * nv[1] + a.g[r][2] * nv[2];
+                for (int j = 0; j < lvv.n; ++j) {
+                  const Pushed3& b = lvv.f[j];
+                  double dnb[3];
+                  for (int r = 0; r < 3; ++r) dnb[r] = b.g[r][0] * nv[0] + b.g[r][1] * nv[1] + b.g[r][2] * nv[2];
+                  double t_ab = 0.0, t_ba = 0.0, uv = 0.0;
+                  for (int r = 0; r < 3; ++r) { t_ab += dnb[r] * a.v[r]; t_ba += dna[r] * b.v[r]; uv += a.v[r] * b.v[r]; }
+                  const double val = ds * (-nu * t_ab - nu * t_ba + pen_c / h * uv);
+                  outside = std::max(outside, put3(p, lv.rows, lv.ext, lvv.d[i], lvv.gid[i], lvv.d[j], val));
+                }
+              }
+            }
+  }
+  if (outside > 1e-12 * scale) { err = "mapped operator left the record pattern"; return IGAMG_EINVAL; }
+  // multiplier column of the pressure rows
+  for (long long g = sz.n_u; g < sz.n_total - 1; ++g) {
+    Dof3 d = decode3(sz, g);
+    lv.rows[(size_t)g * RU + RU - 1] = lv.f.mq[d.i[0]] * lv.f.mq[d.i[1]] * lv.f.mq[d.i[2]];
+  }
+  // physical quadrature points and J^T for the load vector
+  H.quad_xyz.assign((size_t)3 * nG * nG * nG, 0.0);
+  H.jt.assign((size_t)9 * nG * nG * nG, 0.0);
+  const size_t np3 = (size_t)nG * nG * nG;
+  for (int iz = 0; iz < nG; ++iz)
+    for (int iy = 0; iy < nG; ++iy)
+      for (int ix = 0; ix < nG; ++ix) {
+        const double xi3[3] = {(ix / G + gx[ix % G]) / n, (iy / G + gx[iy % G]) / n, (iz / G + gx[iz % G]) / n};
+        double X[3], DF[3][3], D2[3][3][3];
+        cylinder_map(ri, ro, depth, xi3, X, DF, D2);
+        const size_t o = ((size_t)iz * nG + iy) * nG + ix;
+        for (int c = 0; c < 3; ++c) H.quad_xyz[c * np3 + o] = X[c];
+        for (int kk = 0; kk < 3; ++kk)
+          for (int i = 0; i < 3; ++i) H.jt[o * 9 + kk * 3 + i] = DF[i][kk];
+      }
+  return IGAMG_OK;
+}
+
+// K_c = P^T K_f P (Sec. 5.1) for whole per-row records (all boxes and the extra box): the
+// operator on a mapped domain has no re-assembly formula on coarse levels.
+int galerkin_rows3(int p, const LevelHost3& F, LevelHost3& C, const Transfer1D& tp, const Transfer1D& tq,
+                   std::string& err) {
+  const int q = p - 1, W = 2 * q + 1, RU = (2 * p + 1) * W * W + 4 * p * W * W + 1, BX = 4 * p * p * W;
+  constexpr int WP = Transfer1D::WP, WR = Transfer1D::WR;
+  const Sizes3 &sf = F.sz, &sc = C.sz;
+  C.rows.assign((size_t)(sc.n_total - 1) * RU, 0.0);
+  const bool has_ext = !F.ext.empty();
+  if (has_ext) C.ext.assign((size_t)2 * sc.n_uc * BX, 0.0);
+  std::atomic<long long> next{0};
+  std::atomic<int> bad{0};
+  auto view = [&](int blk, int ax) -> const Transfer1D& { return (blk < 3 && ax == blk) ? tp : tq; };
+  auto work = [&]() {
+    for (;;) {
+      const long long i0 = next.fetch_add(128);
+      if (i0 >= sc.n_total - 1) break;
+      for (long long gi = i0; gi < std::min(sc.n_total - 1, i0 + 128); ++gi) {
+        const Dof3 ci = decode3(sc, gi);
+        int li[3];
+        for (int ax = 0; ax < 3; ++ax) li[ax] = ci.i[ax] - ((ci.blk < 3 && ax == ci.blk) ? 1 : 0);
+        double* orow = &C.rows[(size_t)gi * RU];
+        double* oext = (has_ext && ci.blk < 2) ? &C.ext[(size_t)gi * BX] : nullptr;
+        for (int rz = 0; rz < WR; ++rz)
+          for (int ry = 0; ry < WR; ++ry)
+            for (int rx = 0; rx < WR; ++rx) {
+              const int r[3] = {rx, ry, rz};
+              int fa[3];
+              double wa = 1.0;
+              bool ok = true;
+              for (int ax = 0; ax < 3 && ok; ++ax) {
+                const Transfer1D& T = view(ci.blk, ax);
+                const int f = T.f0[li[ax]] + r[ax];
+                const double w = f < T.nf ? T.rv[(size_t)li[ax] * WR + r[ax]] : 0.0;
+                if (w == 0.0) { ok = false; break; }
+                wa *= w;
+                fa[ax] = f + ((ci.blk < 3 && ax == ci.blk) ? 1 : 0);
+              }
+              if (!ok) continue;
+              const long long ga = gid3(sf, ci.blk, fa);
+              if (ga < 0) continue;
+              const Dof3 da{ci.blk, {fa[0], fa[1], fa[2]}};
+              const double* frow = &F.rows[(size_t)ga * RU];
+              const double* fext = (has_ext && ci.blk < 2) ? &F.ext[(size_t)ga * BX] : nullptr;
+              double fscale = 0.0;
+              for (int e = 0; e < RU; ++e) fscale = std::max(fscale, std::fabs(frow[e]));
+              if (fext) for (int e = 0; e < BX; ++e) fscale = std::max(fscale, std::fabs(fext[e]));
+              const int ne = fext ? RU + BX : RU;
+              for (int e = 0; e < ne; ++e) {
+                const double v = e < RU ? frow[e] : fext[e - RU];
+                if (v == 0.0) continue;
+                const Dof3 cb = e < RU ? rec_col3(sf, p, da, e) : ext_col3(sf, p, da, e - RU);
+                if (cb.blk < 0) continue;
+                if (cb.blk == 4) { orow[RU - 1] += wa * v; continue; }
+                int lb[3];
+                for (int ax = 0; ax < 3; ++ax) lb[ax] = cb.i[ax] - ((cb.blk < 3 && ax == cb.blk) ? 1 : 0);
+                for (int kz = 0; kz < WP; ++kz)
+                  for (int ky = 0; ky < WP; ++ky)
+                    for (int kx = 0; kx < WP; ++kx) {
+                      const int k[3] = {kx, ky, kz};
+                      Dof3 cj{cb.blk, {0, 0, 0}};
+                      double wb = wa * v;
+                      bool okj = true;
+                      for (int ax = 0; ax < 3 && okj; ++ax) {
+                        const Transfer1D& T = view(cb.blk, ax);
+                        const int cc = T.c0[lb[ax]] + k[ax];
+                        const double w = cc < T.nc ? T.pv[(size_t)lb[ax] * WP + k[ax]] : 0.0;
+                        if (w == 0.0) { okj = false; break; }
+                        wb *= w;
+                        cj.i[ax] = cc + ((cb.blk < 3 && ax == cb.blk) ? 1 : 0);
+                      }
+                      if (!okj) continue;
+                      int pos = rec_pos3(p, ci, cj);
+                      if (pos >= 0) { orow[pos] += wb; continue; }
+                      pos = oext ? ext_pos3(p, ci, cj) : -1;
+                      if (pos >= 0) { oext[pos] += wb; continue; }
+                      // only round-off may fall outside the pattern
+                      if (std::fabs(v) > 1e-12 * fscale) bad = 1;
+                    }
+              }
+            }
+      }
+    }
+  };
+  const int nth = std::max(1, std::min(32, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  for (int t = 0; t < nth; ++t) th.emplace_back(work);
+  for (auto& t : th) t.join();
+  if (bad) { err = "Galerkin product left the coarse record pattern"; return IGAMG_EINVAL; }
+  return IGAMG_OK;
+}
+
 }  // namespace
 
 // entry (g1, g2) from the per-row records (generalized Oseen)
@@ -535,6 +953,10 @@ double k_entry3_rows(const LevelHost3& lv, int p, long long g1, long long g2) {
   }
   const double* r = &lv.rows[(size_t)g1 * RU];
   if (b.blk == 4) return a.blk == 3 ? r[RU - 1] : 0.0;
+  if (!lv.ext.empty() && a.blk < 2 && b.blk < 2 && a.blk != b.blk) {
+    const int pos = ext_pos3(p, a, b);
+    return pos < 0 ? 0.0 : lv.ext[(size_t)g1 * (4 * p * p * W) + pos];
+  }
   const int nbox = a.blk < 3 ? 2 : 3;
   for (int k = 0; k < nbox; ++k) {
     Box3 bx = box_of(p, a.blk, k);
@@ -629,8 +1051,17 @@ int build3(const igamg_problem& pr, HierarchyHost3& H, std::string& err, bool fu
     auto Pq = prolong_dense(p - 1, nc, a, b);
     if (Pq.empty() || !make_transfer(Pq, a, b, 0, H.tq[l])) { err = "degree-(p-1) prolongation"; return IGAMG_ESINGULAR; }
   }
-  const bool general = pr.beta_qp != nullptr;     // generalized Oseen: per-row records
-  if (general) {
+  const bool mapped = pr.geometry == IGAMG_GEOM_HOLLOW_CYLINDER;
+  const bool general = pr.beta_qp != nullptr || mapped;   // Oseen, mapped: per-row records
+  H.geometry = pr.geometry;
+  if (mapped) {
+    // fine level assembled on the mapped domain; coarse levels whole-row Galerkin products
+    const double ri = pr.r_inner > 0 ? pr.r_inner : 0.075, ro = pr.r_outer > 0 ? pr.r_outer : 0.225;
+    int rc = assemble_mapped3(p, H.lev[L - 1], pr.sigma, pr.nu, H.cpen, ri, ro, 0.1, H, err);
+    if (rc) return rc;
+    for (int l = L - 2; l >= 0; --l)
+      if ((rc = galerkin_rows3(p, H.lev[l + 1], H.lev[l], H.tp_free[l + 1], H.tq[l + 1], err))) return rc;
+  } else if (general) {
     add_advection3(p, H.lev[L - 1].sz, pr.beta_qp, H.lev[L - 1].adv);
     for (int l = L - 2; l >= 0; --l)
       galerkin_adv3(p, H.lev[l + 1].sz, H.lev[l].sz, H.lev[l + 1].adv, H.tp_free[l + 1], H.tq[l + 1], H.lev[l].adv);

@@ -77,12 +77,15 @@ class Solver:
         return x
 
     def quad_points_xy(self):
-        """Physical quadrature points (2, nG, nG) [x or y][eta point][xi point]."""
+        """Physical quadrature points: 2D (2, nG, nG) [x or y][eta][xi], 3D (3, nG, nG, nG)."""
         n = ctypes.c_size_t()
         check(lib().igamg_quad_points_xy(self._h, None, 0, ctypes.byref(n)), "igamg_quad_points_xy")
         xy = np.zeros(n.value)
         check(lib().igamg_quad_points_xy(self._h, xy.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)),
               "igamg_quad_points_xy")
+        if self.dim == 3:
+            nG = int(round((n.value // 3) ** (1.0 / 3.0)))
+            return xy.reshape(3, nG, nG, nG)
         nG = int(round(np.sqrt(n.value // 2)))
         return xy.reshape(2, nG, nG)
 
