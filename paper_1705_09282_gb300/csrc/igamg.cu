@@ -1248,12 +1248,43 @@ int setup_fused(igamg_handle* h, Typed<T>& ty) {
 // shape (p, n_fine, levels, value type, smoother) and is cached per process.
 struct TuneKey {
   int p, n, L, bytes, sm, nu1, nu2;
+  int rows;                     // 1: per-row operators (Oseen, mapped domains), 0: class stencils
   bool operator<(const TuneKey& o) const {
-    return std::tie(p, n, L, bytes, sm, nu1, nu2) < std::tie(o.p, o.n, o.L, o.bytes, o.sm, o.nu1, o.nu2);
+    return std::tie(p, n, L, bytes, sm, nu1, nu2, rows) < std::tie(o.p, o.n, o.L, o.bytes, o.sm, o.nu1, o.nu2, o.rows);
   }
 };
 std::map<TuneKey, std::pair<int, int>>& tune_cache() { static std::map<TuneKey, std::pair<int, int>> m; return m; }
 std::mutex& tune_mutex() { static std::mutex m; return m; }
+
+// IGAMG_TUNE_CACHE=<file>: the tuned coarse-end choices persist across processes, one line per
+// shape ("p n_fine levels bytes smoother nu1 nu2 rows depth kind"), so that a run under a
+// profiler reuses what a plain run measured (the profiler's serialised launches would skew a
+// fresh tuning).  The file is advisory: unreadable or missing means tune as usual.  Call with
+// tune_mutex held.
+void tune_file_load() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  const char* path = std::getenv("IGAMG_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  TuneKey k{};
+  int d = 0, kind = 0;
+  while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d", &k.p, &k.n, &k.L, &k.bytes, &k.sm, &k.nu1, &k.nu2, &k.rows, &d,
+                     &kind) == 10)
+    tune_cache()[k] = {d, kind};
+  std::fclose(f);
+}
+
+void tune_file_append(const TuneKey& k, int d, int kind) {
+  const char* path = std::getenv("IGAMG_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d\n", k.p, k.n, k.L, k.bytes, k.sm, k.nu1, k.nu2, k.rows, d, kind);
+  std::fclose(f);
+}
 
 template <typename T>
 int autotune_fused(igamg_handle* h, Typed<T>& ty) {
@@ -1261,7 +1292,8 @@ int autotune_fused(igamg_handle* h, Typed<T>& ty) {
   if (ty.fused_max < 1 && ty.cluster_max < 1) { ty.fused_lc = -1; return IGAMG_OK; }
   if (h->prob.gamma > 1) { ty.fused_lc = -1; return IGAMG_OK; }   // W-cycles run level by level
   const int L = h->prob.n_levels;
-  TuneKey key{h->prob.p, h->prob.n_fine, L, (int)sizeof(T), h->prob.smoother, h->prob.nu1, h->prob.nu2};
+  TuneKey key{h->prob.p, h->prob.n_fine, L, (int)sizeof(T), h->prob.smoother, h->prob.nu1, h->prob.nu2,
+              (h->prob.beta_qp || h->prob.geometry != IGAMG_GEOM_SQUARE) ? 1 : 0};
   // fixed choices (tests, experiments): IGAMG_FUSED_LEVELS = depth, IGAMG_FUSED_CLUSTER = blocks
   const char* env = std::getenv("IGAMG_FUSED_LEVELS");
   if (env) {
@@ -1275,6 +1307,7 @@ int autotune_fused(igamg_handle* h, Typed<T>& ty) {
   }
   {
     std::lock_guard<std::mutex> lk(tune_mutex());
+    tune_file_load();
     auto it = tune_cache().find(key);
     if (it != tune_cache().end()) { ty.fused_lc = it->second.first; ty.fused_kind = it->second.second; return IGAMG_OK; }
   }
@@ -1339,6 +1372,7 @@ int autotune_fused(igamg_handle* h, Typed<T>& ty) {
   if (verbose) std::fprintf(stderr, "igamg: chose fused coarse levels %d (blocks %d)\n", best, best_kind);
   std::lock_guard<std::mutex> lk(tune_mutex());
   tune_cache()[key] = {best, best_kind};
+  tune_file_append(key, best, best_kind);
   return IGAMG_OK;
 }
 
