@@ -732,45 +732,66 @@ int assemble_mapped3(int p, LevelHost3& lv, double sigma, double nu, double cpen
     for (int ez = ph; ez < n; ez += p + 2) ezs.push_back(ez);
     auto work = [&](unsigned t, size_t i0, size_t i1) {
       LocalVel3 lvv;
+      const int nq3 = (q + 1) * (q + 1) * (q + 1);
+      std::vector<double> M, B;                      // element matrices, summed over its points
       for (size_t ii = i0; ii < i1; ++ii) {
         const int ez = ezs[ii];
         for (int ey = 0; ey < n; ++ey)
-          for (int ex = 0; ex < n; ++ex)
+          for (int ex = 0; ex < n; ++ex) {
+            const int e[3] = {ex, ey, ez};
+            int nv = -1;
             for (int gzi = 0; gzi < G; ++gzi)
               for (int gyi = 0; gyi < G; ++gyi)
                 for (int gxi = 0; gxi < G; ++gxi) {
-                  const int e[3] = {ex, ey, ez};
                   const double xi3[3] = {(ex + gx[gxi]) / n, (ey + gx[gyi]) / n, (ez + gx[gzi]) / n};
                   const double w = gw[gxi] * gw[gyi] * gw[gzi] / ((double)n * n * n);
                   Geo3 g = geo3_at(ri, ro, depth, xi3);
-                  local_velocity3(sz, p, e, tp, tq, xi3, g, lvv);
+                  local_velocity3(sz, p, e, tp, tq, xi3, g, lvv);   // same functions, same order at every point
+                  if (nv < 0) {
+                    nv = lvv.n;
+                    M.assign((size_t)nv * nv, 0.0);
+                    B.assign((size_t)nv * nq3, 0.0);
+                  }
                   double Nq[3][8];
                   for (int ax = 0; ax < 3; ++ax) span_values(tq, q, e[ax] + q, xi3[ax], Nq[ax]);
                   const double wJ = w * g.J;
-                  for (int i = 0; i < lvv.n; ++i) {
+                  for (int i = 0; i < nv; ++i) {
                     const Pushed3& a = lvv.f[i];
-                    for (int j = 0; j < lvv.n; ++j) {
+                    for (int j = 0; j < nv; ++j) {
                       const Pushed3& b = lvv.f[j];
-                      double m = a.v[0] * b.v[0] + a.v[1] * b.v[1] + a.v[2] * b.v[2];
+                      const double m = a.v[0] * b.v[0] + a.v[1] * b.v[1] + a.v[2] * b.v[2];
                       double k = 0.0;
                       for (int r = 0; r < 3; ++r)
                         for (int c = 0; c < 3; ++c) k += a.g[r][c] * b.g[r][c];
-                      const double val = wJ * (sigma * m + nu * k);
-                      sc_max[t] = std::max(sc_max[t], std::fabs(val));
-                      out_max[t] = std::max(out_max[t], put3(p, lv.rows, lv.ext, lvv.d[i], lvv.gid[i], lvv.d[j], val));
+                      M[(size_t)i * nv + j] += wJ * (sigma * m + nu * k);
                     }
                     // b(v, q) = int divhat vhat qhat / det J dxi
+                    int kq = 0;
                     for (int kz = 0; kz <= q; ++kz)
                       for (int ky = 0; ky <= q; ++ky)
-                        for (int kx = 0; kx <= q; ++kx) {
-                          const Dof3 dq{3, {ex + kx, ey + ky, ez + kz}};
-                          const long long gq = gid3(sz, 3, dq.i);
-                          const double bval = w * a.divh * Nq[0][kx] * Nq[1][ky] * Nq[2][kz] / g.J;
-                          put3(p, lv.rows, lv.ext, lvv.d[i], lvv.gid[i], dq, -bval);
-                          put3(p, lv.rows, lv.ext, dq, gq, lvv.d[i], bval);
-                        }
+                        for (int kx = 0; kx <= q; ++kx)
+                          B[(size_t)i * nq3 + kq++] += w * a.divh * Nq[0][kx] * Nq[1][ky] * Nq[2][kz] / g.J;
                   }
                 }
+            // scatter the element's matrices into the records
+            for (int i = 0; i < nv; ++i) {
+              for (int j = 0; j < nv; ++j) {
+                const double val = M[(size_t)i * nv + j];
+                sc_max[t] = std::max(sc_max[t], std::fabs(val));
+                out_max[t] = std::max(out_max[t], put3(p, lv.rows, lv.ext, lvv.d[i], lvv.gid[i], lvv.d[j], val));
+              }
+              int kq = 0;
+              for (int kz = 0; kz <= q; ++kz)
+                for (int ky = 0; ky <= q; ++ky)
+                  for (int kx = 0; kx <= q; ++kx) {
+                    const Dof3 dq{3, {ex + kx, ey + ky, ez + kz}};
+                    const long long gq = gid3(sz, 3, dq.i);
+                    const double bval = B[(size_t)i * nq3 + kq++];
+                    put3(p, lv.rows, lv.ext, lvv.d[i], lvv.gid[i], dq, -bval);
+                    put3(p, lv.rows, lv.ext, dq, gq, lvv.d[i], bval);
+                  }
+            }
+          }
       }
     };
     std::vector<std::thread> th;
