@@ -131,6 +131,9 @@ struct HierarchyHost {
 
 // Builds everything; returns IGAMG_OK or an error code with a message in err.
 int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err);
+// What the colour kernels rely on: every patch DOF is a row of the level (not lambda), and
+// within one colour no DOF appears twice (same-colour updates never touch the same entry).
+bool validate_patch_tables(const PatchTables& pt, long long n_rows, std::string& err);
 igamg_sizes level_sizes(int p, int n);
 double k_entry(const Level1D& L, const igamg_sizes& s, long long g1, long long g2);
 // entry (g1, g2) of a level given by per-row stencil records

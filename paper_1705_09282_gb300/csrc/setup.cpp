@@ -816,6 +816,7 @@ int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt
   pt.n8.assign(pt.n_colours, 0);
   for (int c = 0; c < pt.n_colours; ++c)
     for (int k = pt.colour_off[c]; k < pt.colour_off[c + 1] && all[k].dofs.size() == 8; ++k) pt.n8[c]++;
+  if (!validate_patch_tables(pt, s.n_total - 1, err)) return IGAMG_EINVAL;
   // bordered local inverses, one per class (Sec. 5.2 local problems; zero-mean local
   // pressure through the border m_j = int N^q_j)
   auto local_inverse = [&](const P& P_, std::vector<double>& inv) -> bool {
@@ -928,6 +929,20 @@ double k_entry_rows(const LevelHost& lv, int p, long long g1, long long g2) {
     if (idx >= 0) return lv.ext[(size_t)g1 * BX + idx];
   }
   return 0.0;
+}
+
+bool validate_patch_tables(const PatchTables& pt, long long n_rows, std::string& err) {
+  std::vector<int> stamp((size_t)n_rows, -1);
+  for (int c = 0; c < pt.n_colours; ++c)
+    for (int i = pt.colour_off[c]; i < pt.colour_off[c + 1]; ++i)
+      for (int k = 0; k < pt.maxl; ++k) {
+        const long long g = pt.dofs[(size_t)i * pt.maxl + k];
+        if (g < 0) continue;                                    // padding
+        if (g >= n_rows) { err = "patch table: DOF id out of range"; return false; }
+        if (stamp[(size_t)g] == c) { err = "patch table: a DOF twice in one colour"; return false; }
+        stamp[(size_t)g] = c;
+      }
+  return true;
 }
 
 igamg_sizes level_sizes(int p, int n) {

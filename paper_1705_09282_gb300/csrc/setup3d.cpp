@@ -255,6 +255,7 @@ int build_patches3(int p, const Level1D& L, const Sizes3& s, PatchTables& pt, st
   pt.n8.assign(pt.n_colours, 0);
   for (int c = 0; c < pt.n_colours; ++c)
     for (int k = pt.colour_off[c]; k < pt.colour_off[c + 1] && all[k].dofs.size() == 8; ++k) pt.n8[c]++;
+  if (!validate_patch_tables(pt, s.n_total - 1, err)) return IGAMG_EINVAL;
   // bordered local inverses (zero-mean local pressure through m_j = int N^q_j), one per class
   auto local_inverse = [&](const P& P_, std::vector<double>& inv) -> bool {
     int nl = (int)P_.dofs.size(), nb = nl + 1;
