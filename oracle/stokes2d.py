@@ -337,10 +337,23 @@ class Level:
         self.patches = None
         self.colour_order = None
 
-    def build_patches(self):
-        """Subdomains = supports of interior streamfunction basis functions (Sec. 5.2);
-        local spaces = velocity / pressure basis functions supported inside."""
+    def build_patches(self, patch_set="interior", local_pressure="border"):
+        """Subdomains = supports of streamfunction basis functions (Sec. 5.2); local spaces
+        = velocity / pressure basis functions supported inside.
+
+        patch_set: "interior" takes the supports of the basis functions of Psi_h, which
+        vanish on the boundary (Sec. 4.3 defines Psi_h with psi = 0 on the boundary), the
+        reading used everywhere else; "all" adds the supports of the boundary streamfunction
+        basis functions, so that the subdomains are the supports of all (n+p)^2 functions
+        that the tables' DOF column counts.
+        local_pressure: how the local pressure space's constant-like null direction is
+        removed (Sec. 5.2 footnote: the local pressures satisfy a zero-average constraint).
+        "border": bordered local system with m_j = int N^q_j (zero integral mean);
+        "pin": the first local pressure function is dropped (its coefficient held fixed);
+        "lstsq": the unbordered singular local system solved in the least-squares sense
+        with the minimum-norm solution (the pseudo-inverse)."""
         p, q, n, L = self.p, self.p - 1, self.n, self.layout
+        self.local_pressure = local_pressure
 
         def sup(i, deg):
             return max(0, i - deg), min(n - 1, i)
@@ -353,9 +366,10 @@ class Level:
             # index within p+1 of the patch index (supports have at most p+1 elements)
             return range(max(lo, c - p - 1), min(hi, c + p + 2))
 
+        lo_psi, hi_psi = (1, n + p - 1) if patch_set == "interior" else (0, n + p)
         patches = []
-        for b in range(1, n + p - 1):
-            for a in range(1, n + p - 1):
+        for b in range(lo_psi, hi_psi):
+            for a in range(lo_psi, hi_psi):
                 bx, by = sup(a, p), sup(b, p)
                 vd, qd = [], []
                 for iy in near(b, 0, n + q):
@@ -370,6 +384,8 @@ class Level:
                     for ix in near(a, 0, n + q):
                         if inside(sup(ix, q), bx) and inside(sup(iy, q), by):
                             qd.append(L.gid_p(ix, iy))
+                if not vd and not qd:
+                    continue
                 P = Patch()
                 P.a, P.b = a, b
                 P.colour = (b % (p + 1)) * (p + 1) + (a % (p + 1))
@@ -381,19 +397,33 @@ class Level:
             d = P.dofs
             Kl = K[d][:, d].toarray()
             nl = len(d)
-            Kb = np.zeros((nl + 1, nl + 1))
-            Kb[:nl, :nl] = Kl
-            Kb[nl, :nl] = self.m[d]
-            Kb[:nl, nl] = self.m[d]
-            P.lu = sla.lu_factor(Kb)
+            if local_pressure == "border":
+                Kb = np.zeros((nl + 1, nl + 1))
+                Kb[:nl, :nl] = Kl
+                Kb[nl, :nl] = self.m[d]
+                Kb[:nl, nl] = self.m[d]
+                P.lu = sla.lu_factor(Kb)
+            elif local_pressure == "pin":
+                keep = [k for k in range(nl) if not (P.n_q > 0 and k == P.n_v)]
+                P.lu = (np.array(keep), np.linalg.pinv(Kl[np.ix_(keep, keep)]))
+            else:
+                P.lu = np.linalg.pinv(Kl)
             P.Krows = K[d]
         self.patches = patches
         # colour-major, lexicographic (b, a) inside a colour (list is already b-major)
         self.colour_order = sorted(range(len(patches)), key=lambda i: patches[i].colour)
 
     def local_correction(self, P, r_local):
-        rhs = np.concatenate([r_local, [0.0]])
-        return sla.lu_solve(P.lu, rhs)[:-1]
+        lp = getattr(self, "local_pressure", "border")
+        if lp == "border":
+            rhs = np.concatenate([r_local, [0.0]])
+            return sla.lu_solve(P.lu, rhs)[:-1]
+        if lp == "pin":
+            keep, Ki = P.lu
+            out = np.zeros_like(r_local)
+            out[keep] = Ki @ r_local[keep]
+            return out
+        return P.lu @ r_local
 
     def sweep_multiplicative(self, U, F):
         """One application of eq. MSM: patches solved one after another, each from the
@@ -417,9 +447,12 @@ class Hierarchy:
     """Nested levels l = 0 (coarsest) .. L-1 (finest) with Galerkin coarse operators."""
 
     def __init__(self, p, n_fine, n_levels, sigma, nu, c_pen=None, beta=None,
-                 smoother="mult", eta=0.5, nu1=2, nu2=2, gamma=1, fine=None):
+                 smoother="mult", eta=0.5, nu1=2, nu2=2, gamma=1, fine=None,
+                 patch_set="interior", local_pressure="border"):
         """fine: a prebuilt finest-level discretization (e.g. on a mapped domain) in place
-        of the unit square's; the coarse levels are its Galerkin products either way."""
+        of the unit square's; the coarse levels are its Galerkin products either way.
+        patch_set / local_pressure: alternative readings of Sec. 5.2's subdomains and local
+        pressure spaces (Level.build_patches); the defaults are the readings used throughout."""
         self.p, self.n_levels = p, n_levels
         self.smoother, self.eta, self.nu1, self.nu2 = smoother, eta, nu1, nu2
         self.gamma = gamma
@@ -443,7 +476,7 @@ class Hierarchy:
             n = nc
         self.levels, self.P = levels, Ps
         for l in range(1, n_levels):
-            levels[l].build_patches()
+            levels[l].build_patches(patch_set, local_pressure)
         self.coarse_lu = sla.lu_factor(levels[0].K.toarray())
 
     def smooth(self, l, U, F):

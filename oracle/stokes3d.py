@@ -293,10 +293,17 @@ class Level3D:
     def __init__(self, p, n, K, m, layout):
         self.p, self.n, self.K, self.m, self.layout = p, n, K, m, layout
 
-    def build_patches(self):
-        """Subdomains = supports of the vector-potential basis functions (Sec. 5.2)."""
+    def build_patches(self, patch_set="interior", local_pressure="border"):
+        """Subdomains = supports of the vector-potential basis functions (Sec. 5.2).
+
+        patch_set "interior" takes the functions of the constrained space (tangential
+        trace zero); "all" adds the supports of the constrained (boundary) ones as well.
+        local_pressure "border" (zero integral mean by a bordered row), "pin" (the first
+        local pressure function dropped) or "lstsq" (minimum-norm least squares): readings
+        of the Sec. 5.2 footnote on the local pressure space's zero-average constraint."""
         p, q, n, Lo = self.p, self.p - 1, self.n, self.layout
         ni, nq = n + p - 2, n + q
+        self.local_pressure = local_pressure
 
         def sup(i, d):
             return max(0, i - d), min(n - 1, i)
@@ -310,7 +317,10 @@ class Level3D:
         ncol_fam = p * (p + 1) ** 2
         for fam in range(3):
             dg = fam_deg[fam]
-            rng = [range(nq) if dg[a] == q else range(1, ni + 1) for a in range(3)]
+            if patch_set == "interior":
+                rng = [range(nq) if dg[a] == q else range(1, ni + 1) for a in range(3)]
+            else:
+                rng = [range(nq) if dg[a] == q else range(0, n + p) for a in range(3)]
             st = strides_all[fam]
             for k in rng[2]:
                 for j in rng[1]:
@@ -335,6 +345,8 @@ class Level3D:
                                 for ii in near[0]:
                                     if all(inside(sup(v, q), box[a]) for a, v in enumerate((ii, jj, kk))):
                                         qd.append(Lo.gid_p(ii, jj, kk))
+                        if not vd and not qd:
+                            continue
                         P = Patch3D()
                         P.fam, P.i, P.j, P.k = fam, i, j, k
                         P.colour = fam * ncol_fam + ((k % st[2]) * st[1] + (j % st[1])) * st[0] + (i % st[0])
@@ -345,11 +357,18 @@ class Level3D:
         for P in patches:
             d = P.dofs
             nl = len(d)
-            Kb = np.zeros((nl + 1, nl + 1))
-            Kb[:nl, :nl] = K[d][:, d].toarray()
-            Kb[nl, :nl] = self.m[d]
-            Kb[:nl, nl] = self.m[d]
-            P.lu = sla.lu_factor(Kb)
+            Kl = K[d][:, d].toarray()
+            if local_pressure == "border":
+                Kb = np.zeros((nl + 1, nl + 1))
+                Kb[:nl, :nl] = Kl
+                Kb[nl, :nl] = self.m[d]
+                Kb[:nl, nl] = self.m[d]
+                P.lu = sla.lu_factor(Kb)
+            elif local_pressure == "pin":
+                keep = [t for t in range(nl) if not (P.n_q > 0 and t == P.n_v)]
+                P.lu = (np.array(keep), np.linalg.pinv(Kl[np.ix_(keep, keep)]))
+            else:
+                P.lu = np.linalg.pinv(Kl)
             P.Krows = K[d]
         self.patches = patches
         self.colour_order = sorted(range(len(patches)), key=lambda t: patches[t].colour)
@@ -358,13 +377,23 @@ class Level3D:
         for t in self.colour_order:
             P = self.patches[t]
             r = F[P.dofs] - P.Krows @ U
-            U[P.dofs] += sla.lu_solve(P.lu, np.concatenate([r, [0.0]]))[:-1]
+            lp = getattr(self, "local_pressure", "border")
+            if lp == "border":
+                U[P.dofs] += sla.lu_solve(P.lu, np.concatenate([r, [0.0]]))[:-1]
+            elif lp == "pin":
+                keep, Ki = P.lu
+                U[P.dofs[keep]] += Ki @ r[keep]
+            else:
+                U[P.dofs] += P.lu @ r
 
 
 class Hierarchy3D:
-    def __init__(self, p, n_fine, n_levels, sigma, nu, nu1=2, nu2=2, beta=None, gamma=1, fine=None):
+    def __init__(self, p, n_fine, n_levels, sigma, nu, nu1=2, nu2=2, beta=None, gamma=1, fine=None,
+                 patch_set="interior", local_pressure="border"):
         """fine: a prebuilt finest-level discretization (e.g. on a mapped domain) in place of
-        the unit cube's; the coarse levels are its Galerkin products either way."""
+        the unit cube's; the coarse levels are its Galerkin products either way.
+        patch_set / local_pressure: alternative readings of Sec. 5.2 (Level3D.build_patches);
+        the defaults are the readings used throughout."""
         self.p, self.n_levels, self.nu1, self.nu2 = p, n_levels, nu1, nu2
         self.gamma = gamma
         if fine is None:
@@ -384,7 +413,7 @@ class Hierarchy3D:
             n = nc
         self.levels, self.P = levels, Ps
         for l in range(1, n_levels):
-            levels[l].build_patches()
+            levels[l].build_patches(patch_set, local_pressure)
         self.coarse_lu = sla.lu_factor(levels[0].K.toarray())
 
     def mgv(self, l, U, F):

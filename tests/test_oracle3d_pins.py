@@ -283,9 +283,11 @@ def test_divergence_free_invariant():
 
 def test_paper_table4_cycle_counts_loosely():
     # Table 4 protocol (V(1,2), multiplicative, random divergence-free guess, 1e6 reduction,
-    # coarsest mesh one element).  The guess's scale and the norm are not stated; the
-    # oracle needs a few cycles more than the table at these small n_l, so only an upper
-    # bound and the n_l = 1 value are asked (p = 2).
+    # coarsest mesh one element).  Only n_l = 1 is a pin against the paper: on two elements
+    # per direction some vector-potential support is the whole cube, so one cycle is exact
+    # and the paper's 1 follows.  For n_l = 2, 3 the oracle needs 3-6 cycles where the table
+    # prints 1-2 under every reading of Sec. 5.2 tried (oracle/paper_tables.py); those bounds
+    # are the oracle's own counts, kept as a regression check, not a parity claim.
     tab = {r[0]: r for r in _table("table4")}
     for nl, bound in ((1, 1), (2, 4), (3, 6)):
         n = 2 ** nl

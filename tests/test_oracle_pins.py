@@ -326,10 +326,55 @@ def test_divergence_free_invariant(sm, eta):
         assert S.div_inf(U) <= 1e-12 * max(1.0, np.abs(U[: S.n_u]).max())
 
 
+@pytest.mark.parametrize("n,n_whole", [(1, 1), (2, 4)])
+def test_additive_sweep_scales_by_eta(n, n_whole):
+    # eq. ASM: U += eta * sum_i E_i^T K_i^{-1} E_i r.  For p = 2 on one element the single
+    # interior streamfunction support is the whole domain, and on two elements all four are,
+    # so one additive sweep from zero is n_whole * eta * the direct solve (velocity and
+    # pressure; the multiplier is not a subdomain unknown and stays 0).  A dropped, squared or
+    # misplaced eta, or a sum that skips a subdomain, fails this.
+    S = o2.Stokes2D(2, n, 1.0, 1.0)
+    L = o2.Level(2, n, S.K, S.m, S)
+    L.build_patches()
+    assert len(L.patches) == n_whole
+    F = S.load_vector(inputs.grf_forcing(2, n, seed=31))
+    Ux = spla.spsolve(S.K.tocsc(), F)
+    assert abs(Ux[-1]) <= 1e-12 * np.abs(Ux).max()     # lambda = 0 for a velocity-only load
+    for eta in (0.5, 0.3):
+        U = np.zeros(S.ndof)
+        L.sweep_additive(U, F, eta)
+        assert np.allclose(U, n_whole * eta * Ux, rtol=0, atol=1e-12 * np.abs(Ux).max())
+
+
+@pytest.mark.parametrize("p,n_l", [(2, 1), (3, 1), (3, 2)])
+def test_table1_smallest_meshes_take_one_cycle(p, n_l):
+    # The n_l = 1 row of Table 1 (and n_l = 2 for p = 3) is not compared with the paper's
+    # counts (3 / 2 and 6 / 6 at n_l = 1; 12 / 14 at n_l = 2, p = 3): on 2^n_l elements with
+    # p + 1 >= 2^n_l some interior streamfunction support (p + 1 elements wide, clipped to
+    # the domain) is the whole domain, so under Sec. 5.2's subdomains that patch's solve in
+    # the first pre-smoothing sweep is exact up to the pressure mean (later patches then see
+    # a zero residual), and the exact coarse solve of Algorithm 1 restores the mean: one
+    # V(1,2) cycle, whatever the guess.  The oracle must show exactly that.
+    n = 2 ** n_l
+    S = o2.Stokes2D(p, n, 1.0, 1.0)
+    L = o2.Level(p, n, S.K, S.m, S)
+    L.build_patches()
+    assert any(len(P.dofs) == S.ndof - 1 for P in L.patches)
+    for sigma in (1.0, 1000.0):
+        H = o2.Hierarchy(p, n, n_l + 1, sigma, 1.0, smoother="mult", nu1=1, nu2=2)
+        psi, pr = inputs.random_divfree_guess(p, n, seed=n_l)
+        U = H.fine.curl(psi)
+        U[H.fine.n_u: H.fine.n_u + H.fine.n_p] = pr
+        F = H.fine.load_vector(inputs.manufactured_forcing(p, n, sigma, 1.0))
+        k, hist = H.solve(U, F, 1e-6, 10)
+        assert k == 1 and hist[-1] <= 1e-12 * hist[0], (k, hist)
+
+
 def test_paper_table1_cycle_counts_loosely():
     # protocol of Sec. 6: V(1,2), multiplicative, random divergence-free guess, 1e6 reduction,
     # coarsest mesh one element.  The paper leaves ordering, guess and norm open, so only
-    # +-2 cycles are asked (p = 2).
+    # +-2 cycles are asked (p = 2).  Row n_l = 1 is pinned separately: there the method is
+    # exact in one cycle (test_table1_smallest_meshes_take_one_cycle).
     tab = _table("table1")
     for row in tab[1:4]:
         nl, da1, da1000 = row[0], row[2], row[3]
