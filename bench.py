@@ -121,14 +121,44 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_fma_peak(dev, stream, fp64=True, repeats=5):
+    """Measured FMA throughput of this GPU (TFLOP/s): igamg_probe_fma, 8 independent
+    multiply-add chains per thread, 8 blocks of 256 threads per SM, best of `repeats`
+    CUDA-event timings on `stream` after one warm-up launch."""
+    import ctypes
+
+    import torch
+
+    from paper_1705_09282_gb300 import _lib
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = sms * 8, (4096 if fp64 else 65536)
+    out = torch.empty(blocks * 256, dtype=torch.float64 if fp64 else torch.float32, device=dev)
+    flops = ctypes.c_double()
+    st = ctypes.c_void_p(stream.cuda_stream)
+    best = None
+    for k in range(repeats + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rc = _lib.lib().igamg_probe_fma(1 if fp64 else 0, blocks, iters, ctypes.c_void_p(out.data_ptr()), st,
+                                        ctypes.byref(flops))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert rc == 0, rc
+        t = e0.elapsed_time(e1) / 1e3
+        if k > 0:
+            best = t if best is None else min(best, t)
+    return flops.value / best / 1e12
+
+
 def launches_per_solve(p, cycles, mixed=False):
-    """Kernels of ours in one igamg_solve: per V-cycle, per smoothed level (nu1+nu2)
-    colour launches + residual (2) + restriction + prolongation; coarse solve; the
-    fine residual norm (2).  The FP32 mode adds the down-cast, the streamfunction
-    integration and the curl update per cycle.  Plus the initial residual (2) and the
-    final divergence check."""
-    colours = (p + 1) ** 2
-    per_cycle = (N_LEVELS - 1) * (4 * colours + 2 + 1 + 1) + 1 + 2 + (3 if mixed else 0)
+    """Kernels of ours in one igamg_solve (an upper estimate: a fused coarse end, when the
+    autotuner picks one, replaces several of them by one): per V-cycle, per smoothed level
+    two pipelined sweep launches (pre and post) + residual (2) + restriction +
+    prolongation; coarse solve; the fine residual norm (2).  The FP32 mode adds the
+    down-cast, the streamfunction integration and the curl update per cycle.  Plus the
+    initial residual (2) and the final divergence check."""
+    per_cycle = (N_LEVELS - 1) * (2 + 2 + 1 + 1) + 1 + 2 + (3 if mixed else 0)
     return 2 + cycles * per_cycle + 1
 
 
@@ -249,41 +279,96 @@ def run_ours(args):
              "cycles": {f"p{pr['p']}_sigma{pr['sigma']:g}": c for pr, c in zip(problems, cyc32)},
              "max_div_inf": div32}
 
-    # ---- dominant kernel: one multiplicative colour sweep on the finest level ---------
+    # ---- dominant kernel: the finest level's multiplicative sweep ------------------------
+    # nu = 2 sweeps (all colours) of the finest level, as in every V-cycle's pre- and
+    # post-smoothing, in the form the autotuner chose for that level, captured into a CUDA
+    # graph (the way solves run it) on a side stream and replayed 10 times between CUDA
+    # events on that stream; the average per colour launch (or per pipelined launch) is the
+    # kernel's launch duration.
     pk, pk_src = peaks()
-    S0 = problems[0]["S"]
-    sz = S0.sizes()
-    U0, F0 = problems[0]["U"], problems[0]["F"]
-    sweeps = 20
-    flush.fill_(1.0)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    S0.smooth(U0, F0, sweeps=sweeps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    colours = sz.n_colours
-    launch_s = e0.elapsed_time(e1) / 1e3 / (sweeps * colours)
-    # algorithmic FP64 flops of one colour launch (per-unit figures in the design notes):
-    # per patch, its 8 residual rows (2 flops per stencil coefficient: u_x, u_y rows
-    # (4p+1)(2p-1), p rows 4p(2p-1)+1), the 8x8 local inverse (2 x 64) and 16 adds.
-    p0 = problems[0]["p"]
+    pr0 = problems[0]
+    p0 = pr0["p"]
+    side = torch.cuda.Stream(dev)
+    Sr = Solver(p0, N_FINE, N_LEVELS, pr0["sigma"], 1.0, nu1=2, nu2=2, device=dev, stream=side,
+                precision=IGAMG_FP32_IR)
+    sz = Sr.sizes()
+    form = Sr.level_form()
+    with torch.cuda.stream(side):
+        Ur = torch.zeros(sz.n_total, dtype=torch.float64, device=dev)
+        Fr = pr0["F"].clone()
+        Ur32 = torch.zeros(sz.n_total, dtype=torch.float32, device=dev)
+        Fr32 = Fr.to(torch.float32)
+    side.synchronize()
+    # algorithmic FP64 flops per patch and sweep: its 8 residual rows (2 flops per stencil
+    # coefficient: u_x, u_y rows (4p+1)(2p-1), p rows 4p(2p-1)+1), the 8x8 local inverse
+    # (2 x 64) and 16 adds
     rx, rp = (4 * p0 + 1) * (2 * p0 - 1), 4 * p0 * (2 * p0 - 1) + 1
     flops_patch = 2 * (4 * rx + 4 * rp) + 2 * 64 + 16
-    n_patch_colour = sz.n_patches / colours
-    achieved = n_patch_colour * flops_patch / launch_s / 1e12
+    sweeps_per_replay, replays = 2, 10
+
+    def graph_sweep_s(smooth, U, F):
+        for _ in range(2):
+            with torch.cuda.stream(side):
+                smooth(U, F, sweeps=sweeps_per_replay)
+        side.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            smooth(U, F, sweeps=sweeps_per_replay)
+        g.replay()
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        for _ in range(replays):
+            g.replay()
+        e1.record(side)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / replays
+
+    t_sweeps = graph_sweep_s(Sr.smooth, Ur, Fr)
+    t_sweeps32 = graph_sweep_s(Sr.smooth32, Ur32, Fr32)
+    launches_per_replay = 1 if form["tiles"] else sweeps_per_replay * sz.n_colours
+    launch_s = t_sweeps / launches_per_replay
+    flops_replay = sz.n_patches * sweeps_per_replay * flops_patch
+    achieved = flops_replay / t_sweeps / 1e12
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12    # 152 SMs x 2 DFMA/clk x 2 flops
-    # DRAM bytes (read + write) of one such launch, from an ncu capture of this kernel on
-    # this workload (--profile-case p2-fp64; cold L2 under the profiler)
-    traffic = 3.19e6 + 0.0
-    roofline = {"kernel": "k_mult_colour<2,double> (one colour, finest level, p=2, 128-thread blocks)", "bound": "alu",
+    fp64_derived = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12    # 152 SMs x 2 DFMA/clk x 2 flops
+    fp64_peak = measured_fma_peak(dev, stream, fp64=True)
+    fp32_peak = measured_fma_peak(dev, stream, fp64=False)
+    # algorithmic bytes per sweep: U read and written once, F read once, the patch DOF lists
+    # (8 int32 per patch) and class ids read once
+    bytes_replay = sweeps_per_replay * (3 * 8 * sz.n_total + sz.n_patches * (8 + 1) * 4)
+    if form["tiles"]:
+        kname = (f"k_sweep_tiles<{p0},double> (pipelined: {form['tiles']} tiles of {form['threads']} threads; "
+                 f"one launch = 2 sweeps x {sz.n_colours} colours)")
+    else:
+        kname = (f"k_mult_colour<{p0},double,{form['lanes']}> (one colour of the finest level {N_FINE}^2, "
+                 f"{form['lanes']} lane(s) per patch row, {form['threads']}-thread blocks; autotuned form)")
+    roofline = {"kernel": kname, "bound": "alu",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s (FP64)", "frac": achieved / fp64_peak,
-                "traffic": traffic, "traffic_unit": "bytes per launch",
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flops x median SM clock",
-                "avg_launch_us": launch_s * 1e6, "flops_per_launch": n_patch_colour * flops_patch,
-                "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_source": pk_src,
+                "traffic": None, "traffic_unit": "bytes per launch",
+                "traffic_note": "ncu DRAM bytes of this kernel: profiles/k_mult_colour_p2_fp64_256x256.md",
+                "peak_source": "measured: igamg_probe_fma, FP64 FMA chains on every SM, best of 5 (CUDA events)",
+                "peak_derived": fp64_derived, "fp32_peak_measured": fp32_peak,
+                "avg_launch_us": launch_s * 1e6, "launches_timed": launches_per_replay * replays,
+                "flops_per_launch": flops_replay / launches_per_replay,
+                "algorithmic_bytes_per_launch": bytes_replay / launches_per_replay,
+                "achieved_gbs_algorithmic": bytes_replay / t_sweeps / 1e9,
+                "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_source": pk_src, "form": form,
+                "timing": "2 sweeps captured in a CUDA graph on a side stream, 10 replays between CUDA events",
                 "working_set_note": "finest-level vectors (1.6 MB) stay in L2; the kernel is FP64-issue bound"}
+    # the FP32 inner smoother of the mixed mode, same launches
+    bytes32 = sweeps_per_replay * (3 * 4 * sz.n_total + sz.n_patches * (8 + 1) * 4)
+    roofline32 = {"kernel": kname.replace(",double", ",float"), "bound": "latency",
+                  "avg_launch_us": t_sweeps32 / launches_per_replay * 1e6,
+                  "achieved_tflops": flops_replay / t_sweeps32 / 1e12, "fp32_peak_measured": fp32_peak,
+                  "frac_fp32_peak": flops_replay / t_sweeps32 / 1e12 / fp32_peak,
+                  "algorithmic_bytes_per_launch": bytes32 / launches_per_replay,
+                  "achieved_gbs_algorithmic": bytes32 / t_sweeps32 / 1e9, "hbm_peak_gbs": pk["hbm_gbs"],
+                  "frac_hbm": bytes32 / t_sweeps32 / 1e9 / pk["hbm_gbs"],
+                  "speedup_vs_fp64": t_sweeps / t_sweeps32}
+    mixed["roofline"] = roofline32
+    Sr.close()
 
     # ---- end to end through the host-buffer C-ABI call --------------------------------
     pin = {}
@@ -352,7 +437,8 @@ def cpu_baseline_sample():
     t0 = time.perf_counter()
     H.vcycle(U, F)
     dt = time.perf_counter() - t0
-    return {"value": len(F) / dt / 1e6, "unit": "MDOF/s per V-cycle", "cores": 1, "kind": "oracle",
+    return {"value": len(F) / dt / 1e6, "unit": "MDOF/s per V-cycle", "cores": 1, "host_cores": os.cpu_count(),
+            "kind": "oracle",
             "sample": "one V-cycle of the p=2, sigma=nu=1 solve at 256x256 (7 grids, V(2,2)), "
                       "single-threaded numpy/scipy, set-up not timed", "seconds": dt}
 
@@ -375,6 +461,7 @@ def run_reference(args):
             "data": "synthetic (seeded Gaussian random field forcing)", "config": workload_config(),
             "impl": "reference",
             "cpu_baseline": {"value": v, "unit": "MDOF/s per V-cycle", "kind": "oracle", "cores": 1,
+                             "host_cores": os.cpu_count(),
                              "sample": "each step one V-cycle of the p=2, sigma=nu=1 solve at 256x256"},
             "e2e": {"value": v, "unit": "MDOF/s per V-cycle", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -78,7 +78,8 @@ typedef struct {
   const double* beta_qp; /* host; advection at the quadrature points, (2, nG, nG) like f,
                             or NULL for generalized Stokes */
   int smoother;       /* IGAMG_MULT or IGAMG_ADD */
-  double eta;         /* additive scaling factor (Sec. 5.2, eq. ASM); <= 0 selects 0.5 */
+  double eta;         /* additive scaling factor (Sec. 5.2, eq. ASM); <= 0 selects 0.3 (the
+                       * paper runs 0.5, under which these subdomains diverge in pressure) */
   int nu1, nu2;       /* pre- / post-smoothing sweeps (Algorithm 1) */
   int precision;      /* IGAMG_FP64, IGAMG_FP32_IR, IGAMG_FGMRES_FP64 or IGAMG_FGMRES_FP32 */
   int restart;        /* FGMRES: Krylov directions per restart cycle; <= 0 selects 20 */
@@ -169,6 +170,18 @@ int igamg_residual(igamg_handle* h, int level, const double* U, const double* F,
 
 /* `sweeps` applications of the level's Schwarz smoother to U in place (Sec. 5.2). */
 int igamg_smooth(igamg_handle* h, int level, double* U, const double* F, int sweeps);
+
+/* The form of level `level`'s multiplicative sweep that the autotuner chose at creation (2D):
+ * *lanes = lanes per local row of the 8-DOF patches (1 or 2), *threads = threads per block,
+ * *tiles = 0 for one launch per colour, else the number of tiles of the pipelined sweep
+ * (1: the whole level in one block).  Any output may be NULL.  Errors: IGAMG_EINVAL,
+ * IGAMG_EUNSUPPORTED (3D handle). */
+int igamg_level_form(const igamg_handle* h, int level, int* lanes, int* threads, int* tiles);
+
+/* The same in FP32 (the inner smoother of the FP32-in-FP64 modes): U, F are FP32 device
+ * vectors in the level's layout; the handle must be 2D with precision IGAMG_FP32_IR or
+ * IGAMG_FGMRES_FP32 (else IGAMG_EUNSUPPORTED). */
+int igamg_smooth_f32(igamg_handle* h, int level, float* U, const float* F, int sweeps);
 
 /* G = R_l r = P_{l-1}^T r: restriction from level l to level l-1 (Sec. 5.1). */
 int igamg_restrict(igamg_handle* h, int level, const double* r_fine, double* g_coarse);
@@ -287,23 +300,39 @@ int igamg_curl(igamg_handle* h, const double* psi, double* U);
 
 /* Same result as igamg_residual on level `level` of the hierarchy that *prob describes,
  * but without a handle and without allocating device memory: for callers that cannot
- * call cudaMalloc (their device memory is owned by a pool, an arena or a host framework,
- * or allocation is forbidden where they run).  The paper has no counterpart; this is a
- * deployment convenience.
+ * call cudaMalloc (their device memory is owned by a pool, an arena or a host framework).
+ * The paper has no counterpart; this is a deployment convenience.
  *   Scratch: a 1 MiB array that the library declares statically in device memory
- *   (each GPU that loads the library keeps it until exit) holds this level's 1D
- *   operator tables and the per-block partial sums of the norm.  A level that needs
- *   more (about n > 1000 elements per direction) is rejected before any GPU work: the
- *   call returns IGAMG_EINVAL and prints the needed and available sizes on stderr.
+ *   (each GPU that loads the library keeps it until exit) holds this level's class
+ *   stencil tables (10,164 doubles for p = 2, 44,550 for p = 3) and two partial sums per
+ *   256 rows.  That fits levels of up to n = 2270 elements per direction for p = 2 and
+ *   n = 1919 for p = 3; a larger level is rejected before any GPU work: the call returns
+ *   IGAMG_EINVAL and prints the needed and available sizes on stderr.
  *   The first call on a device looks up the array's device address (with that device
- *   current); make that first call before any stream capture.
+ *   current, under a lock, so first calls from several threads are safe) and keeps it
+ *   for the life of the process; make that first call before any stream capture.  After
+ *   cudaDeviceReset on a device the kept address is stale: do not call this entry point
+ *   on that device again in the same process.
  *   Every call reuses the same array and rewrites all of it that it reads, so nothing
  *   carries over; calls whose GPU work overlaps (other streams, other threads) race on
  *   it and must be serialised by the caller.
  *   U, F, R: device, layout above, R written; norm_out: host or NULL (if given, the call
- *   synchronises the stream).  cuda_stream: a cudaStream_t as void*, or NULL. */
+ *   synchronises the stream).  cuda_stream: a cudaStream_t as void*, or NULL.
+ *   Errors: IGAMG_EINVAL (bad sizes or pointers, level too large), IGAMG_EUNSUPPORTED
+ *   (not 2D Stokes on the square with p = 2 or 3, or cuda_stream in capture mode),
+ *   IGAMG_ECUDA. */
 int igamg_residual_static(const igamg_problem* prob, int level, const double* U,
                           const double* F, double* R, double* norm_out, void* cuda_stream);
+
+/* ---- measurement ----------------------------------------------------------------------
+ * Arithmetic peak probe, not part of the method: enqueues one kernel of `blocks` blocks of
+ * 256 threads, each thread running 8 independent multiply-add chains for `iters` rounds in
+ * FP64 (fp64 != 0) or FP32, and stores one value per thread into out (device, blocks * 256
+ * doubles or floats).  *flops (host, may be NULL) receives the kernel's multiply-add flops
+ * (2 per FMA).  Timed by the caller with events on cuda_stream, it gives the GPU's
+ * measured FMA throughput, the denominator of the roofline of FMA-issue-bound kernels.
+ * Errors: IGAMG_EINVAL (non-positive sizes, null out), IGAMG_ECUDA (launch failed). */
+int igamg_probe_fma(int fp64, int blocks, int iters, void* out, void* cuda_stream, double* flops);
 
 /* ---- host-only inspection of the set-up (no GPU needed; for tests) -------------------
  * Each call builds the hierarchy on the host and copies one piece out, dense, row-major.

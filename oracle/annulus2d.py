@@ -14,7 +14,7 @@ What it follows:
   * Nitsche terms on all four walls for the tangential velocity, the normal component
     removed strongly (v_hat . n_hat = 0 is v . n = 0 under the Piola map)
 
-Readings (also in the design notes):
+Readings where the paper is silent:
   * parametric directions: xi (first) is radial, eta (second) is angular; the arc is the
     rational quadratic Bezier curve with control points (1,0), (1,1), (0,1) and weights
     (1, sqrt(2)/2, 1), scaled by r(xi) = r_i + (r_o - r_i) xi;

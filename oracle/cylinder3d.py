@@ -14,7 +14,7 @@ What it follows:
   * Nitsche terms on the six faces for the tangential velocity; the normal component is
     removed strongly as on the cube (the Piola map keeps v . n = 0)
 
-Readings (also in the design notes):
+Readings where the paper is silent:
   * map: (x, y) = the quarter-annulus map of oracle/annulus2d.py in (xi, eta), z = d zeta;
   * Nitsche length h at a face point = the element's height normal to the face,
     det J / (|t1 x t2| n) with t1, t2 the face's tangent columns of J (1/n on the cube);

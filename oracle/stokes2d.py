@@ -20,7 +20,7 @@ What it follows, step by step:
     the basis functions supported inside; additive (eq. ASM) and
     multiplicative (eq. MSM) Schwarz smoothers                                  -- Sec. 5.2
 
-Readings where the paper is silent (each also listed in the design notes):
+Readings where the paper is silent:
   * local pressure null space: the local system is bordered with
     m_j = int N^q_j over the patch pressure functions (zero-mean local pressure);
   * multiplicative order: colour-major, colour of patch (a,b) =

@@ -78,6 +78,9 @@ SIGNATURES = {
     "igamg_div_inf": (_I, [_P, _P, ctypes.POINTER(_D)]),
     "igamg_curl": (_I, [_P, _P, _P]),
     "igamg_residual_static": (_I, [ctypes.POINTER(Problem), _I, _P, _P, _P, ctypes.POINTER(_D), _P]),
+    "igamg_probe_fma": (_I, [_I, _I, _I, _P, _P, ctypes.POINTER(_D)]),
+    "igamg_smooth_f32": (_I, [_P, _I, _P, _P, _I]),
+    "igamg_level_form": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "igamg_host_level_matrix": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL)]),
     "igamg_host_operator_rows": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL)]),
     "igamg_host_operator_apply": (_I, [ctypes.POINTER(Problem), _I, _P, _P, _SZ]),
@@ -119,7 +122,7 @@ def check(code, where):
     return code
 
 
-def make_problem(p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.5, nu1=2, nu2=2,
+def make_problem(p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.0, nu1=2, nu2=2,
                  c_penalty=0.0, precision=IGAMG_FP64, beta=None, dim=2, restart=0, gamma=1, fmg=False,
                  geometry=IGAMG_GEOM_SQUARE, r_inner=0.0, r_outer=0.0):
     pr = Problem()

@@ -40,7 +40,24 @@ def _run(cmd):
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("build failed:\n" + " ".join(cmd) + "\n" + r.stdout)
+    if "-c" in cmd:                                   # remember how the object was built
+        with open(cmd[cmd.index("-o") + 1] + ".cmd", "w") as fh:
+            fh.write(" ".join(cmd))
     return r.stdout
+
+
+def _stale(src, obj, cmd):
+    """An object is rebuilt when it is missing, older than its source or any header of the
+    package, or was built with another command line (kept beside it as <obj>.cmd)."""
+    stamp = obj + ".cmd"
+    if not (os.path.exists(obj) and os.path.exists(stamp)):
+        return True
+    if open(stamp).read() != " ".join(cmd):
+        return True
+    heads = [os.path.join(d, f) for d in (CSRC, INCLUDE) for f in os.listdir(d)
+             if f.endswith((".h", ".cuh"))]
+    newest = max(os.path.getmtime(x) for x in [src] + heads)
+    return os.path.getmtime(obj) < newest
 
 
 def build(verbose=False, extra_nvcc=()):
@@ -50,13 +67,17 @@ def build(verbose=False, extra_nvcc=()):
     jobs, objs = [], []
     for f in cu:
         o = os.path.join(BUILD, f + ".o")
-        jobs.append([nvcc, "-c", os.path.join(CSRC, f), "-o", o] + NVCC_FLAGS + list(extra_nvcc))
+        cmd = [nvcc, "-c", os.path.join(CSRC, f), "-o", o] + NVCC_FLAGS + list(extra_nvcc)
+        if _stale(os.path.join(CSRC, f), o, cmd):
+            jobs.append(cmd)
         objs.append(o)
     for f in cpp:
         o = os.path.join(BUILD, f + ".o")
-        jobs.append(["g++", "-c", os.path.join(CSRC, f), "-o", o] + CXX_FLAGS)
+        cmd = ["g++", "-c", os.path.join(CSRC, f), "-o", o] + CXX_FLAGS
+        if _stale(os.path.join(CSRC, f), o, cmd):
+            jobs.append(cmd)
         objs.append(o)
-    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
+    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs) or 1, os.cpu_count() or 4))) as ex:
         outs = list(ex.map(_run, jobs))
     if verbose:
         for o in outs:

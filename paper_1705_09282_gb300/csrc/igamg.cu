@@ -194,6 +194,7 @@ struct TypedLevel {
   T* cinv8 = nullptr;
   Xfer<T> tp{}, tq{};            // transfer from level l-1 into level l (l >= 1)
   T *U = nullptr, *F = nullptr, *R = nullptr;
+  unsigned* prog = nullptr;      // pipelined sweep: colour steps finished per tile
 };
 
 template <typename T>
@@ -218,6 +219,12 @@ struct LevelCommon {
   int *dofs = nullptr, *cls = nullptr, *nloc = nullptr, *d2p_off = nullptr, *d2p_idx = nullptr;
   double* dcoef = nullptr;      // derivative coefficients (n+p-1), device
   double* inv_dcoef = nullptr;  // their reciprocals
+  // pipelined multiplicative sweep (k_sweep_tiles): tiles of tw x tw patch positions, or
+  // ntx = 0 where the level uses one launch per colour
+  int tw = 0, ntx = 0, nty = 0;
+  int *tile_list = nullptr, *tile_off = nullptr, *tile_n8 = nullptr;
+  int lpr = 1;                  // lanes per local row of an 8-DOF patch in the colour kernels
+  int tpb = 0;                  // threads per block of the colour kernels (0: colour_block())
 };
 
 }  // namespace
@@ -269,7 +276,11 @@ struct igamg_handle {
   Typed<float> f;
   int ndof0 = 0;
   double* part = nullptr;      // residual partials (2 per block of the finest level)
-  double* norm2 = nullptr;     // device scalar
+  double* norm2 = nullptr;     // device: [0] squared residual norm, [1] holds the sweep
+                               // timeout flag (an int in its first four bytes)
+  int* sweep_err = nullptr;    // = (int*)(norm2 + 1): read back with the norm
+  int stall_tile = -1;         // IGAMG_TEST_STALL_TILE: a tile that never reports progress,
+                               // to exercise the sweep's timeout path in tests
   unsigned long long* divmax = nullptr;
   double *lv_p = nullptr, *lv_q = nullptr;
   double* h_pinned = nullptr;  // 2 doubles
@@ -387,18 +398,26 @@ int do_smooth(igamg_handle* h, int l, T* U, const T* F, cudaStream_t s) {
         k_mult_colour_split<3, T><<<nb, 512, shm16, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
     }
   } else if (h->prob.smoother == IGAMG_MULT) {
-    const int tpb = colour_block(), wpb = tpb / 32;
+    const int tpb = lc.tpb > 0 ? lc.tpb : colour_block(), wpb = tpb / 32;
     const size_t shmc = (size_t)wpb * lc.maxl * sizeof(T);
+    const int ppw = lc.lpr == 2 ? 2 : 4;            // 8-DOF patches per warp
     for (int c = 0; c < lc.n_colours; ++c) {
       int first = lc.colour_off[c], count = lc.colour_off[c + 1] - first;
       if (count == 0) continue;
       int n8 = lc.n8[c], ngen = count - n8;
-      int nb8 = (n8 + 4 * wpb - 1) / (4 * wpb), nbg = (ngen + wpb - 1) / wpb;
+      int nb8 = (n8 + ppw * wpb - 1) / (ppw * wpb), nbg = (ngen + wpb - 1) / wpb;
       unsigned nb = (unsigned)(nb8 + nbg);
-      if (h->prob.p == 2)
-        k_mult_colour<2, T><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
-      else
-        k_mult_colour<3, T><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+      if (h->prob.p == 2) {
+        if (lc.lpr == 2)
+          k_mult_colour<2, T, 2><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+        else
+          k_mult_colour<2, T><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+      } else {
+        if (lc.lpr == 2)
+          k_mult_colour<3, T, 2><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+        else
+          k_mult_colour<3, T><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+      }
     }
   } else {
     int rc = do_residual<T>(h, l, U, F, tl.R, nullptr, s);
@@ -408,10 +427,68 @@ int do_smooth(igamg_handle* h, int l, T* U, const T* F, cudaStream_t s) {
       k_add_local<2, T><<<nb, kBlock, shm, s>>>(tl.R, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, lc.n_patches, typed<T>(h).delta);
     else
       k_add_local<3, T><<<nb, kBlock, shm, s>>>(tl.R, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, lc.n_patches, typed<T>(h).delta);
-    T eta = (T)(h->prob.eta > 0 ? h->prob.eta : 0.5);
+    T eta = (T)(h->prob.eta > 0 ? h->prob.eta : 0.3);
     k_add_gather<T><<<nblk(lc.sz.n_total), kBlock, 0, s>>>((int)lc.sz.n_total, U, typed<T>(h).delta, lc.d2p_off, lc.d2p_idx, eta);
   }
   return launch_check();
+}
+
+// Threads per block of the pipelined sweep (tiled levels; a level that is one tile runs in
+// one block of kSoloThreads) and the dynamic shared memory of its wall patches.
+constexpr int kTileThreads = 128, kSoloThreads = 512;
+template <typename T>
+size_t tile_smem(int maxl, int threads = kTileThreads) { return (size_t)(threads / 32) * maxl * sizeof(T); }
+
+// Pipelined multiplicative sweep (k_sweep_tiles): all colours of `sweeps` sweeps in one
+// cooperative launch, one block per tile.
+template <typename T>
+int do_sweep_tiles(igamg_handle* h, int l, T* U, const T* F, int sweeps, cudaStream_t s) {
+  auto& lc = h->lc[l];
+  auto& tl = typed<T>(h).lev[l];
+  TileSched ts{lc.ntx, lc.nty, lc.n_colours, lc.tile_list, lc.tile_off, lc.tile_n8, tl.prog, h->sweep_err,
+               h->stall_tile};
+  const bool solo = lc.ntx * lc.nty == 1;
+  const int nthr = solo ? kSoloThreads : kTileThreads;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(lc.ntx * lc.nty));
+  cfg.blockDim = dim3(nthr);
+  cfg.dynamicSmemBytes = tile_smem<T>(lc.maxl, nthr);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const int steps = sweeps * lc.n_colours;
+  const T* ci = tl.cinv;
+  const T* ci8 = tl.cinv8;
+  const int* nloc = lc.nloc;
+  cudaError_t e;
+  if (h->prob.p == 2)
+    e = solo ? cudaLaunchKernelEx(&cfg, k_sweep_tiles<2, T, kSoloThreads>, tl.L, U, F, (const int*)lc.dofs,
+                                  (const int*)lc.cls, ci, ci8, nloc, lc.maxl, ts, steps)
+             : cudaLaunchKernelEx(&cfg, k_sweep_tiles<2, T, kTileThreads>, tl.L, U, F, (const int*)lc.dofs,
+                                  (const int*)lc.cls, ci, ci8, nloc, lc.maxl, ts, steps);
+  else
+    e = solo ? cudaLaunchKernelEx(&cfg, k_sweep_tiles<3, T, kSoloThreads>, tl.L, U, F, (const int*)lc.dofs,
+                                  (const int*)lc.cls, ci, ci8, nloc, lc.maxl, ts, steps)
+             : cudaLaunchKernelEx(&cfg, k_sweep_tiles<3, T, kTileThreads>, tl.L, U, F, (const int*)lc.dofs,
+                                  (const int*)lc.cls, ci, ci8, nloc, lc.maxl, ts, steps);
+  if (e != cudaSuccess) { g_err = cudaGetErrorString(e); return IGAMG_ECUDA; }
+  return IGAMG_OK;
+}
+
+// nu sweeps of the level's smoother: one pipelined launch where the level has a tile
+// schedule (multiplicative smoother), else one do_smooth per sweep.
+template <typename T>
+int do_smooth_n(igamg_handle* h, int l, T* U, const T* F, int sweeps, cudaStream_t s) {
+  if (sweeps <= 0) return IGAMG_OK;
+  if (h->prob.smoother == IGAMG_MULT && h->lc[l].ntx > 0) return do_sweep_tiles<T>(h, l, U, F, sweeps, s);
+  for (int k = 0; k < sweeps; ++k) {
+    int rc = do_smooth<T>(h, l, U, F, s);
+    if (rc) return rc;
+  }
+  return IGAMG_OK;
 }
 
 template <typename T>
@@ -475,14 +552,14 @@ int do_cycle(igamg_handle* h, int l, T* Ul, const T* Fl, bool zero, cudaStream_t
   if (l == 0) return do_coarse<T>(h, Fl, Ul, s);
   int rc;
   if (zero) CK(cudaMemsetAsync(Ul, 0, ty.lev[l].L.n_total * sizeof(T), s));
-  for (int k = 0; k < h->prob.nu1; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+  if ((rc = do_smooth_n<T>(h, l, Ul, Fl, h->prob.nu1, s))) return rc;
   if ((rc = do_residual<T>(h, l, Ul, Fl, ty.lev[l].R, nullptr, s))) return rc;
   if ((rc = do_restrict<T>(h, l, ty.lev[l].R, ty.lev[l - 1].F, s))) return rc;
   const int gamma = std::max(1, h->prob.gamma);
   for (int g = 0; g < gamma; ++g)
     if ((rc = do_cycle<T>(h, l - 1, ty.lev[l - 1].U, ty.lev[l - 1].F, g == 0, s))) return rc;
   if ((rc = do_prolong<T>(h, l, ty.lev[l - 1].U, Ul, s))) return rc;
-  for (int k = 0; k < h->prob.nu2; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+  if ((rc = do_smooth_n<T>(h, l, Ul, Fl, h->prob.nu2, s))) return rc;
   return IGAMG_OK;
 }
 
@@ -502,7 +579,7 @@ int do_vcycle(igamg_handle* h, T* U, const T* F, cudaStream_t s) {
       T* Ul = (l == L - 1) ? U : ty.lev[l].U;
       const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
       if (l < L - 1) CK(cudaMemsetAsync(Ul, 0, ty.lev[l].L.n_total * sizeof(T), s));
-      for (int k = 0; k < h->prob.nu1; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+      if ((rc = do_smooth_n<T>(h, l, Ul, Fl, h->prob.nu1, s))) return rc;
       if ((rc = do_residual<T>(h, l, Ul, Fl, ty.lev[l].R, nullptr, s))) return rc;
       if ((rc = do_restrict<T>(h, l, ty.lev[l].R, ty.lev[l - 1].F, s))) return rc;
     }
@@ -511,7 +588,7 @@ int do_vcycle(igamg_handle* h, T* U, const T* F, cudaStream_t s) {
       T* Ul = (l == L - 1) ? U : ty.lev[l].U;
       const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
       if ((rc = do_prolong<T>(h, l, ty.lev[l - 1].U, Ul, s))) return rc;
-      for (int k = 0; k < h->prob.nu2; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+      if ((rc = do_smooth_n<T>(h, l, Ul, Fl, h->prob.nu2, s))) return rc;
     }
     return IGAMG_OK;
   }
@@ -519,7 +596,7 @@ int do_vcycle(igamg_handle* h, T* U, const T* F, cudaStream_t s) {
     T* Ul = (l == L - 1) ? U : ty.lev[l].U;
     const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
     if (l < L - 1) CK(cudaMemsetAsync(Ul, 0, ty.lev[l].L.n_total * sizeof(T), s));
-    for (int k = 0; k < h->prob.nu1; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+    if ((rc = do_smooth_n<T>(h, l, Ul, Fl, h->prob.nu1, s))) return rc;
     if ((rc = do_residual<T>(h, l, Ul, Fl, ty.lev[l].R, nullptr, s))) return rc;
     if ((rc = do_restrict<T>(h, l, ty.lev[l].R, ty.lev[l - 1].F, s))) return rc;
   }
@@ -528,7 +605,7 @@ int do_vcycle(igamg_handle* h, T* U, const T* F, cudaStream_t s) {
     T* Ul = (l == L - 1) ? U : ty.lev[l].U;
     const T* Fl = (l == L - 1) ? F : ty.lev[l].F;
     if ((rc = do_prolong<T>(h, l, ty.lev[l - 1].U, Ul, s))) return rc;
-    for (int k = 0; k < h->prob.nu2; ++k) if ((rc = do_smooth<T>(h, l, Ul, Fl, s))) return rc;
+    if ((rc = do_smooth_n<T>(h, l, Ul, Fl, h->prob.nu2, s))) return rc;
   }
   return IGAMG_OK;
 }
@@ -619,9 +696,31 @@ int ensure_graph(igamg_handle* h, int kind, double* U, const double* F) {
   return IGAMG_OK;
 }
 
-int read_norm(igamg_handle* h, double* out, cudaStream_t s) {
-  CK(cudaMemcpyAsync(h->h_pinned, h->norm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+// A pipelined sweep gave up waiting (the flag beside the norm): its tiles' step counters
+// may disagree, so all of them and the flag are reset before the timeout is reported.
+int sweep_timeout(igamg_handle* h, cudaStream_t s) {
+  for (size_t l = 0; l < h->lc.size(); ++l) {
+    const size_t nt = (size_t)h->lc[l].ntx * h->lc[l].nty;
+    if (!nt) continue;
+    if (l < h->d.lev.size() && h->d.lev[l].prog) CK(cudaMemsetAsync(h->d.lev[l].prog, 0, nt * sizeof(unsigned), s));
+    if (l < h->f.lev.size() && h->f.lev[l].prog) CK(cudaMemsetAsync(h->f.lev[l].prog, 0, nt * sizeof(unsigned), s));
+  }
+  CK(cudaMemsetAsync(h->sweep_err, 0, sizeof(int), s));
   CK(cudaStreamSynchronize(s));
+  g_err = "a pipelined smoothing sweep gave up waiting for a neighbouring tile";
+  return IGAMG_ETIMEOUT;
+}
+
+bool sweep_flag(const double* pinned_pair) {
+  int flag = 0;
+  std::memcpy(&flag, pinned_pair + 1, sizeof(int));
+  return flag != 0;
+}
+
+int read_norm(igamg_handle* h, double* out, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h->h_pinned, h->norm2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (sweep_flag(h->h_pinned)) return sweep_timeout(h, s);
   *out = std::sqrt(h->h_pinned[0]);
   return IGAMG_OK;
 }
@@ -667,7 +766,8 @@ bool same_structure(const igamg_handle* a, const igamg_handle* b) {
       x.geometry != y.geometry || (x.beta_qp == nullptr) != (y.beta_qp == nullptr))
     return false;
   for (size_t l = 0; l < a->lc.size(); ++l)
-    if (a->lc[l].maxl != b->lc[l].maxl || a->lc[l].colour_off != b->lc[l].colour_off || a->lc[l].n8 != b->lc[l].n8)
+    if (a->lc[l].maxl != b->lc[l].maxl || a->lc[l].colour_off != b->lc[l].colour_off || a->lc[l].n8 != b->lc[l].n8 ||
+        a->lc[l].lpr != b->lc[l].lpr)
       return false;
   return true;
 }
@@ -711,16 +811,22 @@ int batch_chunk(igamg_handle** hs, double** Us, const double** Fs, const BatchCa
   };
   auto smooth = [&](int l) {
     const auto& lc = h0->lc[l];
-    const int tpb = colour_block(), wpb = tpb / 32;
+    const int tpb = lc.tpb > 0 ? lc.tpb : colour_block(), wpb = tpb / 32;
     const size_t shmc = (size_t)wpb * lc.maxl * sizeof(double);
+    const int ppw = lc.lpr == 2 ? 2 : 4;            // 8-DOF patches per warp
     for (int c = 0; c < lc.n_colours; ++c) {
       int first = lc.colour_off[c], count = lc.colour_off[c + 1] - first;
       if (count == 0) continue;
       int n8 = lc.n8[c], ngen = count - n8;
-      int nb8 = (n8 + 4 * wpb - 1) / (4 * wpb), nbg = (ngen + wpb - 1) / wpb;
+      int nb8 = (n8 + ppw * wpb - 1) / (ppw * wpb), nbg = (ngen + wpb - 1) / wpb;
       dim3 grid((unsigned)(nb8 + nbg), ns);
-      if (p == 2) k_mult_colour_b<2, double><<<grid, tpb, shmc, s>>>(A[l], lc.dofs, lc.cls, lc.nloc, lc.maxl, first, n8, ngen, nb8);
-      else k_mult_colour_b<3, double><<<grid, tpb, shmc, s>>>(A[l], lc.dofs, lc.cls, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+      if (p == 2) {
+        if (lc.lpr == 2) k_mult_colour_b<2, double, 2><<<grid, tpb, shmc, s>>>(A[l], lc.dofs, lc.cls, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+        else k_mult_colour_b<2, double><<<grid, tpb, shmc, s>>>(A[l], lc.dofs, lc.cls, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+      } else {
+        if (lc.lpr == 2) k_mult_colour_b<3, double, 2><<<grid, tpb, shmc, s>>>(A[l], lc.dofs, lc.cls, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+        else k_mult_colour_b<3, double><<<grid, tpb, shmc, s>>>(A[l], lc.dofs, lc.cls, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+      }
     }
   };
   if (cycle) {
@@ -995,10 +1101,11 @@ int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, d
     CK(cudaStreamWaitEvent(h->exec_stream, h->ev, 0));
     int L = (int)h->d.lev.size();
     if ((rc = do_residual<double>(h, L - 1, Us[i], Fs[i], h->d.lev[L - 1].R, h->norm2, h->exec_stream))) return rc;
-    CK(cudaMemcpyAsync(h->h_pinned, h->norm2, sizeof(double), cudaMemcpyDeviceToHost, h->exec_stream));
+    CK(cudaMemcpyAsync(h->h_pinned, h->norm2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->exec_stream));
   }
   for (int i = 0; i < n; ++i) {
     CK(cudaStreamSynchronize(hs[i]->exec_stream));
+    if (sweep_flag(hs[i]->h_pinned)) return sweep_timeout(hs[i], hs[i]->exec_stream);
     r0[i] = rk[i] = std::sqrt(hs[i]->h_pinned[0]);
     if (!std::isfinite(r0[i])) st[i] = IGAMG_ENONFINITE;
     else if (r0[i] == 0.0 || (atol && r0[i] <= atol[i])) st[i] = IGAMG_OK;
@@ -1011,7 +1118,7 @@ int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, d
       if (st[i] != IGAMG_NOT_CONVERGED || k[i] >= max_cycles) continue;
       igamg_handle* h = hs[i];
       CK(cudaGraphLaunch(h->graph[(k[i] == 0 && h->prob.fmg) ? 2 : 0], h->exec_stream));
-      CK(cudaMemcpyAsync(h->h_pinned, h->norm2, sizeof(double), cudaMemcpyDeviceToHost, h->exec_stream));
+      CK(cudaMemcpyAsync(h->h_pinned, h->norm2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->exec_stream));
       ++k[i];
       ++active;
     }
@@ -1020,6 +1127,7 @@ int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, d
       if (st[i] != IGAMG_NOT_CONVERGED || k[i] == 0) continue;
       igamg_handle* h = hs[i];
       CK(cudaStreamSynchronize(h->exec_stream));
+      if (sweep_flag(h->h_pinned)) return sweep_timeout(h, h->exec_stream);
       rk[i] = std::sqrt(h->h_pinned[0]);
       igamg_report* rep = reps ? &reps[i] : nullptr;
       if (rep && rep->history && k[i] - 1 < rep->history_cap) rep->history[k[i] - 1] = rk[i] / r0[i];
@@ -1413,6 +1521,216 @@ int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
   return setup_fused<T>(h, ty);
 }
 
+// Tile forms of the sweep allowed (default) or not (IGAMG_PIPELINE=0: colour launches only);
+// read when a handle is created.
+bool pipeline_on() {
+  const char* e = std::getenv("IGAMG_PIPELINE");
+  return !e || std::atoi(e) != 0;
+}
+
+// Blocks of k_sweep_tiles that the whole GPU holds at once (a cooperative launch may not
+// ask for more).
+template <typename T>
+int tile_capacity(int p, int maxl) {
+  int dev = 0, sms = 0, nb = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cudaError_t e = p == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_tiles<2, T, kTileThreads>, kTileThreads, tile_smem<T>(maxl))
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_tiles<3, T, kTileThreads>, kTileThreads, tile_smem<T>(maxl));
+  return e == cudaSuccess ? nb * sms : 0;
+}
+
+// The smoother form of each level, chosen at creation (the project's autotuner; thread and
+// tile shapes of the multiplicative sweep):
+//   colour launches, one lane per patch row   (lpr 1: k_mult_colour, four patches per warp),
+//                                              blocks of 128 (or 64, 256) threads
+//   colour launches, two lanes per patch row  (lpr 2: two patches per warp; 128 or 64)
+//   one block for the whole level             (k_sweep_tiles with one tile of 512 threads)
+//   pipelined tiles of (p + 1) m positions    (k_sweep_tiles, 128 threads, m = 1, 2, 4)
+// Each candidate is timed the way solves run it: nu1 sweeps of the level captured into a CUDA
+// graph, replayed after a warm-up (best of three), on the level's zeroed FP64 workspaces (the
+// arithmetic does not depend on the values).  Choices are cached per process by (p, n, per-row
+// records, mapped).  IGAMG_PIPELINE=0 leaves out the tile forms; IGAMG_SWEEP_FORM pins one
+// ("lanes1", "lanes2", "lanes1_b64", "lanes2_b64", "lanes1_b256", "solo", "tiles1", "tiles2",
+// "tiles4").
+struct SweepForm { int lpr = 1, tiles = 0, tpb = 0; };   // tiles: 0 colour launches, -1 one block, m > 0
+std::map<std::tuple<int, int, int, int>, SweepForm>& form_cache() {
+  static std::map<std::tuple<int, int, int, int>, SweepForm> m;
+  return m;
+}
+
+std::string form_name(const SweepForm& f) {
+  if (f.tiles == 0) return std::string(f.lpr == 2 ? "lanes2" : "lanes1") + (f.tpb ? "_b" + std::to_string(f.tpb) : "");
+  if (f.tiles < 0) return "solo";
+  return "tiles" + std::to_string(f.tiles);
+}
+
+// Installs form f on level l (uploading its tile schedule); the step counters must hold
+// nt_max entries.  Returns IGAMG_EUNSUPPORTED if the form does not fit the level.
+int apply_form(igamg_handle* h, int l, const SweepForm& f) {
+  auto& lc = h->lc[l];
+  const int p = h->prob.p;
+  const PatchTables& pt = h->host.lev[l].pt;
+  lc.lpr = f.lpr;
+  lc.tpb = f.tpb;
+  lc.ntx = lc.nty = 0;
+  if (f.tiles == 0) return IGAMG_OK;
+  const int nint = lc.sz.n + p - 2;
+  const int tw = f.tiles < 0 ? nint : (p + 1) * f.tiles;
+  TileTables tt;
+  build_tile_tables(pt, nint, tw, tt);
+  const int C = pt.n_colours, nt = tt.ntx * tt.nty;
+  // every patch exactly once, in a run of its own colour, its 8-DOF patches first
+  std::vector<char> seen(pt.n_patches, 0);
+  bool ok = (int)tt.list.size() == pt.n_patches && (int)tt.off.size() == nt * C + 1 && tt.off[nt * C] == pt.n_patches;
+  for (int r = 0; ok && r < nt * C; ++r) {
+    const int c = r % C;
+    ok = tt.off[r] <= tt.off[r + 1] && tt.n8[r] <= tt.off[r + 1] - tt.off[r];
+    for (int j = tt.off[r]; ok && j < tt.off[r + 1]; ++j) {
+      const int i = tt.list[j];
+      const bool is8 = i < pt.colour_off[c] + pt.n8[c];
+      ok = i >= pt.colour_off[c] && i < pt.colour_off[c + 1] && !seen[i] && (is8 == (j < tt.off[r] + tt.n8[r]));
+      if (ok) seen[i] = 1;
+    }
+  }
+  if (!ok) { g_err = "tile schedule inconsistent with the patch tables"; return IGAMG_EINVAL; }
+  int rc;
+  if ((rc = upload_as(h, &lc.tile_list, tt.list)) || (rc = upload_as(h, &lc.tile_off, tt.off)) ||
+      (rc = upload_as(h, &lc.tile_n8, tt.n8)))
+    return rc;
+  lc.tw = tw; lc.ntx = tt.ntx; lc.nty = tt.nty;
+  return IGAMG_OK;
+}
+
+// Graph-replayed time (ms) of nu1 (at least one) sweeps of level l in its current form.
+int time_level_sweeps(igamg_handle* h, int l, float* ms_out) {
+  auto& tl = h->d.lev[l];
+  const int sw = std::max(1, h->prob.nu1);
+  cudaGraph_t g;
+  cudaGraphExec_t ge = nullptr;
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = do_smooth_n<double>(h, l, tl.U, tl.F, sw, h->cap_stream);
+  cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
+  if (rc) { if (ec == cudaSuccess) cudaGraphDestroy(g); return rc; }
+  CK(ec);
+  cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  CK(ei);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  cudaError_t e = cudaGraphLaunch(ge, h->stream);
+  for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+    float ms = 0;
+    e = cudaEventRecord(e0, h->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  cudaGraphExecDestroy(ge);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(e);
+  double flag[2];
+  CK(cudaMemcpy(flag, h->norm2, sizeof(flag), cudaMemcpyDeviceToHost));
+  if (sweep_flag(flag)) return sweep_timeout(h, h->stream);
+  *ms_out = best;
+  return IGAMG_OK;
+}
+
+int setup_sweep_forms(igamg_handle* h) {
+  if (const char* e = std::getenv("IGAMG_TEST_STALL_TILE")) h->stall_tile = std::atoi(e);
+  if (h->prob.smoother != IGAMG_MULT) return IGAMG_OK;
+  const int p = h->prob.p, L = (int)h->lc.size();
+  const bool mapped = h->prob.geometry != IGAMG_GEOM_SQUARE;
+  const bool tiles_ok = pipeline_on();
+  const char* pin = std::getenv("IGAMG_SWEEP_FORM");
+  const char* env_lanes = std::getenv("IGAMG_ROW_LANES");
+  const char* env_mult = std::getenv("IGAMG_TILE_MULT");
+  const bool verbose = std::getenv("IGAMG_VERBOSE") != nullptr;
+  int rc;
+  for (int l = 1; l < L; ++l) {
+    auto& lc = h->lc[l];
+    const PatchTables& pt = h->host.lev[l].pt;
+    const bool has_pos = (int)pt.pos.size() == pt.n_patches;
+    const int nint = lc.sz.n + p - 2;
+    int cap = tile_capacity<double>(p, lc.maxl);
+    if (fp32_base(h->prob)) cap = std::min(cap, tile_capacity<float>(p, lc.maxl));
+    auto ntiles = [&](int m) { const int tw = (p + 1) * m, k = (nint + tw - 1) / tw; return (long long)k * k; };
+    std::vector<SweepForm> cands;
+    auto add = [&](SweepForm f) {
+      if (f.lpr == 2 && mapped) return;                        // the split row has no third box
+      if (f.tiles != 0 && (!has_pos || !tiles_ok)) return;
+      if (f.tiles > 0 && (ntiles(f.tiles) > cap || ntiles(f.tiles) < 2)) return;
+      if (f.tiles < 0 && pt.n_patches > 40000) return;         // one SM would be far too slow
+      cands.push_back(f);
+    };
+    if (pin) {
+      std::string w(pin);
+      SweepForm f;
+      if (w.rfind("lanes2", 0) == 0) f.lpr = 2;
+      if (w.find("_b") != std::string::npos) f.tpb = std::atoi(w.c_str() + w.find("_b") + 2);
+      else if (w == "solo") f.tiles = -1;
+      else if (w.rfind("tiles", 0) == 0) f.tiles = std::max(1, std::atoi(w.c_str() + 5));
+      add(f);
+    } else if (env_lanes || env_mult) {                        // experiments: one form
+      SweepForm f;
+      if (env_mult && tiles_ok) f.tiles = std::max(1, std::atoi(env_mult));
+      else if (env_lanes) f.lpr = std::atoi(env_lanes) == 2 ? 2 : 1;
+      add(f);
+      if (cands.empty() && f.tiles > 0) {                      // widen until the tiles fit
+        for (int m = f.tiles + 1; m <= 4096 && cands.empty(); ++m) add(SweepForm{1, m});
+      }
+    } else {
+      for (SweepForm f : {SweepForm{1, 0}, SweepForm{2, 0}, SweepForm{1, 0, 64}, SweepForm{2, 0, 64},
+                          SweepForm{1, 0, 256}, SweepForm{1, -1}, SweepForm{1, 1}, SweepForm{1, 2}, SweepForm{1, 4}})
+        add(f);
+    }
+    if (cands.empty()) cands.push_back(SweepForm{1, 0});
+    // step counters sized for the most tiles any candidate has
+    size_t nt_max = 1;
+    for (auto& f : cands) if (f.tiles > 0) nt_max = std::max(nt_max, (size_t)ntiles(f.tiles));
+    if (has_pos && tiles_ok) {
+      for (int which = 0; which < 2; ++which) {
+        if (which == 1 && !fp32_base(h->prob)) continue;
+        unsigned** prog = which ? &h->f.lev[l].prog : &h->d.lev[l].prog;
+        if ((rc = dmalloc(h, (void**)prog, nt_max * sizeof(unsigned)))) return rc;
+        CK(cudaMemset(*prog, 0, nt_max * sizeof(unsigned)));
+      }
+    }
+    const auto key = std::make_tuple(p, lc.sz.n, h->prob.beta_qp ? 1 : 0, mapped ? 1 : 0);
+    SweepForm chosen = cands[0];
+    auto it = form_cache().find(key);
+    if (cands.size() > 1 && it != form_cache().end()) {
+      chosen = it->second;
+    } else if (cands.size() > 1) {
+      auto& tl = h->d.lev[l];
+      const size_t nb = (size_t)tl.L.n_total * sizeof(double);
+      CK(cudaMemsetAsync(tl.U, 0, nb, h->stream));
+      CK(cudaMemsetAsync(tl.F, 0, nb, h->stream));
+      float best = 1e30f;
+      for (auto& f : cands) {
+        if ((rc = apply_form(h, l, f))) return rc;
+        float ms = 0;
+        if ((rc = time_level_sweeps(h, l, &ms))) return rc;
+        if (verbose) std::fprintf(stderr, "igamg: level %d (n = %d) %s: %.1f us per %d sweep(s)\n", l, lc.sz.n,
+                                  form_name(f).c_str(), 1e3f * ms, std::max(1, h->prob.nu1));
+        if (ms < best) { best = ms; chosen = f; }
+      }
+      form_cache()[key] = chosen;
+    }
+    if ((rc = apply_form(h, l, chosen))) return rc;
+    if (h->d.lev[l].prog) {   // the timing runs advanced different tile sets: start from 0
+      CK(cudaMemset(h->d.lev[l].prog, 0, nt_max * sizeof(unsigned)));
+    }
+    if (verbose) std::fprintf(stderr, "igamg: level %d (n = %d): %s\n", l, lc.sz.n, form_name(chosen).c_str());
+  }
+  return IGAMG_OK;
+}
+
 bool any_3d(int n, igamg_handle** hs) {
   for (int i = 0; i < n; ++i) if (hs[i]->d3) return true;
   return false;
@@ -1537,9 +1855,12 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
   h->ndof0 = h->host.ndof0;
   long long nfine = h->lc[L - 1].sz.n_total;
   if ((rc = dmalloc(h, (void**)&h->part, 2 * sizeof(double) * (nblk(nfine) + 1)))) return fail(rc);
-  if ((rc = dmalloc(h, (void**)&h->norm2, sizeof(double)))) return fail(rc);
+  if ((rc = dmalloc(h, (void**)&h->norm2, 2 * sizeof(double)))) return fail(rc);
+  if (cudaMemset(h->norm2, 0, 2 * sizeof(double)) != cudaSuccess) return fail(IGAMG_ECUDA);
+  h->sweep_err = (int*)(h->norm2 + 1);
   if ((rc = dmalloc(h, (void**)&h->divmax, sizeof(unsigned long long)))) return fail(rc);
   if ((rc = upload_as(h, &h->lv_p, h->host.lv_p)) || (rc = upload_as(h, &h->lv_q, h->host.lv_q))) return fail(rc);
+  if ((rc = setup_sweep_forms(h))) return fail(rc);
   size_t nG = (size_t)pr.n_fine * (p + 2);
   if ((rc = dmalloc(h, (void**)&h->f_dev, 2 * nG * nG * sizeof(double)))) return fail(rc);
   if ((rc = dmalloc(h, (void**)&h->Fh, nfine * sizeof(double)))) return fail(rc);
@@ -1653,8 +1974,26 @@ int igamg_residual(igamg_handle* h, int level, const double* U, const double* F,
 int igamg_smooth(igamg_handle* h, int level, double* U, const double* F, int sweeps) {
   if (h && U && F && h->d3) return h3_smooth(h->d3, level, U, F, sweeps);
   if (!h || !U || !F || level < 1 || level >= (int)h->lc.size() || sweeps < 0) return IGAMG_EINVAL;
-  for (int k = 0; k < sweeps; ++k) { int rc = do_smooth<double>(h, level, U, F, h->stream); if (rc) return rc; }
+  return do_smooth_n<double>(h, level, U, F, sweeps, h->stream);
+}
+
+int igamg_level_form(const igamg_handle* h, int level, int* lanes, int* threads, int* tiles) {
+  if (!h || level < 0) return IGAMG_EINVAL;
+  if (h->d3) return IGAMG_EUNSUPPORTED;
+  if (level >= (int)h->lc.size()) return IGAMG_EINVAL;
+  const auto& lc = h->lc[level];
+  const bool tiled = lc.ntx > 0;
+  if (lanes) *lanes = tiled ? 1 : lc.lpr;
+  if (threads) *threads = tiled ? (lc.ntx * lc.nty == 1 ? kSoloThreads : kTileThreads) : (lc.tpb > 0 ? lc.tpb : colour_block());
+  if (tiles) *tiles = tiled ? lc.ntx * lc.nty : 0;
   return IGAMG_OK;
+}
+
+int igamg_smooth_f32(igamg_handle* h, int level, float* U, const float* F, int sweeps) {
+  if (!h || !U || !F || sweeps < 0) return IGAMG_EINVAL;
+  if (h->d3 || !fp32_base(h->prob)) return IGAMG_EUNSUPPORTED;
+  if (level < 1 || level >= (int)h->lc.size()) return IGAMG_EINVAL;
+  return do_smooth_n<float>(h, level, U, F, sweeps, h->stream);
 }
 
 int igamg_restrict(igamg_handle* h, int level, const double* r_fine, double* g_coarse) {
@@ -1823,11 +2162,11 @@ int igamg_curl(igamg_handle* h, const double* psi, double* U) {
 // Residual entry point that allocates no device memory.
 //
 // For callers that cannot call cudaMalloc (a host program whose allocations all go
-// through its own pool or arena, code running inside a captured region that forbids new
-// allocations, or an embedding that owns the whole device memory budget): the scratch
-// of the residual kernel -- its level operator tables and its per-block partial sums --
-// lives in one fixed array in device memory that the library declares statically.
-// Every GPU that loads the library holds that array (1 MiB) until the process exits.
+// through its own pool or arena, or an embedding that owns the whole device memory
+// budget): the scratch of the residual kernel -- its level operator tables and its
+// per-block partial sums -- lives in one fixed array in device memory that the library
+// declares statically.  Every GPU that loads the library holds that array (1 MiB) until
+// the process exits.
 // ---------------------------------------------------------------------------------------
 namespace {
 
@@ -1836,6 +2175,7 @@ static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
 
 constexpr int kMaxDevices = 64;
 double* g_static_ptr[kMaxDevices] = {};
+std::mutex g_static_mutex;                        // guards the first lookup per device
 
 }  // namespace
 
@@ -1851,6 +2191,16 @@ extern "C" int igamg_residual_static(const igamg_problem* prob, int level, const
   if (level < 0 || level >= pr.n_levels || !(pr.sigma > 0) || !(pr.nu > 0)) return IGAMG_EINVAL;
   const int p = pr.p, n = pr.n_fine >> (pr.n_levels - 1 - level);
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  {
+    // the tables go up through a pageable host copy that is freed on return, and norm_out
+    // synchronises the stream: neither is valid while the stream is being captured
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+      g_err = "igamg_residual_static: the stream is being captured";
+      return IGAMG_EUNSUPPORTED;
+    }
+  }
 
   // size check before any work: class stencil tables + partials + the norm slot
   igamg_sizes sz = level_sizes(p, n);
@@ -1869,12 +2219,16 @@ extern "C" int igamg_residual_static(const igamg_problem* prob, int level, const
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return IGAMG_EUNSUPPORTED;
-  if (!g_static_ptr[dev]) {
-    double* ptr = nullptr;
-    CK(cudaGetSymbolAddress((void**)&ptr, g_static_scratch));
-    g_static_ptr[dev] = ptr;
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+      double* ptr = nullptr;
+      CK(cudaGetSymbolAddress((void**)&ptr, g_static_scratch));
+      g_static_ptr[dev] = ptr;
+    }
+    scratch = g_static_ptr[dev];
   }
-  double* scratch = g_static_ptr[dev];
 
   // this level's class stencils (host), copied into the front of the static array
   Level1D f;

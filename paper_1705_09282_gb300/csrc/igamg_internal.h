@@ -1,6 +1,7 @@
 // Internal declarations shared by the host set-up (setup.cpp) and the CUDA side (igamg.cu).
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -57,6 +58,7 @@ struct PatchTables {
   std::vector<double> cinv8;   // n_cls8 * 64: the same for 8-DOF patches, packed 8 x 8
   std::vector<int> colour_off; // n_colours + 1
   std::vector<int> n8;         // per colour: patches with 4+4 DOFs, stored first in the colour
+  std::vector<int> pos;         // 2D: per patch its streamfunction position a | b << 16
   std::vector<int> d2p_off;    // dof -> list of (patch * maxl + local row), CSR over dofs
   std::vector<int> d2p_idx;
   // Row-flat view for the row-parallel colour kernel: each colour is cut into blocks of
@@ -74,6 +76,15 @@ struct PatchTables {
 
 // Fills the row-flat view (slot_*, colour_blk, cinv_all) from dofs / cls / nloc / cinv / cinv8.
 void build_row_slots(PatchTables& pt);
+
+// Schedule of the pipelined sweep (2D): patch positions 1..nint cut into tiles of tw x tw,
+// tiles row-major (ntx per row); for tile t and colour c, list[off[t*C+c] .. off[t*C+c+1])
+// holds the patch indices of that colour in the tile, its n8[t*C+c] 8-DOF patches first.
+struct TileTables {
+  int tw = 0, ntx = 0, nty = 0;
+  std::vector<int> list, off, n8;
+};
+void build_tile_tables(const PatchTables& pt, int nint, int tw, TileTables& tt);
 
 // Row stencils of K_l by row class.  A row's class is the pair of 1D position classes
 // of its two indices (cls1 below): positions within T of either end are their own class,
@@ -131,9 +142,20 @@ struct HierarchyHost {
 
 // Builds everything; returns IGAMG_OK or an error code with a message in err.
 int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err);
-// What the colour kernels rely on: every patch DOF is a row of the level (not lambda), and
-// within one colour no DOF appears twice (same-colour updates never touch the same entry).
-bool validate_patch_tables(const PatchTables& pt, long long n_rows, std::string& err);
+// What the colour kernels rely on: every patch DOF is a row of the level (not lambda);
+// within one colour no DOF appears twice (same-colour updates never touch the same entry);
+// and no two patches of one colour are coupled through K.  The last is checked the way the
+// method argues it (Sec. 5.2: subdomains of one colour overlap only on sets of measure
+// zero): the element boxes spanned by the supports of each patch's DOFs must not share an
+// element with another patch of the same colour.  Two basis functions whose supports share
+// no element have a zero entry in every block of K (volume terms, Nitsche wall terms and,
+// on coarse levels, the Galerkin products of functions supported inside the same boxes),
+// so a patch's local residual never reads a value that a same-colour patch writes, and a
+// colour's patches may run in any order or at once with the sequential sweep's result.
+// support(g, lo, hi): element index range [lo, hi] of DOF g's support per direction;
+// n_elem: elements per direction (dims beyond the level's dimension = 1).
+bool validate_patch_tables(const PatchTables& pt, long long n_rows, std::string& err,
+                           const std::function<void(long long, int*, int*)>& support, const int* n_elem);
 igamg_sizes level_sizes(int p, int n);
 double k_entry(const Level1D& L, const igamg_sizes& s, long long g1, long long g2);
 // entry (g1, g2) of a level given by per-row stencil records

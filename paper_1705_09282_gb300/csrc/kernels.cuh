@@ -90,14 +90,17 @@ __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __re
   const int b1_base = is_p ? L.n_ux : nu;
   const int b1_x0 = is_x ? -P : -Q, b1_y0 = is_x ? -Q : (is_p ? -Q : -P), b1_wy = is_x ? WQ : 2 * P;
   const int b1_ylo = is_p ? 1 : 0, b1_yhi = is_p ? L.nint : L.lastq, b1_ysh = is_p ? 1 : 0;
-  T acc = T(0), acc2 = T(0);
+  // four independent multiply-add chains (even and odd terms of each box): FP64 latency on
+  // this GPU is long, so a row's critical path is its longest chain
+  T acc = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
   if (PART != 1) {
 #pragma unroll
     for (int j = 0; j < B0; ++j) {
       int dx = j / b0_wy, dy = j - dx * b0_wy;
       int x = clampi(ix + b0_x0 + dx, b0_xlo, b0_xhi) - b0_xsh;
       int y = clampi(iy + b0_y0 + dy, b0_ylo, b0_yhi) - b0_ysh;
-      acc = fma(st[j], U[b0_base + y * b0_stride + x], acc);
+      if (j & 1) acc1 = fma(st[j], U[b0_base + y * b0_stride + x], acc1);
+      else acc = fma(st[j], U[b0_base + y * b0_stride + x], acc);
     }
   }
   if (PART != 0) {
@@ -106,9 +109,10 @@ __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __re
       int dx = j / b1_wy, dy = j - dx * b1_wy;
       int x = clampi(ix + b1_x0 + dx, 0, L.lastq);
       int y = clampi(iy + b1_y0 + dy, b1_ylo, b1_yhi) - b1_ysh;
-      acc2 = fma(st[B0 + j], U[b1_base + y * L.npd + x], acc2);
+      if (j & 1) acc3 = fma(st[B0 + j], U[b1_base + y * L.npd + x], acc3);
+      else acc2 = fma(st[B0 + j], U[b1_base + y * L.npd + x], acc2);
     }
-    acc = fma(st[RU - 1], U[L.n_total - 1], acc);
+    acc3 = fma(st[RU - 1], U[L.n_total - 1], acc3);
     if (L.sext && !is_p) {
       // third box (mapped domains): u_x row -> u_y columns (x - P .. x + Q, y - Q .. y + P),
       // u_y row -> u_x columns (x - Q .. x + P, y - P .. y + Q); clamped positions carry 0
@@ -121,11 +125,12 @@ __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __re
         int cx = ix + ox + dx, cy = iy + oy + dy;
         int idx = is_x ? L.n_ux + (clampi(cy, 1, L.nint) - 1) * L.npd + clampi(cx, 0, L.lastq)
                        : clampi(cy, 0, L.lastq) * L.nxu + clampi(cx, 1, L.nint) - 1;
-        acc2 = fma(se[j], U[idx], acc2);
+        if (j & 1) acc3 = fma(se[j], U[idx], acc3);
+        else acc2 = fma(se[j], U[idx], acc2);
       }
     }
   }
-  return acc + acc2;
+  return (acc + acc1) + (acc2 + acc3);
 }
 
 // m_k for a pressure row (the last stencil entry).
@@ -202,13 +207,86 @@ __device__ __forceinline__ void fast_patch_lane(const LevelTab<T>& L, T* U, cons
   int g = dofs[patch * maxl + row];
   T r = F[g] - row_KU<P>(L, U, g);
   const T* A = cinv8 + (size_t)cls[patch] * 64 + row * 8;
+  T d[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int s = 0; s < 8; ++s) d[s & 3] = fma(A[s], __shfl_sync(0xffffffffu, r, (lane & ~7) + s), d[s & 3]);
+  if (active) U[g] += (d[0] + d[1]) + (d[2] + d[3]);
+}
+
+// Half of row g of K U for the two-lanes-per-row patch form: half 0 sums box 0, half 1 box 1
+// and the lambda term.  Both halves run the same instruction stream (no divergence between
+// the two lanes of a row): a loop of B0 terms over their own box, half 1's past its B1 + 1
+// terms padded with zero coefficients at a valid (clamped) index.  Not for mapped domains
+// (their third box is not split).
+template <int P, typename T>
+__device__ __forceinline__ T row_half(const LevelTab<T>& L, const T* __restrict__ U, int g, int half) {
+  constexpr int Q = P - 1, TC = 2 * P + 1, NC = 2 * TC + 1;
+  constexpr int WQ = 2 * Q + 1, WPP = 2 * P + 1;
+  constexpr int B0 = WPP * WQ, B1 = 2 * P * WQ, RU = B0 + B1 + 1;
+  static_assert(B0 >= B1 + 1, "box 0 must cover box 1 and the lambda term");
+  const int nu = L.n_ux + L.n_uy;
+  const bool is_x = g < L.n_ux, is_p = g >= nu, is_y = !is_x && !is_p;
+  const int off = is_x ? 0 : (is_p ? nu : L.n_ux);
+  const int rs = is_x ? L.nxu : L.npd;
+  const int r = g - off;
+  const int q_ = r / rs;
+  const int iy = q_ + (is_y ? 1 : 0);
+  const int ix = r - q_ * rs + (is_x ? 1 : 0);
+  const int cx = cls1d<P>(ix, is_x ? L.lastp : L.lastq);
+  const int cy = cls1d<P>(iy, is_y ? L.lastp : L.lastq);
+  const T* st = L.srow ? L.srow + (size_t)g * RU : (is_x ? L.sx : (is_p ? L.sp : L.sy)) + (cx * NC + cy) * RU;
+  // box 0: own velocity block (u rows) or u_x (p rows); box 1: pressure (u rows) or u_y (p rows)
+  const int base = half ? (is_p ? L.n_ux : nu) : (is_y ? L.n_ux : 0);
+  const int stride = half ? L.npd : (is_y ? L.npd : L.nxu);
+  const int x0 = (is_x ? -P : -Q);
+  const int y0 = half ? (is_x ? -Q : (is_p ? -Q : -P)) : (is_y ? -P : -Q);
+  const int wy = half ? (is_x ? WQ : 2 * P) : (is_y ? WPP : WQ);
+  const int xlo = half ? 0 : (is_y ? 0 : 1), xhi = half ? L.lastq : (is_y ? L.lastq : L.nint);
+  const int xsh = half ? 0 : (is_y ? 0 : 1);
+  const int ylo = half ? (is_p ? 1 : 0) : (is_y ? 1 : 0), yhi = half ? (is_p ? L.nint : L.lastq) : (is_y ? L.nint : L.lastq);
+  const int ysh = half ? (is_p ? 1 : 0) : (is_y ? 1 : 0);
+  const int cnt = half ? B1 : B0, coff = half ? B0 : 0;
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  int dx = 0, dy = 0;
+#pragma unroll
+  for (int j = 0; j < B0; ++j) {
+    const int x = clampi(ix + x0 + dx, xlo, xhi) - xsh;
+    const int y = clampi(iy + y0 + dy, ylo, yhi) - ysh;
+    const bool lam = half && j == B1;
+    const T c = j < cnt ? st[coff + j] : (lam ? st[RU - 1] : T(0));
+    const int idx = lam ? L.n_total - 1 : base + y * stride + x;
+    acc[j & 3] = fma(c, U[idx], acc[j & 3]);
+    if (j + 1 < cnt) { ++dy; if (dy == wy) { dy = 0; ++dx; } }   // stays on the last entry past cnt
+  }
+  return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
+// One lane of an 8-DOF patch in the two-lanes-per-row form: two patches per warp, lane =
+// (patch, local row, half).  The row's two halves meet by one shuffle; each half then
+// applies four of the eight columns of the bordered local inverse and the halves meet
+// again.  Compared with fast_patch_lane: half the dependent multiply-adds per lane and
+// twice the warps per colour, for about 16 % more FP64 instructions per patch.
+template <int P, typename T>
+__device__ __forceinline__ void fast_patch_lane2(const LevelTab<T>& L, T* U, const T* F, const int* __restrict__ dofs,
+                                                 const int* __restrict__ cls, const T* __restrict__ cinv8, int maxl,
+                                                 int first, int n8, int grp, int lane) {
+  const int half = lane & 1, row = (lane >> 1) & 7, lane0 = lane & 16;
+  const bool active = grp < n8;
+  const int patch = first + (active ? grp : 0);
+  const int g = dofs[patch * maxl + row];
+  const T fv = F[g];
+  const T v = (half ? T(0) : fv) - row_half<P>(L, U, g, half);
+  const T r = v + __shfl_xor_sync(0xffffffffu, v, 1);
+  const T* A = cinv8 + (size_t)cls[patch] * 64 + row * 8 + half * 4;
   T d0 = T(0), d1 = T(0);
 #pragma unroll
-  for (int s = 0; s < 8; s += 2) {
-    d0 = fma(A[s], __shfl_sync(0xffffffffu, r, (lane & ~7) + s), d0);
-    d1 = fma(A[s + 1], __shfl_sync(0xffffffffu, r, (lane & ~7) + s + 1), d1);
+  for (int k = 0; k < 4; k += 2) {
+    d0 = fma(A[k], __shfl_sync(0xffffffffu, r, lane0 + (half * 4 + k) * 2), d0);
+    d1 = fma(A[k + 1], __shfl_sync(0xffffffffu, r, lane0 + (half * 4 + k + 1) * 2), d1);
   }
-  if (active) U[g] += d0 + d1;
+  T d = d0 + d1;
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  if (active && half == 0) U[g] += d;
 }
 
 // A larger (wall) patch solved by one warp; r is warp-private scratch of maxl entries.
@@ -287,7 +365,7 @@ __device__ __forceinline__ T prolong_elem(const LevelTab<T>& Lf, const LevelTab<
 // that is a multiple of 32 (the launch picks 128 threads so that a colour's blocks spread
 // evenly over the SMs).  Same-colour
 // patches share no DOF and are not coupled by K, so they may be solved in any order.
-template <int P, typename T>
+template <int P, typename T, int LPR = 1>
 __device__ __forceinline__ void mult_colour_block(const LevelTab<T>& L, T* __restrict__ U, const T* __restrict__ F,
                                                   const int* __restrict__ dofs, const int* __restrict__ cls,
                                                   const T* __restrict__ cinv, const T* __restrict__ cinv8,
@@ -295,7 +373,10 @@ __device__ __forceinline__ void mult_colour_block(const LevelTab<T>& L, T* __res
                                                   int ngen, int nb8, int blk) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   if (blk < nb8) {
-    fast_patch_lane<P>(L, U, F, dofs, cls, cinv8, maxl, first, n8, (blk * wpb + wib) * 4 + (lane >> 3), lane);
+    if (LPR == 2)
+      fast_patch_lane2<P>(L, U, F, dofs, cls, cinv8, maxl, first, n8, (blk * wpb + wib) * 2 + (lane >> 4), lane);
+    else
+      fast_patch_lane<P>(L, U, F, dofs, cls, cinv8, maxl, first, n8, (blk * wpb + wib) * 4 + (lane >> 3), lane);
     return;
   }
   extern __shared__ unsigned char smem_raw[];
@@ -305,13 +386,13 @@ __device__ __forceinline__ void mult_colour_block(const LevelTab<T>& L, T* __res
   general_patch_warp<P>(L, U, F, dofs, cls, cinv, nloc, maxl, first + n8 + w, lane, sh + wib * maxl);
 }
 
-template <int P, typename T>
+template <int P, typename T, int LPR = 1>
 __global__ void __launch_bounds__(256) k_mult_colour(LevelTab<T> L, T* __restrict__ U, const T* __restrict__ F,
                                                      const int* __restrict__ dofs, const int* __restrict__ cls,
                                                      const T* __restrict__ cinv, const T* __restrict__ cinv8,
                                                      const int* __restrict__ nloc,
                                                      int maxl, int first, int n8, int ngen, int nb8) {
-  mult_colour_block<P>(L, U, F, dofs, cls, cinv, cinv8, nloc, maxl, first, n8, ngen, nb8, (int)blockIdx.x);
+  mult_colour_block<P, T, LPR>(L, U, F, dofs, cls, cinv, cinv8, nloc, maxl, first, n8, ngen, nb8, (int)blockIdx.x);
 }
 
 // The same colour step with each 8-DOF patch row split over two warps: warps 0-7 of the
@@ -358,6 +439,171 @@ __global__ void __launch_bounds__(512) k_mult_colour_split(LevelTab<T> L, T* __r
   int w = ((int)blockIdx.x - nb8) * 16 + wib;
   if (w >= ngen) return;
   general_patch_warp<P>(L, U, F, dofs, cls, cinv, nloc, maxl, first + n8 + w, lane, sh + wib * maxl);
+}
+
+// ---- pipelined multiplicative sweep: all colours of nu sweeps in one persistent launch ----
+//
+// The patches are cut into square tiles of patch positions (tw x tw, tw >= p); one block
+// owns one tile and runs its patches colour by colour.  A patch at position (a, b) reads
+// and writes only DOFs whose supports lie in, or overlap, the elements [a-p, a] x [b-p, b],
+// so it depends on patches within p positions, i.e. on the eight neighbouring tiles.  Each
+// tile publishes how many colour steps it has finished (prog, monotone across launches);
+// a tile starts step k once every neighbour has finished step k-1.  Neighbours are then
+// never more than one step apart, which gives every patch exactly the values it would see
+// in the sequential colour-major sweep (eq. MSM): the earlier colours' updates near it are
+// done (read after write) and no later colour near it has started (write after read).
+// The launch is cooperative (all blocks resident), and every wait is bounded: a block that
+// gives up sets *err and returns, the others notice *err and return too, and the host
+// resets prog and err before it reports the timeout.
+struct TileSched {
+  int ntx, nty, n_colours;
+  const int* list;      // patch indices (colour-major tables) by (tile, colour), 8-DOF first
+  const int* off;       // ntx * nty * n_colours + 1 offsets into list
+  const int* n8;        // per (tile, colour): 8-DOF patches at the front of its run
+  unsigned* prog;       // per tile: colour steps finished
+  int* err;             // 1 once a wait has given up
+  int stall;            // failure-path test only: this tile never publishes (-1: none)
+};
+
+constexpr long kSpinLimit = 1L << 21;   // polls (about 0.5-1 us each) before giving up
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// With a relaxed load before it (acquire pattern) or a relaxed store after it (release
+// pattern), this fence orders the block's U updates against the step counters.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(const volatile int*)p; }
+
+// What one lane needs of its first 8-DOF patch of a colour step, loaded before the wait for
+// the neighbouring tiles (none of it depends on U): the row, its forcing entry and the
+// patch's inverse row.
+template <typename T>
+struct LanePatch {
+  int g;
+  T f;
+  const T* A;
+  bool active, any;
+};
+
+template <typename T>
+__device__ __forceinline__ LanePatch<T> lane_patch_load(const TileSched& ts, const T* __restrict__ F,
+                                                        const int* __restrict__ dofs, const int* __restrict__ cls,
+                                                        const T* __restrict__ cinv8, int maxl, int run, int grp,
+                                                        int lane) {
+  LanePatch<T> lp;
+  const int o0 = ts.off[run], n8 = ts.n8[run];
+  lp.any = n8 > 0;
+  lp.active = grp < n8;
+  lp.g = 0; lp.f = T(0); lp.A = cinv8;
+  if (lp.any) {
+    const int patch = ts.list[o0 + (lp.active ? grp : 0)];
+    lp.g = dofs[patch * maxl + (lane & 7)];
+    lp.f = F[lp.g];
+    lp.A = cinv8 + (size_t)cls[patch] * 64 + (lane & 7) * 8;
+  }
+  return lp;
+}
+
+// The rest of list_patch_lane for a prefetched lane: residual row, local inverse, update.
+template <int P, typename T>
+__device__ __forceinline__ void lane_patch_solve(const LevelTab<T>& L, T* U, const LanePatch<T>& lp, int lane) {
+  T r = lp.f - row_KU<P>(L, U, lp.g);
+  T d[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int s = 0; s < 8; ++s) d[s & 3] = fma(lp.A[s], __shfl_sync(0xffffffffu, r, (lane & ~7) + s), d[s & 3]);
+  if (lp.active) U[lp.g] += (d[0] + d[1]) + (d[2] + d[3]);
+}
+
+// fast_patch_lane for a patch taken from an index list (four patches per warp).
+template <int P, typename T>
+__device__ __forceinline__ void list_patch_lane(const LevelTab<T>& L, T* U, const T* F, const int* __restrict__ dofs,
+                                                const int* __restrict__ cls, const T* __restrict__ cinv8, int maxl,
+                                                const int* __restrict__ list, int n8, int grp, int lane) {
+  int row = lane & 7;
+  bool active = grp < n8;
+  int patch = list[active ? grp : (grp & ~3)];
+  int g = dofs[patch * maxl + row];
+  T r = F[g] - row_KU<P>(L, U, g);
+  const T* A = cinv8 + (size_t)cls[patch] * 64 + row * 8;
+  T d[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int s = 0; s < 8; ++s) d[s & 3] = fma(A[s], __shfl_sync(0xffffffffu, r, (lane & ~7) + s), d[s & 3]);
+  if (active) U[g] += (d[0] + d[1]) + (d[2] + d[3]);
+}
+
+// NT: threads per block (128 for tiled levels, 6 blocks per SM; 512 for a level that is
+// one tile).  With one tile there is nobody to wait for: the steps are separated by the
+// block barrier alone, without counters or fences.
+template <int P, typename T, int NT>
+__global__ void __launch_bounds__(NT, NT <= 128 ? 6 : 1) k_sweep_tiles(LevelTab<T> L, T* __restrict__ U, const T* __restrict__ F,
+                                                     const int* __restrict__ dofs, const int* __restrict__ cls,
+                                                     const T* __restrict__ cinv, const T* __restrict__ cinv8,
+                                                     const int* __restrict__ nloc, int maxl, TileSched ts, int steps) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sh = reinterpret_cast<T*>(smem_raw);
+  __shared__ int s_go;
+  const int t = blockIdx.x, tx = t % ts.ntx, ty = t / ts.ntx;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const bool solo = gridDim.x == 1;
+  if (threadIdx.x == 0) s_go = ld_volatile_i32(ts.err) == 0;
+  __syncthreads();
+  if (!s_go) return;
+  const unsigned base = ts.prog[t];     // every tile ended the previous launch at the same count
+  // the neighbour that lane j < 8 of warp 0 watches
+  const unsigned* watch = nullptr;
+  if (wib == 0 && lane < 8) {
+    const int j = lane < 4 ? lane : lane + 1;     // 3 x 3 stencil without its centre
+    const int x = tx + j % 3 - 1, y = ty + j / 3 - 1;
+    if (x >= 0 && y >= 0 && x < ts.ntx && y < ts.nty) watch = ts.prog + y * ts.ntx + x;
+  }
+  const int grp0 = wib * 4 + (lane >> 3);
+  LanePatch<T> lp = lane_patch_load(ts, F, dofs, cls, cinv8, maxl, t * ts.n_colours, grp0, lane);
+  for (int k = 0; k < steps; ++k) {
+    if (k > 0 && solo) __syncthreads();
+    if (k > 0 && !solo) {
+      if (wib == 0) {
+        const unsigned need = base + (unsigned)k;
+        bool ok = false;
+        for (long it = 0; it < kSpinLimit; ++it) {
+          const bool mine = watch == nullptr || (int)(ld_relaxed_u32(watch) - need) >= 0;
+          ok = __all_sync(0xffffffffu, mine);
+          if (ok) break;
+          int stop = lane == 0 ? ld_volatile_i32(ts.err) : 0;
+          if (__shfl_sync(0xffffffffu, stop, 0)) break;
+          __nanosleep(20);
+        }
+        fence_acq_rel_gpu();
+        if (lane == 0) {
+          if (!ok) atomicExch(ts.err, 1);
+          s_go = ok;
+        }
+      }
+      __syncthreads();
+      if (!s_go) return;
+    }
+    const int run = t * ts.n_colours + k % ts.n_colours;
+    const int o0 = ts.off[run], n8 = ts.n8[run], ngen = ts.off[run + 1] - o0 - n8;
+    if (lp.any && wib * 4 < n8) lane_patch_solve<P>(L, U, lp, lane);
+    for (int g0 = wib * 4 + wpb * 4; g0 < n8; g0 += wpb * 4)
+      list_patch_lane<P>(L, U, F, dofs, cls, cinv8, maxl, ts.list + o0, n8, g0 + (lane >> 3), lane);
+    for (int w = wib; w < ngen; w += wpb)
+      general_patch_warp<P>(L, U, F, dofs, cls, cinv, nloc, maxl, ts.list[o0 + n8 + w], lane, sh + wib * maxl);
+    if (!solo) {
+      __syncthreads();
+      if (threadIdx.x == 0 && t != ts.stall) {
+        fence_acq_rel_gpu();
+        st_relaxed_u32(ts.prog + t, base + (unsigned)k + 1u);
+      }
+    }
+    if (k + 1 < steps)                  // the next step's rows, while the neighbours finish
+      lp = lane_patch_load(ts, F, dofs, cls, cinv8, maxl, t * ts.n_colours + (k + 1) % ts.n_colours, grp0, lane);
+  }
 }
 
 // Additive sweep (eq. ASM), part 1: local corrections from one common residual, kept per patch.
@@ -455,14 +701,15 @@ struct BatchArgs {
   BatchLevel<T> s[kBatchMax];
 };
 
-template <int P, typename T>
+template <int P, typename T, int LPR = 1>
 __global__ void __launch_bounds__(256) k_mult_colour_b(const __grid_constant__ BatchArgs<T> B,
                                                        const int* __restrict__ dofs, const int* __restrict__ cls,
                                                        const int* __restrict__ nloc, int maxl, int first, int n8,
                                                        int ngen, int nb8) {
   const BatchLevel<T>& b = B.s[blockIdx.y];
   if (!*b.active) return;
-  mult_colour_block<P>(b.L, b.U, b.F, dofs, cls, b.cinv, b.cinv8, nloc, maxl, first, n8, ngen, nb8, (int)blockIdx.x);
+  mult_colour_block<P, T, LPR>(b.L, b.U, b.F, dofs, cls, b.cinv, b.cinv8, nloc, maxl, first, n8, ngen, nb8,
+                               (int)blockIdx.x);
 }
 
 // R = F - K U (per solve) with per-block partials into the solve's part (top level: its norm)

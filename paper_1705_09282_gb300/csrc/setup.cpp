@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <functional>
 #include <atomic>
 #include <map>
 #include <thread>
@@ -794,6 +795,7 @@ int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt
   pt.n_patches = (int)all.size(); pt.maxl = maxl; pt.n_colours = np1 * np1;
   pt.dofs.assign((size_t)pt.n_patches * maxl, -1);
   pt.cls.assign(pt.n_patches, 0);
+  pt.pos.assign(pt.n_patches, 0);
   pt.colour_off.assign(pt.n_colours + 1, 0);
   // classes: patches whose local matrices are equal share one inverse (translation
   // invariance of the constant-coefficient Stokes operator); with per_patch every patch
@@ -803,6 +805,7 @@ int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt
   for (int i = 0; i < pt.n_patches; ++i) {
     auto& P_ = all[i];
     for (size_t k = 0; k < P_.dofs.size(); ++k) pt.dofs[(size_t)i * maxl + k] = P_.dofs[k];
+    pt.pos[i] = P_.a | (P_.b << 16);
     pt.colour_off[P_.colour + 1]++;
     bool is8 = P_.dofs.size() == 8;
     auto& cmap = is8 ? cmap8 : cmapg;
@@ -816,7 +819,18 @@ int build_patches(int p, const Level1D& L, const igamg_sizes& s, PatchTables& pt
   pt.n8.assign(pt.n_colours, 0);
   for (int c = 0; c < pt.n_colours; ++c)
     for (int k = pt.colour_off[c]; k < pt.colour_off[c + 1] && all[k].dofs.size() == 8; ++k) pt.n8[c]++;
-  if (!validate_patch_tables(pt, s.n_total - 1, err)) return IGAMG_EINVAL;
+  {
+    // support of a basis function of degree d with index i on n elements: [i - d, i] clipped
+    auto sup = [&](long long g, int* lo, int* hi) {
+      const Dof r = decode(s, g);
+      const int dx = r.blk == 0 ? p : q, dy = r.blk == 1 ? p : q;
+      lo[0] = std::max(0, r.x - dx); hi[0] = std::min(n - 1, r.x);
+      lo[1] = std::max(0, r.y - dy); hi[1] = std::min(n - 1, r.y);
+      lo[2] = hi[2] = 0;
+    };
+    const int ne[3] = {n, n, 1};
+    if (!validate_patch_tables(pt, s.n_total - 1, err, sup, ne)) return IGAMG_EINVAL;
+  }
   // bordered local inverses, one per class (Sec. 5.2 local problems; zero-mean local
   // pressure through the border m_j = int N^q_j)
   auto local_inverse = [&](const P& P_, std::vector<double>& inv) -> bool {
@@ -931,18 +945,66 @@ double k_entry_rows(const LevelHost& lv, int p, long long g1, long long g2) {
   return 0.0;
 }
 
-bool validate_patch_tables(const PatchTables& pt, long long n_rows, std::string& err) {
+bool validate_patch_tables(const PatchTables& pt, long long n_rows, std::string& err,
+                           const std::function<void(long long, int*, int*)>& support, const int* n_elem) {
   std::vector<int> stamp((size_t)n_rows, -1);
+  const size_t ne = (size_t)n_elem[0] * n_elem[1] * n_elem[2];
+  std::vector<int> cover(support ? ne : 0, -1), cover_col(support ? ne : 0, -1);
   for (int c = 0; c < pt.n_colours; ++c)
-    for (int i = pt.colour_off[c]; i < pt.colour_off[c + 1]; ++i)
+    for (int i = pt.colour_off[c]; i < pt.colour_off[c + 1]; ++i) {
+      int blo[3] = {1 << 30, 1 << 30, 1 << 30}, bhi[3] = {-1, -1, -1};
       for (int k = 0; k < pt.maxl; ++k) {
         const long long g = pt.dofs[(size_t)i * pt.maxl + k];
         if (g < 0) continue;                                    // padding
         if (g >= n_rows) { err = "patch table: DOF id out of range"; return false; }
         if (stamp[(size_t)g] == c) { err = "patch table: a DOF twice in one colour"; return false; }
         stamp[(size_t)g] = c;
+        if (support) {
+          int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+          support(g, lo, hi);
+          for (int d = 0; d < 3; ++d) { blo[d] = std::min(blo[d], lo[d]); bhi[d] = std::max(bhi[d], hi[d]); }
+        }
       }
+      if (!support || bhi[0] < 0) continue;
+      for (int d = 0; d < 3; ++d)
+        if (blo[d] < 0 || bhi[d] >= n_elem[d]) { err = "patch table: a DOF support outside the mesh"; return false; }
+      for (int z = blo[2]; z <= bhi[2]; ++z)
+        for (int y = blo[1]; y <= bhi[1]; ++y)
+          for (int x = blo[0]; x <= bhi[0]; ++x) {
+            const size_t e = ((size_t)z * n_elem[1] + y) * n_elem[0] + x;
+            if (cover_col[e] == c && cover[e] != i) {
+              err = "patch table: two patches of colour " + std::to_string(c) + " share element (" +
+                    std::to_string(x) + ", " + std::to_string(y) + ", " + std::to_string(z) +
+                    "), so they may be coupled through K";
+              return false;
+            }
+            cover_col[e] = c;
+            cover[e] = i;
+          }
+    }
   return true;
+}
+
+void build_tile_tables(const PatchTables& pt, int nint, int tw, TileTables& tt) {
+  tt.tw = tw;
+  tt.ntx = tt.nty = (nint + tw - 1) / tw;
+  const int C = pt.n_colours, nt = tt.ntx * tt.nty;
+  std::vector<std::vector<int>> run((size_t)nt * C);
+  tt.n8.assign((size_t)nt * C, 0);
+  for (int c = 0; c < C; ++c)
+    for (int i = pt.colour_off[c]; i < pt.colour_off[c + 1]; ++i) {   // table order: 8-DOF first
+      const int a = pt.pos[i] & 0xffff, b = pt.pos[i] >> 16;
+      const int t = ((b - 1) / tw) * tt.ntx + (a - 1) / tw;
+      run[(size_t)t * C + c].push_back(i);
+      if (i < pt.colour_off[c] + pt.n8[c]) tt.n8[(size_t)t * C + c]++;
+    }
+  tt.off.assign((size_t)nt * C + 1, 0);
+  tt.list.clear();
+  tt.list.reserve(pt.n_patches);
+  for (size_t r = 0; r < run.size(); ++r) {
+    tt.list.insert(tt.list.end(), run[r].begin(), run[r].end());
+    tt.off[r + 1] = (int)tt.list.size();
+  }
 }
 
 igamg_sizes level_sizes(int p, int n) {

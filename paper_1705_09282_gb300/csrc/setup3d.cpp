@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <functional>
 #include <map>
 #include <thread>
 #include <tuple>
@@ -255,7 +256,20 @@ int build_patches3(int p, const Level1D& L, const Sizes3& s, PatchTables& pt, st
   pt.n8.assign(pt.n_colours, 0);
   for (int c = 0; c < pt.n_colours; ++c)
     for (int k = pt.colour_off[c]; k < pt.colour_off[c + 1] && all[k].dofs.size() == 8; ++k) pt.n8[c]++;
-  if (!validate_patch_tables(pt, s.n_total - 1, err)) return IGAMG_EINVAL;
+  {
+    // support of a basis function of degree d with index i on n elements: [i - d, i] clipped;
+    // velocity component c has degree p along axis c and q across
+    auto sup = [&](long long g, int* lo, int* hi) {
+      const Dof3 r = decode3(s, g);
+      for (int a = 0; a < 3; ++a) {
+        const int d = (r.blk < 3 && r.blk == a) ? p : q;
+        lo[a] = std::max(0, r.i[a] - d);
+        hi[a] = std::min(n - 1, r.i[a]);
+      }
+    };
+    const int ne[3] = {n, n, n};
+    if (!validate_patch_tables(pt, s.n_total - 1, err, sup, ne)) return IGAMG_EINVAL;
+  }
   // bordered local inverses (zero-mean local pressure through m_j = int N^q_j), one per class
   auto local_inverse = [&](const P& P_, std::vector<double>& inv) -> bool {
     int nl = (int)P_.dofs.size(), nb = nl + 1;

@@ -12,11 +12,11 @@ from . import _lib
 from ._lib import check, lib
 
 
-def _ptr(t):
+def _ptr(t, dtype=torch.float64):
     if t is None:
         return None
-    if t.dtype != torch.float64 or not t.is_contiguous():
-        raise ValueError("expected a contiguous float64 tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous {dtype} tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -24,7 +24,7 @@ class Solver:
     """Owns one igamg_handle: the level hierarchy of Sec. 5.1 for a 2D (unit square) or
     3D (unit cube, dim=3) problem."""
 
-    def __init__(self, p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.5, nu1=2, nu2=2,
+    def __init__(self, p, n_fine, n_levels, sigma, nu, smoother="mult", eta=0.0, nu1=2, nu2=2,
                  c_penalty=0.0, precision=_lib.IGAMG_FP64, device="cuda", stream=None, beta=None, dim=2,
                  restart=0, gamma=1, fmg=False, geometry=_lib.IGAMG_GEOM_SQUARE, r_inner=0.0, r_outer=0.0):
         """beta: advection at the quadrature points (host array (2, nG, nG)) for the
@@ -109,6 +109,21 @@ class Solver:
     def smooth(self, U, F, level=None, sweeps=1):
         level = self.n_levels - 1 if level is None else level
         check(lib().igamg_smooth(self._h, level, _ptr(U), _ptr(F), sweeps), "igamg_smooth")
+        return U
+
+    def level_form(self, level=None):
+        """The sweep form the autotuner chose for a level (2D): dict(lanes, threads, tiles)."""
+        level = self.n_levels - 1 if level is None else level
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib().igamg_level_form(self._h, level, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+              "igamg_level_form")
+        return {"lanes": a.value, "threads": b.value, "tiles": c.value}
+
+    def smooth32(self, U, F, level=None, sweeps=1):
+        """FP32 smoothing sweeps (FP32-in-FP64 handles): U, F float32 device tensors."""
+        level = self.n_levels - 1 if level is None else level
+        check(lib().igamg_smooth_f32(self._h, level, _ptr(U, torch.float32), _ptr(F, torch.float32), sweeps),
+              "igamg_smooth_f32")
         return U
 
     def restrict(self, r_fine, level, out=None):
