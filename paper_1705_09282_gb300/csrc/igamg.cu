@@ -240,9 +240,12 @@ struct BatchCache {
   int* h_flags = nullptr;              // pinned host copies
   double* h_norms = nullptr;
   cudaStream_t stream = nullptr;       // the batch's own stream (the graphs fork from it)
-  std::vector<cudaStream_t> side;      // capture streams of the chunks
   cudaEvent_t ev = nullptr;
+  std::vector<cudaStream_t> side;      // capture streams of the branches after the first
   std::vector<cudaEvent_t> side_ev;
+  std::vector<MixLevel<double>> mix;   // descriptors, solve-major, nd depths per solve
+  int nd = 0;                          // depths: the most grids of any solve
+  std::vector<std::vector<int>> branch;  // solve indices of each branch (at most kMixChunk)
   cudaGraphExec_t g_res = nullptr;     // residual norms of all active solves
   cudaGraphExec_t g_cycle = nullptr;   // one V-cycle, then the residual norms
 };
@@ -747,12 +750,13 @@ int solve_impl(igamg_handle* h, double* U, const double* F, double rtol, int max
                double atol);
 
 // ---- lockstep batches ---------------------------------------------------------------------
-// Solves of one structure (2D, FP64, multiplicative V-cycles, same p, n, levels, sweeps,
-// domain and operator form) step their V-cycles together: every colour, residual, transfer
-// and coarse solve is one launch over up to kBatchMax solves (blockIdx.y = solve), chunks of
-// solves run as parallel branches of one captured graph, and converged solves are switched
-// off by a device flag that their blocks read first.  Per solve the arithmetic is the
-// per-handle V-cycle's (per-level launches).
+// Solves of one cycle shape (2D, FP64, multiplicative V-cycles, same p, sweeps, domain and
+// operator form; any mesh sizes and numbers of grids) step their V-cycles together, aligned
+// from the finest grid down: every colour, residual, transfer and coarse solve of a depth is
+// one launch over all solves of the batch (blockIdx.y = solve, descriptors in a device
+// array), captured once into a graph; converged solves are switched off by a device flag
+// that their blocks read first.  Per solve the arithmetic is the per-handle V-cycle's
+// (per-level launches).
 
 bool batchable(const igamg_handle* h) {
   const auto& pr = h->prob;
@@ -760,113 +764,145 @@ bool batchable(const igamg_handle* h) {
          !split_colour(h->d.lev.back().L.srow != nullptr);
 }
 
-bool same_structure(const igamg_handle* a, const igamg_handle* b) {
+// Handles whose solves can share lockstep launches: the same p (colour count) and cycle shape,
+// the same operator form (generalized Stokes or Oseen, square or mapped); mesh sizes and
+// numbers of grids may differ.
+bool mix_compatible(const igamg_handle* a, const igamg_handle* b) {
   const auto &x = a->prob, &y = b->prob;
-  if (x.p != y.p || x.n_fine != y.n_fine || x.n_levels != y.n_levels || x.nu1 != y.nu1 || x.nu2 != y.nu2 ||
-      x.geometry != y.geometry || (x.beta_qp == nullptr) != (y.beta_qp == nullptr))
-    return false;
-  for (size_t l = 0; l < a->lc.size(); ++l)
-    if (a->lc[l].maxl != b->lc[l].maxl || a->lc[l].colour_off != b->lc[l].colour_off || a->lc[l].n8 != b->lc[l].n8 ||
-        a->lc[l].lpr != b->lc[l].lpr)
-      return false;
-  return true;
+  return x.p == y.p && x.nu1 == y.nu1 && x.nu2 == y.nu2 && x.geometry == y.geometry &&
+         (x.beta_qp == nullptr) == (y.beta_qp == nullptr);
 }
 
-// descriptors of solves [c0, c1) on level l
-BatchArgs<double> batch_args(igamg_handle** hs, double** Us, const double** Fs, const BatchCache& bc, int l, int c0,
-                             int c1) {
-  BatchArgs<double> A{};
-  A.count = c1 - c0;
-  for (int i = c0; i < c1; ++i) {
+// Descriptors of every solve at every depth (solve-major): depth t is level L - 1 - t of a
+// solve with L grids.
+void mix_descriptors(int n, igamg_handle** hs, double** Us, const double** Fs, const BatchCache& bc, int nd,
+                     std::vector<MixLevel<double>>& D) {
+  for (int i = 0; i < n; ++i) {
     igamg_handle* h = hs[i];
     const int L = (int)h->d.lev.size();
-    const auto& tl = h->d.lev[l];
-    BatchLevel<double>& b = A.s[i - c0];
-    b.L = tl.L;
-    b.cinv = tl.cinv; b.cinv8 = tl.cinv8; b.kinv = h->d.coarse_inv;
-    b.U = l == L - 1 ? Us[i] : tl.U;
-    b.F = l == L - 1 ? const_cast<double*>(Fs[i]) : tl.F;
-    b.R = tl.R;
-    b.part = h->part;
-    b.norm2 = bc.norms + i;
-    b.active = bc.flags + i;
+    const size_t base = D.size();
+    D.resize(base + nd);
+    for (int t = 0; t < nd; ++t) {
+      MixLevel<double>& d = D[base + t];
+      d = MixLevel<double>{};
+      const int l = L - 1 - t;
+      d.level = l;
+      d.active = bc.flags + i;
+      d.norm2 = bc.norms + i;
+      d.part = h->part;
+      if (l < 0) continue;
+      const auto& tl = h->d.lev[l];
+      const auto& lc = h->lc[l];
+      d.L = tl.L;
+      d.U = l == L - 1 ? Us[i] : tl.U;
+      d.F = l == L - 1 ? const_cast<double*>(Fs[i]) : tl.F;
+      d.R = tl.R;
+      d.kinv = h->d.coarse_inv;
+      if (l >= 1) {
+        const auto& tc = h->d.lev[l - 1];
+        d.Lc = tc.L;
+        d.Uc = tc.U;
+        d.Fc = tc.F;
+        d.tp = tl.tp;
+        d.tq = tl.tq;
+        d.cinv = tl.cinv;
+        d.cinv8 = tl.cinv8;
+        d.dofs = lc.dofs;
+        d.cls = lc.cls;
+        d.nloc = lc.nloc;
+        d.maxl = lc.maxl;
+        d.lpr = 1;            // one lane per row: the batch launches are throughput-bound
+        for (int c = 0; c < lc.n_colours && c < kMaxColours; ++c) {
+          d.first[c] = lc.colour_off[c];
+          d.cnt[c] = lc.colour_off[c + 1] - lc.colour_off[c];
+          d.n8[c] = lc.n8[c];
+        }
+      }
+    }
   }
-  return A;
 }
 
-// one chunk's V-cycle (top residual norm included when cycle), or only its residual norm
-int batch_chunk(igamg_handle** hs, double** Us, const double** Fs, const BatchCache& bc, int c0, int c1, bool cycle,
-                cudaStream_t s) {
-  igamg_handle* h0 = hs[c0];
-  const int L = (int)h0->d.lev.size(), p = h0->prob.p;
-  const unsigned ns = (unsigned)(c1 - c0);
-  std::vector<BatchArgs<double>> A(L);
-  for (int l = 0; l < L; ++l) A[l] = batch_args(hs, Us, Fs, bc, l, c0, c1);
-  auto residual = [&](int l, int want_norm) {
-    const auto& Lt = h0->d.lev[l].L;
-    unsigned nb = nblk(Lt.n_total - 1);
-    if (p == 2) k_residual_b<2, double><<<dim3(nb, ns), kBlock, 0, s>>>(A[l]);
-    else k_residual_b<3, double><<<dim3(nb, ns), kBlock, 0, s>>>(A[l]);
-    k_residual_finish_b<double><<<ns, 1024, 0, s>>>(A[l], (int)nb, want_norm);
+// One V-cycle of every solve (top residual norms included when cycle), or only the residual
+// norms, as launches over all solves of the batch (blockIdx.y = solve).
+int batch_launches(igamg_handle** all, const std::vector<int>& idx, const std::vector<MixLevel<double>>& mix, int nd,
+                   bool cycle, cudaStream_t s) {
+  const int n = (int)idx.size(), p = all[idx[0]]->prob.p;
+  std::vector<igamg_handle*> hv(n);
+  for (int i = 0; i < n; ++i) hv[i] = all[idx[i]];
+  igamg_handle** hs = hv.data();
+  const unsigned ns = (unsigned)n;
+  std::vector<MixArgs<double>> A(nd);             // the chunk's descriptors, one block per depth
+  for (int t = 0; t < nd; ++t) {
+    A[t].count = n;
+    for (int i = 0; i < n; ++i) A[t].s[i] = mix[(size_t)idx[i] * nd + t];
+  }
+  const int tpb = 128, wpb = tpb / 32;
+  auto lev = [&](int i, int t) { return (int)hs[i]->d.lev.size() - 1 - t; };
+  auto max_over = [&](int t, int min_level, auto f) {
+    long long m = 0;
+    for (int i = 0; i < n; ++i) { int l = lev(i, t); if (l >= min_level) m = std::max(m, (long long)f(i, l)); }
+    return (unsigned)std::max(1LL, m);
   };
-  auto smooth = [&](int l) {
-    const auto& lc = h0->lc[l];
-    const int tpb = lc.tpb > 0 ? lc.tpb : colour_block(), wpb = tpb / 32;
-    const size_t shmc = (size_t)wpb * lc.maxl * sizeof(double);
-    const int ppw = lc.lpr == 2 ? 2 : 4;            // 8-DOF patches per warp
-    for (int c = 0; c < lc.n_colours; ++c) {
-      int first = lc.colour_off[c], count = lc.colour_off[c + 1] - first;
-      if (count == 0) continue;
-      int n8 = lc.n8[c], ngen = count - n8;
-      int nb8 = (n8 + ppw * wpb - 1) / (ppw * wpb), nbg = (ngen + wpb - 1) / wpb;
-      dim3 grid((unsigned)(nb8 + nbg), ns);
-      if (p == 2) {
-        if (lc.lpr == 2) k_mult_colour_b<2, double, 2><<<grid, tpb, shmc, s>>>(A[l], lc.dofs, lc.cls, lc.nloc, lc.maxl, first, n8, ngen, nb8);
-        else k_mult_colour_b<2, double><<<grid, tpb, shmc, s>>>(A[l], lc.dofs, lc.cls, lc.nloc, lc.maxl, first, n8, ngen, nb8);
-      } else {
-        if (lc.lpr == 2) k_mult_colour_b<3, double, 2><<<grid, tpb, shmc, s>>>(A[l], lc.dofs, lc.cls, lc.nloc, lc.maxl, first, n8, ngen, nb8);
-        else k_mult_colour_b<3, double><<<grid, tpb, shmc, s>>>(A[l], lc.dofs, lc.cls, lc.nloc, lc.maxl, first, n8, ngen, nb8);
-      }
+  auto residual = [&](int t, int any, int want) {
+    unsigned nb = max_over(t, any ? 0 : 1, [&](int i, int l) { return nblk(hs[i]->d.lev[l].L.n_total - 1); });
+    if (p == 2) k_mix_residual<2, double><<<dim3(nb, ns), kBlock, 0, s>>>(A[t], any);
+    else k_mix_residual<3, double><<<dim3(nb, ns), kBlock, 0, s>>>(A[t], any);
+    k_mix_residual_finish<double><<<ns, 1024, 0, s>>>(A[t], any, want, kBlock);
+  };
+  auto smooth = [&](int t) {
+    const int C = hs[0]->lc.back().n_colours;
+    const size_t shm = (size_t)wpb * max_over(t, 1, [&](int i, int l) { return hs[i]->lc[l].maxl; }) * sizeof(double);
+    for (int c = 0; c < C; ++c) {
+      unsigned nb = max_over(t, 1, [&](int i, int l) {
+        const auto& lc = hs[i]->lc[l];
+        const int ppw = 4;
+        const int n8 = lc.n8[c], ngen = lc.colour_off[c + 1] - lc.colour_off[c] - n8;
+        return (n8 + ppw * wpb - 1) / (ppw * wpb) + (ngen + wpb - 1) / wpb;
+      });
+      if (p == 2) k_mix_colour<2, double><<<dim3(nb, ns), tpb, shm, s>>>(A[t], c);
+      else k_mix_colour<3, double><<<dim3(nb, ns), tpb, shm, s>>>(A[t], c);
     }
   };
   if (cycle) {
-    if (L == 1) {
-      k_coarse_b<double><<<ns, 1024, h0->ndof0 * sizeof(double), s>>>(A[0]);
-    } else {
-      for (int l = L - 1; l >= 1; --l) {
-        if (l < L - 1) k_zero_b<double><<<dim3(nblk(h0->d.lev[l].L.n_total), ns), kBlock, 0, s>>>(A[l]);
-        for (int k = 0; k < h0->prob.nu1; ++k) smooth(l);
-        residual(l, 0);
-        const auto& tl = h0->d.lev[l];
-        k_restrict_b<double><<<dim3(nblk(h0->d.lev[l - 1].L.n_total), ns), kBlock, 0, s>>>(A[l], A[l - 1], tl.tp, tl.tq);
+    const int nu1 = hs[0]->prob.nu1, nu2 = hs[0]->prob.nu2;
+    for (int t = 0; t < nd; ++t) {
+      if (t > 0) {
+        unsigned nb = max_over(t, 1, [&](int i, int l) { return nblk(hs[i]->d.lev[l].L.n_total); });
+        k_mix_zero<double><<<dim3(nb, ns), kBlock, 0, s>>>(A[t]);
       }
-      k_coarse_b<double><<<ns, 1024, h0->ndof0 * sizeof(double), s>>>(A[0]);
-      for (int l = 1; l <= L - 1; ++l) {
-        const auto& tl = h0->d.lev[l];
-        k_prolong_add_b<double><<<dim3(nblk(tl.L.n_total), ns), kBlock, 0, s>>>(A[l], A[l - 1], tl.tp, tl.tq);
-        for (int k = 0; k < h0->prob.nu2; ++k) smooth(l);
-      }
+      for (int k = 0; k < nu1; ++k) smooth(t);
+      residual(t, 0, 0);
+      unsigned nbr = max_over(t, 1, [&](int i, int l) { return nblk(hs[i]->d.lev[l - 1].L.n_total); });
+      k_mix_restrict<double><<<dim3(nbr, ns), kBlock, 0, s>>>(A[t]);
+      int smem = 0;
+      for (int i = 0; i < n; ++i)
+        if (lev(i, t) == 0) smem = std::max(smem, (int)(hs[i]->d.lev[0].L.n_total * sizeof(double)));
+      if (smem > 0) k_mix_coarse<double><<<ns, 1024, smem, s>>>(A[t]);
+    }
+    for (int t = nd - 2; t >= 0; --t) {
+      unsigned nb = max_over(t, 1, [&](int i, int l) { return nblk(hs[i]->d.lev[l].L.n_total); });
+      k_mix_prolong_add<double><<<dim3(nb, ns), kBlock, 0, s>>>(A[t]);
+      for (int k = 0; k < nu2; ++k) smooth(t);
     }
   }
-  residual(L - 1, 1);
+  residual(0, 1, 1);
   return launch_check();
 }
 
-// Captures the whole batch (all chunks as parallel branches) into one graph.
-int batch_capture(igamg_handle** hs, double** Us, const double** Fs, BatchCache& bc, bool cycle,
-                  cudaGraphExec_t* out) {
-  const int nch = (bc.count + kBatchMax - 1) / kBatchMax;
+// Captures the batch's launches into one graph, its branches side by side.
+int batch_capture(igamg_handle** hs, BatchCache& bc, bool cycle, cudaGraphExec_t* out) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(bc.stream, cudaStreamCaptureModeThreadLocal));
   int rc = IGAMG_OK;
   cudaError_t e = cudaEventRecord(bc.ev, bc.stream);
-  for (int c = 0; c < nch && !rc && e == cudaSuccess; ++c) {
-    cudaStream_t st = c == 0 ? bc.stream : bc.side[c - 1];
-    if (c > 0) e = cudaStreamWaitEvent(st, bc.ev, 0);
-    if (e == cudaSuccess) rc = batch_chunk(hs, Us, Fs, bc, c * kBatchMax, std::min(bc.count, (c + 1) * kBatchMax), cycle, st);
-    if (!rc && c > 0 && e == cudaSuccess) e = cudaEventRecord(bc.side_ev[c - 1], st);
+  const int nb = (int)bc.branch.size();
+  for (int b = 0; b < nb && !rc && e == cudaSuccess; ++b) {
+    cudaStream_t st = b == 0 ? bc.stream : bc.side[b - 1];
+    if (b > 0) e = cudaStreamWaitEvent(st, bc.ev, 0);
+    if (e == cudaSuccess) rc = batch_launches(hs, bc.branch[b], bc.mix, bc.nd, cycle, st);
+    if (!rc && b > 0 && e == cudaSuccess) e = cudaEventRecord(bc.side_ev[b - 1], st);
   }
-  for (int c = 1; c < nch && !rc && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(bc.stream, bc.side_ev[c - 1], 0);
+  for (int b = 1; b < nb && !rc && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(bc.stream, bc.side_ev[b - 1], 0);
   cudaError_t ee = cudaStreamEndCapture(bc.stream, &g);
   if (rc || e != cudaSuccess || ee != cudaSuccess) {
     if (ee == cudaSuccess) cudaGraphDestroy(g);
@@ -894,7 +930,6 @@ int batch_prepare(int n, igamg_handle** hs, double** Us, const double** Fs, Batc
   auto* bc = new BatchCache();
   bc->key = key;
   bc->count = n;
-  const int nch = (n + kBatchMax - 1) / kBatchMax;
   int rc = IGAMG_OK;
   auto ck = [&](cudaError_t e) { if (e != cudaSuccess && !rc) { g_err = cudaGetErrorString(e); rc = IGAMG_ECUDA; } };
   ck(cudaMalloc((void**)&bc->flags, n * sizeof(int)));
@@ -903,7 +938,14 @@ int batch_prepare(int n, igamg_handle** hs, double** Us, const double** Fs, Batc
   ck(cudaMallocHost((void**)&bc->h_norms, n * sizeof(double)));
   ck(cudaStreamCreateWithFlags(&bc->stream, cudaStreamNonBlocking));
   ck(cudaEventCreateWithFlags(&bc->ev, cudaEventDisableTiming));
-  for (int c = 1; c < nch && !rc; ++c) {
+  bc->nd = 0;
+  for (int i = 0; i < n; ++i) bc->nd = std::max(bc->nd, (int)hs[i]->d.lev.size());
+  // branches of at most kMixChunk solves, run side by side; the solves are dealt round-robin,
+  // so every branch holds a share of every mesh size
+  const int nbr = (n + kMixChunk - 1) / kMixChunk;
+  bc->branch.assign(nbr, {});
+  for (int i = 0; i < n; ++i) bc->branch[i % nbr].push_back(i);
+  for (int b = 1; b < nbr && !rc; ++b) {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -911,8 +953,9 @@ int batch_prepare(int n, igamg_handle** hs, double** Us, const double** Fs, Batc
     bc->side.push_back(st);
     bc->side_ev.push_back(ev);
   }
-  if (!rc) rc = batch_capture(hs, Us, Fs, *bc, false, &bc->g_res);
-  if (!rc) rc = batch_capture(hs, Us, Fs, *bc, true, &bc->g_cycle);
+  if (!rc) mix_descriptors(n, hs, Us, Fs, *bc, bc->nd, bc->mix);
+  if (!rc) rc = batch_capture(hs, *bc, false, &bc->g_res);
+  if (!rc) rc = batch_capture(hs, *bc, true, &bc->g_cycle);
   if (rc) { batch_cache_free(bc); return rc; }
   h0->bc = bc;
   bcr = bc;
@@ -1039,17 +1082,37 @@ int lockstep_min() {
 int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, double rtol, int max_cycles,
                      igamg_report* reps, int* status, const double* atol = nullptr, bool allow_lockstep = true) {
   if (allow_lockstep && lockstep_enabled()) {
-    // groups of two or more batchable handles of one structure step in lockstep
+    // groups of batchable handles step in lockstep: first one group per mesh structure with
+    // at least lockstep_min() solves (their launches need no padding blocks and each group
+    // stops when its own solves have converged), then one mixed-size group per cycle shape
+    // from the handles left over, if it reaches lockstep_min()
     std::vector<std::vector<int>> groups;
     std::vector<int> rest;                       // in their original order below
     std::vector<char> used(n, 0);
+    auto same_mesh = [&](int a, int b) {
+      return mix_compatible(hs[a], hs[b]) && hs[a]->prob.n_fine == hs[b]->prob.n_fine &&
+             hs[a]->prob.n_levels == hs[b]->prob.n_levels;
+    };
+    std::vector<int> left;
     for (int i = 0; i < n; ++i) {
       if (used[i]) continue;
       used[i] = 1;
       if (!batchable(hs[i])) { rest.push_back(i); continue; }
       std::vector<int> g{i};
       for (int j = i + 1; j < n; ++j)
-        if (!used[j] && batchable(hs[j]) && same_structure(hs[i], hs[j])) { g.push_back(j); used[j] = 1; }
+        if (!used[j] && batchable(hs[j]) && same_mesh(i, j)) { g.push_back(j); used[j] = 1; }
+      if ((int)g.size() >= lockstep_min()) groups.push_back(g);
+      else left.insert(left.end(), g.begin(), g.end());
+    }
+    std::sort(left.begin(), left.end());
+    std::vector<char> used2(n, 0);
+    for (size_t a = 0; a < left.size(); ++a) {
+      const int i = left[a];
+      if (used2[i]) continue;
+      used2[i] = 1;
+      std::vector<int> g{i};
+      for (size_t b = a + 1; b < left.size(); ++b)
+        if (!used2[left[b]] && mix_compatible(hs[i], hs[left[b]])) { g.push_back(left[b]); used2[left[b]] = 1; }
       if ((int)g.size() >= lockstep_min()) groups.push_back(g);
       else rest.insert(rest.end(), g.begin(), g.end());
     }

@@ -64,7 +64,9 @@ __host__ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v
 // cycles per warp on GB300) and every load can be issued ahead of the FMAs.
 // PART = 2: the whole row; PART = 0: box 0 only; PART = 1: box 1 and the lambda term (the
 // split form lets two warps share one row's multiply-adds, see k_mult_colour_split).
-template <int P, typename T, int PART = 2>
+// CH = 4: four independent multiply-add chains (latency-bound launches); CH = 2: one chain per
+// box and two fewer FP64 adds per row (throughput-bound lockstep batches).
+template <int P, typename T, int PART = 2, int CH = 4>
 __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __restrict__ U, int g) {
   constexpr int Q = P - 1, TC = 2 * P + 1, NC = 2 * TC + 1;
   constexpr int WQ = 2 * Q + 1, WPP = 2 * P + 1;
@@ -90,16 +92,17 @@ __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __re
   const int b1_base = is_p ? L.n_ux : nu;
   const int b1_x0 = is_x ? -P : -Q, b1_y0 = is_x ? -Q : (is_p ? -Q : -P), b1_wy = is_x ? WQ : 2 * P;
   const int b1_ylo = is_p ? 1 : 0, b1_yhi = is_p ? L.nint : L.lastq, b1_ysh = is_p ? 1 : 0;
-  // four independent multiply-add chains (even and odd terms of each box): FP64 latency on
-  // this GPU is long, so a row's critical path is its longest chain
+  // with CH = 4, the even and odd terms of each box in separate chains: FP64 latency on this
+  // GPU is long, so a row's critical path is its longest chain
   T acc = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
+  constexpr bool kSplit = CH == 4;
   if (PART != 1) {
 #pragma unroll
     for (int j = 0; j < B0; ++j) {
       int dx = j / b0_wy, dy = j - dx * b0_wy;
       int x = clampi(ix + b0_x0 + dx, b0_xlo, b0_xhi) - b0_xsh;
       int y = clampi(iy + b0_y0 + dy, b0_ylo, b0_yhi) - b0_ysh;
-      if (j & 1) acc1 = fma(st[j], U[b0_base + y * b0_stride + x], acc1);
+      if (kSplit && (j & 1)) acc1 = fma(st[j], U[b0_base + y * b0_stride + x], acc1);
       else acc = fma(st[j], U[b0_base + y * b0_stride + x], acc);
     }
   }
@@ -109,10 +112,11 @@ __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __re
       int dx = j / b1_wy, dy = j - dx * b1_wy;
       int x = clampi(ix + b1_x0 + dx, 0, L.lastq);
       int y = clampi(iy + b1_y0 + dy, b1_ylo, b1_yhi) - b1_ysh;
-      if (j & 1) acc3 = fma(st[B0 + j], U[b1_base + y * L.npd + x], acc3);
+      if (kSplit && (j & 1)) acc3 = fma(st[B0 + j], U[b1_base + y * L.npd + x], acc3);
       else acc2 = fma(st[B0 + j], U[b1_base + y * L.npd + x], acc2);
     }
-    acc3 = fma(st[RU - 1], U[L.n_total - 1], acc3);
+    if (kSplit) acc3 = fma(st[RU - 1], U[L.n_total - 1], acc3);
+    else acc = fma(st[RU - 1], U[L.n_total - 1], acc);
     if (L.sext && !is_p) {
       // third box (mapped domains): u_x row -> u_y columns (x - P .. x + Q, y - Q .. y + P),
       // u_y row -> u_x columns (x - Q .. x + P, y - P .. y + Q); clamped positions carry 0
@@ -125,12 +129,12 @@ __host__ __device__ __forceinline__ T row_KU(const LevelTab<T>& L, const T* __re
         int cx = ix + ox + dx, cy = iy + oy + dy;
         int idx = is_x ? L.n_ux + (clampi(cy, 1, L.nint) - 1) * L.npd + clampi(cx, 0, L.lastq)
                        : clampi(cy, 0, L.lastq) * L.nxu + clampi(cx, 1, L.nint) - 1;
-        if (j & 1) acc3 = fma(se[j], U[idx], acc3);
+        if (kSplit && (j & 1)) acc3 = fma(se[j], U[idx], acc3);
         else acc2 = fma(se[j], U[idx], acc2);
       }
     }
   }
-  return (acc + acc1) + (acc2 + acc3);
+  return kSplit ? (acc + acc1) + (acc2 + acc3) : acc + acc2;
 }
 
 // m_k for a pressure row (the last stencil entry).
@@ -197,7 +201,7 @@ __global__ void k_residual_finish(int n_total, const T* __restrict__ F, T* __res
 // One lane of an 8-DOF patch (four patches per warp, lane = (patch, local row)): the local
 // residual row, then the bordered local inverse through shuffles, then the update.  All
 // 32 lanes of the warp must call it together (the shuffles span the warp).
-template <int P, typename T>
+template <int P, typename T, int CH = 4>
 __device__ __forceinline__ void fast_patch_lane(const LevelTab<T>& L, T* U, const T* F, const int* __restrict__ dofs,
                                                 const int* __restrict__ cls, const T* __restrict__ cinv8, int maxl,
                                                 int first, int n8, int grp, int lane) {
@@ -205,12 +209,12 @@ __device__ __forceinline__ void fast_patch_lane(const LevelTab<T>& L, T* U, cons
   bool active = grp < n8;
   int patch = first + (active ? grp : 0);
   int g = dofs[patch * maxl + row];
-  T r = F[g] - row_KU<P>(L, U, g);
+  T r = F[g] - row_KU<P, T, 2, CH>(L, U, g);
   const T* A = cinv8 + (size_t)cls[patch] * 64 + row * 8;
   T d[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-  for (int s = 0; s < 8; ++s) d[s & 3] = fma(A[s], __shfl_sync(0xffffffffu, r, (lane & ~7) + s), d[s & 3]);
-  if (active) U[g] += (d[0] + d[1]) + (d[2] + d[3]);
+  for (int s = 0; s < 8; ++s) d[s & (CH - 1)] = fma(A[s], __shfl_sync(0xffffffffu, r, (lane & ~7) + s), d[s & (CH - 1)]);
+  if (active) U[g] += CH == 4 ? (d[0] + d[1]) + (d[2] + d[3]) : d[0] + d[1];
 }
 
 // Half of row g of K U for the two-lanes-per-row patch form: half 0 sums box 0, half 1 box 1
@@ -290,13 +294,13 @@ __device__ __forceinline__ void fast_patch_lane2(const LevelTab<T>& L, T* U, con
 }
 
 // A larger (wall) patch solved by one warp; r is warp-private scratch of maxl entries.
-template <int P, typename T>
+template <int P, typename T, int CH = 4>
 __device__ __forceinline__ void general_patch_warp(const LevelTab<T>& L, T* U, const T* F, const int* __restrict__ dofs,
                                                    const int* __restrict__ cls, const T* __restrict__ cinv,
                                                    const int* __restrict__ nloc, int maxl, int patch, int lane, T* r) {
   int c = cls[patch], nl = nloc[c];
   const int* pd = dofs + (size_t)patch * maxl;
-  for (int k = lane; k < nl; k += 32) { int g = pd[k]; r[k] = F[g] - row_KU<P>(L, U, g); }
+  for (int k = lane; k < nl; k += 32) { int g = pd[k]; r[k] = F[g] - row_KU<P, T, 2, CH>(L, U, g); }
   __syncwarp();
   const T* A = cinv + (size_t)c * maxl * maxl;
   for (int k = lane; k < nl; k += 32) U[pd[k]] += dot_n(A + (size_t)k * maxl, r, nl);
@@ -365,7 +369,7 @@ __device__ __forceinline__ T prolong_elem(const LevelTab<T>& Lf, const LevelTab<
 // that is a multiple of 32 (the launch picks 128 threads so that a colour's blocks spread
 // evenly over the SMs).  Same-colour
 // patches share no DOF and are not coupled by K, so they may be solved in any order.
-template <int P, typename T, int LPR = 1>
+template <int P, typename T, int LPR = 1, int CH = 4>
 __device__ __forceinline__ void mult_colour_block(const LevelTab<T>& L, T* __restrict__ U, const T* __restrict__ F,
                                                   const int* __restrict__ dofs, const int* __restrict__ cls,
                                                   const T* __restrict__ cinv, const T* __restrict__ cinv8,
@@ -376,14 +380,14 @@ __device__ __forceinline__ void mult_colour_block(const LevelTab<T>& L, T* __res
     if (LPR == 2)
       fast_patch_lane2<P>(L, U, F, dofs, cls, cinv8, maxl, first, n8, (blk * wpb + wib) * 2 + (lane >> 4), lane);
     else
-      fast_patch_lane<P>(L, U, F, dofs, cls, cinv8, maxl, first, n8, (blk * wpb + wib) * 4 + (lane >> 3), lane);
+      fast_patch_lane<P, T, CH>(L, U, F, dofs, cls, cinv8, maxl, first, n8, (blk * wpb + wib) * 4 + (lane >> 3), lane);
     return;
   }
   extern __shared__ unsigned char smem_raw[];
   T* sh = reinterpret_cast<T*>(smem_raw);
   int w = (blk - nb8) * wpb + wib;
   if (w >= ngen) return;
-  general_patch_warp<P>(L, U, F, dofs, cls, cinv, nloc, maxl, first + n8 + w, lane, sh + wib * maxl);
+  general_patch_warp<P, T, CH>(L, U, F, dofs, cls, cinv, nloc, maxl, first + n8 + w, lane, sh + wib * maxl);
 }
 
 template <int P, typename T, int LPR = 1>
@@ -1071,6 +1075,155 @@ __global__ void k_curl_update(LT L, const double* __restrict__ dcoef, const doub
     U[g] -= dcoef[kx] * (PS(kx + 1, iy) - PS(kx, iy));
   } else {
     U[g] += (double)e[g];
+  }
+}
+
+// ---- lockstep batches of any mesh sizes: one launch per V-cycle step over every solve -------
+// The solves of a batch share p and the cycle shape but may differ in mesh size and number
+// of grids.  Their V-cycles are aligned from the finest grid down: at depth t (0 = finest) a
+// solve with L grids is on its level L - 1 - t.  A launch covers up to kMixChunk solves of any
+// sizes (blockIdx.y = solve), their descriptors for that depth in the kernel parameters;
+// larger batches are cut into chunks that run as parallel branches of one graph.  A block
+// whose solve is converged, past its coarsest level, not on a level that takes part in the
+// step, or beyond that solve's work, returns at once.
+template <typename T>
+struct MixLevel {
+  int level;                      // level index in the solve's hierarchy, -1 past its coarsest
+  int lpr;                        // lanes per 8-DOF patch row of the level's colour kernel
+  LevelTab<T> L, Lc;              // this level and (level >= 1) the next coarser one
+  Xfer<T> tp, tq;                 // transfers between Lc and L
+  const T *cinv, *cinv8, *kinv;   // local inverses; kinv: the coarsest level's dense inverse
+  T *U, *F, *R, *Uc, *Fc;
+  const int *dofs, *cls, *nloc;
+  int maxl;
+  int first[kMaxColours], n8[kMaxColours], cnt[kMaxColours];
+  double* part;                   // residual partials (two per block of 256 rows)
+  double* norm2;                  // ||F - K U||^2 of the finest level
+  const int* active;              // 1 while the solve is iterating
+};
+
+constexpr int kMixChunk = 24;     // solves per launch (descriptors in the kernel parameters)
+
+template <typename T>
+struct MixArgs {
+  int count;
+  MixLevel<T> s[kMixChunk];
+};
+
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_mix_colour(const __grid_constant__ MixArgs<T> A, int c) {
+  const MixLevel<T>& d = A.s[blockIdx.y];
+  if (d.level < 1 || !*d.active) return;
+  const int wpb = blockDim.x >> 5, ppw = d.lpr == 2 ? 2 : 4;
+  const int n8 = d.n8[c], ngen = d.cnt[c] - n8;
+  const int nb8 = (n8 + ppw * wpb - 1) / (ppw * wpb), nbg = (ngen + wpb - 1) / wpb;
+  if ((int)blockIdx.x >= nb8 + nbg) return;
+  const LevelTab<T> L = d.L;
+  T* U = d.U;
+  const T* F = d.F;
+  const int *dofs = d.dofs, *cls = d.cls, *nloc = d.nloc;
+  const T *cinv = d.cinv, *cinv8 = d.cinv8;
+  const int maxl = d.maxl, first = d.first[c];
+  // the block walks the solve's blocks with the grid's stride (a descriptor read serves
+  // several rounds of patches)
+  for (int b = blockIdx.x; b < nb8 + nbg; b += gridDim.x) {
+    if (d.lpr == 2)
+      mult_colour_block<P, T, 2>(L, U, F, dofs, cls, cinv, cinv8, nloc, maxl, first, n8, ngen, nb8, b);
+    else
+      mult_colour_block<P, T, 1, 2>(L, U, F, dofs, cls, cinv, cinv8, nloc, maxl, first, n8, ngen, nb8, b);
+  }
+}
+
+// R = F - K U with per-block partials; any_level: also for solves on their coarsest level
+// (the finest level of a one-grid solve, for its norm)
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_mix_residual(const __grid_constant__ MixArgs<T> A,
+                                                      int any_level) {
+  __shared__ double sh[32];
+  const MixLevel<T>& d = A.s[blockIdx.y];
+  if (d.level < (any_level ? 0 : 1) || !*d.active) return;
+  const LevelTab<T> L = d.L;
+  if ((int)(blockIdx.x * blockDim.x) >= L.n_total - 1) return;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  double r2 = 0.0, mp = 0.0;
+  if (g < L.n_total - 1) {
+    T r = d.F[g] - row_KU<P, T, 2, 2>(L, d.U, g);
+    d.R[g] = r;
+    r2 = (double)r * (double)r;
+    int off = g - L.n_ux - L.n_uy;
+    if (off >= 0) mp = (double)mean_coef<P>(L, off) * (double)d.U[g];
+  }
+  double s1 = block_sum(r2, sh);
+  double s2 = block_sum(mp, sh);
+  if (threadIdx.x == 0) { d.part[2 * blockIdx.x] = s1; d.part[2 * blockIdx.x + 1] = s2; }
+}
+
+template <typename T>
+__global__ void k_mix_residual_finish(const __grid_constant__ MixArgs<T> A, int any_level,
+                                      int want_norm, int rows_per_part) {
+  __shared__ double sh[32];
+  const MixLevel<T>& d = A.s[blockIdx.x];
+  if (d.level < (any_level ? 0 : 1) || !*d.active) return;
+  const int n_total = d.L.n_total, nparts = (n_total - 1 + rows_per_part - 1) / rows_per_part;
+  double a = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) { a += d.part[2 * i]; c += d.part[2 * i + 1]; }
+  double s1 = block_sum(a, sh);
+  double s2 = block_sum(c, sh);
+  if (threadIdx.x == 0) {
+    double rl = (double)d.F[n_total - 1] - s2;
+    d.R[n_total - 1] = (T)rl;
+    if (want_norm) *d.norm2 = s1 + rl * rl;
+  }
+}
+
+// coarse F = P^T R
+template <typename T>
+__global__ void k_mix_restrict(const __grid_constant__ MixArgs<T> A) {
+  const MixLevel<T>& d = A.s[blockIdx.y];
+  if (d.level < 1 || !*d.active) return;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nc = d.Lc.n_total;
+  if (g >= nc) return;
+  d.Fc[g] = (g == nc - 1) ? d.R[d.L.n_total - 1] : restrict_elem(d.L, d.Lc, d.tp, d.tq, d.R, g);
+}
+
+// U += P Uc
+template <typename T>
+__global__ void k_mix_prolong_add(const __grid_constant__ MixArgs<T> A) {
+  const MixLevel<T>& d = A.s[blockIdx.y];
+  if (d.level < 1 || !*d.active) return;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nf = d.L.n_total;
+  if (g >= nf) return;
+  d.U[g] += (g == nf - 1) ? d.Uc[d.Lc.n_total - 1] : prolong_elem(d.L, d.Lc, d.tp, d.tq, d.Uc, g);
+}
+
+template <typename T>
+__global__ void k_mix_zero(const __grid_constant__ MixArgs<T> A) {
+  const MixLevel<T>& d = A.s[blockIdx.y];
+  if (d.level < 1 || !*d.active) return;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < d.L.n_total) d.U[g] = T(0);
+}
+
+// U = K_0^{-1} F for the solves on their coarsest level at this depth, one block per solve
+template <typename T>
+__global__ void k_mix_coarse(const __grid_constant__ MixArgs<T> A) {
+  const MixLevel<T>& d = A.s[blockIdx.x];
+  if (d.level != 0 || !*d.active) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* g = reinterpret_cast<T*>(smem_raw);
+  const int n = d.L.n_total;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) g[i] = d.F[i];
+  __syncthreads();
+  int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x >> 5; i < n; i += nw) {
+    const T* row = d.kinv + (size_t)i * n;
+    T acc = T(0);
+#pragma unroll 4
+    for (int j = lane; j < n; j += 32) acc = fma(row[j], g[j], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) d.U[i] = acc;
   }
 }
 
