@@ -681,132 +681,6 @@ __global__ void k_coarse(int n, const T* __restrict__ Kinv, const T* __restrict_
   }
 }
 
-// ---- several independent solves of one structure per launch (blockIdx.y = solve) ----------
-// The solves share their level sizes, patch tables and transfers (same p, n, levels) and
-// differ in their operators (sigma, nu), local inverses and vectors.  Their descriptors
-// travel in the kernel parameters, so a block reads its solve's pointers from the constant
-// bank.  A solve whose flag is 0 (converged) is skipped.
-
-constexpr int kBatchMax = 24;            // solves per launch
-
-template <typename T>
-struct BatchLevel {                      // one solve's view of one level
-  LevelTab<T> L;
-  const T *cinv, *cinv8, *kinv;          // local inverses; kinv: coarsest dense inverse (level 0)
-  T *U, *F, *R;
-  double* part;                          // residual partials (finest level)
-  double* norm2;
-  const int* active;
-};
-
-template <typename T>
-struct BatchArgs {
-  int count;
-  BatchLevel<T> s[kBatchMax];
-};
-
-template <int P, typename T, int LPR = 1>
-__global__ void __launch_bounds__(256) k_mult_colour_b(const __grid_constant__ BatchArgs<T> B,
-                                                       const int* __restrict__ dofs, const int* __restrict__ cls,
-                                                       const int* __restrict__ nloc, int maxl, int first, int n8,
-                                                       int ngen, int nb8) {
-  const BatchLevel<T>& b = B.s[blockIdx.y];
-  if (!*b.active) return;
-  mult_colour_block<P, T, LPR>(b.L, b.U, b.F, dofs, cls, b.cinv, b.cinv8, nloc, maxl, first, n8, ngen, nb8,
-                               (int)blockIdx.x);
-}
-
-// R = F - K U (per solve) with per-block partials into the solve's part (top level: its norm)
-template <int P, typename T>
-__global__ void __launch_bounds__(256) k_residual_b(const __grid_constant__ BatchArgs<T> B) {
-  __shared__ double sh[32];
-  const BatchLevel<T>& b = B.s[blockIdx.y];
-  if (!*b.active) return;
-  const LevelTab<T>& L = b.L;
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  double r2 = 0.0, mp = 0.0;
-  if (g < L.n_total - 1) {
-    T r = b.F[g] - row_KU<P>(L, b.U, g);
-    b.R[g] = r;
-    r2 = (double)r * (double)r;
-    int off = g - L.n_ux - L.n_uy;
-    if (off >= 0) mp = (double)mean_coef<P>(L, off) * (double)b.U[g];
-  }
-  double s1 = block_sum(r2, sh);
-  double s2 = block_sum(mp, sh);
-  if (threadIdx.x == 0) { b.part[2 * blockIdx.x] = s1; b.part[2 * blockIdx.x + 1] = s2; }
-}
-
-template <typename T>
-__global__ void k_residual_finish_b(const __grid_constant__ BatchArgs<T> B, int nparts, int want_norm) {
-  __shared__ double sh[32];
-  const BatchLevel<T>& b = B.s[blockIdx.x];
-  if (!*b.active) return;
-  const int n_total = b.L.n_total;
-  double a = 0.0, c = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) { a += b.part[2 * i]; c += b.part[2 * i + 1]; }
-  double s1 = block_sum(a, sh);
-  double s2 = block_sum(c, sh);
-  if (threadIdx.x == 0) {
-    double rl = (double)b.F[n_total - 1] - s2;
-    b.R[n_total - 1] = (T)rl;
-    if (want_norm) *b.norm2 = s1 + rl * rl;
-  }
-}
-
-// coarse F = P^T fine R, per solve
-template <typename T>
-__global__ void k_restrict_b(const __grid_constant__ BatchArgs<T> Bf, const __grid_constant__ BatchArgs<T> Bc,
-                             Xfer<T> tp, Xfer<T> tq) {
-  const BatchLevel<T>& f = Bf.s[blockIdx.y];
-  const BatchLevel<T>& c = Bc.s[blockIdx.y];
-  if (!*f.active) return;
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= c.L.n_total) return;
-  c.F[g] = (g == c.L.n_total - 1) ? f.R[f.L.n_total - 1] : restrict_elem(f.L, c.L, tp, tq, f.R, g);
-}
-
-// fine U += P coarse U, per solve
-template <typename T>
-__global__ void k_prolong_add_b(const __grid_constant__ BatchArgs<T> Bf, const __grid_constant__ BatchArgs<T> Bc,
-                                Xfer<T> tp, Xfer<T> tq) {
-  const BatchLevel<T>& f = Bf.s[blockIdx.y];
-  const BatchLevel<T>& c = Bc.s[blockIdx.y];
-  if (!*f.active) return;
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= f.L.n_total) return;
-  f.U[g] += (g == f.L.n_total - 1) ? c.U[c.L.n_total - 1] : prolong_elem(f.L, c.L, tp, tq, c.U, g);
-}
-
-template <typename T>
-__global__ void k_zero_b(const __grid_constant__ BatchArgs<T> B) {
-  const BatchLevel<T>& b = B.s[blockIdx.y];
-  if (!*b.active) return;
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g < b.L.n_total) b.U[g] = T(0);
-}
-
-// U = K_0^{-1} F on the coarsest level, one block per solve
-template <typename T>
-__global__ void k_coarse_b(const __grid_constant__ BatchArgs<T> B) {
-  const BatchLevel<T>& b = B.s[blockIdx.x];
-  if (!*b.active) return;
-  extern __shared__ unsigned char smem_raw[];
-  T* g = reinterpret_cast<T*>(smem_raw);
-  const int n = b.L.n_total;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) g[i] = b.F[i];
-  __syncthreads();
-  int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x >> 5; i < n; i += nw) {
-    const T* row = b.kinv + (size_t)i * n;
-    T acc = T(0);
-#pragma unroll 4
-    for (int j = lane; j < n; j += 32) acc = fma(row[j], g[j], acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) b.U[i] = acc;
-  }
-}
-
 // ---- the coarse end of the V-cycle in one thread block ------------------------------------
 constexpr int kMaxFused = 8;        // levels handled by one fused launch
 constexpr int kMaxColours = 16;     // (p+1)^2 for p <= 3
