@@ -190,8 +190,12 @@ def run_ours(args):
             S = Solver(p, N_FINE, N_LEVELS, s, 1.0, nu1=2, nu2=2, device=dev, stream=stream)
             S32 = Solver(p, N_FINE, N_LEVELS, s, 1.0, nu1=2, nu2=2, device=dev, stream=stream,
                          precision=IGAMG_FP32_IR)
+            os.environ["IGAMG_BF16_OPERANDS"] = "1"     # the BF16-operand variant of the same
+            S16 = Solver(p, N_FINE, N_LEVELS, s, 1.0, nu1=2, nu2=2, device=dev, stream=stream,
+                         precision=IGAMG_FP32_IR)
+            del os.environ["IGAMG_BF16_OPERANDS"]
             F = S.load_vector(f_dev)
-            problems.append({"p": p, "sigma": s, "S": S, "S32": S32, "F": F, "U": S.empty(),
+            problems.append({"p": p, "sigma": s, "S": S, "S32": S32, "S16": S16, "F": F, "U": S.empty(),
                              "f_host": f_host, "ndof": S.ndof()})
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -203,6 +207,9 @@ def run_ours(args):
                            [pr["F"] for pr in problems], rtol=RTOL, max_cycles=MAXC)
         tot_dof_cycles, cycles, worst = 0, [], 0.0
         for pr, rep in zip(problems, reps):
+            if key == "S16" and not rep["converged"]:      # reported, not fatal: an experiment
+                cycles.append(-1)
+                continue
             assert rep["converged"], (pr["p"], pr["sigma"], key, rep)
             tot_dof_cycles += pr["ndof"] * rep["cycles"]
             cycles.append(rep["cycles"])
@@ -237,6 +244,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step("S")
         step("S32")
+        step("S16")
     torch.cuda.synchronize()
     barrier()
     clk = ClockSampler(local)
@@ -245,6 +253,7 @@ def run_ours(args):
     ms_steps, dofcyc, cyc_list, div64 = timed("S", args.steps)
     torch.cuda.nvtx.range_pop()
     ms32, dofcyc32, cyc32, div32 = timed("S32", args.steps)
+    ms16, dofcyc16, cyc16, div16 = timed("S16", args.steps)
     clocks = clk.stop()
     lat64, lat64_cyc = single_solve_ms("S")
     lat32, lat32_cyc = single_solve_ms("S32")
@@ -278,6 +287,16 @@ def run_ours(args):
              "single_solve_ms": lat32, "single_solve_case": f"p=2, sigma=1e-4, {lat32_cyc} cycles",
              "cycles": {f"p{pr['p']}_sigma{pr['sigma']:g}": c for pr, c in zip(problems, cyc32)},
              "max_div_inf": div32}
+    t16 = sum(ms16) / 1e3
+    bf16 = {"precision": "as mixed_fp32_ir, with the operator's stencil records and the patch solves' local "
+                         "inverses rounded to bfloat16 (FP32 accumulation; transfers and the coarsest solve FP32)",
+            "value": world * dofcyc16 / t16 / 1e6, "unit": "MDOF/s per V-cycle",
+            "solve_ms_to_1e-8": 1e3 * t16 / (args.steps * solves),
+            "speedup_vs_fp64_solve_time": t_total / t16,
+            "cycles": {f"p{pr['p']}_sigma{pr['sigma']:g}": c for pr, c in zip(problems, cyc16)},
+            "max_div_inf": div16,
+            "storage_note": "operands rounded to bf16 values and kept in FP32 words: the arithmetic of bf16 "
+                            "operands, not their storage (the sweep is latency-bound, see the FP32 roofline)"}
 
     # ---- dominant kernel: the finest level's multiplicative sweep ------------------------
     # nu = 2 sweeps (all colours) of the finest level, as in every V-cycle's pre- and
@@ -403,11 +422,12 @@ def run_ours(args):
             "solve_ms_note": "sweep time / solves, the 10 solves running side by side (igamg_solve_batch)",
             "single_solve_ms": lat64, "single_solve_case": f"p=2, sigma=1e-4, {lat64_cyc} cycles, alone",
             "cycles": {f"p{pr['p']}_sigma{pr['sigma']:g}": c for pr, c in zip(problems, cyc_list)},
-            "roofline": roofline, "e2e": e2e, "clocks": clocks, "mixed_fp32_ir": mixed,
+            "roofline": roofline, "e2e": e2e, "clocks": clocks, "mixed_fp32_ir": mixed, "mixed_bf16_operands_ir": bf16,
             "krylov_single_solve": krylov,
             "max_div_inf": div64,
             "gpu_launches": (sum(launches_per_solve(pr["p"], c) for pr, c in zip(problems, cyc_list))
-                             + sum(launches_per_solve(pr["p"], c, mixed=True) for pr, c in zip(problems, cyc32))) * args.steps}
+                             + sum(launches_per_solve(pr["p"], c, mixed=True) for pr, c in zip(problems, cyc32))
+            + sum(launches_per_solve(pr["p"], c, mixed=True) for pr, c in zip(problems, cyc16))) * args.steps}
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample()
@@ -415,6 +435,7 @@ def run_ours(args):
     for pr in problems:
         pr["S"].close()
         pr["S32"].close()
+        pr["S16"].close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

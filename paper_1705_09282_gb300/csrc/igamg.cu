@@ -1547,23 +1547,49 @@ int autotune_fused(igamg_handle* h, Typed<T>& ty) {
   return IGAMG_OK;
 }
 
+bool bf16_operands() {
+  const char* e = std::getenv("IGAMG_BF16_OPERANDS");
+  return e && std::atoi(e) != 0;
+}
+
+// Values rounded to the nearest bfloat16 (ties to even), returned in double.
+std::vector<double> round_bf16(const std::vector<double>& v) {
+  std::vector<double> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    float f = (float)v[i];
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+    std::memcpy(&f, &u, 4);
+    out[i] = f;
+  }
+  return out;
+}
+
 // Upload the typed (double or float) copy of every level's tables and workspaces.
 template <typename T>
 int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
   const int L = h->prob.n_levels, p = h->prob.p;
   ty.lev.resize(L);
   int rc;
+  // BF16 operands (FP32 V-cycles only, IGAMG_BF16_OPERANDS=1 at creation): the operator's
+  // stencil records and the patch solves' local inverses rounded to bfloat16 (round to
+  // nearest even), applied with FP32 accumulation; transfers and the coarsest solve stay FP32
+  const bool bf16 = sizeof(T) == 4 && bf16_operands();
+  auto ops = [&](const std::vector<double>& v) { return bf16 ? round_bf16(v) : v; };
   for (int l = 0; l < L; ++l) {
     auto& lh = h->host.lev[l];
     auto& tl = ty.lev[l];
     T *sx, *sy, *sp, *srow = nullptr, *sext = nullptr;
-    if ((rc = upload_as(h, &sx, lh.st.sx)) || (rc = upload_as(h, &sy, lh.st.sy)) || (rc = upload_as(h, &sp, lh.st.sp))) return rc;
-    if (!lh.rows.empty() && (rc = upload_as(h, &srow, lh.rows))) return rc;
-    if (!lh.ext.empty() && (rc = upload_as(h, &sext, lh.ext))) return rc;
+    if ((rc = upload_as(h, &sx, ops(lh.st.sx))) || (rc = upload_as(h, &sy, ops(lh.st.sy))) ||
+        (rc = upload_as(h, &sp, ops(lh.st.sp))))
+      return rc;
+    if (!lh.rows.empty() && (rc = upload_as(h, &srow, ops(lh.rows)))) return rc;
+    if (!lh.ext.empty() && (rc = upload_as(h, &sext, ops(lh.ext)))) return rc;
     tl.L = make_tab<T>(lh.sz, p, sx, sy, sp, srow, sext);
     if (l >= 1) {
-      if ((rc = upload_as(h, &tl.cinv, lh.pt.cinv))) return rc;
-      if ((rc = upload_as(h, &tl.cinv8, lh.pt.cinv8))) return rc;
+      if ((rc = upload_as(h, &tl.cinv, ops(lh.pt.cinv)))) return rc;
+      if ((rc = upload_as(h, &tl.cinv8, ops(lh.pt.cinv8)))) return rc;
       for (int which = 0; which < 2; ++which) {
         const Transfer1D& Tr = which ? h->host.tq[l] : h->host.tp_free[l];
         Xfer<T>& X = which ? tl.tq : tl.tp;

@@ -67,3 +67,35 @@ def test_fp32_vcycle_entry_point_is_one_refinement_step():
         r.append(S.residual(U, F, norm=True)[1])
     assert all(r[i + 1] < 0.5 * r[i] for i in range(4))
     assert S.div_inf(U) <= 1e-12 * float(U.abs().max())
+
+
+@pytest.mark.parametrize("p,sigma", [(2, 1.0), (3, 1e-4), (2, 1e4)])
+def test_bf16_operand_refinement_reaches_fp64_solution(p, sigma, monkeypatch):
+    # FP32 V-cycles whose operator records and local inverses are rounded to bfloat16 (FP32
+    # accumulation) inside FP64 refinement: the outer FP64 residual still reaches 1e-8, the
+    # velocity stays divergence-free at FP64 round-off, and the solution is the oracle's to 1e-6
+    torch = _torch()
+    from paper_1705_09282_gb300._lib import IGAMG_FP32_IR
+    from paper_1705_09282_gb300.solver import Solver
+    n, L = 32, 4
+    H = o2.Hierarchy(p, n, L, sigma, 1.0)
+    f = inputs.grf_forcing(p, n, seed=31)
+    F = H.fine.load_vector(f)
+    U = np.zeros_like(F)
+    H.solve(U, F, 1e-11, 80)
+    monkeypatch.setenv("IGAMG_BF16_OPERANDS", "1")
+    S16 = Solver(p, n, L, sigma, 1.0, precision=IGAMG_FP32_IR)
+    monkeypatch.delenv("IGAMG_BF16_OPERANDS")
+    S32 = Solver(p, n, L, sigma, 1.0, precision=IGAMG_FP32_IR)
+    reps = []
+    for S in (S16, S32):
+        Ug = S.empty()
+        rep = S.solve(Ug, S.load_vector(torch.tensor(f, device="cuda")), rtol=1e-8, max_cycles=80)
+        assert rep["converged"] and rep["rel_residual"] <= 1e-8
+        assert rep["div_inf"] <= 1e-11 * np.abs(U).max()
+        assert np.abs(Ug.cpu().numpy() - U).max() <= 1e-6 * np.abs(U).max()
+        reps.append(rep)
+    # bf16 operands cost cycles but not many (their inner V-cycle is a coarser approximation)
+    assert reps[0]["cycles"] <= 2 * reps[1]["cycles"] + 2, (reps[0]["cycles"], reps[1]["cycles"])
+    S16.close()
+    S32.close()
