@@ -676,6 +676,17 @@ def run_batch(args):
     cold()
     warm()
     warm(True)
+
+    def infer_all():
+        for pr in probs:
+            net.forward(pr.x.unsqueeze(0).contiguous())
+
+    infer = {}
+    for mode in ("1", "0"):                  # tensor-core (tcgen05) or SIMT 32 -> 32 layers
+        os.environ["IGAMG_NN_TC"] = mode
+        infer_all()
+        infer["tcgen05" if mode == "1" else "simt"] = _timed(infer_all, stream)[0]
+    del os.environ["IGAMG_NN_TC"]
     tc, rc = _timed(cold, stream)
     tw, rw = _timed(warm, stream)
     ts, rs = _timed(lambda: warm(True), stream)
@@ -695,6 +706,7 @@ def run_batch(args):
                                               "predicted fields (igamg_warm_start_minres) for every solve",
                                   "cycles_saved_total": int(cc.sum() - cs.sum()), "worse_count": int((cs > cc).sum()),
                                   "max_res0_over_normF": max(r["res0"] / (a / 1e-8) for r, a in zip(rs, atol))},
+            "inference_s_all_solves": infer,
             "max_div_inf": max(r["div_inf"] for r in rw + rs), "setup_s": t_setup, "train_s": t_train,
             "train_loss_first_last": [float(np.mean(losses[:5])), float(np.mean(losses[-20:]))]}
     print(json.dumps(line), flush=True)

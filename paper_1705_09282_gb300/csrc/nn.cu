@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -80,6 +81,144 @@ __global__ void __launch_bounds__(NT) k_conv(int H, int W, int tiles_x, int tile
     else if (epi == EPI_LINEAR) outz[idx] = z;
     else outz[idx] = z * gelu_grad_f(aux[idx]);
   }
+}
+
+// ---- 32 -> 32 convolution on the tensor cores (tcgen05, inference) -----------------------
+// An implicit GEMM per block: D (128 pixels x 32 output channels, FP32 in tensor memory) =
+// A (128 pixels x K, BF16) * B^T (32 channels x K, BF16), K = 32 input channels x 9 taps = 288,
+// as 18 tcgen05.mma instructions of 128 x 32 x 16 issued by one thread.  A (the dilated 3 x 3
+// neighbourhoods of 128 consecutive pixels, zero outside the image) and B (the layer's BF16
+// weights) are staged in shared memory in the no-swizzle K-major layout of 8-row x 16-byte
+// core matrices: core matrix (r, k) of an operand at ((r * KC + k) * 128) bytes, KC = K / 8,
+// so the descriptor's K-direction stride is 128 bytes and its row-group stride KC * 128.  The
+// accumulator is read back per warp (32 pixels x 32 channels) with tcgen05.ld and the bias and
+// GELU are applied on the way out.
+constexpr int TC_M = 128, TC_N = 32, TC_K = 288, TC_KC = TC_K / 8;
+constexpr int TC_A_BYTES = TC_M * TC_K * 2, TC_B_BYTES = TC_N * TC_K * 2;
+constexpr size_t TC_SMEM = TC_A_BYTES + TC_B_BYTES + 64;
+constexpr int TC_TMEM_COLS = 32;
+constexpr long TC_SPIN = 1L << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor: start address, K-direction (leading) and row-group (stride)
+// byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M
+constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int DIL>
+__global__ void __launch_bounds__(128) k_conv32_tc(int H, int W, int tiles, const float* __restrict__ in,
+                                                   const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
+                                                   float* __restrict__ outz, float* __restrict__ outa, int epi,
+                                                   int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(smem + TC_A_BYTES);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + TC_A_BYTES + TC_B_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + TC_A_BYTES + TC_B_BYTES + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.x / tiles, t = blockIdx.x - b * tiles;
+  const int HW = H * W, p0 = t * TC_M;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // A: thread m stages pixel p0 + m's 288 neighbourhood values (coalesced over m per (c, tap))
+  {
+    const int m = tid, pix = p0 + m;
+    const int y = pix / W, x = pix - (pix / W) * W;
+    const float* inb = in + (size_t)b * 32 * HW;
+    __nv_bfloat16* arow = As + (m >> 3) * (TC_KC * 64) + (m & 7) * 8;
+    for (int c = 0; c < 32; ++c) {
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int yy = y + DIL * (tap / 3 - 1), xx = x + DIL * (tap % 3 - 1);
+        float v = 0.0f;
+        if (pix < HW && yy >= 0 && yy < H && xx >= 0 && xx < W) v = inb[(size_t)c * HW + yy * W + xx];
+        const int k = c * 9 + tap;
+        arow[(k >> 3) * 64 + (k & 7)] = __float2bfloat16_rn(v);
+      }
+    }
+  }
+  // B: the weights w[o][k] (k = c * 9 + tap), o = output channel
+  for (int i = tid; i < TC_N * TC_K; i += 128) {
+    const int o = i / TC_K, k = i - o * TC_K;
+    Bs[((o >> 3) * TC_KC + (k >> 3)) * 64 + (o & 7) * 8 + (k & 7)] = w[i];
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+    constexpr uint32_t idesc = tc_idesc(TC_M, TC_N);
+#pragma unroll 1
+    for (int s = 0; s < TC_K / 16; ++s) {
+      const uint64_t ad = tc_smem_desc(a0 + s * 256, 128, TC_KC * 128);
+      const uint64_t bd = tc_smem_desc(b0 + s * 256, 128, TC_KC * 128);
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(s));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                 : "memory");
+  }
+  // wait for the accumulator (bounded)
+  uint32_t done = 0;
+  for (long it = 0; it < TC_SPIN && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(mbar))
+        : "memory");
+  }
+  if (!done && tid == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (done) {
+    uint32_t r[32];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int pix = p0 + warp * 32 + lane;
+    if (pix < HW) {
+#pragma unroll
+      for (int o = 0; o < 32; ++o) {
+        const size_t idx = ((size_t)b * 32 + o) * HW + pix;
+        const float z = __uint_as_float(r[o]) + (bias ? bias[o] : 0.0f);
+        if (epi == EPI_GELU) { outz[idx] = z; outa[idx] = gelu_f(z); }
+        else outz[idx] = z;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
 // dw[o,c,tap] += sum_{b,p} dz[b,o,p] in[b,c,p+tap], dbias[o] += sum dz[b,o,p]; blocks loop
@@ -205,6 +344,8 @@ struct igamg_nn {
   float *d0 = nullptr, *d1 = nullptr;
   double* loss = nullptr;
   double* h_loss = nullptr;
+  int* tc_err = nullptr;                            // set by a tensor-core convolution whose wait gave up
+  int* h_tc_err = nullptr;
 };
 
 namespace {
@@ -236,6 +377,34 @@ int set_smem_one() {
                            (int)wgrad_smem<CIN, COUT, DIL>()));
   return IGAMG_OK;
 }
+template <int DIL>
+int set_smem_tc() {
+  NCK(cudaFuncSetAttribute(k_conv32_tc<DIL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+  return IGAMG_OK;
+}
+
+// Tensor-core forward of the 32 -> 32 layers (default) or the SIMT kernel (IGAMG_NN_TC=0).
+bool nn_tc() {
+  const char* e = std::getenv("IGAMG_NN_TC");
+  return !e || std::atoi(e) != 0;
+}
+
+template <int DIL>
+void conv32_tc_d(igamg_nn* nn, int B, int H, int W, const float* in, const __nv_bfloat16* w, const float* bias,
+                 float* outz, float* outa, int epi) {
+  const int tiles = (int)cdiv((long long)H * W, TC_M);
+  k_conv32_tc<DIL><<<B * tiles, 128, TC_SMEM, nn->stream>>>(H, W, tiles, in, w, bias, outz, outa, epi, nn->tc_err);
+}
+void conv32_tc(igamg_nn* nn, int dil, int B, int H, int W, const float* in, const __nv_bfloat16* w, const float* bias,
+               float* outz, float* outa, int epi) {
+  switch (dil) {
+    case 2: conv32_tc_d<2>(nn, B, H, W, in, w, bias, outz, outa, epi); break;
+    case 4: conv32_tc_d<4>(nn, B, H, W, in, w, bias, outz, outa, epi); break;
+    case 8: conv32_tc_d<8>(nn, B, H, W, in, w, bias, outz, outa, epi); break;
+    default: conv32_tc_d<1>(nn, B, H, W, in, w, bias, outz, outa, epi);
+  }
+}
+
 template <int CIN, int COUT>
 int set_smem_all() {
   int rc;
@@ -306,12 +475,19 @@ int refresh(igamg_nn* nn) {
   return IGAMG_OK;
 }
 
-int forward(igamg_nn* nn, int B, int H, int W, const float* x) {
+// tc: the two 32 -> 32 layers on the tensor cores (BF16 activations and weights, FP32
+// accumulation); training keeps the SIMT path (FP32 activations, used by the backward pass)
+int forward(igamg_nn* nn, int B, int H, int W, const float* x, bool tc = false) {
   const float* P = nn->master;
   const int* d = nn->dil;
   conv<3, 32>(nn, d[0], B, H, W, x, nn->wb + nn->off_w[0], P + nn->off_b[0], nullptr, nn->z[0], nn->a[0], EPI_GELU);
-  conv<32, 32>(nn, d[1], B, H, W, nn->a[0], nn->wb + nn->off_w[1], P + nn->off_b[1], nullptr, nn->z[1], nn->a[1], EPI_GELU);
-  conv<32, 32>(nn, d[2], B, H, W, nn->a[1], nn->wb + nn->off_w[2], P + nn->off_b[2], nullptr, nn->z[2], nn->a[2], EPI_GELU);
+  if (tc) {
+    conv32_tc(nn, d[1], B, H, W, nn->a[0], nn->wb + nn->off_w[1], P + nn->off_b[1], nn->z[1], nn->a[1], EPI_GELU);
+    conv32_tc(nn, d[2], B, H, W, nn->a[1], nn->wb + nn->off_w[2], P + nn->off_b[2], nn->z[2], nn->a[2], EPI_GELU);
+  } else {
+    conv<32, 32>(nn, d[1], B, H, W, nn->a[0], nn->wb + nn->off_w[1], P + nn->off_b[1], nullptr, nn->z[1], nn->a[1], EPI_GELU);
+    conv<32, 32>(nn, d[2], B, H, W, nn->a[1], nn->wb + nn->off_w[2], P + nn->off_b[2], nullptr, nn->z[2], nn->a[2], EPI_GELU);
+  }
   conv<32, 2>(nn, d[3], B, H, W, nn->a[2], nn->wb + nn->off_w[3], P + nn->off_b[3], nullptr, nn->z[3], nullptr, EPI_LINEAR);
   NCK(cudaGetLastError());
   return IGAMG_OK;
@@ -379,14 +555,17 @@ int igamg_nn_create(int in_channels, int width, const int* dilations, unsigned l
   size_t pb = off * sizeof(float);
   if (cudaMalloc(&nn->master, pb) || cudaMalloc(&nn->grad, pb) || cudaMalloc(&nn->m, pb) || cudaMalloc(&nn->v, pb) ||
       cudaMalloc(&nn->wb, off * sizeof(__nv_bfloat16)) || cudaMalloc(&nn->wt, off * sizeof(__nv_bfloat16)) ||
-      cudaMalloc(&nn->loss, sizeof(double)) || cudaMallocHost(&nn->h_loss, sizeof(double)))
+      cudaMalloc(&nn->loss, sizeof(double)) || cudaMallocHost(&nn->h_loss, sizeof(double)) ||
+      cudaMalloc(&nn->tc_err, sizeof(int)) || cudaMallocHost(&nn->h_tc_err, sizeof(int)))
     return fail(IGAMG_ECUDA);
+  if (cudaMemset(nn->tc_err, 0, sizeof(int))) return fail(IGAMG_ECUDA);
   if (cudaMemcpy(nn->master, h.data(), pb, cudaMemcpyHostToDevice) || cudaMemset(nn->m, 0, pb) ||
       cudaMemset(nn->v, 0, pb) || cudaMemset(nn->wt, 0, off * sizeof(__nv_bfloat16)))
     return fail(IGAMG_ECUDA);
   int rc;
   if ((rc = set_smem_all<3, 32>()) || (rc = set_smem_all<32, 32>()) || (rc = set_smem_all<32, 2>()) ||
-      (rc = set_smem_all<2, 32>()))
+      (rc = set_smem_all<2, 32>()) || (rc = set_smem_tc<1>()) || (rc = set_smem_tc<2>()) || (rc = set_smem_tc<4>()) ||
+      (rc = set_smem_tc<8>()))
     return fail(rc);
   if ((rc = refresh(nn))) return fail(rc);
   if (cudaStreamSynchronize(nn->stream)) return fail(IGAMG_ECUDA);
@@ -397,8 +576,9 @@ int igamg_nn_create(int in_channels, int width, const int* dilations, unsigned l
 void igamg_nn_destroy(igamg_nn* nn) {
   if (!nn) return;
   for (void* p : {(void*)nn->master, (void*)nn->grad, (void*)nn->m, (void*)nn->v, (void*)nn->wb, (void*)nn->wt,
-                  (void*)nn->loss, (void*)nn->d0, (void*)nn->d1})
+                  (void*)nn->loss, (void*)nn->d0, (void*)nn->d1, (void*)nn->tc_err})
     if (p) cudaFree(p);
+  if (nn->h_tc_err) cudaFreeHost(nn->h_tc_err);
   for (auto* p : nn->z) if (p) cudaFree(p);
   for (auto* p : nn->a) if (p) cudaFree(p);
   if (nn->h_loss) cudaFreeHost(nn->h_loss);
@@ -430,8 +610,18 @@ int igamg_nn_forward(igamg_nn* nn, int B, int H, int W, const float* x, float* o
   int rc = check_dims(nn, B, H, W);
   if (rc) return rc;
   if (!x || !out) return IGAMG_EINVAL;
-  if ((rc = forward(nn, B, H, W, x))) return rc;
+  const bool tc = nn_tc();
+  if ((rc = forward(nn, B, H, W, x, tc))) return rc;
   NCK(cudaMemcpyAsync(out, nn->z[3], (size_t)B * 2 * H * W * sizeof(float), cudaMemcpyDeviceToDevice, nn->stream));
+  if (tc) {                                   // a tensor-core wait that gave up is reported here
+    NCK(cudaMemcpyAsync(nn->h_tc_err, nn->tc_err, sizeof(int), cudaMemcpyDeviceToHost, nn->stream));
+    NCK(cudaStreamSynchronize(nn->stream));
+    if (*nn->h_tc_err) {
+      NCK(cudaMemset(nn->tc_err, 0, sizeof(int)));
+      g_nn_err = "a tensor-core convolution gave up waiting for its accumulator";
+      return IGAMG_ETIMEOUT;
+    }
+  }
   return IGAMG_OK;
 }
 

@@ -34,7 +34,9 @@ def _split(flat):
 
 
 @pytest.mark.parametrize("B,H,W,dil", [(2, 18, 21, (1, 1, 1, 1)), (1, 35, 33, (1, 2, 4, 8)), (2, 20, 19, (2, 4, 8, 1))])
-def test_forward_and_gradients_match_oracle(B, H, W, dil):
+def test_forward_and_gradients_match_oracle(B, H, W, dil, monkeypatch):
+    # the FP32-activation path (training's forward); the tensor-core forward is tested below
+    monkeypatch.setenv("IGAMG_NN_TC", "0")
     torch = _torch()
     from paper_1705_09282_gb300.warmstart import Network
     net = Network(seed=5, dilations=dil)
@@ -78,3 +80,26 @@ def test_training_reduces_loss_and_adam_matches_oracle():
     for _ in range(60):
         l_last = net.train_step(xg, tg, lr=3e-3)
     assert l_last < 0.5 * l_first
+
+
+@pytest.mark.parametrize("B,H,W,dil", [(2, 18, 21, (1, 1, 1, 1)), (1, 35, 33, (1, 2, 4, 8)), (3, 67, 66, (1, 2, 4, 8)),
+                                       (1, 131, 130, (2, 4, 8, 1))])
+def test_tensor_core_forward_matches_bf16_reference(B, H, W, dil):
+    # inference runs the two 32 -> 32 layers as tcgen05 implicit GEMMs: BF16 weights and BF16
+    # activations, FP32 accumulation in tensor memory.  Reference: the oracle's layers in FP64
+    # with those layers' inputs rounded to BF16 (images of several 128-pixel tiles with a
+    # ragged last tile, every dilation)
+    torch = _torch()
+    from paper_1705_09282_gb300.warmstart import Network
+    net = Network(seed=7, dilations=dil)
+    params = _split(net.get_params().astype(np.float64))
+    for k in (0, 2, 4, 6):
+        params[k] = _bf16(params[k])
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((B, 3, H, W)).astype(np.float32)
+    out = net.forward(torch.tensor(x, device="cuda")).cpu().numpy()
+    a = cnn.gelu(cnn.conv3x3(x.astype(np.float64), params[0], params[1], dil[0]))
+    a = cnn.gelu(cnn.conv3x3(_bf16(a), params[2], params[3], dil[1]))
+    a = cnn.gelu(cnn.conv3x3(_bf16(a), params[4], params[5], dil[2]))
+    ref = cnn.conv3x3(a, params[6], params[7], dil[3])
+    assert np.abs(out - ref).max() <= 2e-3 * np.abs(ref).max(), np.abs(out - ref).max() / np.abs(ref).max()
