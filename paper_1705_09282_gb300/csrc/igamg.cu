@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <tuple>
 #include <cstdio>
 #include <cstring>
@@ -1175,28 +1176,49 @@ int solve_batch_impl(int n, igamg_handle** hs, double** Us, const double** Fs, d
     if ((rc = ensure_graph(hs[i], 0, Us[i], Fs[i]))) return rc;
     if (hs[i]->prob.fmg && (rc = ensure_graph(hs[i], 2, Us[i], Fs[i]))) return rc;
   }
-  for (;;) {
-    int active = 0;
-    for (int i = 0; i < n; ++i) {
-      if (st[i] != IGAMG_NOT_CONVERGED || k[i] >= max_cycles) continue;
-      igamg_handle* h = hs[i];
-      CK(cudaGraphLaunch(h->graph[(k[i] == 0 && h->prob.fmg) ? 2 : 0], h->exec_stream));
-      CK(cudaMemcpyAsync(h->h_pinned, h->norm2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->exec_stream));
-      ++k[i];
-      ++active;
+  // every solve advances on its own: its next cycle is launched as soon as its last norm is
+  // back (an event per solve, polled), so solves whose cycles cost different times (p = 2 and
+  // p = 3, other mesh sizes) never wait for each other
+  auto launch = [&](int i) -> int {
+    igamg_handle* h = hs[i];
+    CK(cudaGraphLaunch(h->graph[(k[i] == 0 && h->prob.fmg) ? 2 : 0], h->exec_stream));
+    CK(cudaMemcpyAsync(h->h_pinned, h->norm2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->exec_stream));
+    CK(cudaEventRecord(h->ev, h->exec_stream));
+    ++k[i];
+    return IGAMG_OK;
+  };
+  std::vector<char> busy(n, 0);
+  int inflight = 0;
+  for (int i = 0; i < n; ++i)
+    if (st[i] == IGAMG_NOT_CONVERGED && k[i] < max_cycles) {
+      if ((rc = launch(i))) return rc;
+      busy[i] = 1;
+      ++inflight;
     }
-    if (!active) break;
+  while (inflight) {
+    bool any = false;
     for (int i = 0; i < n; ++i) {
-      if (st[i] != IGAMG_NOT_CONVERGED || k[i] == 0) continue;
+      if (!busy[i]) continue;
       igamg_handle* h = hs[i];
-      CK(cudaStreamSynchronize(h->exec_stream));
+      const cudaError_t q = cudaEventQuery(h->ev);
+      if (q == cudaErrorNotReady) continue;
+      CK(q);
+      any = true;
+      busy[i] = 0;
+      --inflight;
       if (sweep_flag(h->h_pinned)) return sweep_timeout(h, h->exec_stream);
       rk[i] = std::sqrt(h->h_pinned[0]);
       igamg_report* rep = reps ? &reps[i] : nullptr;
       if (rep && rep->history && k[i] - 1 < rep->history_cap) rep->history[k[i] - 1] = rk[i] / r0[i];
       if (!std::isfinite(rk[i])) st[i] = IGAMG_ENONFINITE;
       else if (rk[i] <= (atol ? atol[i] : rtol * r0[i])) st[i] = IGAMG_OK;
+      if (st[i] == IGAMG_NOT_CONVERGED && k[i] < max_cycles) {
+        if ((rc = launch(i))) return rc;
+        busy[i] = 1;
+        ++inflight;
+      }
     }
+    if (!any) std::this_thread::yield();
   }
   for (int i = 0; i < n; ++i) {
     igamg_handle* h = hs[i];
