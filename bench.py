@@ -587,7 +587,8 @@ def _timed(fn, stream):
 def run_oseen(args):
     """Generalized Oseen, 512 x 512, 8 grids, p = 2, nu = 1e-2, sigma = 1, advection the curl
     of sin^2(pi x) sin^2(pi y) scaled to max |beta| = 0.5 (Re = 50 < Da = 100), GRF forcing:
-    FP64 and FP32-in-FP64 solves to 1e-8; per-row operators (HBM-resident)."""
+    FP64 and FP32-in-FP64 solves to 1e-8; the finest residual in both operator forms (per-row
+    records, matrix-free advection) with their rooflines."""
     import torch
 
     from paper_1705_09282_gb300 import inputs
@@ -624,37 +625,69 @@ def run_oseen(args):
         sweeps = 10
         dt_sm, _ = _timed(lambda: S.smooth(U, F, sweeps=sweeps), stream)
         colour_us = 1e6 * dt_sm / (sweeps * sz.n_colours)
-        # the FP64 operator apply (residual) on the finest level: it streams one 28-coefficient
-        # record per row from HBM (the advection field makes every row different)
-        R = S.empty()
-        reps_r = 20
-        dt_r, _ = _timed(lambda: [S.residual(U, F, out=R) for _ in range(reps_r)], stream)
-        res_us = 1e6 * dt_r / reps_r
-        ntot = sz.n_total
+        # the finest residual (operator apply) in both forms: per-row records (Stokes part and
+        # advection stored per row, streamed from HBM) and the advection matrix-free (element by
+        # element at the (p+2)^2 Gauss points, sum-factorised; Stokes part from class stencils)
+        ntot, G = sz.n_total, p + 2
+        nG = n * G
         RU = (2 * p + 1) * (2 * p - 1) + 2 * p * (2 * p - 1) + 1   # padded row record (2 boxes + lambda)
-        res_bytes = (ntot - 1) * (RU * 8 + 3 * 8)                 # records + U, F, R once
+        Q = p - 1
+        fma_ux = (2 * (Q + 1) * G * (p + 1) + 2 * G * G * (Q + 1) + 2 * G * G + G * (p + 1) * G
+                  + G * (p + 1) * (Q + 1))
+        fma_uy = (2 * (p + 1) * G * (Q + 1) + 2 * G * G * (p + 1) + 2 * G * G + G * (Q + 1) * G
+                  + G * (Q + 1) * (p + 1))
+        forms = S.residual_form()
+        res = {}
+        for prec_name, w in (("fp64", 8), ("fp32", 4)):
+            if forms[prec_name] < 1:
+                continue
+            if prec_name == "fp64":
+                Ur, Fr, Rr = U, F, S.empty()
+                call = lambda: S.residual(Ur, Fr, out=Rr)        # noqa: E731
+            else:
+                Ur = torch.randn(ntot, dtype=torch.float32, device="cuda")
+                Fr = torch.randn(ntot, dtype=torch.float32, device="cuda")
+                Rr = torch.empty_like(Fr)
+                call = lambda: S.residual32(Ur, Fr, out=Rr)      # noqa: E731
+            entry = {"chosen": "matrix_free" if forms[prec_name] == 2 else "records"}
+            for code, fname in ((1, "records"), (2, "matrix_free")):
+                S.set_residual_form(**{prec_name: code})
+                call()
+                reps_r = 50
+                dt_r, _ = _timed(lambda: [call() for _ in range(reps_r)], stream)
+                us = 1e6 * dt_r / reps_r
+                if code == 1:
+                    nbytes = (ntot - 1) * (RU + 3) * w                    # records + U, F, R once
+                    flops = 2.0 * (ntot - 1) * RU
+                else:
+                    nbytes = (3 * ntot + 2 * nG * nG) * w                 # U, F, R + w*beta at the Gauss points
+                    flops = 2.0 * (n * n * (fma_ux + fma_uy) + (ntot - 1) * RU)
+                entry[fname] = {"us_per_launch": us, "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / us / 1e3,
+                                "algorithmic_flops": flops, "achieved_tflops": flops / us / 1e6}
+            S.set_residual_form(**{prec_name: forms[prec_name]})
+            res[prec_name] = entry
         # colour: per 8-DOF patch 8 records, its own 8x8 inverse, dof ids, class id, F and U rows
         patches_colour = sz.n_patches / sz.n_colours
         col_bytes = patches_colour * (8 * RU * 8 + 64 * 8 + 8 * 4 + 4 + 3 * 8 * 8)
-        # the same residual against the FP64 pipe: one multiply-add per record coefficient
-        res_flops = 2.0 * (ntot - 1) * RU
-        fp64_peak = 152 * 2 * 2 * 2070e6 / 1e12
         out[name] = {"solve_ms": 1e3 * t, "cycles": cyc, "mdof_per_s_per_cycle": S.ndof() * cyc / t / 1e6,
                      "div_inf": div, "setup_s": setup, "fp64_colour_launch_us": colour_us,
-                     "fp64_residual_us": res_us,
-                     "residual_fp64": {"flops": res_flops, "achieved_tflops": res_flops / res_us / 1e6,
-                                       "peak_tflops": fp64_peak, "frac": res_flops / res_us / 1e6 / fp64_peak,
-                                       "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz"},
-                     "residual_hbm": {"bytes": res_bytes, "achieved_gbs": res_bytes / res_us / 1e3},
+                     "residual_forms": res,
                      "colour_hbm": {"bytes": col_bytes, "achieved_gbs": col_bytes / colour_us / 1e3}}
         S.close()
     pk, src = peaks()
+    dev = torch.device("cuda")
+    fma = {"fp64": measured_fma_peak(dev, stream, True), "fp32": measured_fma_peak(dev, stream, False)}
     for v in out.values():
         if "error" in v:
             continue
-        for key in ("residual_hbm", "colour_hbm"):
-            v[key]["peak_gbs"] = pk["hbm_gbs"]
-            v[key]["frac"] = v[key]["achieved_gbs"] / pk["hbm_gbs"]
+        v["colour_hbm"]["peak_gbs"] = pk["hbm_gbs"]
+        v["colour_hbm"]["frac"] = v["colour_hbm"]["achieved_gbs"] / pk["hbm_gbs"]
+        for prec_name, entry in v["residual_forms"].items():
+            for fname in ("records", "matrix_free"):
+                e = entry[fname]
+                e["frac_hbm"] = e["achieved_gbs"] / pk["hbm_gbs"]
+                e["frac_fma_peak"] = e["achieved_tflops"] / fma[prec_name]
+            entry["fma_peak_tflops_measured"] = fma[prec_name]
     line = {"metric": "Oseen solve time to 1e-8 rel. residual (2D, 512^2)", "workload": "oseen",
             "config": {"workload": "2D generalized Oseen, unit square, p=2, 512x512, 8 levels, nu=1e-2, sigma=1, "
                                    "max|beta|=0.5 (Re=50, Da=100), GRF forcing seed 1707, V(2,2) multiplicative",

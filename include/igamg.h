@@ -183,6 +183,31 @@ int igamg_level_form(const igamg_handle* h, int level, int* lanes, int* threads,
  * IGAMG_FGMRES_FP32 (else IGAMG_EUNSUPPORTED). */
 int igamg_smooth_f32(igamg_handle* h, int level, float* U, const float* F, int sweeps);
 
+/* R = F - K_l U in FP32 on level `level` (the inner residual of the FP32-in-FP64 modes, Sec. 5.1
+ * step 2 of the V-cycle): U, F, R are FP32 device vectors in the level's layout; the lambda row
+ * and the norm as in igamg_residual (the norm is accumulated in FP64).  Same handle
+ * requirements and errors as igamg_smooth_f32. */
+int igamg_residual_f32(igamg_handle* h, int level, const float* U, const float* F, float* R,
+                       double* norm_out);
+
+/* How the finest level's residual applies the operator, per precision (2D handles):
+ * 0 = class stencils (generalized Stokes on the square, no advection), 1 = one stored record
+ * per row (Stokes part plus the advection term of Sec. 3.1's generalized Oseen problem),
+ * 2 = Stokes part from the class stencils plus the advection term evaluated matrix-free,
+ * element by element at the (p+2)^2 Gauss points with sum factorisation.  The handle times
+ * forms 1 and 2 at creation and keeps the faster (IGAMG_ADV_FORM=records or =mf pins one).
+ * *form64 is the FP64 path's form; *form32 the FP32 V-cycle's, or -1 if the handle has none.
+ * Either output may be NULL.  Errors: IGAMG_EINVAL (NULL handle), IGAMG_EUNSUPPORTED (3D). */
+int igamg_residual_form(const igamg_handle* h, int* form64, int* form32);
+
+/* Sets the finest residual's operator form of a generalized-Oseen handle on the square:
+ * 1 = per-row records, 2 = matrix-free advection, 0 = leave that precision's form as it is;
+ * form64 for the FP64 path, form32 for the FP32 V-cycle.  Synchronises the handle's streams
+ * and drops its captured solve graphs (they are captured again on the next solve).  Errors:
+ * IGAMG_EINVAL (NULL handle, a form outside 0..2), IGAMG_EUNSUPPORTED (3D handle, no advection
+ * term, or form32 set on a handle without an FP32 V-cycle). */
+int igamg_set_residual_form(igamg_handle* h, int form64, int form32);
+
 /* G = R_l r = P_{l-1}^T r: restriction from level l to level l-1 (Sec. 5.1). */
 int igamg_restrict(igamg_handle* h, int level, const double* r_fine, double* g_coarse);
 

@@ -80,6 +80,9 @@ SIGNATURES = {
     "igamg_residual_static": (_I, [ctypes.POINTER(Problem), _I, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "igamg_probe_fma": (_I, [_I, _I, _I, _P, _P, ctypes.POINTER(_D)]),
     "igamg_smooth_f32": (_I, [_P, _I, _P, _P, _I]),
+    "igamg_residual_f32": (_I, [_P, _I, _P, _P, _P, _P]),
+    "igamg_residual_form": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "igamg_set_residual_form": (_I, [_P, _I, _I]),
     "igamg_level_form": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "igamg_host_level_matrix": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL)]),
     "igamg_host_operator_rows": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL)]),

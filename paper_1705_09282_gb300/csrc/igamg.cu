@@ -26,6 +26,7 @@
 #include "igamg3d.h"
 #include "igamg_internal.h"
 #include "kernels.cuh"
+#include "kernels_adv.cuh"
 #include "krylov.h"
 
 using namespace igamg;
@@ -211,6 +212,8 @@ struct Typed {
   int cluster_max = -1;         // deepest feasible cluster choice
   size_t cluster_smem = 0;
   ClusterDesc<T> cdesc{};
+  AdvTab<T> adv{};              // generalized Oseen on the square: matrix-free advection tables
+  int adv_mf = 0;               // 1: the finest level's residual applies the advection matrix-free
 };
 
 struct LevelCommon {
@@ -373,9 +376,28 @@ template <> Typed<double>& typed<double>(igamg_handle* h) { return h->d; }
 template <> Typed<float>& typed<float>(igamg_handle* h) { return h->f; }
 
 // ---- per-step launchers (enqueue on stream s) ------------------------------------------
+// Tiles of the matrix-free Oseen residual (k_residual_adv) on a level of n elements.
+int adv_tiles_x(int p, int n) {
+  const int te = p == 2 ? AdvShape<2>::TE : AdvShape<3>::TE;
+  return (n + p - 1 + te - 1) / te;
+}
+
 template <typename T>
 int do_residual(igamg_handle* h, int l, const T* U, const T* F, T* R, double* norm2, cudaStream_t s) {
-  auto& L = typed<T>(h).lev[l].L;
+  auto& ty = typed<T>(h);
+  auto& L = ty.lev[l].L;
+  if (ty.adv_mf && l == (int)ty.lev.size() - 1) {
+    LevelTab<T> Ls = L;
+    Ls.srow = nullptr;                     // the Stokes part from the class stencils
+    const int tx = adv_tiles_x(h->prob.p, L.n);
+    const unsigned nb = (unsigned)(tx * tx);
+    if (h->prob.p == 2)
+      k_residual_adv<2, T><<<nb, kAdvThreads, AdvShape<2>::smem<T>(), s>>>(Ls, ty.adv, U, F, R, h->part, tx);
+    else
+      k_residual_adv<3, T><<<nb, kAdvThreads, AdvShape<3>::smem<T>(), s>>>(Ls, ty.adv, U, F, R, h->part, tx);
+    k_residual_finish<T><<<1, 1024, 0, s>>>(L.n_total, F, R, h->part, (int)nb, norm2);
+    return launch_check();
+  }
   unsigned nb = nblk(L.n_total - 1);
   if (h->prob.p == 2) k_residual<2, T><<<nb, kBlock, 0, s>>>(L, U, F, R, h->part);
   else k_residual<3, T><<<nb, kBlock, 0, s>>>(L, U, F, R, h->part);
@@ -1628,6 +1650,19 @@ int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
   }
   if ((rc = upload_as(h, &ty.coarse_inv, h->host.coarse_inv))) return rc;
   if ((rc = dmalloc(h, (void**)&ty.delta, std::max<size_t>(max_delta, 1) * sizeof(T)))) return rc;
+  // matrix-free advection tables (not with BF16 operands: those round the stored operator)
+  const auto& H = h->host;
+  const int tx = adv_tiles_x(p, H.n_fine);
+  if (!H.adv_bp.empty() && !bf16 && (size_t)tx * tx <= nblk(H.lev.back().sz.n_total) + 1) {
+    T *bp, *dp, *bq, *dq, *beta;
+    if ((rc = upload_as(h, &bp, H.adv_bp)) || (rc = upload_as(h, &dp, H.adv_dp)) || (rc = upload_as(h, &bq, H.adv_bq)) ||
+        (rc = upload_as(h, &dq, H.adv_dq)) || (rc = upload_as(h, &beta, H.adv_beta)))
+      return rc;
+    ty.adv.n = H.n_fine;
+    ty.adv.bp = bp; ty.adv.dp = dp; ty.adv.bq = bq; ty.adv.dq = dq; ty.adv.beta = beta;
+    if (p == 2) CK(cudaFuncSetAttribute(k_residual_adv<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdvShape<2>::smem<T>()));
+    else CK(cudaFuncSetAttribute(k_residual_adv<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdvShape<3>::smem<T>()));
+  }
   if ((rc = setup_cluster<T>(h, ty))) return rc;
   return setup_fused<T>(h, ty);
 }
@@ -1842,6 +1877,73 @@ int setup_sweep_forms(igamg_handle* h) {
   return IGAMG_OK;
 }
 
+// Residual form of the finest generalized-Oseen level, per precision: the per-row records
+// (Stokes part and advection in one stored record per row) or the advection applied
+// matrix-free (k_residual_adv; the Stokes part from the class stencils).  Both are timed at
+// creation (best of three runs of 20 launches on the level's zeroed workspaces) and the
+// faster is kept; choices are cached per process by (p, n, precision).  IGAMG_ADV_FORM=records
+// or =mf pins one.
+std::map<std::tuple<int, int, int>, int>& adv_cache() {
+  static std::map<std::tuple<int, int, int>, int> m;
+  return m;
+}
+
+template <typename T>
+int time_fine_residual(igamg_handle* h, float* ms_out) {
+  auto& tl = typed<T>(h).lev.back();
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int rc = IGAMG_OK;
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r < 4 && !rc && e == cudaSuccess; ++r) {
+    e = cudaEventRecord(e0, h->stream);
+    for (int k = 0; k < 20 && !rc && e == cudaSuccess; ++k) rc = do_residual<T>(h, (int)h->lc.size() - 1, tl.U, tl.F, tl.R, h->norm2, h->stream);
+    if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0) best = std::min(best, ms);          // the first run warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  CK(e);
+  *ms_out = best / 20;
+  return IGAMG_OK;
+}
+
+template <typename T>
+int choose_adv_form(igamg_handle* h) {
+  auto& ty = typed<T>(h);
+  ty.adv_mf = 0;
+  if (!ty.adv.beta) return IGAMG_OK;
+  if (const char* pin = std::getenv("IGAMG_ADV_FORM")) {
+    ty.adv_mf = std::string(pin) == "mf" ? 1 : 0;
+    return IGAMG_OK;
+  }
+  const auto key = std::make_tuple(h->prob.p, h->prob.n_fine, (int)sizeof(T));
+  auto it = adv_cache().find(key);
+  if (it != adv_cache().end()) { ty.adv_mf = it->second; return IGAMG_OK; }
+  auto& tl = ty.lev.back();
+  const size_t nb = (size_t)tl.L.n_total * sizeof(T);
+  CK(cudaMemsetAsync(tl.U, 0, nb, h->stream));
+  CK(cudaMemsetAsync(tl.F, 0, nb, h->stream));
+  float ms[2];
+  int rc;
+  for (int f = 0; f < 2; ++f) {
+    ty.adv_mf = f;
+    if ((rc = time_fine_residual<T>(h, &ms[f]))) return rc;
+  }
+  ty.adv_mf = ms[1] < ms[0] ? 1 : 0;
+  adv_cache()[key] = ty.adv_mf;
+  if (std::getenv("IGAMG_VERBOSE"))
+    std::fprintf(stderr, "igamg: finest residual (%s): records %.1f us, matrix-free %.1f us -> %s\n",
+                 sizeof(T) == 8 ? "FP64" : "FP32", 1e3f * ms[0], 1e3f * ms[1], ty.adv_mf ? "matrix-free" : "records");
+  return IGAMG_OK;
+}
+
 bool any_3d(int n, igamg_handle** hs) {
   for (int i = 0; i < n; ++i) if (hs[i]->d3) return true;
   return false;
@@ -1972,6 +2074,8 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
   if ((rc = dmalloc(h, (void**)&h->divmax, sizeof(unsigned long long)))) return fail(rc);
   if ((rc = upload_as(h, &h->lv_p, h->host.lv_p)) || (rc = upload_as(h, &h->lv_q, h->host.lv_q))) return fail(rc);
   if ((rc = setup_sweep_forms(h))) return fail(rc);
+  if ((rc = choose_adv_form<double>(h))) return fail(rc);
+  if (fp32_base(pr) && (rc = choose_adv_form<float>(h))) return fail(rc);
   size_t nG = (size_t)pr.n_fine * (p + 2);
   if ((rc = dmalloc(h, (void**)&h->f_dev, 2 * nG * nG * sizeof(double)))) return fail(rc);
   if ((rc = dmalloc(h, (void**)&h->Fh, nfine * sizeof(double)))) return fail(rc);
@@ -2097,6 +2201,39 @@ int igamg_level_form(const igamg_handle* h, int level, int* lanes, int* threads,
   if (lanes) *lanes = tiled ? 1 : lc.lpr;
   if (threads) *threads = tiled ? (lc.ntx * lc.nty == 1 ? kSoloThreads : kTileThreads) : (lc.tpb > 0 ? lc.tpb : colour_block());
   if (tiles) *tiles = tiled ? lc.ntx * lc.nty : 0;
+  return IGAMG_OK;
+}
+
+int igamg_residual_f32(igamg_handle* h, int level, const float* U, const float* F, float* R, double* norm_out) {
+  if (!h || !U || !F || !R) return IGAMG_EINVAL;
+  if (h->d3 || !fp32_base(h->prob)) return IGAMG_EUNSUPPORTED;
+  if (level < 0 || level >= (int)h->lc.size()) return IGAMG_EINVAL;
+  int rc = do_residual<float>(h, level, U, F, R, h->norm2, h->stream);
+  if (rc) return rc;
+  if (norm_out) return read_norm(h, norm_out);
+  return IGAMG_OK;
+}
+
+int igamg_residual_form(const igamg_handle* h, int* form64, int* form32) {
+  if (!h) return IGAMG_EINVAL;
+  if (h->d3) return IGAMG_EUNSUPPORTED;
+  if (form64) *form64 = h->d.adv.beta ? (h->d.adv_mf ? 2 : 1) : 0;
+  if (form32) *form32 = !fp32_base(h->prob) ? -1 : (h->f.adv.beta ? (h->f.adv_mf ? 2 : 1) : 0);
+  return IGAMG_OK;
+}
+
+int igamg_set_residual_form(igamg_handle* h, int form64, int form32) {
+  if (!h || form64 < 0 || form64 > 2 || form32 < 0 || form32 > 2) return IGAMG_EINVAL;
+  if (h->d3) return IGAMG_EUNSUPPORTED;
+  if (form64 && !h->d.adv.beta) return IGAMG_EUNSUPPORTED;
+  if (form32 && (!fp32_base(h->prob) || !h->f.adv.beta)) return IGAMG_EUNSUPPORTED;
+  // the captured solve graphs hold the old form's launches: drop them (re-captured on use)
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->exec_stream) CK(cudaStreamSynchronize(h->exec_stream));
+  for (int k = 0; k < 3; ++k)
+    if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; h->gU[k] = h->gF[k] = nullptr; }
+  if (form64) h->d.adv_mf = form64 == 2 ? 1 : 0;
+  if (form32) h->f.adv_mf = form32 == 2 ? 1 : 0;
   return IGAMG_OK;
 }
 

@@ -138,6 +138,12 @@ struct HierarchyHost {
   // which turns f into the parametric load (J^T f)
   int geometry = 0;
   std::vector<double> quad_xy, jt;
+  // generalized Oseen on the square: the finest level's advection term applied element by
+  // element (matrix-free) needs, per element e and local basis function a, the 1D basis values
+  // and derivatives at the element's G Gauss points, [(e*(d+1)+a)*G + g] for d = p (adv_bp,
+  // adv_dp) and d = p-1 (adv_bq, adv_dq), and the Gauss weight times beta at every Gauss
+  // point, (2, nG, nG) [component][y point][x point]; empty otherwise
+  std::vector<double> adv_bp, adv_dp, adv_bq, adv_dq, adv_beta;
 };
 
 // Builds everything; returns IGAMG_OK or an error code with a message in err.

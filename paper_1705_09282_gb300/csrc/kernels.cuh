@@ -161,23 +161,49 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;  // valid in thread 0
 }
 
-// R = F - K U for every row but lambda; per-block partial sums of R^2 and of m.p (double).
+// Per-block sums of a thread's R^2 and m.p terms into part[2 * block], part[2 * block + 1].
+// FP64 values: two FP64 block reductions.  FP32 values: summed in FP32 within each warp (at
+// most 32 terms) and in FP64 across warps -- every FP64 instruction costs a warp 32 cycles of
+// the SM's FP64 pipe on GB300, and one FP64 reduction per row made the FP32 kernels FP64-bound.
+template <typename T>
+__device__ __forceinline__ void block_partials(T r2, T mp, double* sh, double* __restrict__ part) {
+  if constexpr (sizeof(T) == 8) {
+    const double s1 = block_sum((double)r2, sh);
+    const double s2 = block_sum((double)mp, sh);
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1; part[2 * blockIdx.x + 1] = s2; }
+  } else {
+    for (int o = 16; o > 0; o >>= 1) {
+      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+      mp += __shfl_xor_sync(0xffffffffu, mp, o);
+    }
+    const int w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { sh[w] = (double)r2; sh[32 + w] = (double)mp; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int i = 0; i < nw; ++i) { s1 += sh[i]; s2 += sh[32 + i]; }
+      part[2 * blockIdx.x] = s1;
+      part[2 * blockIdx.x + 1] = s2;
+    }
+  }
+}
+
+// R = F - K U for every row but lambda; per-block partial sums of R^2 and of m.p.
 template <int P, typename T>
 __global__ void __launch_bounds__(256) k_residual(LevelTab<T> L, const T* __restrict__ U, const T* __restrict__ F,
                                                   T* __restrict__ R, double* __restrict__ part) {
-  __shared__ double sh[32];
+  __shared__ double sh[64];
   int g = blockIdx.x * blockDim.x + threadIdx.x;
-  double r2 = 0.0, mp = 0.0;
+  T r2 = T(0), mp = T(0);
   if (g < L.n_total - 1) {
     T r = F[g] - row_KU<P>(L, U, g);
     R[g] = r;
-    r2 = (double)r * (double)r;
+    r2 = r * r;
     int off = g - L.n_ux - L.n_uy;
-    if (off >= 0) mp = (double)mean_coef<P>(L, off) * (double)U[g];
+    if (off >= 0) mp = mean_coef<P>(L, off) * U[g];
   }
-  double s1 = block_sum(r2, sh);
-  double s2 = block_sum(mp, sh);
-  if (threadIdx.x == 0) { part[2 * blockIdx.x] = s1; part[2 * blockIdx.x + 1] = s2; }
+  block_partials<T>(r2, mp, sh, part);
 }
 
 // lambda row and ||R||^2 from the partials (one block, fixed order).

@@ -1161,6 +1161,37 @@ int build_hierarchy(const igamg_problem& pr, HierarchyHost& H, std::string& err)
     if (!invert(K, nd, H.coarse_inv)) { err = "singular coarsest matrix"; return IGAMG_ESINGULAR; }
     H.ndof0 = nd;
   }
+  // matrix-free advection tables of the finest level (generalized Oseen on the square)
+  if (pr.beta_qp && !mapped) {
+    const int G = p + 2, q = p - 1, nG = nf * G;
+    std::vector<double> gx, gw;
+    gauss01(G, gx, gw);
+    auto tp = knots(p, nf), tq = knots(q, nf);
+    H.adv_bp.assign((size_t)nf * (p + 1) * G, 0.0); H.adv_dp.assign(H.adv_bp.size(), 0.0);
+    H.adv_bq.assign((size_t)nf * (q + 1) * G, 0.0); H.adv_dq.assign(H.adv_bq.size(), 0.0);
+    for (int e = 0; e < nf; ++e)
+      for (int g = 0; g < G; ++g) {
+        const double x = (e + gx[g]) / nf;
+        double N[8], dN[8];
+        span_values(tp, p, e + p, x, N); span_derivs(tp, p, e + p, x, dN);
+        for (int a = 0; a <= p; ++a) {
+          H.adv_bp[((size_t)e * (p + 1) + a) * G + g] = N[a];
+          H.adv_dp[((size_t)e * (p + 1) + a) * G + g] = dN[a];
+        }
+        span_values(tq, q, e + q, x, N); span_derivs(tq, q, e + q, x, dN);
+        for (int a = 0; a <= q; ++a) {
+          H.adv_bq[((size_t)e * (q + 1) + a) * G + g] = N[a];
+          H.adv_dq[((size_t)e * (q + 1) + a) * G + g] = dN[a];
+        }
+      }
+    H.adv_beta.assign((size_t)2 * nG * nG, 0.0);
+    for (int c = 0; c < 2; ++c)
+      for (int iy = 0; iy < nG; ++iy)
+        for (int ix = 0; ix < nG; ++ix) {
+          const size_t k = (size_t)c * nG * nG + (size_t)iy * nG + ix;
+          H.adv_beta[k] = gw[ix % G] * gw[iy % G] / ((double)nf * nf) * pr.beta_qp[k];
+        }
+  }
   // load-vector tables on the finest level
   {
     const int G = p + 2, q = p - 1;

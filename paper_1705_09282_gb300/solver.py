@@ -126,6 +126,27 @@ class Solver:
               "igamg_smooth_f32")
         return U
 
+    def residual32(self, U, F, level=None, out=None, norm=False):
+        """FP32 residual (FP32-in-FP64 handles): U, F float32 device tensors."""
+        level = self.n_levels - 1 if level is None else level
+        R = torch.empty(self.ndof(level), dtype=torch.float32, device=self.device) if out is None else out
+        nrm = ctypes.c_double()
+        check(lib().igamg_residual_f32(self._h, level, _ptr(U, torch.float32), _ptr(F, torch.float32),
+                                       _ptr(R, torch.float32), ctypes.byref(nrm) if norm else None),
+              "igamg_residual_f32")
+        return (R, nrm.value) if norm else R
+
+    def residual_form(self):
+        """The finest residual's operator form per precision: {"fp64": f, "fp32": f}, f = 0 class
+        stencils, 1 per-row records, 2 matrix-free advection (-1: no FP32 V-cycle)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        check(lib().igamg_residual_form(self._h, ctypes.byref(a), ctypes.byref(b)), "igamg_residual_form")
+        return {"fp64": a.value, "fp32": b.value}
+
+    def set_residual_form(self, fp64=0, fp32=0):
+        """Pin the finest residual's form (1 records, 2 matrix-free advection, 0 unchanged)."""
+        check(lib().igamg_set_residual_form(self._h, fp64, fp32), "igamg_set_residual_form")
+
     def restrict(self, r_fine, level, out=None):
         g = self.empty(level - 1) if out is None else out
         check(lib().igamg_restrict(self._h, level, _ptr(r_fine), _ptr(g)), "igamg_restrict")
