@@ -1660,6 +1660,41 @@ int upload_typed(igamg_handle* h, Typed<T>& ty, size_t max_delta) {
       return rc;
     ty.adv.n = H.n_fine;
     ty.adv.bp = bp; ty.adv.dp = dp; ty.adv.bq = bq; ty.adv.dq = dq; ty.adv.beta = beta;
+    // interior copies: the tables of element p stand for elements p .. n-1-p (checked: uniform
+    // B-splines there, equal up to the rounding of their evaluation points), the records of
+    // the interior row class (2p+1, 2p+1)
+    const int G = p + 2, q = p - 1, nf = H.n_fine;
+    // (FP32 only: the FP64 kernel is bound by its FP64 multiply-adds, and the longer code of
+    // the constant-operand path measured slower there)
+    bool inner = sizeof(T) == 4 && nf >= 2 * p + 1 && (p + 1) * G <= kAdvMaxPG && H.lev.back().st.RU <= kAdvMaxRU && H.lev.back().st.T == 2 * p + 1;
+    auto same = [&](const std::vector<double>& tab, int d) {
+      const size_t m = (size_t)(d + 1) * G;
+      double scale = 0.0;
+      for (size_t k = 0; k < m; ++k) scale = std::max(scale, std::fabs(tab[(size_t)p * m + k]));
+      for (int e = p; inner && e <= nf - 1 - p; ++e)
+        for (size_t k = 0; k < m; ++k)
+          if (std::fabs(tab[(size_t)e * m + k] - tab[(size_t)p * m + k]) > 1e-12 * scale) return false;
+      return true;
+    };
+    inner = inner && same(H.adv_bp, p) && same(H.adv_dp, p) && same(H.adv_bq, q) && same(H.adv_dq, q);
+    ty.adv.inner = inner ? 1 : 0;
+    if (inner) {
+      for (int k = 0; k < (p + 1) * G; ++k) {
+        ty.adv.ibp[k] = (T)H.adv_bp[(size_t)p * (p + 1) * G + k];
+        ty.adv.idp[k] = (T)H.adv_dp[(size_t)p * (p + 1) * G + k];
+      }
+      for (int k = 0; k < (q + 1) * G; ++k) {
+        ty.adv.ibq[k] = (T)H.adv_bq[(size_t)p * (q + 1) * G + k];
+        ty.adv.idq[k] = (T)H.adv_dq[(size_t)p * (q + 1) * G + k];
+      }
+      const Stencils& st = H.lev.back().st;
+      const size_t off = ((size_t)st.T * st.NC + st.T) * st.RU;
+      for (int j = 0; j < st.RU; ++j) {
+        ty.adv.rx[j] = (T)st.sx[off + j];
+        ty.adv.ry[j] = (T)st.sy[off + j];
+        ty.adv.rp[j] = (T)st.sp[off + j];
+      }
+    }
     if (p == 2) CK(cudaFuncSetAttribute(k_residual_adv<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdvShape<2>::smem<T>()));
     else CK(cudaFuncSetAttribute(k_residual_adv<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdvShape<3>::smem<T>()));
   }
