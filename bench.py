@@ -970,9 +970,11 @@ def run_annulus(args):
 
 def run_cylinder(args):
     """Generalized Stokes on the hollow cylinder section (the quarter annulus extruded by 0.1,
-    push-forward spaces of Sec. 4.3): p = 2, 16^3 elements, 3 grids, sigma = nu = 1, the
-    closed-form manufactured forcing, V(2,2) multiplicative, zero guess, to 1e-8; FP64,
-    FP32-in-FP64 and FGMRES.  Set-up (host assembly on the mapped cube) is not timed."""
+    push-forward spaces of Sec. 4.3): p = 2, n^3 elements for each n in --cyl-n (default 16),
+    coarsest grid 4^3, sigma = nu = 1, the closed-form manufactured forcing, V(2,2)
+    multiplicative, zero guess, to 1e-8 (at most 400 cycles: the V-cycle count grows with n
+    here); FP64, FP32-in-FP64 and FGMRES.  Set-up (host assembly
+    on the mapped cube) is not timed."""
     import torch
 
     from paper_1705_09282_gb300 import inputs
@@ -981,29 +983,33 @@ def run_cylinder(args):
     from paper_1705_09282_gb300.solver import Solver
     stream = torch.cuda.current_stream()
     out = {}
-    for name, prec in (("fp64", IGAMG_FP64), ("fp32-in-fp64", IGAMG_FP32_IR), ("fgmres", IGAMG_FGMRES_FP64)):
+    sizes = [int(v) for v in str(args.cyl_n).split(",")]
+    for n, (name, prec) in ((n, c) for n in sizes for c in (("fp64", IGAMG_FP64), ("fp32-in-fp64", IGAMG_FP32_IR),
+                                                             ("fgmres", IGAMG_FGMRES_FP64))):
+        levels = max(1, (n // 4).bit_length())
         t0 = time.perf_counter()
-        S = Solver(2, 16, 3, 1.0, 1.0, dim=3, precision=prec, geometry=IGAMG_GEOM_HOLLOW_CYLINDER)
+        S = Solver(2, n, levels, 1.0, 1.0, dim=3, precision=prec, geometry=IGAMG_GEOM_HOLLOW_CYLINDER)
         setup = time.perf_counter() - t0
         X = S.quad_points_xy()
         F = S.load_vector(torch.tensor(inputs.cylinder_forcing(X[0], X[1], X[2], 1.0, 1.0), device="cuda"))
         U = S.empty()
         for _ in range(args.warmup):
             U.zero_()
-            S.solve(U, F, rtol=RTOL, max_cycles=MAXC, history=False)
+            S.solve(U, F, rtol=RTOL, max_cycles=400, history=False)
         ts = []
         for _ in range(args.steps):
             U.zero_()
-            dt, rep = _timed(lambda: S.solve(U, F, rtol=RTOL, max_cycles=MAXC, history=False), stream)
+            dt, rep = _timed(lambda: S.solve(U, F, rtol=RTOL, max_cycles=400, history=False), stream)
             ts.append(dt)
         t = sum(ts) / len(ts)
-        out[name] = {"converged": rep["converged"], "cycles": rep["cycles"], "solve_ms": 1e3 * t,
-                     "div_inf": rep["div_inf"], "setup_s": setup, "ndof": S.ndof()}
+        key = name if len(sizes) == 1 else f"{n}^3 {name}"
+        out[key] = {"converged": rep["converged"], "cycles": rep["cycles"], "solve_ms": 1e3 * t,
+                    "div_inf": rep["div_inf"], "setup_s": setup, "ndof": S.ndof(), "levels": levels}
         S.close()
     line = {"metric": "solve time to 1e-8 rel. residual on the hollow cylinder section", "workload": "cylinder",
             "config": {"workload": "3D generalized Stokes on the hollow cylinder section (quarter annulus r 0.075..0.225 "
-                                   "extruded by 0.1), p=2, 16^3, 3 levels, sigma=nu=1, manufactured forcing, V(2,2) "
-                                   "multiplicative, zero guess, to 1e-8, set-up not timed"},
+                                   f"extruded by 0.1), p=2, n^3 for n in {sizes}, coarsest 4^3, sigma=nu=1, "
+                                   "manufactured forcing, V(2,2) multiplicative, zero guess, to 1e-8, set-up not timed"},
             "results": out}
     print(json.dumps(line), flush=True)
 
@@ -1086,6 +1092,7 @@ def main():
                              "cylinder"],
                     help="stokes: the headline sweep (default); the others: extra measurements")
     ap.add_argument("--batch-count", type=int, default=1024)
+    ap.add_argument("--cyl-n", default="16", help="cylinder workload: comma-separated mesh sizes (n^3)")
     ap.add_argument("--train-count", type=int, default=384)
     ap.add_argument("--train-steps", type=int, default=6000)
     ap.add_argument("--profile-case", default=None,
