@@ -362,8 +362,9 @@ def run_ours(args):
         kname = (f"k_sweep_tiles<{p0},double> (pipelined: {form['tiles']} tiles of {form['threads']} threads; "
                  f"one launch = 2 sweeps x {sz.n_colours} colours)")
     else:
-        kname = (f"k_mult_colour<{p0},double,{form['lanes']}> (one colour of the finest level {N_FINE}^2, "
-                 f"{form['lanes']} lane(s) per patch row, {form['threads']}-thread blocks; autotuned form)")
+        kname = (f"k_mult_colour<{p0},double,{form['lanes']},{form['chains']}> (one colour of the finest level "
+                 f"{N_FINE}^2, {form['lanes']} lane(s) per patch row, {form['chains']} multiply-add chains, "
+                 f"{form['threads']}-thread blocks; autotuned form)")
     roofline = {"kernel": kname, "bound": "alu",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s (FP64)", "frac": achieved / fp64_peak,
                 "traffic": None, "traffic_unit": "bytes per launch",
@@ -379,7 +380,8 @@ def run_ours(args):
                 "working_set_note": "finest-level vectors (1.6 MB) stay in L2; the kernel is FP64-issue bound"}
     # the FP32 inner smoother of the mixed mode, same launches
     bytes32 = sweeps_per_replay * (3 * 4 * sz.n_total + sz.n_patches * (8 + 1) * 4)
-    roofline32 = {"kernel": kname.replace(",double", ",float"), "bound": "latency",
+    roofline32 = {"kernel": kname.replace(",double", ",float").replace(f",{form['chains']}>", ",4>").replace(
+                      f"{form['chains']} multiply-add chains", "4 multiply-add chains"), "bound": "latency",
                   "avg_launch_us": t_sweeps32 / launches_per_replay * 1e6,
                   "achieved_tflops": flops_replay / t_sweeps32 / 1e12, "fp32_peak_measured": fp32_peak,
                   "frac_fp32_peak": flops_replay / t_sweeps32 / 1e12 / fp32_peak,

@@ -178,6 +178,13 @@ int igamg_smooth(igamg_handle* h, int level, double* U, const double* F, int swe
  * IGAMG_EUNSUPPORTED (3D handle). */
 int igamg_level_form(const igamg_handle* h, int level, int* lanes, int* threads, int* tiles);
 
+/* The number of independent multiply-add chains per patch row (4 or 2) of level `level`'s
+ * one-lane FP64 colour kernel, as the autotuner chose it at creation (4 for the other forms;
+ * the FP32 kernels always use 4): 4 shortens each lane's dependent chain, 2 spends four fewer
+ * FP64 adds per lane.  Errors:
+ * IGAMG_EINVAL (NULL handle or output, level out of range), IGAMG_EUNSUPPORTED (3D handle). */
+int igamg_level_chains(const igamg_handle* h, int level, int* chains);
+
 /* The same in FP32 (the inner smoother of the FP32-in-FP64 modes): U, F are FP32 device
  * vectors in the level's layout; the handle must be 2D with precision IGAMG_FP32_IR or
  * IGAMG_FGMRES_FP32 (else IGAMG_EUNSUPPORTED). */

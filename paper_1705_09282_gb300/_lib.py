@@ -84,6 +84,7 @@ SIGNATURES = {
     "igamg_residual_form": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "igamg_set_residual_form": (_I, [_P, _I, _I]),
     "igamg_level_form": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "igamg_level_chains": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "igamg_host_level_matrix": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL)]),
     "igamg_host_operator_rows": (_I, [ctypes.POINTER(Problem), _I, _P, _SZ, ctypes.POINTER(_LL)]),
     "igamg_host_operator_apply": (_I, [ctypes.POINTER(Problem), _I, _P, _P, _SZ]),

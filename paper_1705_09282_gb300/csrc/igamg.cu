@@ -229,6 +229,8 @@ struct LevelCommon {
   int *tile_list = nullptr, *tile_off = nullptr, *tile_n8 = nullptr;
   int lpr = 1;                  // lanes per local row of an 8-DOF patch in the colour kernels
   int tpb = 0;                  // threads per block of the colour kernels (0: colour_block())
+  int ch = 4;                   // multiply-add chains per row in the one-lane FP64 colour kernel (4 or 2;
+                                // the FP32 kernels, latency-bound, keep 4)
 };
 
 }  // namespace
@@ -436,11 +438,15 @@ int do_smooth(igamg_handle* h, int l, T* U, const T* F, cudaStream_t s) {
       if (h->prob.p == 2) {
         if (lc.lpr == 2)
           k_mult_colour<2, T, 2><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+        else if (lc.ch == 2 && sizeof(T) == 8)
+          k_mult_colour<2, T, 1, 2><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
         else
           k_mult_colour<2, T><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
       } else {
         if (lc.lpr == 2)
           k_mult_colour<3, T, 2><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
+        else if (lc.ch == 2 && sizeof(T) == 8)
+          k_mult_colour<3, T, 1, 2><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
         else
           k_mult_colour<3, T><<<nb, tpb, shmc, s>>>(tl.L, U, F, lc.dofs, lc.cls, tl.cinv, tl.cinv8, lc.nloc, lc.maxl, first, n8, ngen, nb8);
       }
@@ -1734,14 +1740,16 @@ int tile_capacity(int p, int maxl) {
 // records, mapped).  IGAMG_PIPELINE=0 leaves out the tile forms; IGAMG_SWEEP_FORM pins one
 // ("lanes1", "lanes2", "lanes1_b64", "lanes2_b64", "lanes1_b256", "solo", "tiles1", "tiles2",
 // "tiles4").
-struct SweepForm { int lpr = 1, tiles = 0, tpb = 0; };   // tiles: 0 colour launches, -1 one block, m > 0
+struct SweepForm { int lpr = 1, tiles = 0, tpb = 0, ch = 4; };   // tiles: 0 colour launches, -1 one block, m > 0
 std::map<std::tuple<int, int, int, int>, SweepForm>& form_cache() {
   static std::map<std::tuple<int, int, int, int>, SweepForm> m;
   return m;
 }
 
 std::string form_name(const SweepForm& f) {
-  if (f.tiles == 0) return std::string(f.lpr == 2 ? "lanes2" : "lanes1") + (f.tpb ? "_b" + std::to_string(f.tpb) : "");
+  if (f.tiles == 0)
+    return std::string(f.lpr == 2 ? "lanes2" : "lanes1") + (f.tpb ? "_b" + std::to_string(f.tpb) : "") +
+           (f.ch == 2 ? "_c2" : "");
   if (f.tiles < 0) return "solo";
   return "tiles" + std::to_string(f.tiles);
 }
@@ -1754,6 +1762,7 @@ int apply_form(igamg_handle* h, int l, const SweepForm& f) {
   const PatchTables& pt = h->host.lev[l].pt;
   lc.lpr = f.lpr;
   lc.tpb = f.tpb;
+  lc.ch = f.lpr == 1 && f.tiles == 0 ? f.ch : 4;
   lc.ntx = lc.nty = 0;
   if (f.tiles == 0) return IGAMG_OK;
   const int nint = lc.sz.n + p - 2;
@@ -1854,6 +1863,7 @@ int setup_sweep_forms(igamg_handle* h) {
       SweepForm f;
       if (w.rfind("lanes2", 0) == 0) f.lpr = 2;
       if (w.find("_b") != std::string::npos) f.tpb = std::atoi(w.c_str() + w.find("_b") + 2);
+      if (w.find("_c2") != std::string::npos) f.ch = 2;
       else if (w == "solo") f.tiles = -1;
       else if (w.rfind("tiles", 0) == 0) f.tiles = std::max(1, std::atoi(w.c_str() + 5));
       add(f);
@@ -1867,7 +1877,8 @@ int setup_sweep_forms(igamg_handle* h) {
       }
     } else {
       for (SweepForm f : {SweepForm{1, 0}, SweepForm{2, 0}, SweepForm{1, 0, 64}, SweepForm{2, 0, 64},
-                          SweepForm{1, 0, 256}, SweepForm{1, -1}, SweepForm{1, 1}, SweepForm{1, 2}, SweepForm{1, 4}})
+                          SweepForm{1, 0, 256}, SweepForm{1, 0, 0, 2}, SweepForm{1, 0, 64, 2}, SweepForm{1, 0, 256, 2},
+                          SweepForm{1, -1}, SweepForm{1, 1}, SweepForm{1, 2}, SweepForm{1, 4}})
         add(f);
     }
     if (cands.empty()) cands.push_back(SweepForm{1, 0});
@@ -2269,6 +2280,14 @@ int igamg_set_residual_form(igamg_handle* h, int form64, int form32) {
     if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; h->gU[k] = h->gF[k] = nullptr; }
   if (form64) h->d.adv_mf = form64 == 2 ? 1 : 0;
   if (form32) h->f.adv_mf = form32 == 2 ? 1 : 0;
+  return IGAMG_OK;
+}
+
+int igamg_level_chains(const igamg_handle* h, int level, int* chains) {
+  if (!h || level < 0 || !chains) return IGAMG_EINVAL;
+  if (h->d3) return IGAMG_EUNSUPPORTED;
+  if (level >= (int)h->lc.size()) return IGAMG_EINVAL;
+  *chains = h->lc[level].ch;
   return IGAMG_OK;
 }
 

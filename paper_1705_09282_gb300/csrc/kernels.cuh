@@ -416,13 +416,15 @@ __device__ __forceinline__ void mult_colour_block(const LevelTab<T>& L, T* __res
   general_patch_warp<P, T, CH>(L, U, F, dofs, cls, cinv, nloc, maxl, first + n8 + w, lane, sh + wib * maxl);
 }
 
-template <int P, typename T, int LPR = 1>
+// CH: multiply-add chains per row and per local inverse (4: shorter dependent chains; 2: four
+// fewer FP64 adds per lane, for launches that keep the FP64 pipe busy).
+template <int P, typename T, int LPR = 1, int CH = 4>
 __global__ void __launch_bounds__(256) k_mult_colour(LevelTab<T> L, T* __restrict__ U, const T* __restrict__ F,
                                                      const int* __restrict__ dofs, const int* __restrict__ cls,
                                                      const T* __restrict__ cinv, const T* __restrict__ cinv8,
                                                      const int* __restrict__ nloc,
                                                      int maxl, int first, int n8, int ngen, int nb8) {
-  mult_colour_block<P, T, LPR>(L, U, F, dofs, cls, cinv, cinv8, nloc, maxl, first, n8, ngen, nb8, (int)blockIdx.x);
+  mult_colour_block<P, T, LPR, CH>(L, U, F, dofs, cls, cinv, cinv8, nloc, maxl, first, n8, ngen, nb8, (int)blockIdx.x);
 }
 
 // The same colour step with each 8-DOF patch row split over two warps: warps 0-7 of the

@@ -112,12 +112,14 @@ class Solver:
         return U
 
     def level_form(self, level=None):
-        """The sweep form the autotuner chose for a level (2D): dict(lanes, threads, tiles)."""
+        """The sweep form the autotuner chose for a level (2D): dict(lanes, threads, tiles, chains)."""
         level = self.n_levels - 1 if level is None else level
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(lib().igamg_level_form(self._h, level, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
               "igamg_level_form")
-        return {"lanes": a.value, "threads": b.value, "tiles": c.value}
+        d = ctypes.c_int()
+        check(lib().igamg_level_chains(self._h, level, ctypes.byref(d)), "igamg_level_chains")
+        return {"lanes": a.value, "threads": b.value, "tiles": c.value, "chains": d.value}
 
     def smooth32(self, U, F, level=None, sweeps=1):
         """FP32 smoothing sweeps (FP32-in-FP64 handles): U, F float32 device tensors."""

@@ -143,3 +143,37 @@ def test_two_lanes_per_row_form_matches_one_lane(p, n, L, monkeypatch):
         S[k].close()
     assert res[0][0] == res[1][0]
     assert np.abs(res[0][1] - res[1][1]).max() <= 1e-12 * np.abs(res[0][1]).max()
+
+
+@pytest.mark.parametrize("p,n,L", [(2, 64, 4), (3, 48, 3)])
+def test_two_chain_form_matches_four_chains(p, n, L, monkeypatch):
+    # the one-lane colour kernel with two multiply-add chains per row and local inverse instead
+    # of four: only the summation order changes, so sweeps agree to 1e-13 and solves take the
+    # same cycles to the same iterates
+    torch = _torch()
+    from paper_1705_09282_gb300.solver import Solver
+    S = {}
+    for form in ("lanes1_b64", "lanes1_b64_c2"):
+        monkeypatch.setenv("IGAMG_SWEEP_FORM", form)
+        S[form] = Solver(p, n, L, 1.0, 1.0)
+    monkeypatch.delenv("IGAMG_SWEEP_FORM")
+    assert S["lanes1_b64"].level_form()["chains"] == 4
+    assert S["lanes1_b64_c2"].level_form() == {"lanes": 1, "threads": 64, "tiles": 0, "chains": 2}
+    for lev in range(1, L):
+        nd = S["lanes1_b64"].ndof(lev)
+        U = torch.tensor(inputs.random_vector(nd, seed=270 + lev), device="cuda")
+        F = torch.tensor(inputs.random_vector(nd, seed=280 + lev), device="cuda")
+        U4, U2 = U.clone(), U.clone()
+        S["lanes1_b64"].smooth(U4, F, level=lev, sweeps=2)
+        S["lanes1_b64_c2"].smooth(U2, F, level=lev, sweeps=2)
+        a, b = U2.cpu().numpy(), U4.cpu().numpy()
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max(), lev
+    f = inputs.grf_forcing(p, n, seed=94)
+    res = []
+    for k in ("lanes1_b64", "lanes1_b64_c2"):
+        Ug = S[k].empty()
+        rep = S[k].solve(Ug, S[k].load_vector(torch.tensor(f, device="cuda")), rtol=1e-9, max_cycles=60)
+        res.append((rep["cycles"], Ug.cpu().numpy()))
+        S[k].close()
+    assert res[0][0] == res[1][0]
+    assert np.abs(res[0][1] - res[1][1]).max() <= 1e-12 * np.abs(res[0][1]).max()
