@@ -72,12 +72,13 @@ class Network:
                                        g.ctypes.data_as(ctypes.c_void_p)), "igamg_nn_loss_grad")
         return loss.value, g
 
-    def train_step(self, x, target, lr):
+    def train_step(self, x, target, lr, want_loss=True):
+        """One Adam step; returns the minibatch loss (a host synchronisation) or None."""
         B, _, H, W = x.shape
         loss = ctypes.c_double()
         check(lib().igamg_nn_train_step(self._h, B, H, W, _fptr(x), _fptr(target), ctypes.c_float(lr),
-                                        ctypes.byref(loss)), "igamg_nn_train_step")
-        return loss.value
+                                        ctypes.byref(loss) if want_loss else None), "igamg_nn_train_step")
+        return loss.value if want_loss else None
 
 
 def streamfunction(solver, U):
@@ -175,9 +176,11 @@ def targets(problems, rtol=1e-10, max_cycles=80):
     return out
 
 
-def train(net, problems, grids, steps, batch=8, lr=2e-3, seed=0, lr_final=None):
+def train(net, problems, grids, steps, batch=8, lr=2e-3, seed=0, lr_final=None, loss_every=50):
     """Adam on minibatches of equal-size problems (the network is fully convolutional);
-    the step size decays geometrically from lr to lr_final (default lr / 20)."""
+    the step size decays geometrically from lr to lr_final (default lr / 20).  Returns the
+    minibatch losses of the first 5 steps, of every loss_every-th step and of the last 20, in
+    step order: only those steps wait for the device, the others are queued back to back."""
     lr_final = lr / 20.0 if lr_final is None else lr_final
     by_size = {}
     for i, pr in enumerate(problems):
@@ -191,7 +194,10 @@ def train(net, problems, grids, steps, batch=8, lr=2e-3, seed=0, lr_final=None):
         x = torch.stack([problems[i].x for i in pick]).contiguous()
         t = torch.stack([grids[i] for i in pick]).contiguous()
         rate = lr * (lr_final / lr) ** (s / max(1, steps - 1))
-        losses.append(net.train_step(x, t, rate))
+        want = s < 5 or s >= steps - 20 or s % loss_every == 0
+        loss = net.train_step(x, t, rate, want_loss=want)
+        if want:
+            losses.append(loss)
     return losses
 
 
