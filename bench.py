@@ -365,10 +365,17 @@ def run_ours(args):
         kname = (f"k_mult_colour<{p0},double,{form['lanes']},{form['chains']}> (one colour of the finest level "
                  f"{N_FINE}^2, {form['lanes']} lane(s) per patch row, {form['chains']} multiply-add chains, "
                  f"{form['threads']}-thread blocks; autotuned form)")
+    # DRAM bytes (read + write) per launch from the ncu captures of this kernel in the same form
+    # (colours 0 and 1 of the 256^2 finest level, mean of the two launches), for the forms
+    # captured; none for another form
+    captured = {(1, 64, 0, 4): 3.21e6, (1, 64, 0, 2): 3.208e6}
+    traffic = captured.get((form["lanes"], form["threads"], form["tiles"], form["chains"])) if p0 == 2 else None
     roofline = {"kernel": kname, "bound": "alu",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s (FP64)", "frac": achieved / fp64_peak,
-                "traffic": None, "traffic_unit": "bytes per launch",
-                "traffic_note": "ncu DRAM bytes of this kernel: profiles/k_mult_colour_p2_fp64_256x256.md",
+                "traffic": traffic, "traffic_unit": "bytes per launch",
+                "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of this kernel in this form, one ncu "
+                                 "capture of colours 0 and 1 (cold L2): profiles/k_mult_colour_p2_fp64_256x256.md"
+                                 if traffic else "this form has no ncu capture"),
                 "peak_source": "measured: igamg_probe_fma, FP64 FMA chains on every SM, best of 5 (CUDA events)",
                 "peak_derived": fp64_derived, "fp32_peak_measured": fp32_peak,
                 "avg_launch_us": launch_s * 1e6, "launches_timed": launches_per_replay * replays,
