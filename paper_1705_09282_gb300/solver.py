@@ -211,8 +211,9 @@ class Solver:
 
 
 def solve_batch(solvers, Us, Fs, rtol=1e-8, max_cycles=100, history=False):
-    """Independent solves side by side (igamg_solve_batch): one captured step per
-    unfinished solve per round, each on its handle's own stream."""
+    """Independent solves (igamg_solve_batch): groups of eight or more FP64 solves of one
+    cycle shape step in lockstep; the others run side by side, each on its handle's own
+    stream, and each advances to its next cycle as soon as its own residual norm is back."""
     n = len(solvers)
     hs = (ctypes.c_void_p * n)(*[s._h.value for s in solvers])
     up = (ctypes.c_void_p * n)(*[_ptr(u).value for u in Us])

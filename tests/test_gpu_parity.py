@@ -242,6 +242,34 @@ def test_batch_solve_matches_single_solves(precision, monkeypatch):
         assert rep["history"] == pytest.approx(rep1["history"], rel=0, abs=0)
 
 
+def test_batch_solves_stop_independently(monkeypatch):
+    # side by side (no lockstep), with a cycle budget that the p = 3 solves meet (about 6
+    # cycles) and the p = 2 solves do not (about 17): each solve stops on its own -- converged
+    # or out of cycles -- with the iterate, cycle count and status of its single solve
+    monkeypatch.setenv("IGAMG_LOCKSTEP", "0")
+    torch = _torch()
+    from paper_1705_09282_gb300.solver import Solver, solve_batch
+    cases = [(2, 1e-4), (3, 1.0), (2, 1.0), (3, 1e4), (2, 1e2)]
+    n, L, budget = 32, 4, 8
+    solvers, Fs, Us, singles = [], [], [], []
+    for p, sigma in cases:
+        S = Solver(p, n, L, sigma, 1.0)
+        F = S.load_vector(torch.tensor(inputs.grf_forcing(p, n, seed=int(sigma * 3) + p), device="cuda"))
+        U1 = S.empty()
+        singles.append((S.solve(U1, F, rtol=1e-8, max_cycles=budget), U1.cpu().numpy()))
+        solvers.append(S); Fs.append(F); Us.append(S.empty())
+    reps = solve_batch(solvers, Us, Fs, rtol=1e-8, max_cycles=budget, history=True)
+    kinds = set()
+    for (rep1, U1), rep, U in zip(singles, reps, Us):
+        assert rep["converged"] == rep1["converged"] and rep["cycles"] == rep1["cycles"] <= budget
+        assert rep["history"] == pytest.approx(rep1["history"], rel=0, abs=0)
+        assert np.array_equal(U.cpu().numpy(), U1)
+        kinds.add(rep["converged"])
+    assert kinds == {True, False}
+    for S in solvers:
+        S.close()
+
+
 @pytest.mark.parametrize("depth", ["-1", "1", "2", "3"])
 @pytest.mark.parametrize("p", [2, 3])
 def test_one_block_coarse_levels_same_iterates(depth, p, monkeypatch):
