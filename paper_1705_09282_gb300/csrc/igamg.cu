@@ -2111,6 +2111,10 @@ int igamg_create(const igamg_problem* prob, void* cuda_stream, igamg_handle** ou
   h->ndof0 = h->host.ndof0;
   if ((rc = upload_typed<double>(h, h->d, max_delta))) return fail(rc);
   if (fp32_base(pr) && (rc = upload_typed<float>(h, h->f, max_delta))) return fail(rc);
+  // the matrix-free advection tables live on the device from here on (w * beta alone is
+  // 2 (n (p+2))^2 doubles on the host)
+  for (auto* v : {&h->host.adv_bp, &h->host.adv_dp, &h->host.adv_bq, &h->host.adv_dq, &h->host.adv_beta})
+    std::vector<double>().swap(*v);
   h->ndof0 = h->host.ndof0;
   long long nfine = h->lc[L - 1].sz.n_total;
   if ((rc = dmalloc(h, (void**)&h->part, 2 * sizeof(double) * (nblk(nfine) + 1)))) return fail(rc);
