@@ -111,9 +111,9 @@ __device__ __forceinline__ void adv_element(const T* __restrict__ sU, int cw, XB
 
 // The Stokes part of one row (the class-stencil record st(j), Sec. 3.4's blocks as in row_KU)
 // applied to the staged tiles: sA holds the first box's unknowns, sB the second's, both with
-// row length W; (x0, y0) is the tile position of the box's first entry, wy the box's extent in
-// y.  Same terms in the same order and chains as row_KU with four chains, so the result is the
-// same to the last bit.
+// row length W; (ax0, ay0) and (bx0, by0) are the tile positions of the boxes' first entries,
+// WY0 and WY1 their extents in y.  The same terms in the same order and chains as row_KU with
+// four chains on the class stencils, so the result equals that row's to the last bit.
 template <int B0, int B1, int WY0, int WY1, typename T, typename ST>
 __device__ __forceinline__ T stokes_row_tile(ST st, const T* sA, int ax0, int ay0, const T* sB, int bx0, int by0,
                                              int W, T lam) {
@@ -139,19 +139,21 @@ __device__ __forceinline__ T stokes_row_tile(ST st, const T* sA, int ax0, int ay
 // R = F - K U on the finest Oseen level for every row but lambda, with K = (Stokes part from
 // the class stencils in L; L.srow must be null) + (advection, matrix-free from A).  One block
 // per tile of TE x TE index positions (rows u_x(X, Y), u_y(X, Y), p(X, Y) with X, Y in the tile):
-//  1. the u_x, u_y and p coefficients of the positions around the tile (X - P .. X + TE + P)
-//     and the 1D tables of its E x E elements (positions X - P .. X + TE - 1) are staged in
-//     shared memory;
+//  1. the u_x, u_y and p coefficients of the positions around the tile (X0 - P .. X0 + TE + P
+//     in each direction) and the 1D tables of its E x E elements (X0 - P .. X0 + TE - 1) are
+//     staged in shared memory;
 //  2. each thread evaluates one element's advection integrals for both components into
 //     shared memory (zero for positions outside the mesh);
 //  3. each owned row sums the contributions of the elements in its support in a fixed order
 //     (deterministic), subtracts the Stokes part (its class-stencil record applied to the
 //     staged tiles of u_x, u_y and p), and writes R; per-block partial sums of R^2 and m.p go
 //     to part[2 * block], as in k_residual.
+// Blocks per SM: FP64 one (the registers of the FP64 element evaluation), FP32 three (p = 2)
+// or two (p = 3), the most that fit without register spills.
 template <int P, typename T>
-__global__ void __launch_bounds__(kAdvThreads, sizeof(T) == 8 ? 1 : (P == 2 ? 3 : 2)) k_residual_adv(LevelTab<T> L, AdvTab<T> A, const T* __restrict__ U,
-                                                              const T* __restrict__ F, T* __restrict__ R,
-                                                              double* __restrict__ part, int tiles_x) {
+__global__ void __launch_bounds__(kAdvThreads, sizeof(T) == 8 ? 1 : (P == 2 ? 3 : 2))
+    k_residual_adv(LevelTab<T> L, AdvTab<T> A, const T* __restrict__ U, const T* __restrict__ F, T* __restrict__ R,
+                   double* __restrict__ part, int tiles_x) {
   using S = AdvShape<P>;
   constexpr int Q = S::Q, G = S::G, E = S::E, TE = S::TE, CW = S::CW;
   extern __shared__ __align__(16) unsigned char adv_smem[];
