@@ -203,6 +203,66 @@ def test_oseen_manufactured_convergence():
     assert 1.65 <= rate <= 2.6, (rate, errs)
 
 
+@pytest.mark.parametrize("p,n", [(2, 5), (3, 4)])
+def test_oseen_advection_block_exact(p, n):
+    # The advection term of Sec. 3.1, (beta . grad u, v) over the velocity blocks, against an
+    # independent evaluation: scipy's B-splines on the same open uniform knots, 1D integrals by
+    # 12-point Gauss-Legendre per element (exact here), and beta = (c1 + a1 y, c2 + a2 x), for
+    # which each block is a sum of Kronecker products of 1D integrals.  A non-constant,
+    # direction-dependent field catches a transposed quadrature layout or swapped components;
+    # it need not be divergence-free for the bilinear form's definition.
+    from scipy.interpolate import BSpline
+    c1, a1, c2, a2 = 0.7, -1.3, -0.4, 2.1
+    x = inputs.quad_points_1d(p, n)
+    X, Y = np.meshgrid(x, x)
+    beta = np.stack([c1 + a1 * Y, c2 + a2 * X])
+    K = (o2.Stokes2D(p, n, 1.0, 1.0, beta=beta).K - o2.Stokes2D(p, n, 1.0, 1.0).K).toarray()
+    q = p - 1
+    gx, gw = np.polynomial.legendre.leggauss(12)
+
+    def knots(d):
+        return np.concatenate([np.zeros(d + 1), np.arange(1, n) / n, np.ones(d + 1)])
+
+    def integral(di, dj, derivative_j, weight):
+        # M[i, j] = int_0^1 weight(s) N^di_i(s) (N^dj_j)^(derivative_j)(s) ds
+        ti, tj = knots(di), knots(dj)
+        ni, nj = n + di, n + dj
+        M = np.zeros((ni, nj))
+        for e in range(n):
+            s = (e + 0.5 * (gx + 1)) / n
+            w = 0.5 * gw / n * weight(s)
+            Bi = np.array([BSpline(ti, np.eye(ni)[i], di, extrapolate=False)(s) for i in range(ni)])
+            Bj = np.array([BSpline(tj, np.eye(nj)[j], dj, extrapolate=False).derivative(derivative_j)(s)
+                           if derivative_j else BSpline(tj, np.eye(nj)[j], dj, extrapolate=False)(s)
+                           for j in range(nj)])
+            M += (np.nan_to_num(Bi) * w) @ np.nan_to_num(Bj).T
+        return M
+
+    one = lambda s: np.ones_like(s)   # noqa: E731
+    lin = lambda s: s                 # noqa: E731
+    S = o2.Stokes2D(p, n, 1.0, 1.0)
+    # u_x block (x-degree p, y-degree q; x indices 1..n+p-2 free): rows (iy, ix), columns (jy, jx)
+    #   b1 d/dx: (c1 + a1 y) -> [int N_ix N'_jx dx] (x) [int (c1 + a1 y) N_iy N_jy dy]
+    #   b2 d/dy: (c2 + a2 x) -> [int (c2 + a2 x) N_ix N_jx dx] (x) [int N_iy N'_jy dy]
+    Dx_p, Mx_p, Mx_p_lin = integral(p, p, 1, one), integral(p, p, 0, one), integral(p, p, 0, lin)
+    My_q, My_q_lin, Dy_q = integral(q, q, 0, one), integral(q, q, 0, lin), integral(q, q, 1, one)
+    fx = slice(1, n + p - 1)
+    Axx = (np.kron(c1 * My_q + a1 * My_q_lin, Dx_p[fx, fx]) + np.kron(Dy_q, c2 * Mx_p[fx, fx] + a2 * Mx_p_lin[fx, fx]))
+    ux = slice(0, S.n_ux)
+    assert np.abs(K[ux, ux] - Axx).max() <= 1e-13 * np.abs(Axx).max()
+    # u_y block (x-degree q, y-degree p; y indices 1..n+p-2 free)
+    Dx_q, Mx_q, Mx_q_lin = integral(q, q, 1, one), integral(q, q, 0, one), integral(q, q, 0, lin)
+    My_p, My_p_lin, Dy_p = integral(p, p, 0, one), integral(p, p, 0, lin), integral(p, p, 1, one)
+    Ayy = (np.kron((c1 * My_p + a1 * My_p_lin)[fx, fx], Dx_q) + np.kron(Dy_p[fx, fx], c2 * Mx_q + a2 * Mx_q_lin))
+    uy = slice(S.n_ux, S.n_u)
+    assert np.abs(K[uy, uy] - Ayy).max() <= 1e-13 * np.abs(Ayy).max()
+    # nothing else: no coupling between the components, the pressure or the multiplier (up to
+    # the rounding of the two assemblies' Stokes parts, which the difference cancels)
+    K[ux, ux] = 0.0
+    K[uy, uy] = 0.0
+    assert np.abs(K).max() <= 1e-15 * np.abs(Axx).max()
+
+
 # ---------------------------------------------------------------- multigrid --
 
 @pytest.mark.parametrize("p", [2, 3])
