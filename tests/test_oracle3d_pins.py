@@ -326,6 +326,58 @@ def test_oseen_manufactured_convergence_3d():
     assert np.abs(K - K.T).max() > 1e-6 * np.abs(K).max()
 
 
+@pytest.mark.parametrize("p,n", [(2, 3), (3, 2)])
+def test_oseen_advection_blocks_exact_3d(p, n):
+    # The 3D advection term (beta . grad u_c, v_c), per velocity component, against an
+    # independent evaluation: scipy's B-splines on the same open uniform knots, 1D integrals by
+    # 12-point Gauss-Legendre per element (exact here), beta = (c1 + a1 y, c2 + a2 z, c3 + a3 x),
+    # for which each block is a sum of three-factor Kronecker products (z slowest, x fastest).
+    from scipy.interpolate import BSpline
+    c1, a1, c2, a2, c3, a3 = 0.7, -1.3, -0.4, 2.1, 0.25, 0.9
+    x = inputs.quad_points_1d(p, n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    beta = np.stack([c1 + a1 * Y, c2 + a2 * Z, c3 + a3 * X])
+    K = (o3.Stokes3D(p, n, 1.0, 1.0, beta=beta).K - o3.Stokes3D(p, n, 1.0, 1.0).K).toarray()
+    S = o3.Stokes3D(p, n, 1.0, 1.0, assemble=False)
+    q = p - 1
+    gx, gw = np.polynomial.legendre.leggauss(12)
+
+    def integral(d, derivative_j, weight):
+        # M[i, j] = int_0^1 weight(s) N^d_i(s) (N^d_j)^(derivative_j)(s) ds
+        t = np.concatenate([np.zeros(d + 1), np.arange(1, n) / n, np.ones(d + 1)])
+        m = n + d
+        M = np.zeros((m, m))
+        for e in range(n):
+            s = (e + 0.5 * (gx + 1)) / n
+            w = 0.5 * gw / n * weight(s)
+            B = np.nan_to_num(np.array([BSpline(t, np.eye(m)[i], d, extrapolate=False)(s) for i in range(m)]))
+            Bd = B if not derivative_j else np.nan_to_num(np.array(
+                [BSpline(t, np.eye(m)[j], d, extrapolate=False).derivative(derivative_j)(s) for j in range(m)]))
+            M += (B * w) @ Bd.T
+        return M
+
+    one = lambda s: np.ones_like(s)   # noqa: E731
+    lin = lambda s: s                 # noqa: E731
+    kron3 = lambda Mz, My, Mx: np.kron(Mz, np.kron(My, Mx))   # noqa: E731
+    free = slice(1, n + p - 1)
+    for c in range(3):
+        deg = [q, q, q]
+        deg[c] = p
+        M = [integral(deg[a], 0, one) for a in range(3)]
+        Ml = [integral(deg[a], 0, lin) for a in range(3)]
+        D = [integral(deg[a], 1, one) for a in range(3)]
+        cut = lambda A, a: A[free, free] if a == c else A   # noqa: E731
+        Mc = [cut(M[a], a) for a in range(3)]
+        W = [cut(c0 * M[a] + s0 * Ml[a], a) for a, (c0, s0) in enumerate(((c3, a3), (c1, a1), (c2, a2)))]
+        Dc = [cut(D[a], a) for a in range(3)]
+        # b1(y) d/dx + b2(z) d/dy + b3(x) d/dz; W[a] is the weight that depends on axis a
+        A = kron3(Mc[2], W[1], Dc[0]) + kron3(W[2], Dc[1], Mc[0]) + kron3(Dc[2], Mc[1], W[0])
+        blk = slice(c * S.n_uc, (c + 1) * S.n_uc)
+        assert np.abs(K[blk, blk] - A).max() <= 1e-13 * np.abs(A).max(), c
+        K[blk, blk] = 0.0
+    assert np.abs(K).max() <= 1e-15 * np.abs(A).max()
+
+
 def test_oseen_forcing_matches_closed_form_derivatives():
     # beta . grad u from the polynomial terms against central differences
     p, n, h = 2, 1, 1e-4
