@@ -1745,6 +1745,12 @@ std::map<std::tuple<int, int, int, int>, SweepForm>& form_cache() {
   static std::map<std::tuple<int, int, int, int>, SweepForm> m;
   return m;
 }
+// guards form_cache and adv_cache: handles may be created from several host threads at once
+// (the lookups and inserts are locked; the timings between them are not)
+std::mutex& form_mutex() {
+  static std::mutex m;
+  return m;
+}
 
 std::string form_name(const SweepForm& f) {
   if (f.tiles == 0)
@@ -1895,24 +1901,30 @@ int setup_sweep_forms(igamg_handle* h) {
     }
     const auto key = std::make_tuple(p, lc.sz.n, h->prob.beta_qp ? 1 : 0, mapped ? 1 : 0);
     SweepForm chosen = cands[0];
-    auto it = form_cache().find(key);
-    if (cands.size() > 1 && it != form_cache().end()) {
-      chosen = it->second;
-    } else if (cands.size() > 1) {
-      auto& tl = h->d.lev[l];
-      const size_t nb = (size_t)tl.L.n_total * sizeof(double);
-      CK(cudaMemsetAsync(tl.U, 0, nb, h->stream));
-      CK(cudaMemsetAsync(tl.F, 0, nb, h->stream));
-      float best = 1e30f;
-      for (auto& f : cands) {
-        if ((rc = apply_form(h, l, f))) return rc;
-        float ms = 0;
-        if ((rc = time_level_sweeps(h, l, &ms))) return rc;
-        if (verbose) std::fprintf(stderr, "igamg: level %d (n = %d) %s: %.1f us per %d sweep(s)\n", l, lc.sz.n,
-                                  form_name(f).c_str(), 1e3f * ms, std::max(1, h->prob.nu1));
-        if (ms < best) { best = ms; chosen = f; }
+    if (cands.size() > 1) {
+      bool cached = false;
+      {
+        std::lock_guard<std::mutex> lk(form_mutex());
+        auto it = form_cache().find(key);
+        if (it != form_cache().end()) { cached = true; chosen = it->second; }
       }
-      form_cache()[key] = chosen;
+      if (!cached) {
+        auto& tl = h->d.lev[l];
+        const size_t nb = (size_t)tl.L.n_total * sizeof(double);
+        CK(cudaMemsetAsync(tl.U, 0, nb, h->stream));
+        CK(cudaMemsetAsync(tl.F, 0, nb, h->stream));
+        float best = 1e30f;
+        for (auto& f : cands) {
+          if ((rc = apply_form(h, l, f))) return rc;
+          float ms = 0;
+          if ((rc = time_level_sweeps(h, l, &ms))) return rc;
+          if (verbose) std::fprintf(stderr, "igamg: level %d (n = %d) %s: %.1f us per %d sweep(s)\n", l, lc.sz.n,
+                                    form_name(f).c_str(), 1e3f * ms, std::max(1, h->prob.nu1));
+          if (ms < best) { best = ms; chosen = f; }
+        }
+        std::lock_guard<std::mutex> lk(form_mutex());
+        form_cache()[key] = chosen;
+      }
     }
     if ((rc = apply_form(h, l, chosen))) return rc;
     if (h->d.lev[l].prog) {   // the timing runs advanced different tile sets: start from 0
@@ -1970,8 +1982,11 @@ int choose_adv_form(igamg_handle* h) {
     return IGAMG_OK;
   }
   const auto key = std::make_tuple(h->prob.p, h->prob.n_fine, (int)sizeof(T));
-  auto it = adv_cache().find(key);
-  if (it != adv_cache().end()) { ty.adv_mf = it->second; return IGAMG_OK; }
+  {
+    std::lock_guard<std::mutex> lk(form_mutex());
+    auto it = adv_cache().find(key);
+    if (it != adv_cache().end()) { ty.adv_mf = it->second; return IGAMG_OK; }
+  }
   auto& tl = ty.lev.back();
   const size_t nb = (size_t)tl.L.n_total * sizeof(T);
   CK(cudaMemsetAsync(tl.U, 0, nb, h->stream));
@@ -1983,7 +1998,10 @@ int choose_adv_form(igamg_handle* h) {
     if ((rc = time_fine_residual<T>(h, &ms[f]))) return rc;
   }
   ty.adv_mf = ms[1] < ms[0] ? 1 : 0;
-  adv_cache()[key] = ty.adv_mf;
+  {
+    std::lock_guard<std::mutex> lk(form_mutex());
+    adv_cache()[key] = ty.adv_mf;
+  }
   if (std::getenv("IGAMG_VERBOSE"))
     std::fprintf(stderr, "igamg: finest residual (%s): records %.1f us, matrix-free %.1f us -> %s\n",
                  sizeof(T) == 8 ? "FP64" : "FP32", 1e3f * ms[0], 1e3f * ms[1], ty.adv_mf ? "matrix-free" : "records");
