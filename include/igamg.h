@@ -244,14 +244,17 @@ int igamg_solve_host(igamg_handle* h, const double* f_qp_host, double* U_host, d
                      int max_cycles, igamg_report* rep);
 
 /* n independent solves at once (same contract as igamg_solve for each), e.g. a sweep of
- * sigma/nu values or of right-hand sides.  Groups of 8 or more 2D FP64 multiplicative V-cycle
- * solves of one structure (same p, n_fine, levels, sweeps, domain and operator form) step
- * in lockstep: each V-cycle step is one launch over up to 24 of them, converged solves
- * switched off on the device; the group's first call with a new list of handles and vectors
- * allocates its small workspace and captures its graphs (kept with the group's first handle
- * and reused while the list is the same).  All other solves run on their handles' own
- * internal streams, each step a captured graph, so latency-bound small solves overlap.  Work
- * is ordered after, and joined back into, the streams given to igamg_create.  U[i], F[i]:
+ * sigma/nu values or of right-hand sides.  2D FP64 multiplicative V-cycle solves step in
+ * lockstep in groups of 8 or more: first one group per mesh structure (same p, n_fine,
+ * levels, sweeps, domain and operator form), then one group of the remaining solves of one
+ * cycle shape whatever their mesh sizes (their V-cycles aligned from the finest grid); each
+ * V-cycle step is one launch over up to 24 of them, converged solves switched off on the
+ * device; the group's first call with a new list of handles and vectors allocates its small
+ * workspace and captures its graphs (kept with the group's first handle and reused while the
+ * list is the same).  All other solves run on their handles' own internal streams, each cycle
+ * a captured graph, and each solve's next cycle is launched as soon as its own residual norm
+ * is back, so latency-bound small solves overlap and none waits for another.  Work is ordered
+ * after, and joined back into, the streams given to igamg_create.  U[i], F[i]:
  * device vectors of handles[i]; reports, status: NULL or arrays of n (status[i] =
  * igamg_solve's return value for solve i).  Handles must be distinct (IGAMG_EINVAL).  Returns
  * the first negative status, else IGAMG_NOT_CONVERGED if any solve ran out of cycles, else 0.
