@@ -246,8 +246,9 @@ int igamg_solve_host(igamg_handle* h, const double* f_qp_host, double* U_host, d
 /* n independent solves at once (same contract as igamg_solve for each), e.g. a sweep of
  * sigma/nu values or of right-hand sides.  2D FP64 multiplicative V-cycle solves step in
  * lockstep in groups of 8 or more: first one group per mesh structure (same p, n_fine,
- * levels, sweeps, domain and operator form), then one group of the remaining solves of one
- * cycle shape whatever their mesh sizes (their V-cycles aligned from the finest grid); each
+ * levels, sweeps, domain and operator form), then one group per cycle shape (p, sweeps,
+ * domain, operator form) of the remaining solves, whatever their mesh sizes (their V-cycles
+ * aligned from the finest grid); each
  * V-cycle step is one launch over up to 24 of them, converged solves switched off on the
  * device; the group's first call with a new list of handles and vectors allocates its small
  * workspace and captures its graphs (kept with the group's first handle and reused while the
