@@ -175,3 +175,15 @@ def test_batch_entry_points_reject_bad_lists_on_host():
     assert L.igamg_solve_batch(0, None, None, None, -1.0, 10, None, None) == -1        # rtol < 0
     at = (ctypes.c_double * 1)(1e-8)
     assert L.igamg_solve_batch_abs(0, None, None, None, at, 10, None, None) == 0
+
+
+def test_form_entry_points_reject_bad_arguments_on_host():
+    # the residual-form, chain-count and FP32-residual entry points check their arguments
+    # before touching a handle or the device
+    import ctypes
+    L = _lib().lib()
+    a, b = ctypes.c_int(), ctypes.c_int()
+    assert L.igamg_residual_form(None, ctypes.byref(a), ctypes.byref(b)) == -1
+    assert L.igamg_set_residual_form(None, 1, 0) == -1
+    assert L.igamg_level_chains(None, 0, ctypes.byref(a)) == -1
+    assert L.igamg_residual_f32(None, 0, None, None, None, None) == -1
