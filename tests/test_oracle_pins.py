@@ -263,6 +263,43 @@ def test_oseen_advection_block_exact(p, n):
     assert np.abs(K).max() <= 1e-15 * np.abs(Axx).max()
 
 
+@pytest.mark.parametrize("p,n", [(2, 5), (3, 4)])
+def test_load_vector_exact(p, n):
+    # The load vector (f, v) of Sec. 3.1 for f = (a + b x y, c + d x^2) sampled at the Gauss
+    # points, against an independent evaluation: each velocity row is a sum of products of 1D
+    # moments int s^k N_i(s) ds of scipy's B-splines on the same knots (12-point Gauss-Legendre
+    # per element, exact); the pressure and multiplier rows are zero.
+    from scipy.interpolate import BSpline
+    a, b, c, d = 0.3, -1.7, 0.9, 2.4
+    x = inputs.quad_points_1d(p, n)
+    X, Y = np.meshgrid(x, x)
+    f = np.stack([a + b * X * Y, c + d * X * X])
+    S = o2.Stokes2D(p, n, 1.0, 1.0)
+    F = S.load_vector(f)
+    q = p - 1
+    gx, gw = np.polynomial.legendre.leggauss(12)
+
+    def moments(deg, k):
+        # m[i] = int_0^1 s^k N^deg_i(s) ds
+        t = np.concatenate([np.zeros(deg + 1), np.arange(1, n) / n, np.ones(deg + 1)])
+        m = np.zeros(n + deg)
+        for e in range(n):
+            s_ = (e + 0.5 * (gx + 1)) / n
+            w = 0.5 * gw / n * s_ ** k
+            for i in range(n + deg):
+                m[i] += np.dot(w, np.nan_to_num(BSpline(t, np.eye(n + deg)[i], deg, extrapolate=False)(s_)))
+        return m
+
+    free = slice(1, n + p - 1)
+    # u_x rows (x-degree p free, y-degree q), y-major: F = a m0p(x) m0q(y) + b m1p(x) m1q(y)
+    Fx = a * np.outer(moments(q, 0), moments(p, 0)[free]) + b * np.outer(moments(q, 1), moments(p, 1)[free])
+    # u_y rows (x-degree q, y-degree p free): F = c m0q(x) m0p(y) + d m2q(x) m0p(y)
+    Fy = np.outer(moments(p, 0)[free], c * moments(q, 0) + d * moments(q, 2))
+    expect = np.concatenate([Fx.ravel(), Fy.ravel()])
+    assert np.abs(F[: S.n_u] - expect).max() <= 1e-14 * np.abs(expect).max()
+    assert np.abs(F[S.n_u:]).max() == 0.0
+
+
 # ---------------------------------------------------------------- multigrid --
 
 @pytest.mark.parametrize("p", [2, 3])
