@@ -378,6 +378,43 @@ def test_oseen_advection_blocks_exact_3d(p, n):
     assert np.abs(K).max() <= 1e-15 * np.abs(A).max()
 
 
+@pytest.mark.parametrize("p,n", [(2, 3), (3, 2)])
+def test_load_vector_exact_3d(p, n):
+    # The 3D load vector for f = (a + b y z, c + d x, e + g x y) at the Gauss points against
+    # products of 1D moments int s^k N_i(s) ds of scipy's B-splines (12-point Gauss-Legendre per
+    # element, exact); component c's own axis runs over its interior indices; pressure and
+    # multiplier rows are zero.
+    from scipy.interpolate import BSpline
+    a, b, c, d, e, g = 0.3, -1.7, 0.9, 2.4, -0.6, 1.1
+    x = inputs.quad_points_1d(p, n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    f = np.stack([a + b * Y * Z, c + d * X, e + g * X * Y])
+    S = o3.Stokes3D(p, n, 1.0, 1.0)
+    F = S.load_vector(f)
+    q = p - 1
+    gx, gw = np.polynomial.legendre.leggauss(12)
+
+    def moments(deg, k):
+        t = np.concatenate([np.zeros(deg + 1), np.arange(1, n) / n, np.ones(deg + 1)])
+        m = np.zeros(n + deg)
+        for el in range(n):
+            s_ = (el + 0.5 * (gx + 1)) / n
+            w = 0.5 * gw / n * s_ ** k
+            for i in range(n + deg):
+                m[i] += np.dot(w, np.nan_to_num(BSpline(t, np.eye(n + deg)[i], deg, extrapolate=False)(s_)))
+        return m
+
+    free = slice(1, n + p - 1)
+    kron3 = lambda mz, my, mx: np.kron(mz, np.kron(my, mx))   # noqa: E731
+    mp0, mq0, mq1 = moments(p, 0)[free], moments(q, 0), moments(q, 1)
+    Fx = a * kron3(mq0, mq0, mp0) + b * kron3(mq1, mq1, mp0)          # u_x: x-degree p
+    Fy = c * kron3(mq0, mp0, mq0) + d * kron3(mq0, mp0, mq1)          # u_y: y-degree p
+    Fz = e * kron3(mp0, mq0, mq0) + g * kron3(mp0, mq1, mq1)          # u_z: z-degree p
+    expect = np.concatenate([Fx, Fy, Fz])
+    assert np.abs(F[: S.n_u] - expect).max() <= 1e-14 * np.abs(expect).max()
+    assert np.abs(F[S.n_u:]).max() == 0.0
+
+
 def test_oseen_forcing_matches_closed_form_derivatives():
     # beta . grad u from the polynomial terms against central differences
     p, n, h = 2, 1, 1e-4
