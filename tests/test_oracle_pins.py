@@ -300,6 +300,59 @@ def test_load_vector_exact(p, n):
     assert np.abs(F[S.n_u:]).max() == 0.0
 
 
+@pytest.mark.parametrize("p,n,sigma,nu", [(2, 5, 1.7, 0.3), (3, 4, 0.2, 2.5)])
+def test_velocity_blocks_with_nitsche_terms_exact(p, n, sigma, nu):
+    # The velocity blocks of a_h (Sec. 3.3): sigma (v, u) + nu (grad v : grad u) minus the two
+    # normal-derivative wall integrals plus (C_I nu / h) (v, u) on the walls where the
+    # component is tangential (the normal one is zero strongly), C_I = 4(p-1), h = 1/n.  Each
+    # block is a sum of Kronecker products of 1D matrices: mass and stiffness by 12-point
+    # Gauss-Legendre per element, wall terms by point values and derivatives at 0 and 1, all
+    # from scipy's B-splines (independent of the oracle's element assembly).  There is no
+    # u_x-u_y coupling on the square.
+    from scipy.interpolate import BSpline
+    S = o2.Stokes2D(p, n, sigma, nu)
+    K = S.K.toarray()
+    q = p - 1
+    gx, gw = np.polynomial.legendre.leggauss(12)
+    c_pen, h = 4.0 * (p - 1), 1.0 / n
+
+    def basis(deg):
+        t = np.concatenate([np.zeros(deg + 1), np.arange(1, n) / n, np.ones(deg + 1)])
+        return [BSpline(t, np.eye(n + deg)[i], deg) for i in range(n + deg)]
+
+    def mats(deg):
+        B = basis(deg)
+        m = len(B)
+        M, St = np.zeros((m, m)), np.zeros((m, m))
+        for e in range(n):
+            s_ = (e + 0.5 * (gx + 1)) / n
+            w = 0.5 * gw / n
+            V = np.array([b(s_) for b in B])
+            D = np.array([b.derivative()(s_) for b in B])
+            M += (V * w) @ V.T
+            St += (D * w) @ D.T
+        # wall terms at s = 0 (outward normal -1) and s = 1 (+1)
+        Wl = np.zeros((m, m))
+        for s0, sign in ((0.0, -1.0), (1.0, 1.0)):
+            v = np.array([float(b(s0)) for b in B])
+            dv = np.array([float(b.derivative()(s0)) for b in B])
+            Wl += -sign * (np.outer(v, dv) + np.outer(dv, v)) + (c_pen / h) * np.outer(v, v)
+        return M, St, Wl
+
+    Mp, Sp, _ = mats(p)
+    Mq, Sq, Wq = mats(q)
+    free = slice(1, n + p - 1)
+    Mpf, Spf = Mp[free, free], Sp[free, free]
+    # u_x rows (iy, ix): x-degree p (free), y-degree q; tangential on the walls y = 0, 1
+    Axx = sigma * np.kron(Mq, Mpf) + nu * (np.kron(Mq, Spf) + np.kron(Sq, Mpf) + np.kron(Wq, Mpf))
+    # u_y rows (iy, ix): x-degree q, y-degree p (free); tangential on the walls x = 0, 1
+    Ayy = sigma * np.kron(Mpf, Mq) + nu * (np.kron(Mpf, Sq) + np.kron(Spf, Mq) + np.kron(Mpf, Wq))
+    ux, uy = slice(0, S.n_ux), slice(S.n_ux, S.n_u)
+    for blk, A in ((K[ux, ux], Axx), (K[uy, uy], Ayy)):
+        assert np.abs(blk - A).max() <= 1e-12 * np.abs(A).max()
+    assert np.abs(K[ux, uy]).max() == 0.0 and np.abs(K[uy, ux]).max() == 0.0
+
+
 # ---------------------------------------------------------------- multigrid --
 
 @pytest.mark.parametrize("p", [2, 3])
