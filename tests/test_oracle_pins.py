@@ -298,6 +298,14 @@ def test_load_vector_exact(p, n):
     expect = np.concatenate([Fx.ravel(), Fy.ravel()])
     assert np.abs(F[: S.n_u] - expect).max() <= 1e-14 * np.abs(expect).max()
     assert np.abs(F[S.n_u:]).max() == 0.0
+    # the pressure-mean multiplier (Sec. 4.3 footnote): its row and column hold m_j = int N^q_j,
+    # the products of the 1D moments, and nothing else
+    K = S.K.toarray()
+    m = np.kron(moments(q, 0), moments(q, 0))
+    pr = slice(S.n_u, S.n_u + S.n_p)
+    assert np.abs(K[-1, pr] - m).max() <= 1e-14 * m.max()
+    assert np.abs(K[pr, -1] - m).max() <= 1e-14 * m.max()
+    assert np.abs(K[-1, : S.n_u]).max() == 0.0 and K[-1, -1] == 0.0
 
 
 @pytest.mark.parametrize("p,n,sigma,nu", [(2, 5, 1.7, 0.3), (3, 4, 0.2, 2.5)])
