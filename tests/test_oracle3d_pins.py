@@ -415,6 +415,60 @@ def test_load_vector_exact_3d(p, n):
     assert np.abs(F[S.n_u:]).max() == 0.0
 
 
+@pytest.mark.parametrize("p,n,sigma,nu", [(2, 3, 1.7, 0.3), (3, 2, 0.2, 2.5)])
+def test_velocity_blocks_with_nitsche_terms_exact_3d(p, n, sigma, nu):
+    # Each 3D velocity block of a_h (Sec. 3.3): sigma mass + nu stiffness + the Nitsche wall terms
+    # on the four faces where the component is tangential (C_I = 4(p-1), h = 1/n), as sums of
+    # three-factor Kronecker products of 1D matrices from scipy's B-splines (mass and stiffness by
+    # 12-point Gauss-Legendre per element, wall terms by point values and derivatives at 0 and 1);
+    # no coupling between velocity components on the cube.
+    from scipy.interpolate import BSpline
+    S = o3.Stokes3D(p, n, sigma, nu)
+    K = S.K.toarray()
+    q = p - 1
+    gx, gw = np.polynomial.legendre.leggauss(12)
+    c_pen, h = 4.0 * (p - 1), 1.0 / n
+
+    def mats(deg):
+        t = np.concatenate([np.zeros(deg + 1), np.arange(1, n) / n, np.ones(deg + 1)])
+        B = [BSpline(t, np.eye(n + deg)[i], deg) for i in range(n + deg)]
+        m = len(B)
+        M, St, Wl = np.zeros((m, m)), np.zeros((m, m)), np.zeros((m, m))
+        for e in range(n):
+            s_ = (e + 0.5 * (gx + 1)) / n
+            w = 0.5 * gw / n
+            V = np.array([b(s_) for b in B])
+            D = np.array([b.derivative()(s_) for b in B])
+            M += (V * w) @ V.T
+            St += (D * w) @ D.T
+        for s0, sign in ((0.0, -1.0), (1.0, 1.0)):
+            v = np.array([float(b(s0)) for b in B])
+            dv = np.array([float(b.derivative()(s0)) for b in B])
+            Wl += -sign * (np.outer(v, dv) + np.outer(dv, v)) + (c_pen / h) * np.outer(v, v)
+        return M, St, Wl
+
+    free = slice(1, n + p - 1)
+    Mp, Sp, _ = mats(p)
+    Mq, Sq, Wq = mats(q)
+    kron3 = lambda Az, Ay, Ax: np.kron(Az, np.kron(Ay, Ax))   # noqa: E731
+    for c in range(3):
+        M = [Mq, Mq, Mq]; St = [Sq, Sq, Sq]; W = [Wq, Wq, Wq]
+        M[c], St[c], W[c] = Mp[free, free], Sp[free, free], None
+        A = sigma * kron3(M[2], M[1], M[0])
+        A = A + nu * (kron3(M[2], M[1], St[0]) + kron3(M[2], St[1], M[0]) + kron3(St[2], M[1], M[0]))
+        for a in range(3):                 # walls normal to axis a, where component c is tangential
+            if a == c:
+                continue
+            F = list(M)
+            F[a] = W[a]
+            A = A + nu * kron3(F[2], F[1], F[0])
+        blk = slice(c * S.n_uc, (c + 1) * S.n_uc)
+        assert np.abs(K[blk, blk] - A).max() <= 1e-12 * np.abs(A).max(), c
+        for c2 in range(3):
+            if c2 != c:
+                assert np.abs(K[blk, c2 * S.n_uc:(c2 + 1) * S.n_uc]).max() == 0.0
+
+
 def test_oseen_forcing_matches_closed_form_derivatives():
     # beta . grad u from the polynomial terms against central differences
     p, n, h = 2, 1, 1e-4
