@@ -1,12 +1,16 @@
 // C ABI and launch orchestration of the geometric multigrid V-cycle (arXiv 1705.09282,
 // Algorithm 1 with the overlapping Schwarz smoothers of Sec. 5.2), for sm_103a.
 //
-// Every level's operator is applied matrix-free from class stencils built from its 1D
-// factors (setup.cpp).  The multiplicative smoother runs one launch per patch colour:
-// inside a colour the patches share no degree of freedom and are not coupled by K, so
-// solving them concurrently is the same as solving them one after another (eq. MSM).
-// A V-cycle (and, in the FP32 mode, one step of FP64 iterative refinement around an
-// FP32 V-cycle) is captured once into a CUDA graph and replayed.
+// Generalized Stokes levels on the square apply their operator matrix-free from class
+// stencils built from the 1D factors (setup.cpp); generalized Oseen and mapped levels read one
+// stored record per row, and the finest Oseen residual may apply its advection term element
+// by element instead (kernels_adv.cuh; the faster form per precision is kept at creation).
+// The multiplicative smoother runs one launch per patch colour (or a pipelined tile sweep,
+// per level as the autotuner chose): inside a colour the patches share no degree of freedom
+// and are not coupled by K, so solving them concurrently is the same as solving them one
+// after another (eq. MSM).  A V-cycle (and, in the FP32 mode, one step of FP64 iterative
+// refinement around an FP32 V-cycle) is captured once into a CUDA graph and replayed;
+// independent solves step either in lockstep launches or each on its own stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
